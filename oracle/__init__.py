@@ -1,0 +1,28 @@
+"""CPU FP64 oracle of QUEEN's per-frame residual-training path (arXiv 2412.04469).
+
+TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference legs may import or call this package.  It shares no
+code with the CUDA path (paper_2412_04469_gb300) and never imports it.
+
+Two halves:
+  raster  -- ctypes front-end to queen_oracle.c (decode, gate, projection,
+             binning, compositing and their analytic adjoints), Sec. 3.1-3.2.
+  learn   -- numpy FP64 code for the loss, the viewspace gradient difference
+             and gate initialisation (Sec. 3.3, Eq. 9-10), Adam, and the
+             static-skip MLP.
+
+Parity status per function is recorded in each function's docstring; every
+function listed here is pinned by tests/test_oracle_*.py (closed forms,
+brute force, finite differences or a library routine) except where a
+docstring says "parity unpinned".
+"""
+from .raster import (build, OracleCamera, sh_basis, decode, decode_bwd, project, project_bwd,
+                     bin_sort, render_fwd, render_bwd, num_threads)
+from .learn import (l1_loss, mse_grad, viewspace_score, gate_init, adam_step, mlp_forward,
+                    mlp_backward, bce_loss)
+
+__all__ = [
+    "build", "OracleCamera", "sh_basis", "decode", "decode_bwd", "project", "project_bwd",
+    "bin_sort", "render_fwd", "render_bwd", "num_threads", "l1_loss", "mse_grad",
+    "viewspace_score", "gate_init", "adam_step", "mlp_forward", "mlp_backward", "bce_loss",
+]

@@ -1,0 +1,107 @@
+"""FP64 numpy half of the oracle: loss, viewspace gradient difference and gate
+initialisation (Sec. 3.3), Adam, and the static-skip MLP.  Test
+infrastructure only; shares no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import raster
+
+
+def l1_loss(img, target):
+    """L1 term of Eq. 3 as a mean over the 3 H W values; returns (loss, dL/dimg)
+    with sign(0) = 0.  Pinned by a closed-form test."""
+    d = np.asarray(img, np.float64) - np.asarray(target, np.float64)
+    return float(np.abs(d).mean()), np.sign(d) / d.size
+
+
+def mse_grad(img, target):
+    """dL/dimg of the mean squared error used by Eq. 9."""
+    d = np.asarray(img, np.float64) - np.asarray(target, np.float64)
+    return 2.0 * d / d.size
+
+
+def viewspace_score(projs, gt_t, gt_prev, bg=(0.0, 0.0, 0.0)):
+    """Eq. 9 as written: for every view v the renderer's gradient w.r.t. the 2D
+    means of the MSE to the new frame minus that of the MSE to the previous
+    frame, both at the previous frame's rendering, averaged over views.
+    projs[v] is the oracle projection of A_{t-1} in view v.  Returns d[2][n]."""
+    d = None
+    for proj, It, Ip in zip(projs, gt_t, gt_prev):
+        img, _, _, _ = raster.render_fwd(proj, bg)
+        g_t = raster.render_bwd(proj, mse_grad(img, It), bg)["d_mean2d"]
+        g_p = raster.render_bwd(proj, mse_grad(img, Ip), bg)["d_mean2d"]
+        d = (g_t - g_p) if d is None else d + (g_t - g_p)
+    return d / len(projs)
+
+
+def gate_init(d, tau, gamma0, gamma1):
+    """Eq. 10 and Eq. 8 solved for log alpha:
+         d_i = |d_i| / (|d_i| + median |d|),  sigmoid(log a_i - tau log(-g0/g1)) = d_i.
+    Median of an even count is the lower median; with a zero median d_i is 1
+    for |d_i| > 0 and 0 otherwise; d_i is clamped to [1e-6, 1 - 1e-6]."""
+    nrm = np.sqrt((np.asarray(d, np.float64) ** 2).sum(axis=0))
+    med = np.sort(nrm)[(nrm.size - 1) // 2]
+    if med > 0:
+        p = nrm / (nrm + med)
+    else:
+        p = (nrm > 0).astype(np.float64)
+    p = np.clip(p, 1e-6, 1.0 - 1e-6)
+    return np.log(p / (1.0 - p)) + tau * np.log(-gamma0 / gamma1), nrm, med
+
+
+def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, mask=None):
+    """One Adam update (Kingma & Ba, Algorithm 1) in FP64; `step` counts from 1.
+    Elements with mask != 0 keep their parameter and moments.  Returns new
+    (param, m, v)."""
+    p = np.asarray(param, np.float64).copy()
+    g = np.asarray(grad, np.float64)
+    m1 = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v1 = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mh = m1 / (1.0 - beta1 ** step)
+    vh = v1 / (1.0 - beta2 ** step)
+    p1 = p - lr * mh / (np.sqrt(vh) + eps)
+    if mask is not None:
+        keep = np.asarray(mask) != 0
+        p1 = np.where(keep, p, p1)
+        m1 = np.where(keep, m, m1)
+        v1 = np.where(keep, v, v1)
+    return p1, m1, v1
+
+
+# --------------------------------------------------------------------------
+# Static-skip MLP 16 -> 64 -> 64 -> 1 (ReLU, ReLU, logit).  params is a dict
+# W1[64][16], b1[64], W2[64][64], b2[64], W3[1][64], b3[1].
+# --------------------------------------------------------------------------
+def mlp_forward(X, params):
+    """Returns (logit[n], cache).  X is [n][16]."""
+    X = np.asarray(X, np.float64)
+    z1 = X @ params["W1"].T + params["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ params["W2"].T + params["b2"]
+    h2 = np.maximum(z2, 0.0)
+    z3 = h2 @ params["W3"].T + params["b3"]
+    return z3[:, 0], (X, z1, h1, z2, h2)
+
+
+def bce_loss(logit, label):
+    """Mean binary cross-entropy on logits; returns (loss, dL/dlogit)."""
+    z = np.asarray(logit, np.float64)
+    y = np.asarray(label, np.float64)
+    loss = np.mean(np.maximum(z, 0.0) - z * y + np.log1p(np.exp(-np.abs(z))))
+    return float(loss), (1.0 / (1.0 + np.exp(-z)) - y) / z.size
+
+
+def mlp_backward(d_logit, params, cache):
+    """Gradients of the MLP parameters for an upstream d_logit[n]."""
+    X, z1, h1, z2, h2 = cache
+    d3 = np.asarray(d_logit, np.float64)[:, None]
+    g = {"W3": d3.T @ h2, "b3": d3.sum(axis=0)}
+    d2 = (d3 @ params["W3"]) * (z2 > 0)
+    g["W2"] = d2.T @ h1
+    g["b2"] = d2.sum(axis=0)
+    d1 = (d2 @ params["W2"]) * (z1 > 0)
+    g["W1"] = d1.T @ X
+    g["b1"] = d1.sum(axis=0)
+    return g

@@ -1,0 +1,171 @@
+"""Pins of the oracle's compositing (Eq. 2, Sec. 3.1) and its adjoint."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_04469_gb300 import synthetic as S
+from tests._golden import load
+
+
+def splats(W, H, means, sig, opac, rgb, depth):
+    """Directly built 2D records (isotropic footprints, rects covering the image)."""
+    n = len(opac)
+    sig = np.broadcast_to(np.asarray(sig, float), (n,))
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    return dict(mean2d=np.asarray(means, float).T.copy(),
+                conic=np.stack([1 / sig ** 2, np.zeros(n), 1 / sig ** 2]),
+                opac=np.asarray(opac, float), rgb=np.asarray(rgb, float).T.copy(),
+                depth=np.asarray(depth, float), radius=np.full(n, 3, np.int32),
+                rect=np.tile(np.array([[0], [0], [TX], [TY]], np.int32), (1, n)),
+                fragile=np.zeros(n, np.int32), frag_rect=np.zeros((4, n), np.int32), width=W, height=H)
+
+
+def test_single_gaussian_footprint_and_pixel_centre():
+    W, H, sig, o = 40, 36, 4.0, 0.8
+    c = np.array([0.3, 0.6, 0.9])
+    pr = splats(W, H, [(20.5, 17.5)], sig, [o], [c], [1.0])
+    img, T, last, _ = oracle.render_fwd(pr)
+    v, u = np.mgrid[0:H, 0:W]
+    r2 = (u + 0.5 - 20.5) ** 2 + (v + 0.5 - 17.5) ** 2
+    a = np.minimum(0.99, o * np.exp(-r2 / (2 * sig ** 2)))
+    a = np.where(a >= 1 / 255, a, 0.0)
+    assert np.allclose(img, c[:, None, None] * a[None], atol=1e-15)
+    assert np.allclose(T, 1 - a, atol=1e-15)
+    assert img[0, 17, 20] == pytest.approx(0.3 * o)      # pixel (20, 17) samples the mean exactly
+    # the footprint ends where alpha crosses 1/255: radius sig sqrt(2 ln(255 o))
+    rr = sig * math.sqrt(2 * math.log(255 * o))
+    inside = r2 < rr ** 2 * (1 - 1e-9)
+    assert np.all(last[inside] == 1) and np.all(last[r2 > rr ** 2 * (1 + 1e-9)] == 0)
+
+
+def test_alpha_cap():
+    pr = splats(16, 16, [(8.5, 8.5)], 3.0, [1.0], [(1, 1, 1)], [1.0])
+    img, T, _, _ = oracle.render_fwd(pr)
+    assert img[0, 8, 8] == 0.99 and T[8, 8] == pytest.approx(0.01)
+    r_cap = 3.0 * math.sqrt(2 * math.log(1 / 0.99))     # o G >= 0.99 inside this radius
+    v, u = np.mgrid[0:16, 0:16]
+    r2 = (u + 0.5 - 8.5) ** 2 + (v + 0.5 - 8.5) ** 2
+    assert np.all(img[0][r2 < r_cap ** 2] == 0.99)
+
+
+def test_two_gaussians_by_hand_and_depth_order():
+    g = load("composite_hand.txt")
+    # both centred on pixel (4, 4) with huge footprints, so alpha = opacity there
+    pr = splats(16, 16, [(4.5, 4.5), (4.5, 4.5)], 1e6, [0.5, 0.25], [(1, 0, 0), (0, 1, 0)], [1.0, 2.0])
+    img, T, last, _ = oracle.render_fwd(pr)
+    assert np.allclose([*img[:, 4, 4], T[4, 4]], g["ORDER_AB"], atol=1e-9)
+    assert last[4, 4] == 2
+    pr["depth"] = np.array([2.0, 1.0])
+    img, T, last, _ = oracle.render_fwd(pr)
+    assert np.allclose([*img[:, 4, 4], T[4, 4]], g["ORDER_BA"], atol=1e-9)
+
+
+def test_background_and_termination():
+    g = load("composite_hand.txt")
+    n = 20
+    pr = splats(16, 16, [(8.5, 8.5)] * n, 1e6, [0.5] * n, [(1, 1, 1)] * n, np.arange(1, n + 1, dtype=float))
+    img, T, last, _ = oracle.render_fwd(pr, bg=(0.0, 0.5, 1.0))
+    k = int(g["STACK_LAST"][0])
+    assert last[8, 8] == k and T[8, 8] == pytest.approx(g["STACK_T"][0], rel=1e-6)
+    Tk = 0.5 ** k
+    assert img[:, 8, 8] == pytest.approx([1 - Tk, 1 - Tk + 0.5 * Tk, 1 - Tk + Tk], rel=1e-6)
+
+
+def _scene(n, W, H, seed, degree=0, grow=0.0, cam_eye=(0.0, 0.0, 4.0)):
+    A = S.make_scene(n, degree, seed).astype(np.float64)
+    A[7:10] += grow
+    cam = S.make_camera(W, H, 60.0, eye=cam_eye)
+    return A, oracle.OracleCamera.of(cam)
+
+
+def test_transmittance_invariants_random_scene():
+    A, oc = _scene(2000, 128, 128, 0)
+    pr = oracle.project(A, oc, 0)
+    img, T, last, _ = oracle.render_fwd(pr)
+    assert T.min() >= 1e-4 and T.max() <= 1.0
+    assert np.all(img >= 0) and np.all(img <= 1.0 + 1e-12)
+    assert np.all(T[last == 0] == 1.0)
+
+
+def brute_pixelwise(pr, W, H, bg):
+    """Per pixel, every visible Gaussian whose rect holds the pixel's tile,
+    sorted by (depth, index), composited with Eq. 2 in pure Python."""
+    n = pr["opac"].size
+    img = np.zeros((3, H, W))
+    T_all = np.zeros((H, W))
+    for v in range(H):
+        for u in range(W):
+            tx, ty = u // 16, v // 16
+            lst = sorted((pr["depth"][i], i) for i in range(n)
+                         if pr["rect"][0, i] <= tx < pr["rect"][2, i] and pr["rect"][1, i] <= ty < pr["rect"][3, i])
+            T, C = 1.0, np.zeros(3)
+            for _, i in lst:
+                dx, dy = u + 0.5 - pr["mean2d"][0, i], v + 0.5 - pr["mean2d"][1, i]
+                a, b, c = pr["conic"][:, i]
+                pw = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+                if pw > 0:
+                    continue
+                al = min(0.99, pr["opac"][i] * math.exp(pw))
+                if al < 1 / 255:
+                    continue
+                if T * (1 - al) < 1e-4:
+                    break
+                C += pr["rgb"][:, i] * al * T
+                T *= 1 - al
+            img[:, v, u] = C + T * np.asarray(bg)
+            T_all[v, u] = T
+    return img, T_all
+
+
+@pytest.mark.parametrize("n,W,H,seed", [(40, 32, 32, 1), (64, 33, 17, 2)])
+def test_brute_force_tiny_scenes(n, W, H, seed):
+    A, oc = _scene(n, W, H, seed, grow=1.2)
+    pr = oracle.project(A, oc, 0)
+    bg = (0.1, 0.2, 0.3)
+    img, T, _, _ = oracle.render_fwd(pr, bg=bg)
+    bimg, bT = brute_pixelwise(pr, W, H, bg)
+    assert np.abs(img - bimg).max() < 1e-13 and np.abs(T - bT).max() < 1e-13
+
+
+def _fd_scene(seed):
+    A, oc = _scene(24, 32, 32, seed, degree=0, grow=1.0)
+    pr = oracle.project(A, oc, 0, eps_g=1e-5)
+    return pr
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_backward_matches_finite_differences(seed):
+    pr = _fd_scene(seed)
+    bg = (0.2, 0.1, 0.4)
+    _, _, last0, frag = oracle.render_fwd(pr, bg=bg, eps=1e-4, eps_d=1e-6)
+    rng = np.random.default_rng(seed)
+    Wt = rng.standard_normal((3, 32, 32)) * (frag == 0)[None]   # no weight on pixels near a threshold
+    g = oracle.render_bwd(pr, Wt, bg=bg)
+
+    def f(q):
+        img, _, last, _ = oracle.render_fwd(q, bg=bg)
+        return (Wt * img).sum(), last
+
+    h = 1e-7
+    vis = np.nonzero(pr["radius"] > 0)[0]
+    checked = 0
+    for key, gk in (("mean2d", "d_mean2d"), ("conic", "d_conic"), ("opac", "d_opac"), ("rgb", "d_rgb")):
+        arr = pr[key] if pr[key].ndim == 2 else pr[key][None]
+        grad = g[gk] if g[gk].ndim == 2 else g[gk][None]
+        for row in range(arr.shape[0]):
+            for i in vis:
+                step = h * max(1.0, abs(arr[row, i]))
+                qp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in pr.items()}
+                qm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in pr.items()}
+                (qp[key] if qp[key].ndim == 2 else qp[key][None])[row, i] += step
+                (qm[key] if qm[key].ndim == 2 else qm[key][None])[row, i] -= step
+                fp, lp = f(qp)
+                fm, lm = f(qm)
+                if not (np.array_equal(lp, last0) and np.array_equal(lm, last0)):
+                    continue     # the step crossed a threshold somewhere: not differentiable here
+                fd = (fp - fm) / (2 * step)
+                assert fd == pytest.approx(grad[row, i], rel=1e-5, abs=1e-6), (key, row, i)
+                checked += 1
+    assert checked > 0.9 * 9 * vis.size
