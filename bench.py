@@ -1,0 +1,427 @@
+"""Benchmark of QUEEN's per-frame residual-training iteration on one GB300.
+
+One step = one training view through every stage of the hot path:
+decode + gate -> projection -> binning -> compositing -> L1 loss ->
+compositing adjoint -> projection adjoint -> decode/gate adjoint -> Adam.
+Workload: 300,000 Gaussians, SH degree 3, 20 cameras at 1352 x 1014 on a
+120-degree arc, int8 latents of width 8 per attribute category, synthetic
+inputs (seeded), views cycled.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded tile sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: n, sh degree, width, height, views, latent width
+    "full": (300_000, 3, 1352, 1014, 20, 8),
+    "small": (2_000, 0, 128, 128, 1, 8),
+    "large": (1_000_000, 3, 1920, 1080, 15, 8),
+}
+METRIC = "fwd+bwd rasterize it/s @300k Gaussians 1352x1014; s/frame learned vs plain @dPSNR<=.05"
+L2_FLUSH_BYTES = 256 << 20
+# kernels each C-ABI call launches (memsets are not counted)
+KERNELS_PER_CALL = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 1, "render_bwd": 1,
+                    "project_bwd": 1, "decode_bwd": 1}
+STAGES = ["decode", "project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "decode_bwd", "adam"]
+
+
+def workload_name(name):
+    n, deg, W, H, V, L = WORKLOADS[name]
+    return f"queen_residual_step_n{n}_sh{deg}_{W}x{H}_v{V}"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if not math.isnan(s)]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": num(rows[0][2]),
+                "samples": len(rows), "power_w_max": max(num(r[3]) for r in rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def setup(name, seed=0):
+    import torch
+
+    from paper_2412_04469_gb300 import binding as B
+    from paper_2412_04469_gb300 import synthetic as S
+    from paper_2412_04469_gb300.pipeline import QueenFrame, Rasterizer
+
+    n, deg, W, H, V, L = WORKLOADS[name]
+    lay = S.DecoderLayout.default(sh_degree=deg, latent=L)
+    prev = S.make_scene(n, deg, seed)
+    res = S.make_residuals(n, lay, seed)
+    cams = S.make_arc_cameras(V, W, H) if V > 1 else [S.make_camera(W, H, 60.0)]
+    frame = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    rast = Rasterizer(n, frame.S, deg, W, H, 1)
+    ccams = [B.make_camera(c) for c in cams]
+    targets_host = [torch.from_numpy(S.make_image(W, H, 100 + v)).pin_memory() for v in range(V)]
+    targets = [t.cuda() for t in targets_host]
+    # size the pair buffer from every view (synchronising, outside any timing)
+    Pmax = 0
+    frame.decode()
+    for c in ccams:
+        rast.project(frame.attrs, c, frame.hp.blur)
+        rast.bin_sort(sync=False)
+        torch.cuda.synchronize()
+        Pmax = max(Pmax, int(rast.n_pairs.item()))
+    rast.set_capacity(int(Pmax * 1.25) + 4096)
+    return frame, rast, ccams, targets, targets_host, lay, prev, res, cams
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_04469_gb300 import build as pbuild
+    from paper_2412_04469_gb300.pipeline import training_iteration
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pbuild.build()
+    name = args.workload
+    frame, rast, cams, targets, targets_host, lay, prev, res, cams_py = setup(name)
+    n, deg, W, H, V, L = WORKLOADS[name]
+    hp = frame.hp
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step_timed(v, ev):
+        c = cams[v]
+        ev[0].record(stream)
+        frame.decode()
+        ev[1].record(stream)
+        rast.project(frame.attrs, c, hp.blur)
+        ev[2].record(stream)
+        rast.bin_sort(False)
+        ev[3].record(stream)
+        rast.render_fwd(c, hp.bg)
+        ev[4].record(stream)
+        rast.loss_grad(targets[v])
+        ev[5].record(stream)
+        rast.render_bwd(c, hp.bg)
+        ev[6].record(stream)
+        rast.project_bwd(frame.attrs, c, hp.blur, frame.d_attrs)
+        ev[7].record(stream)
+        frame.decode_bwd()
+        ev[8].record(stream)
+        frame.adam()
+        ev[9].record(stream)
+
+    for w in range(args.warmup):
+        training_iteration(frame, rast, cams[w % V], targets[w % V])
+    torch.cuda.synchronize()
+    assert int(rast.n_pairs.item()) <= rast.capacity, "pair buffer overflow during warm-up"
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (outside the step events)
+        step_timed((args.warmup + k) % V, evs[k])
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    overflow = int(rast.n_pairs.item()) > rast.capacity
+    stage_ms = {s: [] for s in STAGES}
+    step_ms = []
+    for e in evs:
+        for i, s in enumerate(STAGES):
+            stage_ms[s].append(e[i].elapsed_time(e[i + 1]))
+        step_ms.append(e[0].elapsed_time(e[9]))
+    total_ms = float(sum(step_ms))
+    t = torch.tensor([total_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers: H2D of the
+    # view's target from pinned memory and D2H of the loss every step
+    loss_host = torch.zeros(1).pin_memory()
+    tgt_dev = torch.empty_like(targets[0])
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        v = (args.warmup + k) % V
+        tgt_dev.copy_(targets_host[v], non_blocking=True)
+        training_iteration(frame, rast, cams[v], tgt_dev)
+        loss_host.copy_(rast.loss, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+
+    # ---- work counts for the roofline (after timing; one forward per view)
+    P_list, Pvis_list, last_sum, contrib_sum = [], [], [], []
+    ncon = torch.zeros((H, W), device="cuda", dtype=torch.int32)
+    frame.decode()
+    for v in range(V):
+        c = cams[v]
+        rast.project(frame.attrs, c, hp.blur)
+        rast.bin_sort(False)
+        rast.render_fwd(c, hp.bg, n_contrib=ncon)
+        torch.cuda.synchronize()
+        P_list.append(int(rast.n_pairs.item()))
+        TY, TX = rast.TY, rast.TX
+        last = rast.last.long()
+        pad = torch.zeros((TY * 16, TX * 16), dtype=torch.long, device="cuda")
+        pad[:H, :W] = last
+        tile_max = pad.view(TY, 16, TX, 16).amax(dim=(1, 3))
+        Pvis_list.append(int(tile_max.sum().item()))
+        last_sum.append(int(last.sum().item()))
+        contrib_sum.append(int(ncon.long().sum().item()))
+    P = float(np.mean(P_list))
+    Pvis = float(np.mean(Pvis_list))
+    n_vis = int((rast.rects[:, 2] > rast.rects[:, 0]).sum().item())
+    px = W * H
+    algo_bytes = {
+        "decode": 620.0 * n, "project": 300.0 * n, "bin_sort": 20.0 * n + 36.0 * P,
+        "render_fwd": 40.0 * Pvis + 20.0 * px, "loss": 36.0 * px,
+        "render_bwd": 32.0 * px + 40.0 * Pvis + 36.0 * n_vis,
+        "project_bwd": 508.0 * n, "decode_bwd": 524.0 * n,
+        "adam": 28.0 * ((lay.n_latent + 4) * n + lay.n_dec),
+    }
+    avg = {s: float(np.mean(stage_ms[s])) for s in STAGES}
+    dom = max(STAGES, key=lambda s: avg[s])
+    hbm_peak, peak_kind = peaks()
+    achieved = algo_bytes[dom] / (avg[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+            "traffic": None, "algorithmic_bytes": algo_bytes[dom]}
+    # FP32 arithmetic estimate for the compositing adjoint:
+    # 12 flop per alpha evaluation, 41 per contributing evaluation, and a
+    # 45-flop warp reduction per 32 contributions.
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    flops_bwd = 12.0 * np.mean(last_sum) + 41.0 * np.mean(contrib_sum) + 45.0 * np.mean(contrib_sum) / 32.0
+    alu = {"kernel": "render_bwd", "achieved": round(flops_bwd / (avg["render_bwd"] * 1e-3) / 1e12, 3),
+           "peak": round(fp32_peak, 2), "unit": "TFLOP/s"}
+    alu["frac"] = round(alu["achieved"] / alu["peak"], 4)
+    if dom == "render_bwd" and alu["frac"] > roof["frac"]:
+        roof_alu = dict(roof)
+        roof = {"bound": "alu", "kernel": dom, "achieved": alu["achieved"], "peak": alu["peak"],
+                "unit": "TFLOP/s", "frac": alu["frac"], "peak_source": "152 SM x 128 FP32 lanes x 2 x median SM clock",
+                "traffic": None, "hbm": {k: roof_alu[k] for k in ("achieved", "peak", "unit", "frac")}}
+    else:
+        roof["alu_render_bwd"] = alu
+
+    value = world * args.steps / (max_ms * 1e-3)
+    launches = args.steps * (sum(KERNELS_PER_CALL.values()) + 2 * lay.n_cat + 2)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "it/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 decoder weights)",
+        "data": "synthetic (seeded scene, residuals and target images; no dataset)",
+        "config": {"workload": workload_name(name), "n_gaussians": n, "sh_degree": deg, "width": W, "height": H,
+                   "views": V, "latent_dim": L, "pairs_per_view": round(P), "visited_pairs_per_view": round(Pvis),
+                   "visible_gaussians": n_vis, "l2": "flushed between timed steps (256 MB write outside step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "stage_ms": {s: round(avg[s], 4) for s in STAGES},
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": round(world * args.steps / (e2e_ms * 1e-3), 3), "unit": "it/s",
+                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
+        "gpu_launches": launches,
+        "pair_overflow": overflow,
+        "wall_s": round(t_wall, 3),
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_iteration(name, n_tiles_sample, seed=0, view=0):
+    """One oracle training iteration on the workload; the compositing and its
+    adjoint run on a seeded random sample of tiles.  Returns (seconds of the
+    sampled iteration, seconds extrapolated to all tiles, tiles sampled)."""
+    import oracle
+    from paper_2412_04469_gb300 import synthetic as S
+
+    n, deg, W, H, V, L = WORKLOADS[name]
+    lay = S.DecoderLayout.default(sh_degree=deg, latent=L)
+    prev = S.make_scene(n, deg, seed).astype(np.float64)
+    res = S.make_residuals(n, lay, seed)
+    cams = S.make_arc_cameras(V, W, H) if V > 1 else [S.make_camera(W, H, 60.0)]
+    cam = cams[view % V]
+    target = S.make_image(W, H, 100 + view % V)
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    rng = np.random.default_rng(seed + 17)
+    tiles = np.sort(rng.choice(TX * TY, size=min(n_tiles_sample, TX * TY), replace=False))
+    tau, g0, g1 = 0.3, -0.5, 1.01
+    t0 = time.perf_counter()
+    A, _, _ = oracle.decode(prev, res.lat, res.dec, res.lp, res.log_alpha, lay, tau, g0, g1)
+    proj = oracle.project(A, cam, deg, blur=0.3)
+    t1 = time.perf_counter()
+    img, _, _, _ = oracle.render_fwd(proj, tiles=tiles)
+    _, g = oracle.l1_loss(img, target)
+    t2 = time.perf_counter()
+    gr = oracle.render_bwd(proj, g, tiles=tiles)
+    t3 = time.perf_counter()
+    dA = oracle.project_bwd(A, cam, deg, gr["d_mean2d"], gr["d_conic"], gr["d_opac"], gr["d_rgb"], blur=0.3)
+    oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, tau, g0, g1, dA, 0.01)
+    t4 = time.perf_counter()
+    per_gauss = (t1 - t0) + (t4 - t3)
+    per_tile = (t2 - t1) + (t3 - t2)
+    full = per_gauss + per_tile * (TX * TY) / len(tiles)
+    return t4 - t0, full, len(tiles)
+
+
+def cpu_baseline(name, budget_s=20.0):
+    import oracle
+    oracle.build()
+    _, full1, k1 = oracle_iteration(name, 32)
+    # grow the tile sample until the sampled run costs about budget_s seconds
+    per_tile = max(full1 / (4 * 5440), 1e-4)
+    k = int(min(5440, max(32, budget_s / per_tile / 2)))
+    sampled, full, k = oracle_iteration(name, k)
+    return {"value": round(1.0 / full, 6), "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one iteration of the workload with compositing and its adjoint on {k} random tiles of "
+                      f"{(WORKLOADS[name][2] + 15) // 16 * ((WORKLOADS[name][3] + 15) // 16)}; per-tile time "
+                      f"scaled to all tiles; sampled run {sampled:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    name = args.workload
+    n, deg, W, H, V, L = WORKLOADS[name]
+    ntiles = ((W + 15) // 16) * ((H + 15) // 16)
+    budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    _, full1, _ = oracle_iteration(name, 16)
+    k = int(min(ntiles, max(8, budget / max(full1 / ntiles, 1e-4) / 3)))
+    for w in range(args.warmup):
+        oracle_iteration(name, k, view=w)
+    fulls, sampled = [], 0.0
+    for s in range(args.steps):
+        sm, full, k = oracle_iteration(name, k, view=args.warmup + s)
+        fulls.append(full)
+        sampled += sm
+    value = args.steps / sum(fulls)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "it/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(fulls) / args.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name(name), "n_gaussians": n, "width": W,
+                                           "height": H, "views": V, "sh_degree": deg},
+           "cpu_baseline": {"value": round(value, 6), "unit": "it/s", "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": f"per step one iteration with compositing on {k} random tiles of {ntiles}, "
+                                      f"per-tile time scaled to all tiles; sampled time {sampled:.1f} s"},
+           "e2e": {"value": round(value, 6), "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

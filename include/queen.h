@@ -1,0 +1,273 @@
+/*
+ * queen.h -- C ABI of the GB300 (sm_103a) implementation of QUEEN's per-frame
+ * residual-training hot path (arXiv 2412.04469).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_host point to host memory; every other pointer is a
+ *     device pointer owned by the caller.  The library never allocates or
+ *     frees device memory and keeps no state between calls except the
+ *     thread-local error string.
+ *   - Every call enqueues its kernels on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) and returns without synchronising, unless its
+ *     comment says otherwise.
+ *   - Per-Gaussian arrays are structure-of-arrays planes: plane k of an array
+ *     with stride S starts at element k * S.  S (n_stride) must be >= n and a
+ *     multiple of 4.
+ *   - Return value: QN_OK or a negative QN_ERR_* code; qn_last_error() gives a
+ *     message for the calling thread.  Argument checks happen before any
+ *     launch, so an error return never leaves partial output behind, except
+ *     QN_ERR_CUDA, which reports a failed launch.
+ *
+ * Raw Gaussian attributes A ([n_attr][n_stride] float32, n_attr = 11 + 3 K,
+ * K = (sh_degree + 1)^2; Sec. 3.1):
+ *   planes 0-2 position p, 3-6 quaternion (w, x, y, z; need not be unit),
+ *   7-9 log-scale, 10 logit-opacity, 11 + 3 k + ch SH coefficient k
+ *   (k = l^2 + l + m, real SH without the Condon-Shortley phase) of channel ch.
+ */
+#ifndef QUEEN_H
+#define QUEEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    QN_OK = 0,
+    QN_ERR_INVALID_ARG = -1,
+    QN_ERR_CUDA = -2,
+    QN_ERR_CAPACITY = -3,
+    QN_ERR_TIMEOUT = -4,
+    QN_ERR_UNSUPPORTED = -5
+};
+
+#define QN_TILE 16            /* 16 x 16 pixel tiles */
+#define QN_MAX_CATEGORIES 8   /* residual decoder categories */
+#define QN_MAX_LATENT 16      /* latent width per category */
+#define QN_MAX_TILES_X 256    /* image width  <= 4096 */
+#define QN_MAX_TILES_Y 256    /* image height <= 4096 */
+
+typedef void *qn_stream_t;    /* cudaStream_t */
+
+/* Pinhole camera (host struct, passed by pointer, copied at launch).
+ * World -> camera: t_cam = R p + t with R row-major; camera x right, y down,
+ * z forward.  Pixel (u, v) samples the image plane at (u + 0.5, v + 0.5);
+ * p' = (fx x / z + cx, fy y / z + cy).  campos is the camera centre, used
+ * for the SH view direction. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_plane;
+    float campos[3];
+    int32_t width, height;
+} qn_camera;
+
+/* Residual categories (Sec. 3.4): category c decodes lat_dim[c] latents into
+ * attribute planes attr_begin[c] .. attr_begin[c] + attr_count[c] - 1; the
+ * planes must lie in 3 .. n_attr - 1 and not overlap.  Latent planes and
+ * decoder blocks (row-major attr_count x lat_dim) follow category order. */
+typedef struct {
+    int32_t n_cat;
+    int32_t attr_begin[QN_MAX_CATEGORIES];
+    int32_t attr_count[QN_MAX_CATEGORIES];
+    int32_t lat_dim[QN_MAX_CATEGORIES];
+} qn_decoder_layout;
+
+/* Hard-concrete gate hyper-parameters (Eq. 6-8): temperature tau, stretch
+ * interval (gamma0, gamma1) with gamma0 < 0 < 1 < gamma1. */
+typedef struct {
+    float tau, gamma0, gamma1;
+} qn_gate_params;
+
+/* Message of the last error on this host thread ("" if none). */
+const char *qn_last_error(void);
+/* Library version string. */
+const char *qn_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Residual decode and gate -- Sec. 3.2, Eq. 4-8.                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A_t = A_{t-1} + R_t (Eq. 4).  For each category c and Gaussian i:
+ *   l = clamp(round_half_even(lat), -128, 127)          (Eq. 5, STE forward)
+ *   r_c = D_c float(l)   (bf16 decoder, FP32 accumulation) added to its planes
+ * and for the position (Eq. 6-7, deterministic hard-concrete gate):
+ *   g = min(1, max(0, sigmoid(log_alpha / tau) (gamma1 - gamma0) + gamma0))
+ *   p_t = p_{t-1} + g lp
+ * L_reg = sum_i sigmoid(log_alpha_i - tau log(-gamma0 / gamma1))  (Eq. 8).
+ *
+ *   prev  [n_attr][n_stride] f32  A_{t-1}             (read)
+ *   lat   [sum lat_dim][n_stride] f32  continuous latents (read)
+ *   dec   bf16 bits, concatenated row-major D_c blocks  (read)
+ *   lp    [3][n_stride] f32  pre-gated position residual (read)
+ *   log_alpha [n] f32                                   (read)
+ *   out   [n_attr][n_stride] f32  A_t                   (written; may not alias prev)
+ *   gate  [n] f32 g_i                                    (written; nullable)
+ *   lreg  [1] f32 L_reg                                  (written; nullable)
+ * Errors: QN_ERR_INVALID_ARG for n < 0, bad stride, null required pointers,
+ * a layout outside the limits above.
+ */
+int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, const float *prev,
+                        const float *lat, const uint16_t *dec, const qn_decoder_layout *layout_host,
+                        const float *lp, const float *log_alpha, const qn_gate_params *gate_host,
+                        float *out, float *gate, float *lreg, qn_stream_t stream);
+
+/*
+ * Adjoint of qn_decode_residuals for dL/dA_t = d_out and dL/dL_reg = d_lreg:
+ *   d_lat   = D_c^T d_out[c planes]              (straight-through estimator)
+ *   d_dec   = sum_i d_out[c planes]_i float(l_i)^T   (FP32, overwritten)
+ *   d_lp    = g d_out[0..2]
+ *   d_log_alpha = (d_out[0..2] . lp) dg/dlog_alpha + d_lreg p (1 - p),
+ *     dg/dlog_alpha = (gamma1 - gamma0) ghat (1 - ghat) / tau inside the clamp, 0 outside.
+ * skip (nullable, [n] u8): Gaussians with skip != 0 get zero d_lat, d_lp,
+ * d_log_alpha and add nothing to d_dec.
+ *   d_lat [sum lat_dim][n_stride], d_dec [sum attr_count*lat_dim], d_lp [3][n_stride],
+ *   d_log_alpha [n]: written.  d_dec is zeroed on `stream` first.
+ */
+int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_attr, const float *lat,
+                            const uint16_t *dec, const qn_decoder_layout *layout_host,
+                            const float *lp, const float *log_alpha,
+                            const qn_gate_params *gate_host, const float *d_out, float d_lreg,
+                            const uint8_t *skip, float *d_lat, float *d_dec, float *d_lp,
+                            float *d_log_alpha, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* EWA projection and SH colour -- Sec. 3.1, Eq. 1.                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Projected record of one Gaussian ("splat"), 48 bytes, 16-byte aligned:
+ *   s[0] = (mean2d x, mean2d y, opacity, depth t_z)
+ *   s[1] = (conic a, conic b, conic c, 0)   power = -0.5 (a dx^2 + c dy^2) - b dx dy
+ *   s[2] = (r, g, b, 0)                      colour = max(0, 0.5 + sum_k h_k Y_k(dir))
+ * Its gradient record has the same layout: (d mean2d x, d mean2d y,
+ * d opacity, 0), (d a, d b, d c, 0), (d r, d g, d b, 0).
+ * rect = (x0, y0, x1, y1): half-open tile range; (0,0,0,0) when culled.
+ */
+typedef struct {
+    float s[12];
+} qn_splat;
+
+/*
+ * Sigma = R(q) S S^T R(q)^T, S = diag(exp(log-scale)); t = W p;
+ * Sigma' = J W Sigma W^T J^T + blur I with J the affine Jacobian at t (x/z and
+ * y/z clamped to +-1.3 half-extent / focal inside J); conic = Sigma'^-1;
+ * radius = ceil(3 sqrt(mid + sqrt(max(0.1, mid^2 - det))));
+ * rect = [floor((p' - r)/16), floor((p' + r + 15)/16)) clamped to the grid.
+ * Culled (rect zero): t_z <= near_plane, det <= 0, or an empty rect.
+ *   attrs [n_attr][n_stride] f32 A_t (read); splats [n] qn_splat, rects [n] int4
+ *   (written).  sh_degree in 0..3, n_attr == 11 + 3 (sh_degree+1)^2.
+ */
+int qn_project(int32_t n, int32_t n_stride, int32_t sh_degree, const float *attrs,
+               const qn_camera *cam_host, float blur, qn_splat *splats, int32_t *rects,
+               qn_stream_t stream);
+
+/*
+ * Adjoint of qn_project: d_attrs[n_attr][n_stride] (overwritten) from the
+ * gradient records d_splats[n]; culled Gaussians get zero.  The colour clamp
+ * and the Jacobian clamp pass zero gradient.  skip (nullable, [n] u8) zeroes
+ * the Gaussians with skip != 0.
+ */
+int qn_project_bwd(int32_t n, int32_t n_stride, int32_t sh_degree, const float *attrs,
+                   const qn_camera *cam_host, float blur, const qn_splat *d_splats,
+                   const uint8_t *skip, float *d_attrs, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tile binning -- the tile-based rasterizer the paper builds on (Sec. 4).    */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace qn_bin_sort needs for n Gaussians on a
+ * tiles_x x tiles_y grid. */
+size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y);
+
+/*
+ * Emits one (tile, Gaussian) pair per tile of every non-empty rect and sorts
+ * the pairs by the 64-bit key (tile << 32) | bits(float depth) -- stable, so
+ * equal keys keep Gaussian index order.  Implemented as an LSD radix sort of
+ * the 32 depth bits over the n Gaussians followed by one stable counting pass
+ * on the tile digit over the pairs; the result equals the stable sort.
+ *   depth [n] f32 (read; > 0 for every Gaussian with a non-empty rect),
+ *     it may be a strided view: element i at depth[i * depth_stride]
+ *   rects [n] int4 (read)
+ *   vals  [pair_capacity] u32 Gaussian index per sorted pair (written)
+ *   keys  [pair_capacity] u64 sorted keys (written; nullable)
+ *   ranges [tiles_x * tiles_y][2] u32: (#pairs with tile < t, #pairs with tile <= t)
+ *   n_pairs [1] i64 device: the pair count P (written)
+ *   n_pairs_host (nullable): if given, the call synchronises `stream`, stores
+ *     P there and returns QN_ERR_CAPACITY when P > pair_capacity.
+ * When P > pair_capacity no pair is written and every range is (0, 0).
+ */
+int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,
+                int64_t pair_capacity, uint32_t *vals, uint64_t *keys, uint32_t *ranges,
+                int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Compositing -- Sec. 3.1, Eq. 2, and its adjoint.                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Per pixel (u, v) at (u + 0.5, v + 0.5), front to back over its tile's list:
+ *   alpha = min(0.99, o exp(power)); skipped when power > 0 or alpha < 1/255;
+ *   stop before a Gaussian that would leave T < 1e-4;
+ *   C += c alpha T; T *= 1 - alpha.   img = C + T bg.
+ *   img [3][H][W] f32, T_final [H][W] f32, last [H][W] u32 = 1 + list position
+ *   (within the tile) of the last contributor, 0 if none (all written).
+ *   n_contrib [H][W] u32 (nullable): number of contributors of each pixel.
+ *   bg_host: 3 floats in host memory.
+ */
+int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
+                  const qn_splat *splats, const float *bg_host, float *img, float *T_final,
+                  uint32_t *last, uint32_t *n_contrib, qn_stream_t stream);
+
+/*
+ * Adjoint of qn_render_fwd for d_img [3][H][W]: walks each pixel's list from
+ * its last contributor back to the front, rebuilding T by division by
+ * (1 - alpha) and carrying the colour behind each Gaussian:
+ *   dC/dc_k = alpha_k T_k, dC/dalpha_k = T_k (c_k - B_k), B_last = bg,
+ *   B_{k-1} = alpha_k c_k + (1 - alpha_k) B_k; the 0.99 cap passes zero
+ *   gradient to opacity, conic and mean.
+ * Gradients are summed per Gaussian into d_splats[n] (zeroed first on `stream`,
+ * n = number of splats).  skip (nullable, [n] u8): no gradient is written for
+ * Gaussians with skip != 0.
+ */
+int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
+                  const qn_splat *splats, int32_t n, const float *bg_host, const float *T_final,
+                  const uint32_t *last, const float *d_img, const uint8_t *skip,
+                  qn_splat *d_splats, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Loss and optimiser steps of the training iteration (Eq. 3, Eq. 11).       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * L1 term of Eq. 3 over count values, weighted by w:
+ *   loss[0] = w mean |img - target|, d_img = w sign(img - target) / count
+ * (both written; sign(0) = 0).  With mse != 0 the squared error is used
+ * instead (loss[0] = w mean (img - target)^2, d_img = 2 w (img - target) / count),
+ * the loss of Eq. 9.  img, target, d_img: count floats.
+ */
+int qn_image_loss(int64_t count, const float *img, const float *target, float w, int32_t mse,
+                  float *loss, float *d_img, qn_stream_t stream);
+
+/*
+ * Adam (Kingma & Ba) on `rows` planes of n elements with stride `stride`:
+ *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * skip (nullable, [n] u8): columns with skip != 0 keep param, m and v.
+ * param_bf16 (nullable): also writes the updated values rounded to bf16
+ * (round to nearest even), stride as param.
+ */
+int qn_adam(int32_t rows, int32_t n, int32_t stride, float *param, const float *grad, float *m,
+            float *v, int32_t step, float lr, float beta1, float beta2, float eps,
+            const uint8_t *skip, uint16_t *param_bf16, qn_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QUEEN_H */

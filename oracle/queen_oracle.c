@@ -721,6 +721,8 @@ static int or_max_list(int n, const int *rect, int TX, int TY) {
 }
 
 /*
+ * tiles (nullable): composite only these n_tiles_sel tile indices (a bounded
+ * sample); other pixels are left untouched.
  * img: [3][H][W]; T_final, last, fragile: [H][W].  fragile pixel bits: see
  * or_pixel, plus 8 when a fragile Gaussian (frag_g != 0) whose frag_rect
  * covers the pixel's tile reaches alpha >= (1 - eps)/255 there, i.e. when an
@@ -729,8 +731,10 @@ static int or_max_list(int n, const int *rect, int TX, int TY) {
 void or_render_fwd(int n, const double *mean2d, const double *conic, const double *opac,
                    const double *rgb, const double *depth, const int *rect, const int *frag_g,
                    const int *frag_rect, int W, int H, const double *bg, double eps, double eps_d,
-                   double *img, double *T_final, int *last, int *fragile) {
+                   const int *tiles, int n_tiles_sel, double *img, double *T_final, int *last,
+                   int *fragile) {
     int TX = (W + OR_TILE - 1) / OR_TILE, TY = (H + OR_TILE - 1) / OR_TILE;
+    int NT = tiles ? n_tiles_sel : TX * TY;
     int maxl = or_max_list(n, rect, TX, TY);
     int nfrag = 0;
     if (frag_g)
@@ -744,7 +748,8 @@ void or_render_fwd(int n, const double *mean2d, const double *conic, const doubl
     {
         or_dk *buf = (or_dk *)malloc(sizeof(or_dk) * (size_t)(maxl > 0 ? maxl : 1));
 #pragma omp for schedule(dynamic, 1)
-        for (int t = 0; t < TX * TY; ++t) {
+        for (int q = 0; q < NT; ++q) {
+            int t = tiles ? tiles[q] : q;
             int tx = t % TX, ty = t / TX;
             int m = or_tile_list(n, rect, depth, tx, ty, buf);
             for (int v = ty * OR_TILE; v < (ty + 1) * OR_TILE && v < H; ++v)
@@ -787,9 +792,10 @@ void or_render_fwd(int n, const double *mean2d, const double *conic, const doubl
  */
 void or_render_bwd(int n, const double *mean2d, const double *conic, const double *opac,
                    const double *rgb, const double *depth, const int *rect, int W, int H,
-                   const double *bg, const double *d_img, double *d_mean2d, double *d_conic,
-                   double *d_opac, double *d_rgb) {
+                   const double *bg, const double *d_img, const int *tiles, int n_tiles_sel,
+                   double *d_mean2d, double *d_conic, double *d_opac, double *d_rgb) {
     int TX = (W + OR_TILE - 1) / OR_TILE, TY = (H + OR_TILE - 1) / OR_TILE;
+    int NT = tiles ? n_tiles_sel : TX * TY;
     int maxl = or_max_list(n, rect, TX, TY);
     int nthr = 1;
 #ifdef _OPENMP
@@ -806,7 +812,8 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
         or_dk *buf = (or_dk *)malloc(sizeof(or_dk) * (size_t)(maxl > 0 ? maxl : 1));
         or_contrib *rec = (or_contrib *)malloc(sizeof(or_contrib) * (size_t)(maxl > 0 ? maxl : 1));
 #pragma omp for schedule(static, 1)   /* fixed tile -> thread map: reproducible sums */
-        for (int t = 0; t < TX * TY; ++t) {
+        for (int q = 0; q < NT; ++q) {
+            int t = tiles ? tiles[q] : q;
             int tx = t % TX, ty = t / TX;
             int m = or_tile_list(n, rect, depth, tx, ty, buf);
             for (int v = ty * OR_TILE; v < (ty + 1) * OR_TILE && v < H; ++v)

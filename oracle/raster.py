@@ -59,9 +59,9 @@ def _load():
     lib.or_bin_sort.argtypes = [C.c_int, _F, _I, C.c_int, C.c_int, _U64, _U32, _U32]
     lib.or_bin_sort.restype = C.c_int64
     lib.or_render_fwd.argtypes = [C.c_int, _D, _D, _D, _D, _D, _I, _I, _I, C.c_int, C.c_int, _D,
-                                  C.c_double, C.c_double, _D, _D, _I, _I]
+                                  C.c_double, C.c_double, C.c_void_p, C.c_int, _D, _D, _I, _I]
     lib.or_render_bwd.argtypes = [C.c_int, _D, _D, _D, _D, _D, _I, C.c_int, C.c_int, _D, _D,
-                                  _D, _D, _D, _D]
+                                  C.c_void_p, C.c_int, _D, _D, _D, _D]
     lib.or_num_threads.restype = C.c_int
     _lib = lib
     return lib
@@ -202,11 +202,20 @@ def bin_sort(depth_f32, rect, tiles_x, tiles_y):
     return keys[:P], vals[:P], ranges
 
 
-def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0):
+def _tiles(tiles):
+    if tiles is None:
+        return None, 0, None
+    t = np.ascontiguousarray(tiles, dtype=np.int32)
+    return t.ctypes.data, int(t.size), t
+
+
+def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0, tiles=None):
     """Eq. 2 per pixel.  Returns (img[3][H][W], T_final, last, fragile).
     Pinned: single-Gaussian footprint closed form, two-Gaussian hand blend,
-    transmittance invariants, pure-Python brute force."""
+    transmittance invariants, pure-Python brute force.  `tiles` (optional)
+    restricts the work to those tile indices."""
     lib = _load()
+    tp, tn, _keep = _tiles(tiles)
     W, H = proj["width"], proj["height"]
     n = proj["opac"].shape[0]
     img = np.zeros((3, H, W))
@@ -215,19 +224,20 @@ def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0):
     frag = np.zeros((H, W), np.int32)
     lib.or_render_fwd(n, _d(proj["mean2d"]), _d(proj["conic"]), _d(proj["opac"]), _d(proj["rgb"]),
                       _d(proj["depth"]), _i(proj["rect"]), _i(proj["fragile"]), _i(proj["frag_rect"]),
-                      W, H, _d(bg), eps, eps_d, img, T, last, frag)
+                      W, H, _d(bg), eps, eps_d, tp, tn, img, T, last, frag)
     return img, T, last, frag
 
 
-def render_bwd(proj, d_img, bg=(0.0, 0.0, 0.0)):
+def render_bwd(proj, d_img, bg=(0.0, 0.0, 0.0), tiles=None):
     """Adjoint of render_fwd.  Returns dict d_mean2d[2][n], d_conic[3][n],
     d_opac[n], d_rgb[3][n].  Pinned by central finite differences."""
     lib = _load()
+    tp, tn, _keep = _tiles(tiles)
     W, H = proj["width"], proj["height"]
     n = proj["opac"].shape[0]
     g = dict(d_mean2d=np.zeros((2, n)), d_conic=np.zeros((3, n)), d_opac=np.zeros(n),
              d_rgb=np.zeros((3, n)))
     lib.or_render_bwd(n, _d(proj["mean2d"]), _d(proj["conic"]), _d(proj["opac"]), _d(proj["rgb"]),
-                      _d(proj["depth"]), _i(proj["rect"]), W, H, _d(bg), _d(d_img), g["d_mean2d"],
+                      _d(proj["depth"]), _i(proj["rect"]), W, H, _d(bg), _d(d_img), tp, tn, g["d_mean2d"],
                       g["d_conic"], g["d_opac"], g["d_rgb"])
     return g

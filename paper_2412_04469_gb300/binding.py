@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libqueen_gb300.so (include/queen.h).
+
+Each function has the name of its C entry point, takes torch tensors (device
+memory) or plain numbers, marshals them to pointers and raises QueenError on
+a non-zero status.  No computation happens here.  Loading fails loudly when
+the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqueen_gb300.so")
+
+QN_OK, QN_ERR_INVALID_ARG, QN_ERR_CUDA, QN_ERR_CAPACITY, QN_ERR_TIMEOUT, QN_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+QN_TILE = 16
+QN_MAX_CATEGORIES = 8
+
+
+class QueenError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"queen status {code}: {msg}")
+        self.code = code
+
+
+class qn_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("near_plane", C.c_float), ("campos", C.c_float * 3),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class qn_decoder_layout(C.Structure):
+    _fields_ = [("n_cat", C.c_int32), ("attr_begin", C.c_int32 * QN_MAX_CATEGORIES),
+                ("attr_count", C.c_int32 * QN_MAX_CATEGORIES), ("lat_dim", C.c_int32 * QN_MAX_CATEGORIES)]
+
+
+class qn_gate_params(C.Structure):
+    _fields_ = [("tau", C.c_float), ("gamma0", C.c_float), ("gamma1", C.c_float)]
+
+
+_lib = None
+_P = C.c_void_p
+_I32, _I64, _F32, _SZ = C.c_int32, C.c_int64, C.c_float, C.c_size_t
+
+_SIGS = {
+    "qn_last_error": ([], C.c_char_p),
+    "qn_version": ([], C.c_char_p),
+    "qn_decode_residuals": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P],
+                                C.c_int),
+    "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P], C.c_int),
+    "qn_project_bwd": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P, _P], C.c_int),
+    "qn_bin_sort_workspace_size": ([_I32, _I32, _I32], _SZ),
+    "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_render_bwd": ([_P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
+    "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
+}
+
+
+def lib():
+    """Loads the library (built by paper_2412_04469_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise QueenError(QN_ERR_UNSUPPORTED, f"{LIB_PATH} is missing: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise QueenError(QN_ERR_INVALID_ARG, "expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(code):
+    if code != QN_OK:
+        raise QueenError(code, lib().qn_last_error().decode())
+
+
+def make_camera(cam) -> qn_camera:
+    """qn_camera from any object with R, t, fx, fy, cx, cy, near, campos, width, height."""
+    c = qn_camera()
+    R = [float(v) for row in cam.R for v in row]
+    for k in range(9):
+        c.R[k] = R[k]
+    for k in range(3):
+        c.t[k] = float(cam.t[k])
+        c.campos[k] = float(cam.campos[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.near_plane = float(cam.near)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def make_layout(layout) -> qn_decoder_layout:
+    L = qn_decoder_layout()
+    L.n_cat = layout.n_cat
+    for c in range(layout.n_cat):
+        L.attr_begin[c] = layout.attr_begin[c]
+        L.attr_count[c] = layout.attr_count[c]
+        L.lat_dim[c] = layout.lat_dim[c]
+    return L
+
+
+def make_gate(tau, gamma0, gamma1) -> qn_gate_params:
+    return qn_gate_params(tau, gamma0, gamma1)
+
+
+def qn_decode_residuals(n, n_stride, n_attr, prev, lat, dec, layout, lp, log_alpha, gate_params, out, gate=None,
+                        lreg=None, stream=None):
+    _check(lib().qn_decode_residuals(n, n_stride, n_attr, _ptr(prev), _ptr(lat), _ptr(dec), C.byref(layout),
+                                     _ptr(lp), _ptr(log_alpha), C.byref(gate_params), _ptr(out), _ptr(gate),
+                                     _ptr(lreg), _stream(stream)))
+
+
+def qn_decode_residuals_bwd(n, n_stride, n_attr, lat, dec, layout, lp, log_alpha, gate_params, d_out, d_lreg,
+                            skip, d_lat, d_dec, d_lp, d_log_alpha, stream=None):
+    _check(lib().qn_decode_residuals_bwd(n, n_stride, n_attr, _ptr(lat), _ptr(dec), C.byref(layout), _ptr(lp),
+                                         _ptr(log_alpha), C.byref(gate_params), _ptr(d_out), float(d_lreg),
+                                         _ptr(skip), _ptr(d_lat), _ptr(d_dec), _ptr(d_lp), _ptr(d_log_alpha),
+                                         _stream(stream)))
+
+
+def qn_project(n, n_stride, sh_degree, attrs, cam, blur, splats, rects, stream=None):
+    _check(lib().qn_project(n, n_stride, sh_degree, _ptr(attrs), C.byref(cam), float(blur), _ptr(splats),
+                            _ptr(rects), _stream(stream)))
+
+
+def qn_project_bwd(n, n_stride, sh_degree, attrs, cam, blur, d_splats, skip, d_attrs, stream=None):
+    _check(lib().qn_project_bwd(n, n_stride, sh_degree, _ptr(attrs), C.byref(cam), float(blur), _ptr(d_splats),
+                                _ptr(skip), _ptr(d_attrs), _stream(stream)))
+
+
+def qn_bin_sort_workspace_size(n, tiles_x, tiles_y):
+    return int(lib().qn_bin_sort_workspace_size(n, tiles_x, tiles_y))
+
+
+def qn_bin_sort(n, depth, depth_stride, rects, tiles_x, tiles_y, workspace, pair_capacity, vals, keys, ranges,
+                n_pairs, sync=True, stream=None):
+    """Returns P (int) when sync is True (the call synchronises), else None."""
+    host = C.c_int64(0)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().qn_bin_sort(n, _ptr(depth), depth_stride, _ptr(rects), tiles_x, tiles_y, _ptr(workspace),
+                             ws_bytes, int(pair_capacity), _ptr(vals), _ptr(keys), _ptr(ranges), _ptr(n_pairs),
+                             C.addressof(host) if sync else None, _stream(stream)))
+    return int(host.value) if sync else None
+
+
+def _bg(bg):
+    return (C.c_float * 3)(*[float(v) for v in bg])
+
+
+def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=None, stream=None):
+    _check(lib().qn_render_fwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg), _ptr(img),
+                               _ptr(T_final), _ptr(last), _ptr(n_contrib), _stream(stream)))
+
+
+def qn_render_bwd(cam, ranges, vals, splats, n, bg, T_final, last, d_img, skip, d_splats, stream=None):
+    _check(lib().qn_render_bwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), n, _bg(bg), _ptr(T_final),
+                               _ptr(last), _ptr(d_img), _ptr(skip), _ptr(d_splats), _stream(stream)))
+
+
+def qn_image_loss(count, img, target, w, mse, loss, d_img, stream=None):
+    _check(lib().qn_image_loss(count, _ptr(img), _ptr(target), float(w), int(mse), _ptr(loss), _ptr(d_img),
+                               _stream(stream)))
+
+
+def qn_adam(rows, n, stride, param, grad, m, v, step, lr, beta1, beta2, eps, skip=None, param_bf16=None,
+            stream=None):
+    _check(lib().qn_adam(rows, n, stride, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
+                         float(beta1), float(beta2), float(eps), _ptr(skip), _ptr(param_bf16), _stream(stream)))

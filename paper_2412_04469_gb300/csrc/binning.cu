@@ -1,0 +1,476 @@
+// Tile binning: the stable sort of (tile << 32 | depth bits, Gaussian) pairs
+// that the tile-based rasterizer needs (Sec. 4 builds on the 3D-GS
+// rasterizer), computed as an LSD radix sort whose low 32-bit digits are
+// sorted before the pairs are expanded:
+//   1. radix-sort the visible Gaussians by the 32 bits of their depth
+//      (4 stable 8-bit passes over n keys, not over P pairs);
+//   2. one stable counting pass on the tile digit over the P pairs: Gaussians
+//      are cut, in depth order, into chunks of 256; per chunk and tile the
+//      number of members comes from per-warp row/column bitmasks, a prefix
+//      over (tile, chunk) gives each chunk's slot in every tile's range, and
+//      each chunk writes its members tile by tile in depth order.
+// Every pair of one Gaussian shares its depth bits, so sorting the depth
+// digits on the Gaussians first and then the tile digit stably on the pairs is
+// exactly the LSD order of the 64-bit key; the output equals the stable sort.
+#include "common.cuh"
+
+namespace qn {
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per block per pass
+constexpr int RADIX = 256;
+constexpr int CHUNK = 256;                             // Gaussians per binning chunk
+constexpr int CHUNK_WARPS = CHUNK / 32;
+constexpr int LOCAL_MAX = 6144;                        // tiles per band in the scatter (static smem < 48 KB)
+constexpr uint32_t KEY_CULLED = 0xffffffffu;
+
+struct Header {
+    uint32_t n_vis;
+    uint32_t overflow;
+    unsigned long long pairs;
+};
+
+struct Layout {
+    size_t hdr, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, total;
+};
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+Layout layout_of(int n, int n_tiles) {
+    Layout L;
+    const size_t nb = (size_t)div_up(n > 0 ? n : 1, SORT_TILE);
+    const size_t chunks = (size_t)div_up(n > 0 ? n : 1, CHUNK);
+    size_t o = 0;
+    L.hdr = o; o = align_up(o + sizeof(Header));
+    L.keys0 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
+    L.vals0 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
+    L.keys1 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
+    L.vals1 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
+    L.hist = o; o = align_up(o + 4 * (size_t)RADIX * nb);
+    L.counts = o; o = align_up(o + 4 * chunks * (size_t)n_tiles);
+    L.tile_total = o; o = align_up(o + 4 * (size_t)n_tiles);
+    L.tile_off = o; o = align_up(o + 4 * (size_t)(n_tiles + 1));
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------- step 0
+__global__ void k_bin_prep(int n, const float *__restrict__ depth, int dstride,
+                           const int4 *__restrict__ rects, uint32_t *__restrict__ keys,
+                           uint32_t *__restrict__ vals, Header *hdr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool vis = false;
+    if (i < n) {
+        const int4 r = rects[i];
+        vis = r.z > r.x && r.w > r.y;
+        keys[i] = vis ? __float_as_uint(depth[(size_t)i * dstride]) : KEY_CULLED;
+        vals[i] = (uint32_t)i;
+    }
+    const unsigned b = __ballot_sync(FULL, vis);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&hdr->n_vis, (uint32_t)__popc(b));
+}
+
+// ---------------------------------------------------------------- step 1: radix sort of depth keys
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, const uint32_t *__restrict__ keys,
+                                                             uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * SORT_TILE;
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int i = base + r * SORT_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `count` u32 values in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *__restrict__ v, int count) {
+    __shared__ uint32_t part[1024];
+    const int per = div_up_dev(count, 1024);
+    const int b = threadIdx.x * per, e = min(count, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += v[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint32_t x = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += x;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int i = b; i < e; ++i) {
+        const uint32_t x = v[i];
+        v[i] = run;
+        run += x;
+    }
+}
+
+// Stable scatter: within a block items are ranked in their original order
+// (round by round, warp by warp, lane by lane).
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift,
+                                                                const uint32_t *__restrict__ kin,
+                                                                const uint32_t *__restrict__ vin,
+                                                                const uint32_t *__restrict__ offs,
+                                                                uint32_t *__restrict__ kout,
+                                                                uint32_t *__restrict__ vout) {
+    constexpr int W = SORT_THREADS / 32;
+    __shared__ uint32_t base[RADIX];          // running count of each digit in this block
+    __shared__ uint32_t wcnt[W][RADIX];
+    const int warp = threadIdx.x >> 5;
+    base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+    const int blk = blockIdx.x * SORT_TILE;
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        for (int w = 0; w < W; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const int i = blk + r * SORT_THREADS + threadIdx.x;
+        const bool ok = i < n;
+        const uint32_t key = ok ? kin[i] : 0u;
+        const uint32_t d = (key >> shift) & (RADIX - 1);
+        const unsigned act = __ballot_sync(FULL, ok);
+        const unsigned peers = __match_any_sync(FULL, ok ? d : 0xffffffffu) & act;
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // per digit: exclusive prefix over warps, then advance the running base
+        {
+            const uint32_t dd = threadIdx.x;
+            uint32_t run = base[dd];
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = wcnt[w][dd];
+                wcnt[w][dd] = run;
+                run += c;
+            }
+            base[dd] = run;
+        }
+        __syncthreads();
+        if (ok) {
+            const uint32_t pos = wcnt[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = vin[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- step 2: counting pass on the tile digit
+struct ChunkSmem {
+    uint32_t mx[CHUNK_WARPS][QN_MAX_TILES_X];
+    uint32_t my[CHUNK_WARPS][QN_MAX_TILES_Y];
+    int4 rect[CHUNK];
+    uint32_t id[CHUNK];
+    int ux0, uy0, ux1, uy1;
+};
+
+// Loads chunk c of the depth-sorted visible Gaussians and builds, per warp,
+// the bitmask of members covering each tile column and each tile row.
+__device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
+                           const int4 *__restrict__ rects, uint32_t n_vis, ChunkSmem &s) {
+    const int j = threadIdx.x, warp = j >> 5;
+    const uint32_t g = (uint32_t)c * CHUNK + j;
+    int4 r = make_int4(0, 0, 0, 0);
+    uint32_t id = 0;
+    if (g < n_vis) {
+        id = sorted[g];
+        r = rects[id];
+    }
+    s.rect[j] = r;
+    s.id[j] = id;
+    if (j == 0) {
+        s.ux0 = TX; s.uy0 = TY; s.ux1 = 0; s.uy1 = 0;
+    }
+    __syncthreads();
+    const bool has = r.z > r.x;
+    int x0 = has ? r.x : TX, y0 = has ? r.y : TY, x1 = has ? r.z : 0, y1 = has ? r.w : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = min(x0, __shfl_xor_sync(FULL, x0, o));
+        y0 = min(y0, __shfl_xor_sync(FULL, y0, o));
+        x1 = max(x1, __shfl_xor_sync(FULL, x1, o));
+        y1 = max(y1, __shfl_xor_sync(FULL, y1, o));
+    }
+    if ((j & 31) == 0) {
+        atomicMin(&s.ux0, x0); atomicMin(&s.uy0, y0);
+        atomicMax(&s.ux1, x1); atomicMax(&s.uy1, y1);
+    }
+    for (int tx = 0; tx < TX; ++tx) {
+        const unsigned b = __ballot_sync(FULL, r.x <= tx && tx < r.z);
+        if ((j & 31) == 0) s.mx[warp][tx] = b;
+    }
+    for (int ty = 0; ty < TY; ++ty) {
+        const unsigned b = __ballot_sync(FULL, r.y <= ty && ty < r.w);
+        if ((j & 31) == 0) s.my[warp][ty] = b;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t chunk_count(const ChunkSmem &s, int tx, int ty) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < CHUNK_WARPS; ++w) c += __popc(s.mx[w][tx] & s.my[w][ty]);
+    return c;
+}
+
+__global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const uint32_t *__restrict__ sorted,
+                                                        const int4 *__restrict__ rects, const Header *hdr,
+                                                        uint32_t *__restrict__ counts) {
+    __shared__ ChunkSmem s;
+    const int c = blockIdx.x;
+    const uint32_t n_vis = hdr->n_vis;
+    const int n_tiles = TX * TY;
+    uint32_t *row = counts + (size_t)c * n_tiles;
+    if ((uint32_t)c * CHUNK >= n_vis) {
+        for (int t = threadIdx.x; t < n_tiles; t += CHUNK) row[t] = 0;
+        return;
+    }
+    load_chunk(c, TX, TY, sorted, rects, n_vis, s);
+    for (int t = threadIdx.x; t < n_tiles; t += CHUNK) {
+        const int tx = t % TX, ty = t / TX;
+        row[t] = (tx >= s.ux0 && tx < s.ux1 && ty >= s.uy0 && ty < s.uy1) ? chunk_count(s, tx, ty) : 0u;
+    }
+}
+
+// In place: counts[c][t] <- sum_{c' < c} counts[c'][t]; tile_total[t] = sum_c.
+// Block = 32 tiles (lanes) x 32 chunk segments (warps).
+__global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles, uint32_t *__restrict__ counts,
+                                                       uint32_t *__restrict__ tile_total) {
+    __shared__ uint32_t seg[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + lane;
+    const int per = div_up_dev(n_chunks, 32);
+    const int c0 = warp * per, c1 = min(n_chunks, c0 + per);
+    uint32_t s = 0;
+    if (t < n_tiles)
+        for (int c = c0; c < c1; ++c) s += counts[(size_t)c * n_tiles + t];
+    seg[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < 32; ++w) {
+            const uint32_t v = seg[w][lane];
+            seg[w][lane] = run;
+            run += v;
+        }
+        if (t < n_tiles) tile_total[t] = run;
+    }
+    __syncthreads();
+    if (t < n_tiles) {
+        uint32_t run = seg[warp][lane];
+        for (int c = c0; c < c1; ++c) {
+            const size_t o = (size_t)c * n_tiles + t;
+            const uint32_t v = counts[o];
+            counts[o] = run;
+            run += v;
+        }
+    }
+}
+
+// Exclusive scan of tile totals -> tile offsets, ranges and P (one block).
+__global__ void __launch_bounds__(1024) k_tile_offsets(int n_tiles, const uint32_t *__restrict__ total,
+                                                       uint32_t *__restrict__ off, uint32_t *__restrict__ ranges,
+                                                       Header *hdr, unsigned long long capacity,
+                                                       long long *n_pairs) {
+    __shared__ unsigned long long part[1024];
+    const int per = div_up_dev(n_tiles, 1024);
+    const int b = threadIdx.x * per, e = min(n_tiles, b + per);
+    unsigned long long s = 0;
+    for (int t = b; t < e; ++t) s += total[t];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned long long x = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += x;
+        __syncthreads();
+    }
+    const unsigned long long P = part[1023];
+    const bool over = P > capacity || P > 0xffffffffull;
+    unsigned long long run = part[threadIdx.x] - s;
+    for (int t = b; t < e; ++t) {
+        const uint32_t v = total[t];
+        off[t] = (uint32_t)run;
+        ranges[2 * (size_t)t] = over ? 0u : (uint32_t)run;
+        ranges[2 * (size_t)t + 1] = over ? 0u : (uint32_t)(run + v);
+        run += v;
+    }
+    if (threadIdx.x == 0) {
+        hdr->pairs = P;
+        hdr->overflow = over ? 1u : 0u;
+        if (n_pairs) *n_pairs = (long long)P;
+    }
+}
+
+struct BandSmem {
+    uint32_t off[LOCAL_MAX + 1];
+};
+
+// Writes chunk c's members tile by tile: slot k of a band is the r-th member
+// (in depth order) of its tile; consecutive slots go to consecutive addresses.
+__global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const uint32_t *__restrict__ sorted,
+                                                         const int4 *__restrict__ rects,
+                                                         const float *__restrict__ depth, int dstride,
+                                                         const Header *hdr, const uint32_t *__restrict__ gbase,
+                                                         const uint32_t *__restrict__ tile_off,
+                                                         uint32_t *__restrict__ vals,
+                                                         unsigned long long *__restrict__ keys) {
+    __shared__ ChunkSmem s;
+    __shared__ BandSmem band;
+    __shared__ uint32_t wsum[CHUNK_WARPS];
+    const int c = blockIdx.x;
+    const uint32_t n_vis = hdr->n_vis;
+    if (hdr->overflow || (uint32_t)c * CHUNK >= n_vis) return;
+    load_chunk(c, TX, TY, sorted, rects, n_vis, s);
+    const int n_tiles = TX * TY;
+    const int uw = s.ux1 - s.ux0;
+    if (uw <= 0) return;
+    const int rows_per_band = max(1, LOCAL_MAX / uw);
+    const uint32_t *grow = gbase + (size_t)c * n_tiles;
+    for (int yb = s.uy0; yb < s.uy1; yb += rows_per_band) {
+        const int ye = min(s.uy1, yb + rows_per_band);
+        const int nloc = (ye - yb) * uw;
+        // local counts -> exclusive offsets (per-thread serial segments + block scan)
+        const int per = div_up_dev(nloc, CHUNK);
+        const int b0 = threadIdx.x * per, b1 = min(nloc, b0 + per);
+        uint32_t sum = 0;
+        for (int q = b0; q < b1; ++q) {
+            const uint32_t v = chunk_count(s, s.ux0 + q % uw, yb + q / uw);
+            band.off[q] = v;
+            sum += v;
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL, incl, o);
+            if ((threadIdx.x & 31) >= (unsigned)o) incl += x;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbase += wsum[w];
+        uint32_t run = wbase + incl - sum;
+        for (int q = b0; q < b1; ++q) {
+            const uint32_t v = band.off[q];
+            band.off[q] = run;
+            run += v;
+        }
+        __syncthreads();
+        uint32_t total = 0;
+        for (int w = 0; w < CHUNK_WARPS; ++w) total += wsum[w];
+        if (threadIdx.x == 0) band.off[nloc] = total;
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < total; k += CHUNK) {
+            int lo = 0, hi = nloc;               // largest q with off[q] <= k
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (band.off[mid] <= k) lo = mid; else hi = mid;
+            }
+            const int tx = s.ux0 + lo % uw, ty = yb + lo / uw;
+            const uint32_t rank = k - band.off[lo];
+            uint32_t r = rank;
+            int jj = 0;
+            for (int w = 0; w < CHUNK_WARPS; ++w) {
+                uint32_t m = s.mx[w][tx] & s.my[w][ty];
+                const uint32_t cnt = __popc(m);
+                if (r < cnt) {
+                    for (uint32_t q = 0; q < r; ++q) m &= m - 1;
+                    jj = w * 32 + (__ffs(m) - 1);
+                    break;
+                }
+                r -= cnt;
+            }
+            const int t = ty * TX + tx;
+            const uint32_t pos = tile_off[t] + grow[t] + rank;
+            const uint32_t id = s.id[jj];
+            vals[pos] = id;
+            if (keys)
+                keys[pos] = ((unsigned long long)(uint32_t)t << 32) |
+                            (unsigned long long)__float_as_uint(depth[(size_t)id * dstride]);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+}  // namespace qn
+
+extern "C" size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y) {
+    if (n < 0 || tiles_x <= 0 || tiles_y <= 0) return 0;
+    return qn::layout_of(n, tiles_x * tiles_y).total;
+}
+
+extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                           int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,
+                           int64_t pair_capacity, uint32_t *vals, uint64_t *keys, uint32_t *ranges,
+                           int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream) {
+    using namespace qn;
+    QN_REQUIRE(n >= 0, "n must be >= 0");
+    QN_REQUIRE(tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
+               "tile grid %dx%d out of range", tiles_x, tiles_y);
+    QN_REQUIRE(depth_stride >= 1, "depth_stride must be >= 1");
+    QN_REQUIRE(pair_capacity >= 0, "pair_capacity must be >= 0");
+    QN_REQUIRE(ranges && n_pairs, "ranges and n_pairs are required");
+    QN_REQUIRE(n == 0 || (depth && rects && workspace), "null pointer argument");
+    QN_REQUIRE(pair_capacity == 0 || vals, "vals is required when pair_capacity > 0");
+    QN_REQUIRE(((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
+               "rects must be 16-byte and workspace 256-byte aligned");
+    const int n_tiles = tiles_x * tiles_y;
+    const Layout L = layout_of(n, n_tiles);
+    QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) {
+        if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * n_tiles, s) != cudaSuccess ||
+            cudaMemsetAsync(n_pairs, 0, sizeof(int64_t), s) != cudaSuccess)
+            return check_launch("qn_bin_sort memset");
+        if (n_pairs_host) {
+            if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("qn_bin_sort sync");
+            *n_pairs_host = 0;
+        }
+        return QN_OK;
+    }
+    char *ws = static_cast<char *>(workspace);
+    Header *hdr = reinterpret_cast<Header *>(ws + L.hdr);
+    uint32_t *k0 = reinterpret_cast<uint32_t *>(ws + L.keys0), *v0 = reinterpret_cast<uint32_t *>(ws + L.vals0);
+    uint32_t *k1 = reinterpret_cast<uint32_t *>(ws + L.keys1), *v1 = reinterpret_cast<uint32_t *>(ws + L.vals1);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + L.counts);
+    uint32_t *tile_total = reinterpret_cast<uint32_t *>(ws + L.tile_total);
+    uint32_t *tile_off = reinterpret_cast<uint32_t *>(ws + L.tile_off);
+    const int4 *r4 = reinterpret_cast<const int4 *>(rects);
+
+    if (cudaMemsetAsync(hdr, 0, sizeof(Header), s) != cudaSuccess) return check_launch("qn_bin_sort memset");
+    k_bin_prep<<<div_up(n, 256), 256, 0, s>>>(n, depth, depth_stride, r4, k0, v0, hdr);
+    const int nb = div_up(n, SORT_TILE);
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        uint32_t *ki = (pass & 1) ? k1 : k0, *vi = (pass & 1) ? v1 : v0;
+        uint32_t *ko = (pass & 1) ? k0 : k1, *vo = (pass & 1) ? v0 : v1;
+        k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist);
+        k_scan_small<<<1, 1024, 0, s>>>(hist, RADIX * nb);
+        k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo);
+    }
+    // after 4 passes the sorted (depth, index) order is back in k0 / v0
+    const int n_chunks = div_up(n, CHUNK);
+    k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts);
+    k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total);
+    k_tile_offsets<<<1, 1024, 0, s>>>(n_tiles, tile_total, tile_off, ranges, hdr,
+                                      (unsigned long long)pair_capacity, reinterpret_cast<long long *>(n_pairs));
+    k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
+                                               tile_off, vals, reinterpret_cast<unsigned long long *>(keys));
+    int st = check_launch("qn_bin_sort");
+    if (st) return st;
+    if (n_pairs_host) {
+        if (cudaMemcpyAsync(n_pairs_host, n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return check_launch("qn_bin_sort readback");
+        if (*n_pairs_host > pair_capacity) {
+            set_error("pair count %lld exceeds capacity %lld", (long long)*n_pairs_host, (long long)pair_capacity);
+            return QN_ERR_CAPACITY;
+        }
+    }
+    return QN_OK;
+}

@@ -1,0 +1,48 @@
+// Shared helpers of the CUDA translation units: status codes, argument
+// checks, launch checks and warp utilities.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "queen.h"
+
+namespace qn {
+
+// Records a message for qn_last_error() on the calling host thread.
+void set_error(const char *fmt, ...);
+void clear_error();
+
+inline cudaStream_t as_stream(qn_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Returns QN_ERR_CUDA with the message of the last launch error, or QN_OK.
+int check_launch(const char *what);
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ int div_up_dev(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace qn
+
+#define QN_REQUIRE(cond, ...)                 \
+    do {                                      \
+        if (!(cond)) {                        \
+            qn::set_error(__VA_ARGS__);       \
+            return QN_ERR_INVALID_ARG;        \
+        }                                     \
+    } while (0)

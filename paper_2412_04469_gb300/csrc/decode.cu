@@ -1,0 +1,248 @@
+// Residual decode and hard-concrete position gate (Sec. 3.2, Eq. 4-8) and
+// their adjoint.
+//
+// The decoder contraction is r_c = D_c l_c with K = lat_dim (8 by default):
+// about 2 * 56 * 8 flops per 128 bytes of latents, i.e. ~7 flop/byte, far
+// below the tensor-core balance point, so it runs as FP32 FMAs on bf16
+// weights held in shared memory.  Integer latents (|l| <= 128) times bf16
+// weights are exact in FP32; only the sum over K rounds.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace qn {
+namespace {
+
+constexpr int MAX_RES_PLANES = 56;     // attribute planes 3 .. 58 (SH degree 3)
+constexpr int MAX_LAT_TOTAL = 64;      // latent planes over all categories
+
+struct DecodeArgs {
+    int n, stride, n_attr, n_cat, n_dec, n_lat;
+    int ab[QN_MAX_CATEGORIES], ac[QN_MAX_CATEGORIES], ld[QN_MAX_CATEGORIES];
+    int lat_off[QN_MAX_CATEGORIES], dec_off[QN_MAX_CATEGORIES];
+    unsigned long long covered;        // bit k: attribute plane k receives a residual
+    float tau, g0, g1, shift;          // shift = tau log(-gamma0 / gamma1)
+};
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) {
+    return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+
+__device__ __forceinline__ float latent_int(float v) {
+    return fminf(127.f, fmaxf(-128.f, rintf(v)));   // round half to even, int8 saturation
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + __expf(-x)); }
+
+__global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__restrict__ prev,
+                                                const float *__restrict__ lat,
+                                                const uint16_t *__restrict__ dec,
+                                                const float *__restrict__ lp,
+                                                const float *__restrict__ la, float *__restrict__ out,
+                                                float *__restrict__ gate, float *__restrict__ lreg) {
+    __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
+    __shared__ float sred[8];
+    for (int k = threadIdx.x; k < a.n_dec; k += blockDim.x) sD[k] = bf16_to_f32(dec[k]);
+    __syncthreads();
+    const size_t S = a.stride;
+    float reg = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const float l_a = la[i];
+        const float gh = sigmoidf_(l_a / a.tau);                       // Eq. 6
+        const float g = fminf(1.f, fmaxf(0.f, gh * (a.g1 - a.g0) + a.g0));   // Eq. 7
+        if (gate) gate[i] = g;
+        reg += sigmoidf_(l_a - a.shift);                                // Eq. 8
+#pragma unroll
+        for (int d = 0; d < 3; ++d) out[d * S + i] = prev[d * S + i] + g * lp[d * S + i];
+        for (int c = 0; c < a.n_cat; ++c) {
+            float l[QN_MAX_LATENT];
+            const int L = a.ld[c];
+#pragma unroll
+            for (int k = 0; k < QN_MAX_LATENT; ++k)
+                if (k < L) l[k] = latent_int(lat[(size_t)(a.lat_off[c] + k) * S + i]);
+            const float *D = sD + a.dec_off[c];
+            for (int r = 0; r < a.ac[c]; ++r) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < QN_MAX_LATENT; ++k)
+                    if (k < L) acc = fmaf(D[r * L + k], l[k], acc);     // Eq. 5
+                const size_t o = (size_t)(a.ab[c] + r) * S + i;
+                out[o] = prev[o] + acc;                                 // Eq. 4
+            }
+        }
+        for (int k = 3; k < a.n_attr; ++k)
+            if (!((a.covered >> k) & 1ull)) out[(size_t)k * S + i] = prev[(size_t)k * S + i];
+    }
+    if (lreg) {
+        reg = warp_sum(reg);
+        if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = reg;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w];
+            atomicAdd(lreg, s);
+        }
+    }
+}
+
+constexpr int BWD_BLOCK = 64;
+
+__global__ void __launch_bounds__(BWD_BLOCK) k_decode_bwd(
+    DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
+    const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
+    float d_lreg, const uint8_t *__restrict__ skip, float *__restrict__ d_lat,
+    float *__restrict__ d_dec, float *__restrict__ d_lp, float *__restrict__ d_la) {
+    __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
+    __shared__ float s_dr[MAX_RES_PLANES][BWD_BLOCK];
+    __shared__ float s_l[MAX_LAT_TOTAL][BWD_BLOCK];
+    for (int k = threadIdx.x; k < a.n_dec; k += blockDim.x) sD[k] = bf16_to_f32(dec[k]);
+    // each thread owns up to ceil(n_dec / BWD_BLOCK) entries of dD
+    constexpr int MAX_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + BWD_BLOCK - 1) / BWD_BLOCK;
+    float acc[MAX_OWN];
+#pragma unroll
+    for (int q = 0; q < MAX_OWN; ++q) acc[q] = 0.f;
+    const size_t S = a.stride;
+    const int t = threadIdx.x;
+    const int n_res = a.n_attr - 3;
+    __syncthreads();
+    for (int base = blockIdx.x * BWD_BLOCK; base < a.n; base += gridDim.x * BWD_BLOCK) {
+        const int i = base + t;
+        const bool valid = i < a.n;
+        const bool sk = valid && skip && skip[i];
+        if (valid) {
+            const float l_a = la[i];
+            const float gh = sigmoidf_(l_a / a.tau);
+            const float gt = gh * (a.g1 - a.g0) + a.g0;
+            const float g = fminf(1.f, fmaxf(0.f, gt));
+            const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
+            float dot = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float dp = d_out[d * S + i];
+                d_lp[d * S + i] = sk ? 0.f : g * dp;
+                dot = fmaf(dp, lp[d * S + i], dot);
+            }
+            const float p = sigmoidf_(l_a - a.shift);
+            d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
+        }
+        for (int k = 0; k < n_res; ++k)
+            s_dr[k][t] = (valid && !sk) ? d_out[(size_t)(k + 3) * S + i] : 0.f;
+        for (int k = 0; k < a.n_lat; ++k) s_l[k][t] = valid ? latent_int(lat[(size_t)k * S + i]) : 0.f;
+        __syncthreads();
+        if (valid) {
+            for (int c = 0; c < a.n_cat; ++c) {
+                const int L = a.ld[c], M = a.ac[c];
+                const float *D = sD + a.dec_off[c];
+                for (int k = 0; k < L; ++k) {
+                    float s = 0.f;                          // STE: D^T dr
+                    for (int r = 0; r < M; ++r) s = fmaf(D[r * L + k], s_dr[a.ab[c] - 3 + r][t], s);
+                    d_lat[(size_t)(a.lat_off[c] + k) * S + i] = sk ? 0.f : s;
+                }
+            }
+        }
+        // dD[c][r][k] += sum over this block of dr[r] l[k]
+#pragma unroll
+        for (int q = 0; q < MAX_OWN; ++q) {
+            const int e = t + q * BWD_BLOCK;
+            if (e >= a.n_dec) break;
+            int c = 0;
+            while (c + 1 < a.n_cat && e >= a.dec_off[c + 1]) ++c;
+            const int L = a.ld[c];
+            const int r = (e - a.dec_off[c]) / L, k = (e - a.dec_off[c]) % L;
+            const float *pr = s_dr[a.ab[c] - 3 + r];
+            const float *pl = s_l[a.lat_off[c] + k];
+            float s = acc[q];
+            for (int j = 0; j < BWD_BLOCK; ++j) s = fmaf(pr[j], pl[j], s);
+            acc[q] = s;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < MAX_OWN; ++q) {
+        const int e = t + q * BWD_BLOCK;
+        if (e < a.n_dec) atomicAdd(&d_dec[e], acc[q]);
+    }
+}
+
+int make_args(int32_t n, int32_t n_stride, int32_t n_attr, const qn_decoder_layout *lay,
+              const qn_gate_params *gp, DecodeArgs *a) {
+    QN_REQUIRE(n >= 0, "n must be >= 0 (got %d)", n);
+    QN_REQUIRE(n_stride >= n && n_stride % 4 == 0, "n_stride must be >= n and a multiple of 4");
+    QN_REQUIRE(n_attr > 3 && n_attr - 3 <= MAX_RES_PLANES, "n_attr out of range (%d)", n_attr);
+    QN_REQUIRE(lay && gp, "layout and gate parameters are required");
+    QN_REQUIRE(lay->n_cat >= 0 && lay->n_cat <= QN_MAX_CATEGORIES, "n_cat out of range");
+    QN_REQUIRE(gp->tau > 0.f && gp->gamma0 < 0.f && gp->gamma1 > 1.f, "gate parameters out of range");
+    a->n = n; a->stride = n_stride; a->n_attr = n_attr; a->n_cat = lay->n_cat;
+    a->covered = 0;
+    int lo = 0, dofs = 0;
+    for (int c = 0; c < lay->n_cat; ++c) {
+        const int b = lay->attr_begin[c], m = lay->attr_count[c], l = lay->lat_dim[c];
+        QN_REQUIRE(m > 0 && l > 0 && l <= QN_MAX_LATENT, "category %d: bad sizes", c);
+        QN_REQUIRE(b >= 3 && b + m <= n_attr, "category %d: planes outside 3..n_attr-1", c);
+        for (int k = b; k < b + m; ++k) {
+            QN_REQUIRE(!((a->covered >> k) & 1ull), "category %d overlaps another", c);
+            a->covered |= 1ull << k;
+        }
+        a->ab[c] = b; a->ac[c] = m; a->ld[c] = l;
+        a->lat_off[c] = lo; a->dec_off[c] = dofs;
+        lo += l;
+        dofs += m * l;
+    }
+    QN_REQUIRE(lo <= MAX_LAT_TOTAL, "too many latent planes (%d)", lo);
+    a->n_lat = lo;
+    a->n_dec = dofs;
+    a->tau = gp->tau; a->g0 = gp->gamma0; a->g1 = gp->gamma1;
+    a->shift = (float)(gp->tau * std::log(-(double)gp->gamma0 / (double)gp->gamma1));
+    return QN_OK;
+}
+
+// Grid of at most `per_sm` blocks per SM (grid-stride loops cover the rest).
+int grid_for(int n, int block, int per_sm) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int need = div_up(n, block);
+    const int cap = sms * per_sm;
+    return need < 1 ? 1 : (need < cap ? need : cap);
+}
+
+}  // namespace
+}  // namespace qn
+
+extern "C" int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, const float *prev,
+                                   const float *lat, const uint16_t *dec,
+                                   const qn_decoder_layout *layout_host, const float *lp,
+                                   const float *log_alpha, const qn_gate_params *gate_host,
+                                   float *out, float *gate, float *lreg, qn_stream_t stream) {
+    qn::DecodeArgs a;
+    int st = qn::make_args(n, n_stride, n_attr, layout_host, gate_host, &a);
+    if (st) return st;
+    QN_REQUIRE(n == 0 || (prev && out && lp && log_alpha), "null pointer argument");
+    QN_REQUIRE(n == 0 || a.n_cat == 0 || (lat && dec), "null latent or decoder pointer");
+    QN_REQUIRE(prev != out, "out may not alias prev");
+    cudaStream_t s = qn::as_stream(stream);
+    if (lreg && cudaMemsetAsync(lreg, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("decode memset");
+    if (n == 0) return QN_OK;
+    qn::k_decode<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, out, gate, lreg);
+    return qn::check_launch("qn_decode_residuals");
+}
+
+extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_attr, const float *lat,
+                                       const uint16_t *dec, const qn_decoder_layout *layout_host,
+                                       const float *lp, const float *log_alpha,
+                                       const qn_gate_params *gate_host, const float *d_out,
+                                       float d_lreg, const uint8_t *skip, float *d_lat, float *d_dec,
+                                       float *d_lp, float *d_log_alpha, qn_stream_t stream) {
+    qn::DecodeArgs a;
+    int st = qn::make_args(n, n_stride, n_attr, layout_host, gate_host, &a);
+    if (st) return st;
+    QN_REQUIRE(n == 0 || (d_out && lp && log_alpha && d_lp && d_log_alpha), "null pointer argument");
+    QN_REQUIRE(a.n_cat == 0 || (d_dec && (n == 0 || (lat && dec && d_lat))), "null latent/decoder pointer");
+    cudaStream_t s = qn::as_stream(stream);
+    if (a.n_dec > 0 && cudaMemsetAsync(d_dec, 0, sizeof(float) * a.n_dec, s) != cudaSuccess)
+        return qn::check_launch("decode_bwd memset");
+    if (n == 0) return QN_OK;
+    qn::k_decode_bwd<<<qn::grid_for(n, qn::BWD_BLOCK, 4), qn::BWD_BLOCK, 0, s>>>(
+        a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat, d_dec, d_lp, d_log_alpha);
+    return qn::check_launch("qn_decode_residuals_bwd");
+}

@@ -1,0 +1,96 @@
+// Loss (Eq. 3 L1 term, and the MSE of Eq. 9) and the Adam update of the
+// training iteration (App. B trains every residual parameter with Adam).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace qn {
+namespace {
+
+__global__ void __launch_bounds__(256) k_image_loss(long long count, const float *__restrict__ img,
+                                                    const float *__restrict__ tgt, float scale, int mse,
+                                                    float *__restrict__ loss, float *__restrict__ dimg) {
+    __shared__ float red[8];
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float d = img[i] - tgt[i];
+        if (mse) {
+            acc = fmaf(d, d, acc);
+            dimg[i] = 2.f * scale * d;
+        } else {
+            acc += fabsf(d);
+            dimg[i] = d > 0.f ? scale : (d < 0.f ? -scale : 0.f);
+        }
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(loss, s * scale);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adam(int rows, int n, int stride, float *__restrict__ p,
+                                              const float *__restrict__ g, float *__restrict__ m,
+                                              float *__restrict__ v, float lr, float b1, float b2, float eps,
+                                              float ibc1, float ibc2, const uint8_t *__restrict__ skip,
+                                              uint16_t *__restrict__ pb) {
+    const long long total = (long long)rows * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), i = (int)(e % n);
+        const size_t o = (size_t)r * stride + i;
+        if (skip && skip[i]) continue;
+        const float gr = g[o];
+        const float mm = fmaf(b1, m[o], (1.f - b1) * gr);
+        const float vv = fmaf(b2, v[o], (1.f - b2) * gr * gr);
+        m[o] = mm;
+        v[o] = vv;
+        const float np = p[o] - lr * (mm * ibc1) / (sqrtf(vv * ibc2) + eps);
+        p[o] = np;
+        if (pb) pb[o] = __bfloat16_as_ushort(__float2bfloat16_rn(np));
+    }
+}
+
+int grid_cap(long long work, int block) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long need = (work + block - 1) / block;
+    const long long cap = (long long)sms * 8;
+    if (need > cap) need = cap;
+    return need < 1 ? 1 : (int)need;
+}
+
+}  // namespace
+}  // namespace qn
+
+extern "C" int qn_image_loss(int64_t count, const float *img, const float *target, float w, int32_t mse,
+                             float *loss, float *d_img, qn_stream_t stream) {
+    QN_REQUIRE(count >= 0, "count must be >= 0");
+    QN_REQUIRE(loss && (count == 0 || (img && target && d_img)), "null pointer argument");
+    cudaStream_t s = qn::as_stream(stream);
+    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("qn_image_loss memset");
+    if (count == 0) return QN_OK;
+    const float scale = (float)((double)w / (double)count);
+    qn::k_image_loss<<<qn::grid_cap(count, 256), 256, 0, s>>>(count, img, target, scale, mse, loss, d_img);
+    return qn::check_launch("qn_image_loss");
+}
+
+extern "C" int qn_adam(int32_t rows, int32_t n, int32_t stride, float *param, const float *grad, float *m,
+                       float *v, int32_t step, float lr, float beta1, float beta2, float eps,
+                       const uint8_t *skip, uint16_t *param_bf16, qn_stream_t stream) {
+    QN_REQUIRE(rows >= 0 && n >= 0 && stride >= n, "bad rows / n / stride");
+    QN_REQUIRE(step >= 1, "step counts from 1");
+    QN_REQUIRE(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f, "bad Adam constants");
+    if ((long long)rows * n == 0) return QN_OK;
+    QN_REQUIRE(param && grad && m && v, "null pointer argument");
+    const float ibc1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
+    const float ibc2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
+    qn::k_adam<<<qn::grid_cap((long long)rows * n, 256), 256, 0, qn::as_stream(stream)>>>(
+        rows, n, stride, param, grad, m, v, lr, beta1, beta2, eps, ibc1, ibc2, skip, param_bf16);
+    return qn::check_launch("qn_adam");
+}

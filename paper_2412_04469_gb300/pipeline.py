@@ -1,0 +1,206 @@
+"""Device-resident buffers and the per-view training iteration of QUEEN's
+residual training (Sec. 3.2-3.4), every step a C-ABI call:
+
+  decode+gate -> project -> bin/sort -> composite -> loss -> composite adjoint
+  -> projection adjoint -> decode/gate adjoint -> Adam
+
+PyTorch only allocates device memory and provides the stream.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .synthetic import DecoderLayout, n_attr as n_attr_of, bf16_bits
+
+TILE = B.QN_TILE
+
+
+def _stride(n: int) -> int:
+    return max(4, (n + 31) // 32 * 32)
+
+
+@dataclass
+class HParams:
+    """Hyper-parameters, N3DV rows of the paper's tables (App. B)."""
+    tau: float = 0.3
+    gamma0: float = -0.5
+    gamma1: float = 1.01
+    lambda_reg: float = 0.01
+    lr_gate: float = 0.1
+    lr_pos: float = 0.00016
+    # per decoder category (rotation, scale, opacity, colour)
+    lr_latent: tuple = (0.025, 0.01, 0.05, 0.0125)
+    lr_decoder: tuple = (1e-3, 1e-4, 1e-4, 1e-3)
+    blur: float = 0.3
+    bg: tuple = (0.0, 0.0, 0.0)
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+
+
+class _Adam:
+    def __init__(self, shape, dev):
+        self.m = torch.zeros(shape, device=dev, dtype=torch.float32)
+        self.v = torch.zeros(shape, device=dev, dtype=torch.float32)
+
+
+class QueenFrame:
+    """One time-step's trainable residuals on top of the fixed A_{t-1}."""
+
+    def __init__(self, prev: np.ndarray, sh_degree: int, layout: DecoderLayout, lat: np.ndarray, dec: np.ndarray,
+                 lp: np.ndarray, log_alpha: np.ndarray, hp: HParams | None = None, device="cuda"):
+        self.dev = torch.device(device)
+        self.hp = hp or HParams()
+        self.sh_degree = sh_degree
+        self.layout = layout
+        self.n = n = prev.shape[1]
+        self.n_attr = n_attr_of(sh_degree)
+        assert prev.shape[0] == self.n_attr
+        self.S = S = _stride(n)
+        dev = self.dev
+
+        def planes(a, rows):
+            t = torch.zeros((rows, S), device=dev, dtype=torch.float32)
+            if n:
+                t[:, :n] = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+            return t
+
+        self.prev = planes(prev, self.n_attr)
+        self.lat = planes(lat, layout.n_latent)
+        self.lp = planes(lp, 3)
+        self.log_alpha = torch.zeros(S, device=dev, dtype=torch.float32)
+        self.log_alpha[:n] = torch.from_numpy(np.ascontiguousarray(log_alpha, np.float32)).to(dev)
+        self.dec = torch.from_numpy(np.ascontiguousarray(dec, np.float32)).to(dev)
+        self.dec_bf16 = torch.from_numpy(bf16_bits(dec).view(np.int16)).to(dev).view(torch.bfloat16)
+        self.c_layout = B.make_layout(layout)
+        self.c_gate = B.make_gate(self.hp.tau, self.hp.gamma0, self.hp.gamma1)
+        # outputs and gradients
+        self.attrs = torch.zeros((self.n_attr, S), device=dev)
+        self.gate = torch.zeros(S, device=dev)
+        self.lreg = torch.zeros(1, device=dev)
+        self.d_attrs = torch.zeros((self.n_attr, S), device=dev)
+        self.d_lat = torch.zeros_like(self.lat)
+        self.d_dec = torch.zeros_like(self.dec)
+        self.d_lp = torch.zeros_like(self.lp)
+        self.d_log_alpha = torch.zeros_like(self.log_alpha)
+        self.opt = {k: _Adam(getattr(self, k).shape, dev) for k in ("lat", "dec", "lp", "log_alpha")}
+        self.step_count = 0
+
+    # ---------------------------------------------------------------- steps
+    def decode(self, stream=None):
+        B.qn_decode_residuals(self.n, self.S, self.n_attr, self.prev, self.lat, self.dec_bf16, self.c_layout,
+                              self.lp, self.log_alpha, self.c_gate, self.attrs, self.gate, self.lreg, stream)
+
+    def decode_bwd(self, skip=None, stream=None):
+        B.qn_decode_residuals_bwd(self.n, self.S, self.n_attr, self.lat, self.dec_bf16, self.c_layout, self.lp,
+                                  self.log_alpha, self.c_gate, self.d_attrs, self.hp.lambda_reg, skip, self.d_lat,
+                                  self.d_dec, self.d_lp, self.d_log_alpha, stream)
+
+    def adam(self, skip=None, stream=None):
+        self.step_count += 1
+        t, hp, n, S = self.step_count, self.hp, self.n, self.S
+        lay = self.layout
+        lo = 0
+        for c in range(lay.n_cat):
+            L = lay.lat_dim[c]
+            o = self.opt["lat"]
+            B.qn_adam(L, n, S, self.lat[lo:lo + L], self.d_lat[lo:lo + L], o.m[lo:lo + L], o.v[lo:lo + L], t,
+                      hp.lr_latent[min(c, len(hp.lr_latent) - 1)], hp.beta1, hp.beta2, hp.eps, skip, None, stream)
+            lo += L
+        dofs = 0
+        for c in range(lay.n_cat):
+            k = lay.attr_count[c] * lay.lat_dim[c]
+            o = self.opt["dec"]
+            B.qn_adam(1, k, k, self.dec[dofs:dofs + k], self.d_dec[dofs:dofs + k], o.m[dofs:dofs + k],
+                      o.v[dofs:dofs + k], t, hp.lr_decoder[min(c, len(hp.lr_decoder) - 1)], hp.beta1, hp.beta2,
+                      hp.eps, None, self.dec_bf16[dofs:dofs + k], stream)
+            dofs += k
+        o = self.opt["lp"]
+        B.qn_adam(3, n, S, self.lp, self.d_lp, o.m, o.v, t, hp.lr_pos, hp.beta1, hp.beta2, hp.eps, skip, None, stream)
+        o = self.opt["log_alpha"]
+        B.qn_adam(1, n, S, self.log_alpha, self.d_log_alpha, o.m, o.v, t, hp.lr_gate, hp.beta1, hp.beta2, hp.eps,
+                  skip, None, stream)
+
+
+class Rasterizer:
+    """Projection, binning and compositing buffers for n Gaussians on one
+    image size."""
+
+    def __init__(self, n: int, n_stride: int, sh_degree: int, width: int, height: int, pair_capacity: int,
+                 device="cuda", keep_keys: bool = False):
+        dev = torch.device(device)
+        self.n, self.S, self.sh_degree = n, n_stride, sh_degree
+        self.W, self.H = width, height
+        self.TX, self.TY = (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
+        nn = max(n, 1)
+        self.splats = torch.zeros((nn, 12), device=dev)
+        self.rects = torch.zeros((nn, 4), device=dev, dtype=torch.int32)
+        self.d_splats = torch.zeros((nn, 12), device=dev)
+        ws = B.qn_bin_sort_workspace_size(n, self.TX, self.TY)
+        self.workspace = torch.zeros(max(ws, 256), device=dev, dtype=torch.uint8)
+        self.ranges = torch.zeros((self.TX * self.TY, 2), device=dev, dtype=torch.int32)
+        self.n_pairs = torch.zeros(1, device=dev, dtype=torch.int64)
+        self.keep_keys = keep_keys
+        self.set_capacity(pair_capacity)
+        self.img = torch.zeros((3, height, width), device=dev)
+        self.T_final = torch.zeros((height, width), device=dev)
+        self.last = torch.zeros((height, width), device=dev, dtype=torch.int32)
+        self.d_img = torch.zeros((3, height, width), device=dev)
+        self.loss = torch.zeros(1, device=dev)
+
+    def set_capacity(self, cap: int):
+        dev = self.splats.device
+        self.capacity = int(cap)
+        self.vals = torch.zeros(max(self.capacity, 1), device=dev, dtype=torch.int32)
+        self.keys = torch.zeros(max(self.capacity, 1), device=dev, dtype=torch.int64) if self.keep_keys else None
+
+    def project(self, attrs, cam, blur, stream=None):
+        B.qn_project(self.n, self.S, self.sh_degree, attrs, cam, blur, self.splats, self.rects, stream)
+
+    def bin_sort(self, sync=False, stream=None):
+        depth_ptr = self.splats.data_ptr() + 3 * 4
+        return B.qn_bin_sort(self.n, depth_ptr, 12, self.rects, self.TX, self.TY, self.workspace, self.capacity,
+                             self.vals, self.keys, self.ranges, self.n_pairs, sync, stream)
+
+    def render_fwd(self, cam, bg, n_contrib=None, stream=None):
+        B.qn_render_fwd(cam, self.ranges, self.vals, self.splats, bg, self.img, self.T_final, self.last, n_contrib,
+                        stream)
+
+    def loss_grad(self, target, w=1.0, mse=False, stream=None):
+        B.qn_image_loss(self.img.numel(), self.img, target, w, mse, self.loss, self.d_img, stream)
+
+    def render_bwd(self, cam, bg, skip=None, stream=None):
+        B.qn_render_bwd(cam, self.ranges, self.vals, self.splats, self.n, bg, self.T_final, self.last, self.d_img,
+                        skip, self.d_splats, stream)
+
+    def project_bwd(self, attrs, cam, blur, d_attrs, skip=None, stream=None):
+        B.qn_project_bwd(self.n, self.S, self.sh_degree, attrs, cam, blur, self.d_splats, skip, d_attrs, stream)
+
+    def ensure_capacity(self, margin: float = 1.25):
+        """Synchronising: re-runs the binning with a larger buffer if it overflowed."""
+        P = int(self.n_pairs.item())
+        if P > self.capacity:
+            self.set_capacity(int(P * margin) + 1024)
+            self.bin_sort(sync=True)
+        return P
+
+
+def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None):
+    """One view of Eq. 11's optimisation: forward, L1 loss (Eq. 3 L1 term) +
+    lambda_reg L_reg (the L_reg gradient is folded into the gate adjoint), full
+    adjoint and the Adam step.  No host synchronisation."""
+    hp = frame.hp
+    frame.decode(stream)
+    rast.project(frame.attrs, cam, hp.blur, stream)
+    rast.bin_sort(False, stream)
+    rast.render_fwd(cam, hp.bg, stream)
+    rast.loss_grad(target, 1.0, False, stream)
+    rast.render_bwd(cam, hp.bg, skip, stream)
+    rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
+    frame.decode_bwd(skip, stream)
+    frame.adam(skip, stream)

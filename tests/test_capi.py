@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+entry point declared in include/queen.h, and host-side argument validation
+returns the documented status codes before any device work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "queen.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qn_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_04469_gb300 import build
+    path = build.build()
+    from paper_2412_04469_gb300 import binding
+    return binding.lib(), C.CDLL(path)
+
+
+def test_exports_every_declared_symbol(lib):
+    _, raw = lib
+    names = _declared()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(raw, name), name
+
+
+def test_binding_covers_header(lib):
+    from paper_2412_04469_gb300 import binding
+    assert set(_declared()) <= set(binding.exported_symbols())
+
+
+def test_version_and_error_string(lib):
+    L, _ = lib
+    assert b"sm_103a" in L.qn_version()
+
+
+def test_invalid_arguments_fail_before_any_launch(lib):
+    from paper_2412_04469_gb300 import binding as B
+    cam = B.qn_camera()
+    cam.width, cam.height, cam.fx, cam.fy, cam.near_plane = 64, 64, 50.0, 50.0, 0.2
+    assert B.lib().qn_project(-1, 4, 0, None, C.byref(cam), 0.3, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert b"n_stride" in B.lib().qn_last_error() or b"n" in B.lib().qn_last_error()
+    assert B.lib().qn_project(8, 8, 4, None, C.byref(cam), 0.3, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert b"sh_degree" in B.lib().qn_last_error()
+    bad = B.qn_camera()
+    bad.width, bad.height = 0, 64
+    assert B.lib().qn_project(8, 8, 0, None, C.byref(bad), 0.3, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_bin_sort(4, None, 1, None, 300, 2, None, 0, 0, None, None, None, None, None, None) == \
+        B.QN_ERR_INVALID_ARG
+    lay = B.qn_decoder_layout()
+    lay.n_cat = 1
+    lay.attr_begin[0], lay.attr_count[0], lay.lat_dim[0] = 1, 2, 4      # overlaps the position planes
+    gp = B.make_gate(0.3, -0.5, 1.01)
+    assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp),
+                                       None, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert b"category" in B.lib().qn_last_error()
+    gp_bad = B.make_gate(0.3, 0.5, 1.01)
+    lay.attr_begin[0] = 3
+    assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp_bad),
+                                       None, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_adam(1, 4, 4, None, None, None, None, 0, 0.1, 0.9, 0.999, 1e-8, None, None, None) == \
+        B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_bin_sort_workspace_size(-1, 4, 4) == 0

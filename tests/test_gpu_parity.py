@@ -1,0 +1,412 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle on the same
+seeded inputs.  Integer work (keys, order, ranges, last contributor) is
+compared bit for bit; floating point within the stated tolerances.
+
+Pixels whose result hinges on a decision that FP32 rounding can flip (an
+alpha within EPS_A of 1/255 or 0.99, T within EPS_A of 1e-4, contributors
+within EPS_D relative depth, or a projection decision within EPS_G) are
+flagged by the oracle, excluded, counted and bounded; their upstream
+gradient is set to zero so the adjoints are compared on the rest.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2412_04469_gb300 import synthetic as S
+from paper_2412_04469_gb300.synthetic import DecoderLayout
+
+pytestmark = pytest.mark.gpu
+
+EPS_A, EPS_D, EPS_G = 2e-5, 1e-6, 2e-6
+RTOL = 1e-4          # FP32 images, 2D records, gradients (relative, see `close`)
+RTOL_BF16 = 2e-3     # decoder outputs
+MAX_FRAGILE = 0.005  # fraction of excluded pixels
+TAU, G0, G1 = 0.3, -0.5, 1.01
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_04469_gb300 import build
+    build.build()
+
+
+def B():
+    from paper_2412_04469_gb300 import binding
+    return binding
+
+
+def up(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def planes(a, stride):
+    t = torch.zeros((a.shape[0], stride), device="cuda")
+    t[:, :a.shape[1]] = up(a)
+    return t
+
+
+def stride_of(n):
+    return max(4, (n + 31) // 32 * 32)
+
+
+def close(got, ref, rtol=RTOL, floor_frac=1e-2, what=""):
+    """|got - ref| <= rtol * max(|ref|, floor_frac * max|ref|) elementwise: relative
+    for entries above 1% of the array's largest, absolute below."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if ref.size == 0:
+        return 0.0
+    scale = max(np.abs(ref).max(), 1e-30)
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), floor_frac * scale)
+    worst = float(err.max())
+    assert worst <= rtol, f"{what}: max scaled error {worst:.3e} > {rtol:.1e}"
+    return worst
+
+
+def gpu_raster(A, cam, deg, blur, bg=(0.0, 0.0, 0.0), keep_keys=False):
+    from paper_2412_04469_gb300.pipeline import Rasterizer
+    n = A.shape[1]
+    Sd = stride_of(n)
+    r = Rasterizer(n, Sd, deg, cam.width, cam.height, 1, keep_keys=keep_keys)
+    c = B().make_camera(cam)
+    attrs = planes(A, Sd)
+    r.project(attrs, c, blur)
+    r.bin_sort(sync=False)
+    torch.cuda.synchronize()
+    P = int(r.n_pairs.item())
+    r.set_capacity(P + 16)
+    assert r.bin_sort(sync=True) == P
+    r.render_fwd(c, bg)
+    torch.cuda.synchronize()
+    return r, c, attrs
+
+
+def oracle_last_ids(proj, last, W, H):
+    """Gaussian index of each pixel's last contributor from the oracle's lists."""
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    vis = np.nonzero(proj["radius"] > 0)[0]
+    out = np.full((H, W), -1, np.int64)
+    for ty in range(TY):
+        for tx in range(TX):
+            r = proj["rect"][:, vis]
+            m = vis[(r[0] <= tx) & (tx < r[2]) & (r[1] <= ty) & (ty < r[3])]
+            lst = m[np.lexsort((m, proj["depth"][m]))]
+            blk = last[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
+            ids = np.where(blk > 0, lst[np.maximum(blk - 1, 0)] if lst.size else -1, -1)
+            out[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = ids
+    return out
+
+
+def gpu_last_ids(r, W, H):
+    last = r.last.cpu().numpy().astype(np.int64)
+    ranges = r.ranges.cpu().numpy().astype(np.int64)
+    vals = r.vals.cpu().numpy().astype(np.int64)
+    TX = (W + 15) // 16
+    v, u = np.mgrid[0:H, 0:W]
+    start = ranges[(v // 16) * TX + (u // 16), 0]
+    return np.where(last > 0, vals[np.maximum(start + last - 1, 0)], -1)
+
+
+SCENES = [  # n, W, H, sh degree, blur, seed
+    (2000, 128, 128, 0, 0.3, 0),     # the small plain config: 2,000 Gaussians, 128 x 128
+    (900, 97, 61, 3, 0.3, 1),        # SH degree 3, ragged tiles
+    (64, 17, 33, 1, 0.0, 2),         # tiny, no blur, partial tiles
+]
+
+
+def _scene(n, W, H, deg, seed):
+    A = S.make_scene(n, deg, seed)
+    cam = S.make_camera(W, H, 60.0, eye=(0.4, 0.3, 4.0))
+    return A, cam
+
+
+# ---------------------------------------------------------------- projection
+@pytest.mark.parametrize("n,W,H,deg,blur,seed", SCENES)
+def test_project_matches_oracle(n, W, H, deg, blur, seed):
+    A, cam = _scene(n, W, H, deg, seed)
+    r, _, _ = gpu_raster(A, cam, deg, blur)
+    sp = r.splats.cpu().numpy()[:n]
+    rc = r.rects.cpu().numpy()[:n]
+    ref = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    ok = ref["fragile"] == 0
+    assert (~ok).mean() < 0.01
+    vis_ref = ref["radius"] > 0
+    vis_gpu = (rc[:, 2] > rc[:, 0]) & (rc[:, 3] > rc[:, 1])
+    assert np.array_equal(vis_ref[ok], vis_gpu[ok])
+    assert np.array_equal(rc[ok].T, ref["rect"][:, ok])
+    m = ok & vis_ref
+    close(sp[m, 0:2].T, ref["mean2d"][:, m], what="mean2d")
+    close(sp[m, 2], ref["opac"][m], what="opacity")
+    close(sp[m, 3], ref["depth"][m], what="depth")
+    close(sp[m, 4:7].T, ref["conic"][:, m], what="conic")
+    close(sp[m, 8:11].T, ref["rgb"][:, m], what="rgb")
+
+
+@pytest.mark.parametrize("n,W,H,deg,blur,seed", SCENES)
+def test_project_bwd_matches_oracle(n, W, H, deg, blur, seed):
+    A, cam = _scene(n, W, H, deg, seed)
+    A[7:10] += 0.5
+    r, c, attrs = gpu_raster(A, cam, deg, blur)
+    rng = np.random.default_rng(seed)
+    ref = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    d = rng.standard_normal((n, 12)).astype(np.float32)
+    d[:, [3, 7, 11]] = 0.0
+    d[:, 4:7] *= 0.01
+    r.d_splats.copy_(up(d))
+    dA = torch.zeros_like(attrs)
+    r.project_bwd(attrs, c, blur, dA)
+    torch.cuda.synchronize()
+    got = dA.cpu().numpy()[:, :n]
+    want = oracle.project_bwd(A.astype(np.float64), cam, deg, d[:, 0:2].T, d[:, 4:7].T, d[:, 2], d[:, 8:11].T,
+                              blur=blur)
+    ok = ref["fragile"] == 0
+    for name, sl in (("position", slice(0, 3)), ("quaternion", slice(3, 7)), ("log-scale", slice(7, 10)),
+                     ("opacity", slice(10, 11)), ("sh", slice(11, None))):
+        close(got[sl][:, ok], want[sl][:, ok], what=name)
+
+
+# ---------------------------------------------------------------- binning
+BIN_CASES = [  # n, tiles_x, tiles_y, seed, max_extent
+    (0, 3, 2, 0, 4), (1, 1, 1, 1, 1), (7, 4, 3, 2, 3), (257, 9, 7, 3, 5), (2049, 17, 5, 6, 3),
+    (5000, 85, 64, 4, 12), (3000, 120, 68, 5, 40), (20000, 256, 3, 7, 200), (60000, 85, 64, 8, 9),
+]
+
+
+def _gpu_bin(depth, rect, tx, ty, capacity=None):
+    n = depth.size
+    buf = np.zeros((max(n, 1), 12), np.float32)
+    buf[:n, 3] = depth
+    sp = up(buf)
+    rc = up(np.ascontiguousarray(rect.T) if n else np.zeros((1, 4), np.int32), torch.int32)
+    ws = torch.zeros(max(B().qn_bin_sort_workspace_size(n, tx, ty), 256), device="cuda", dtype=torch.uint8)
+    P_ref = int(np.maximum(rect[2] - rect[0], 0).dot(np.maximum(rect[3] - rect[1], 0))) if n else 0
+    cap = P_ref if capacity is None else capacity
+    vals = torch.zeros(max(cap, 1), device="cuda", dtype=torch.int32)
+    keys = torch.zeros(max(cap, 1), device="cuda", dtype=torch.int64)
+    ranges = torch.full((tx * ty, 2), 7, device="cuda", dtype=torch.int32)
+    npairs = torch.zeros(1, device="cuda", dtype=torch.int64)
+    P = B().qn_bin_sort(n, sp.data_ptr() + 12, 12, rc, tx, ty, ws, cap, vals, keys, ranges, npairs, sync=True)
+    return P, keys.cpu().numpy().view(np.uint64)[:P], vals.cpu().numpy().view(np.uint32)[:P], \
+        ranges.cpu().numpy().view(np.uint32), int(npairs.item())
+
+
+@pytest.mark.parametrize("n,tx,ty,seed,ext", BIN_CASES)
+def test_bin_sort_bit_exact(n, tx, ty, seed, ext):
+    depth, rect = S.make_bin_inputs(n, tx, ty, seed, max_extent=ext)
+    k_ref, v_ref, r_ref = oracle.bin_sort(depth, rect, tx, ty)
+    P, k, v, r, p_dev = _gpu_bin(depth, rect, tx, ty)
+    assert P == k_ref.size == p_dev
+    assert np.array_equal(k, k_ref)
+    assert np.array_equal(v, v_ref)
+    assert np.array_equal(r, r_ref)
+
+
+def test_bin_sort_capacity_overflow():
+    depth, rect = S.make_bin_inputs(500, 9, 7, 11, max_extent=4)
+    k_ref, _, _ = oracle.bin_sort(depth, rect, 9, 7)
+    from paper_2412_04469_gb300.binding import QueenError, QN_ERR_CAPACITY
+    with pytest.raises(QueenError) as e:
+        _gpu_bin(depth, rect, 9, 7, capacity=k_ref.size - 1)
+    assert e.value.code == QN_ERR_CAPACITY
+
+
+def test_bin_sort_all_culled_and_tie_heavy():
+    depth, rect = S.make_bin_inputs(1000, 8, 8, 12, max_extent=8, tie_frac=0.9, empty_frac=0.0)
+    depth[:] = depth[0]                                  # every key's depth bits equal
+    k_ref, v_ref, r_ref = oracle.bin_sort(depth, rect, 8, 8)
+    P, k, v, r, _ = _gpu_bin(depth, rect, 8, 8)
+    assert np.array_equal(k, k_ref) and np.array_equal(v, v_ref) and np.array_equal(r, r_ref)
+    rect[:] = 0
+    P, _, _, r, _ = _gpu_bin(depth, rect, 8, 8)
+    assert P == 0 and np.all(r == 0)
+
+
+# ---------------------------------------------------------------- compositing
+@pytest.mark.parametrize("n,W,H,deg,blur,seed", SCENES)
+def test_render_forward_matches_oracle(n, W, H, deg, blur, seed):
+    A, cam = _scene(n, W, H, deg, seed)
+    bg = (0.1, 0.3, 0.2)
+    r, _, _ = gpu_raster(A, cam, deg, blur, bg)
+    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    img, T, last, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
+    ok = frag == 0
+    assert (~ok).mean() <= MAX_FRAGILE
+    gi = r.img.cpu().numpy()
+    close(gi[:, ok], img[:, ok], what="image")
+    close(r.T_final.cpu().numpy()[ok], T[ok], what="T_final")
+    ids_g = gpu_last_ids(r, W, H)
+    ids_o = oracle_last_ids(proj, last, W, H)
+    assert np.array_equal(ids_g[ok], ids_o[ok])      # last contributor: bit-exact identity
+
+
+@pytest.mark.parametrize("n,W,H,deg,blur,seed", SCENES)
+def test_render_backward_matches_oracle(n, W, H, deg, blur, seed):
+    A, cam = _scene(n, W, H, deg, seed)
+    bg = (0.2, 0.1, 0.05)
+    r, c, _ = gpu_raster(A, cam, deg, blur, bg)
+    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    _, _, _, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
+    d_img = (S.make_image(W, H, seed) - 0.5) * (frag == 0)[None]
+    r.d_img.copy_(up(d_img))
+    r.render_bwd(c, bg)
+    torch.cuda.synchronize()
+    g = r.d_splats.cpu().numpy()[:n]
+    ref = oracle.render_bwd(proj, d_img, bg)
+    close(g[:, 0:2].T, ref["d_mean2d"], what="d_mean2d")
+    close(g[:, 2], ref["d_opac"], what="d_opacity")
+    close(g[:, 4:7].T, ref["d_conic"], what="d_conic")
+    close(g[:, 8:11].T, ref["d_rgb"], what="d_rgb")
+
+
+def test_render_skip_mask_zeroes_skipped():
+    A, cam = _scene(800, 64, 64, 0, 3)
+    r, c, _ = gpu_raster(A, cam, 0, 0.3)
+    r.d_img.copy_(up(S.make_image(64, 64, 4) - 0.5))
+    r.render_bwd(c, (0, 0, 0))
+    full = r.d_splats.cpu().numpy().copy()
+    skip = (np.arange(800) % 3 == 0).astype(np.uint8)
+    r.render_bwd(c, (0, 0, 0), skip=up(skip, torch.uint8))
+    part = r.d_splats.cpu().numpy()
+    assert np.all(part[skip == 1] == 0)
+    close(part[skip == 0], full[skip == 0], rtol=1e-5, what="unskipped")
+
+
+def test_empty_and_culled_scenes_render_background():
+    cam = S.make_camera(40, 24, 60.0)
+    bg = (0.25, 0.5, 0.75)
+    for A in (S.make_scene(0, 0, 0), S.make_scene(50, 0, 1) + np.array([[0], [0], [10.0]] + [[0]] * 11, np.float32)):
+        r, _, _ = gpu_raster(A, cam, 0, 0.3, bg)
+        img = r.img.cpu().numpy()
+        assert np.array_equal(img, np.broadcast_to(np.array(bg, np.float32)[:, None, None], img.shape))
+        assert np.all(r.T_final.cpu().numpy() == 1.0) and np.all(r.last.cpu().numpy() == 0)
+
+
+# ---------------------------------------------------------------- decode and gate
+def _decode_problem(n, deg, seed, latent=8):
+    lay = DecoderLayout.default(sh_degree=deg, latent=latent)
+    prev = S.make_scene(n, deg, seed)
+    res = S.make_residuals(n, lay, seed)
+    res.lat[:, :5] = np.array([0.5, 1.5, -2.5, 130.2, -200.0], np.float32)[None, :].repeat(lay.n_latent, 0)
+    return lay, prev, res
+
+
+@pytest.mark.parametrize("n,deg,seed", [(1000, 3, 0), (37, 1, 1), (1, 0, 2)])
+def test_decode_matches_oracle(n, deg, seed):
+    from paper_2412_04469_gb300.pipeline import QueenFrame
+    lay, prev, res = _decode_problem(n, deg, seed)
+    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    f.decode()
+    torch.cuda.synchronize()
+    out, gate, lreg = oracle.decode(prev.astype(np.float64), res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1)
+    got = f.attrs.cpu().numpy()[:, :n]
+    close(got[:3], out[:3], what="position")
+    close(got[3:] - prev[3:], out[3:] - prev[3:].astype(np.float64), rtol=RTOL_BF16, what="decoded residual")
+    close(f.gate.cpu().numpy()[:n], gate, what="gate")
+    assert float(f.lreg.item()) == pytest.approx(lreg, rel=1e-5)
+
+
+@pytest.mark.parametrize("n,deg,seed", [(1000, 3, 0), (37, 1, 1)])
+def test_decode_bwd_matches_oracle(n, deg, seed):
+    from paper_2412_04469_gb300.pipeline import QueenFrame
+    lay, prev, res = _decode_problem(n, deg, seed)
+    res.log_alpha[: n // 2] = np.linspace(-1, 1, n // 2)      # inside the open gate interval
+    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    rng = np.random.default_rng(seed)
+    d_out = rng.standard_normal((prev.shape[0], n)).astype(np.float32)
+    f.d_attrs[:, :n] = up(d_out)
+    skip = (rng.uniform(size=n) < 0.2).astype(np.uint8)
+    f.decode_bwd(skip=up(skip, torch.uint8))
+    torch.cuda.synchronize()
+    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, d_out, f.hp.lambda_reg,
+                             skip=skip)
+    close(f.d_lat.cpu().numpy()[:, :n], want[0], what="d_lat")
+    close(f.d_dec.cpu().numpy(), want[1], what="d_dec")
+    close(f.d_lp.cpu().numpy()[:, :n], want[2], what="d_lp")
+    close(f.d_log_alpha.cpu().numpy()[:n], want[3], what="d_log_alpha")
+
+
+# ---------------------------------------------------------------- loss and Adam
+def test_image_loss_matches_oracle():
+    img = S.make_image(37, 29, 1)
+    tgt = S.make_image(37, 29, 2)
+    loss = torch.zeros(1, device="cuda")
+    d = torch.zeros((3, 29, 37), device="cuda")
+    for mse in (False, True):
+        B().qn_image_loss(img.size, up(img), up(tgt), 1.0, mse, loss, d)
+        torch.cuda.synchronize()
+        if mse:
+            ref_g = oracle.mse_grad(img, tgt)
+            ref_l = float(((img.astype(np.float64) - tgt) ** 2).mean())
+        else:
+            ref_l, ref_g = oracle.l1_loss(img, tgt)
+        assert float(loss.item()) == pytest.approx(ref_l, rel=1e-5)
+        close(d.cpu().numpy(), ref_g, what="d_img")
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(0)
+    rows, n, stride = 3, 1000, 1024
+    p = rng.standard_normal((rows, n)).astype(np.float32)
+    skip = (rng.uniform(size=n) < 0.3).astype(np.uint8)
+    P, M, V = planes(p, stride), torch.zeros((rows, stride), device="cuda"), torch.zeros((rows, stride), device="cuda")
+    pb = torch.zeros((rows, stride), device="cuda", dtype=torch.bfloat16)
+    rp, rm, rv = p.astype(np.float64), np.zeros((rows, n)), np.zeros((rows, n))
+    for step in (1, 2, 3):
+        g = rng.standard_normal((rows, n)).astype(np.float32)
+        B().qn_adam(rows, n, stride, P, planes(g, stride), M, V, step, 0.01, 0.9, 0.999, 1e-8, up(skip, torch.uint8), pb)
+        rp, rm, rv = oracle.adam_step(rp, g, rm, rv, step, 0.01, mask=np.broadcast_to(skip, (rows, n)))
+    torch.cuda.synchronize()
+    close(P.cpu().numpy()[:, :n], rp, rtol=1e-5, what="param")
+    close(M.cpu().numpy()[:, :n], rm, rtol=1e-5, what="m")
+    got_b = pb.float().cpu().numpy()[:, :n]
+    assert np.array_equal(got_b[:, skip == 0], S.to_bf16_values(P.cpu().numpy()[:, :n][:, skip == 0]))
+
+
+# ---------------------------------------------------------------- whole iteration
+def test_end_to_end_gradients_match_oracle_chain():
+    """decode -> project -> bin -> composite -> L1 -> every adjoint, against the
+    oracle's chain on the same inputs (the small config's camera, SH degree 1)."""
+    from paper_2412_04469_gb300.pipeline import QueenFrame, Rasterizer
+    n, deg, W, H = 1500, 1, 96, 80
+    lay = DecoderLayout.default(sh_degree=deg, latent=4)
+    prev = S.make_scene(n, deg, 5)
+    res = S.make_residuals(n, lay, 5)
+    res.log_alpha[:] = np.random.default_rng(5).uniform(-0.8, 0.8, n).astype(np.float32)
+    cam = S.make_camera(W, H, 60.0, eye=(0.5, 0.2, 4.0))
+    target = S.make_image(W, H, 9)
+    bg = (0.0, 0.0, 0.0)
+    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    f.decode()
+    A_ref, _, _ = oracle.decode(prev.astype(np.float64), res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1)
+    proj = oracle.project(A_ref, cam, deg, blur=0.3, eps_g=EPS_G)
+    img_ref, _, _, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
+    _, g_ref = oracle.l1_loss(img_ref, target)
+    near = np.abs(img_ref - target).min(axis=0) < 1e-4          # sign of the L1 term could flip
+    mask = (frag == 0) & ~near
+    g_ref = g_ref * mask[None]
+    r = Rasterizer(n, f.S, deg, W, H, 1)
+    c = B().make_camera(cam)
+    r.project(f.attrs, c, 0.3)
+    r.bin_sort()
+    torch.cuda.synchronize()
+    r.set_capacity(int(r.n_pairs.item()) + 16)
+    r.bin_sort(sync=True)
+    r.render_fwd(c, bg)
+    r.loss_grad(up(target))
+    r.d_img.mul_(up(mask.astype(np.float32))[None])
+    r.render_bwd(c, bg)
+    r.project_bwd(f.attrs, c, 0.3, f.d_attrs)
+    f.decode_bwd()
+    torch.cuda.synchronize()
+    close(r.d_img.cpu().numpy(), g_ref, what="d_img")
+    g2 = oracle.render_bwd(proj, g_ref, bg)
+    dA = oracle.project_bwd(A_ref, cam, deg, g2["d_mean2d"], g2["d_conic"], g2["d_opac"], g2["d_rgb"], blur=0.3)
+    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, dA, f.hp.lambda_reg)
+    close(f.d_attrs.cpu().numpy()[:, :n], dA, what="d_attrs")
+    close(f.d_lat.cpu().numpy()[:, :n], want[0], what="d_lat")
+    close(f.d_dec.cpu().numpy(), want[1], what="d_dec")
+    close(f.d_lp.cpu().numpy()[:, :n], want[2], what="d_lp")
+    close(f.d_log_alpha.cpu().numpy()[:n], want[3], what="d_log_alpha")
