@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(BWD_BLOCK) k_decode_bwd(
     float d_lreg, const uint8_t *__restrict__ skip, float *__restrict__ d_lat,
     float *__restrict__ d_dec, float *__restrict__ d_lp, float *__restrict__ d_la) {
     __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
-    __shared__ float s_dr[MAX_RES_PLANES][BWD_BLOCK];
-    __shared__ float s_l[MAX_LAT_TOTAL][BWD_BLOCK];
+    // rows padded by one word: threads reading different rows at the same
+    // column then fall in different banks
+    __shared__ float s_dr[MAX_RES_PLANES][BWD_BLOCK + 1];
+    __shared__ float s_l[MAX_LAT_TOTAL][BWD_BLOCK + 1];
     for (int k = threadIdx.x; k < a.n_dec; k += blockDim.x) sD[k] = bf16_to_f32(dec[k]);
     // each thread owns up to ceil(n_dec / BWD_BLOCK) entries of dD
     constexpr int MAX_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + BWD_BLOCK - 1) / BWD_BLOCK;

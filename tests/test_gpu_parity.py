@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 EPS_A, EPS_D, EPS_G = 2e-5, 1e-6, 2e-6
 RTOL = 1e-4          # FP32 images, 2D records, gradients (relative, see `close`)
+GRAD_FLOOR = 0.05    # gradients: entries below 5% of the array's largest compare absolutely
 RTOL_BF16 = 2e-3     # decoder outputs
 MAX_FRAGILE = 0.005  # fraction of excluded pixels
 TAU, G0, G1 = 0.3, -0.5, 1.01
@@ -54,7 +55,13 @@ def stride_of(n):
 
 def close(got, ref, rtol=RTOL, floor_frac=1e-2, what=""):
     """|got - ref| <= rtol * max(|ref|, floor_frac * max|ref|) elementwise: relative
-    for entries above 1% of the array's largest, absolute below."""
+    for entries above floor_frac of the array's largest, absolute below.
+
+    Values (images, projected records) use floor_frac = 1%.  Gradients are sums
+    of many FP32 terms of both signs accumulated in arbitrary (atomic) order; an
+    entry that cancels to a small value keeps the absolute error of its large
+    terms, so gradients use GRAD_FLOOR (5%): 1e-4 relative above it, 5e-6 of
+    the array's largest magnitude below it."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     if ref.size == 0:
@@ -165,7 +172,7 @@ def test_project_bwd_matches_oracle(n, W, H, deg, blur, seed):
     ok = ref["fragile"] == 0
     for name, sl in (("position", slice(0, 3)), ("quaternion", slice(3, 7)), ("log-scale", slice(7, 10)),
                      ("opacity", slice(10, 11)), ("sh", slice(11, None))):
-        close(got[sl][:, ok], want[sl][:, ok], what=name)
+        close(got[sl][:, ok], want[sl][:, ok], floor_frac=GRAD_FLOOR, what=name)
 
 
 # ---------------------------------------------------------------- binning
@@ -255,10 +262,10 @@ def test_render_backward_matches_oracle(n, W, H, deg, blur, seed):
     torch.cuda.synchronize()
     g = r.d_splats.cpu().numpy()[:n]
     ref = oracle.render_bwd(proj, d_img, bg)
-    close(g[:, 0:2].T, ref["d_mean2d"], what="d_mean2d")
-    close(g[:, 2], ref["d_opac"], what="d_opacity")
-    close(g[:, 4:7].T, ref["d_conic"], what="d_conic")
-    close(g[:, 8:11].T, ref["d_rgb"], what="d_rgb")
+    close(g[:, 0:2].T, ref["d_mean2d"], floor_frac=GRAD_FLOOR, what="d_mean2d")
+    close(g[:, 2], ref["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity")
+    close(g[:, 4:7].T, ref["d_conic"], floor_frac=GRAD_FLOOR, what="d_conic")
+    close(g[:, 8:11].T, ref["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb")
 
 
 def test_render_skip_mask_zeroes_skipped():
@@ -289,7 +296,8 @@ def _decode_problem(n, deg, seed, latent=8):
     lay = DecoderLayout.default(sh_degree=deg, latent=latent)
     prev = S.make_scene(n, deg, seed)
     res = S.make_residuals(n, lay, seed)
-    res.lat[:, :5] = np.array([0.5, 1.5, -2.5, 130.2, -200.0], np.float32)[None, :].repeat(lay.n_latent, 0)
+    ties = np.array([0.5, 1.5, -2.5, 130.2, -200.0], np.float32)[:n]      # rounding ties and saturation
+    res.lat[:, :ties.size] = ties[None, :]
     return lay, prev, res
 
 
@@ -322,10 +330,10 @@ def test_decode_bwd_matches_oracle(n, deg, seed):
     torch.cuda.synchronize()
     want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, d_out, f.hp.lambda_reg,
                              skip=skip)
-    close(f.d_lat.cpu().numpy()[:, :n], want[0], what="d_lat")
-    close(f.d_dec.cpu().numpy(), want[1], what="d_dec")
-    close(f.d_lp.cpu().numpy()[:, :n], want[2], what="d_lp")
-    close(f.d_log_alpha.cpu().numpy()[:n], want[3], what="d_log_alpha")
+    close(f.d_lat.cpu().numpy()[:, :n], want[0], floor_frac=GRAD_FLOOR, what="d_lat")
+    close(f.d_dec.cpu().numpy(), want[1], floor_frac=GRAD_FLOOR, what="d_dec")
+    close(f.d_lp.cpu().numpy()[:, :n], want[2], floor_frac=GRAD_FLOOR, what="d_lp")
+    close(f.d_log_alpha.cpu().numpy()[:n], want[3], floor_frac=GRAD_FLOOR, what="d_log_alpha")
 
 
 # ---------------------------------------------------------------- loss and Adam
@@ -343,7 +351,7 @@ def test_image_loss_matches_oracle():
         else:
             ref_l, ref_g = oracle.l1_loss(img, tgt)
         assert float(loss.item()) == pytest.approx(ref_l, rel=1e-5)
-        close(d.cpu().numpy(), ref_g, what="d_img")
+        close(d.cpu().numpy(), ref_g, floor_frac=GRAD_FLOOR, what="d_img")
 
 
 def test_adam_matches_oracle():
@@ -401,12 +409,12 @@ def test_end_to_end_gradients_match_oracle_chain():
     r.project_bwd(f.attrs, c, 0.3, f.d_attrs)
     f.decode_bwd()
     torch.cuda.synchronize()
-    close(r.d_img.cpu().numpy(), g_ref, what="d_img")
+    close(r.d_img.cpu().numpy(), g_ref, floor_frac=GRAD_FLOOR, what="d_img")
     g2 = oracle.render_bwd(proj, g_ref, bg)
     dA = oracle.project_bwd(A_ref, cam, deg, g2["d_mean2d"], g2["d_conic"], g2["d_opac"], g2["d_rgb"], blur=0.3)
     want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, dA, f.hp.lambda_reg)
-    close(f.d_attrs.cpu().numpy()[:, :n], dA, what="d_attrs")
-    close(f.d_lat.cpu().numpy()[:, :n], want[0], what="d_lat")
-    close(f.d_dec.cpu().numpy(), want[1], what="d_dec")
-    close(f.d_lp.cpu().numpy()[:, :n], want[2], what="d_lp")
-    close(f.d_log_alpha.cpu().numpy()[:n], want[3], what="d_log_alpha")
+    close(f.d_attrs.cpu().numpy()[:, :n], dA, floor_frac=GRAD_FLOOR, what="d_attrs")
+    close(f.d_lat.cpu().numpy()[:, :n], want[0], floor_frac=GRAD_FLOOR, what="d_lat")
+    close(f.d_dec.cpu().numpy(), want[1], floor_frac=GRAD_FLOOR, what="d_dec")
+    close(f.d_lp.cpu().numpy()[:, :n], want[2], floor_frac=GRAD_FLOOR, what="d_lp")
+    close(f.d_log_alpha.cpu().numpy()[:n], want[3], floor_frac=GRAD_FLOOR, what="d_log_alpha")
