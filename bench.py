@@ -70,7 +70,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -112,7 +112,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
-def setup(name, seed=0):
+def setup(name, seed=0, quick=False):
     import torch
 
     from paper_2412_04469_gb300 import binding as B
@@ -124,6 +124,8 @@ def setup(name, seed=0):
     prev = S.make_scene(n, deg, seed)
     res = S.make_residuals(n, lay, seed)
     cams = S.make_arc_cameras(V, W, H) if V > 1 else [S.make_camera(W, H, 60.0)]
+    if quick:
+        V, cams = 1, cams[:1]
     frame = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
     rast = Rasterizer(n, frame.S, deg, W, H, 1)
     ccams = [B.make_camera(c) for c in cams]
@@ -156,8 +158,9 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pbuild.build()
     name = args.workload
-    frame, rast, cams, targets, targets_host, lay, prev, res, cams_py = setup(name)
+    frame, rast, cams, targets, targets_host, lay, prev, res, cams_py = setup(name, quick=args.quick)
     n, deg, W, H, V, L = WORKLOADS[name]
+    V = len(cams)
     hp = frame.hp
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -216,6 +219,11 @@ def run_gpu(args):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": max_ms / args.steps,
+                              "stage_ms": {s: float(np.mean(stage_ms[s])) for s in STAGES}}), flush=True)
+        return
 
     # ---- end to end through the public API with host buffers: H2D of the
     # view's target from pinned memory and D2H of the loss every step
@@ -408,12 +416,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="one view, timed steps only (for profiler captures); prints stage times")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
