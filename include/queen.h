@@ -206,6 +206,34 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
                 int64_t pair_capacity, uint32_t *vals, uint64_t *keys, uint32_t *ranges,
                 int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream);
 
+/* Size of the device array that qn_bin_sort_noalloc uses as its workspace. */
+#define QN_BIN_SORT_STATIC_BYTES (32u << 20)
+
+/*
+ * qn_bin_sort without a caller-provided workspace, for callers that cannot
+ * allocate device memory while binning -- code running inside a memory pool
+ * or allocator hook, a plugin that must not touch the host application's
+ * allocator, or a real-time loop that forbids allocation.  The paper has no
+ * counterpart; this is a convenience of this library.
+ *
+ * Arguments, results and errors are those of qn_bin_sort, minus `workspace`
+ * and `workspace_bytes`.  The scratch space is a fixed file-scope device
+ * array of QN_BIN_SORT_STATIC_BYTES (32 MiB), which every GPU that loads this
+ * library keeps until the process exits.  A problem whose
+ * qn_bin_sort_workspace_size exceeds that is rejected with
+ * QN_ERR_INVALID_ARG before any launch (32 MiB covers 300,000 Gaussians on a
+ * 1352 x 1014 image).
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * No call allocates or frees memory.  All calls share the one array, and each
+ * call re-initialises what it reads: calls that overlap on the GPU (another
+ * stream, another host thread) race on it and must be serialised by the caller.
+ */
+int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                        int32_t tiles_x, int32_t tiles_y, int64_t pair_capacity, uint32_t *vals,
+                        uint64_t *keys, uint32_t *ranges, int64_t *n_pairs, int64_t *n_pairs_host,
+                        qn_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Compositing -- Sec. 3.1, Eq. 2, and its adjoint.                          */
 /* ------------------------------------------------------------------------ */

@@ -55,6 +55,7 @@ _SIGS = {
     "qn_project_bwd": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_workspace_size": ([_I32, _I32, _I32], _SZ),
     "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_bin_sort_noalloc": ([_I32, _P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_bwd": ([_P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
@@ -168,6 +169,18 @@ def qn_bin_sort(n, depth, depth_stride, rects, tiles_x, tiles_y, workspace, pair
     _check(lib().qn_bin_sort(n, _ptr(depth), depth_stride, _ptr(rects), tiles_x, tiles_y, _ptr(workspace),
                              ws_bytes, int(pair_capacity), _ptr(vals), _ptr(keys), _ptr(ranges), _ptr(n_pairs),
                              C.addressof(host) if sync else None, _stream(stream)))
+    return int(host.value) if sync else None
+
+
+def qn_bin_sort_noalloc(n, depth, depth_stride, rects, tiles_x, tiles_y, pair_capacity, vals, keys, ranges,
+                        n_pairs, sync=True, stream=None):
+    """qn_bin_sort on the library's fixed device workspace, for callers that
+    may not allocate device memory (allocator hooks, plugins in another
+    application's memory pool, real-time loops); returns P when sync is True."""
+    host = C.c_int64(0)
+    _check(lib().qn_bin_sort_noalloc(n, _ptr(depth), depth_stride, _ptr(rects), tiles_x, tiles_y,
+                                     int(pair_capacity), _ptr(vals), _ptr(keys), _ptr(ranges), _ptr(n_pairs),
+                                     C.addressof(host) if sync else None, _stream(stream)))
     return int(host.value) if sync else None
 
 

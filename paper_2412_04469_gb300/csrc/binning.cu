@@ -12,6 +12,8 @@
 // Every pair of one Gaussian shares its depth bits, so sorting the depth
 // digits on the Gaussians first and then the tile digit stably on the pairs is
 // exactly the LSD order of the 64-bit key; the output equals the stable sort.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace qn {
@@ -473,4 +475,50 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
         }
     }
     return QN_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+// Workspace of qn_bin_sort_noalloc: a fixed device array, so that callers
+// which may not allocate can still bin.  Host code only sees a host-side
+// stand-in under this name; the device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_bin_scratch[QN_BIN_SORT_STATIC_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                                   int32_t tiles_x, int32_t tiles_y, int64_t pair_capacity, uint32_t *vals,
+                                   uint64_t *keys, uint32_t *ranges, int64_t *n_pairs, int64_t *n_pairs_host,
+                                   qn_stream_t stream) {
+    QN_REQUIRE(n >= 0 && tiles_x > 0 && tiles_y > 0, "bad n or tile grid");
+    const size_t need = qn_bin_sort_workspace_size(n, tiles_x, tiles_y);
+    if (need > (size_t)QN_BIN_SORT_STATIC_BYTES) {
+        qn::set_error("qn_bin_sort_noalloc: %d Gaussians on a %dx%d tile grid need %zu bytes of workspace, "
+                      "more than the static %u bytes; use qn_bin_sort with a caller workspace",
+                      n, tiles_x, tiles_y, need, (unsigned)QN_BIN_SORT_STATIC_BYTES);
+        return QN_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return qn::check_launch("qn_bin_sort_noalloc: cudaGetDevice");
+    QN_REQUIRE(dev >= 0 && dev < kMaxDevices, "device ordinal %d out of range", dev);
+    void *ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
+            if (e != cudaSuccess) {
+                qn::set_error("qn_bin_sort_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+                return QN_ERR_CUDA;
+            }
+            g_scratch_ptr[dev] = p;
+        }
+        ptr = g_scratch_ptr[dev];
+    }
+    return qn_bin_sort(n, depth, depth_stride, rects, tiles_x, tiles_y, ptr, (size_t)QN_BIN_SORT_STATIC_BYTES,
+                       pair_capacity, vals, keys, ranges, n_pairs, n_pairs_host, stream);
 }
