@@ -158,13 +158,20 @@ typedef struct {
  * y/z clamped to +-1.3 half-extent / focal inside J); conic = Sigma'^-1;
  * radius = ceil(3 sqrt(mid + sqrt(max(0.1, mid^2 - det))));
  * rect = [floor((p' - r)/16), floor((p' + r + 15)/16)) clamped to the grid.
+ * With tight_rects != 0 the rect is further intersected with the tiles
+ * [floor((p' - h)/16), floor((p' + h)/16) + 1) where h = sqrt(1.01 k Sigma'_xx)
+ * + 0.01 (likewise y), k = 2 ln(255 o) + 0.01: a slightly widened bounding box
+ * of the ellipse outside which o exp(power) < 1/255.  Every dropped
+ * (tile, Gaussian) pair is skipped by every pixel of its tile, so images and
+ * gradients are unchanged; only the pair lists shrink.  A Gaussian with k <= 0
+ * (o < 0.995/255, never visible) gets an empty rect.
  * Culled (rect zero): t_z <= near_plane, det <= 0, or an empty rect.
  *   attrs [n_attr][n_stride] f32 A_t (read); splats [n] qn_splat, rects [n] int4
  *   (written).  sh_degree in 0..3, n_attr == 11 + 3 (sh_degree+1)^2.
  */
 int qn_project(int32_t n, int32_t n_stride, int32_t sh_degree, const float *attrs,
-               const qn_camera *cam_host, float blur, qn_splat *splats, int32_t *rects,
-               qn_stream_t stream);
+               const qn_camera *cam_host, float blur, int32_t tight_rects, qn_splat *splats,
+               int32_t *rects, qn_stream_t stream);
 
 /*
  * Adjoint of qn_project: d_attrs[n_attr][n_stride] (overwritten) from the

@@ -288,8 +288,9 @@ typedef struct {
  * Gaussian the 2D footprint is filled in even when it is culled, so that the
  * renderer can tell which pixels the flipped decision could reach. */
 static int or_project_one(int i, int n, int sh_degree, const double *A, const double *cam,
-                          int W, int H, double blur, double eps_g, or_proj_tmp *w, double out2d[10],
-                          int *radius_out, int rect_out[4], int frag_rect[4], int *fr) {
+                          int W, int H, double blur, int tight, double eps_g, or_proj_tmp *w,
+                          double out2d[10], int *radius_out, int rect_out[4], int frag_rect[4],
+                          int *fr) {
     const double *R = cam, *tv = cam + 9;
     double fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15], nearp = cam[16];
     const double *cpos = cam + 17;
@@ -361,6 +362,28 @@ static int or_project_one(int i, int n, int sh_degree, const double *A, const do
         if (or_near_int(ex[k], eps_g)) *fr |= 4;
     int rc[4] = {or_clampi((int)floor(ex[0]), 0, TX), or_clampi((int)floor(ex[1]), 0, TY),
                  or_clampi((int)floor(ex[2]), 0, TX), or_clampi((int)floor(ex[3]), 0, TY)};
+    if (tight) {
+        /* tiles the alpha >= 1/255 region can reach: the bounding box of the
+         * ellipse q(d) <= k, k = 2 ln(255 o) (+0.01, then +1%), half-widths
+         * sqrt(k Sigma'_xx) + 0.01 and sqrt(k Sigma'_yy) + 0.01 */
+        double op = or_sigmoid(A[(size_t)10 * n + i]);
+        double k = 2.0 * log(255.0 * op) + 0.01;
+        if (fabs(k) <= eps_g * 10.0) *fr |= 16;
+        if (k <= 0.0) {
+            rc[0] = rc[1] = rc[2] = rc[3] = 0;
+        } else {
+            double hx = sqrt(1.01 * k * w->a) + 0.01, hy = sqrt(1.01 * k * w->c) + 0.01;
+            double tb[4] = {(mx - hx) / OR_TILE, (my - hy) / OR_TILE, (mx + hx) / OR_TILE, (my + hy) / OR_TILE};
+            for (int q = 0; q < 4; ++q)
+                if (or_near_int(tb[q], eps_g)) *fr |= 4;
+            int t0 = or_clampi((int)floor(tb[0]), 0, TX), t1 = or_clampi((int)floor(tb[1]), 0, TY);
+            int t2 = or_clampi((int)floor(tb[2]) + 1, 0, TX), t3 = or_clampi((int)floor(tb[3]) + 1, 0, TY);
+            rc[0] = rc[0] > t0 ? rc[0] : t0;
+            rc[1] = rc[1] > t1 ? rc[1] : t1;
+            rc[2] = rc[2] < t2 ? rc[2] : t2;
+            rc[3] = rc[3] < t3 ? rc[3] : t3;
+        }
+    }
     if (*fr) {
         frag_rect[0] = or_clampi(rc[0] - 1, 0, TX);
         frag_rect[1] = or_clampi(rc[1] - 1, 0, TY);
@@ -397,13 +420,15 @@ static int or_project_one(int i, int n, int sh_degree, const double *A, const do
 /*
  * Outputs (all [.][n] planes): mean2d[2], conic[3] (a, b, c of Sigma'^-1 with
  * power = -0.5 (a dx^2 + c dy^2) - b dx dy), opac, rgb[3], depth, radius,
- * rect[4] = (x0, y0, x1, y1) in tiles (half-open; all 0 when culled),
+ * rect[4] = (x0, y0, x1, y1) in tiles (half-open; all 0 when culled; with
+ * `tight` also limited to the tiles the alpha >= 1/255 ellipse can reach),
  * fragile bits, and frag_rect[4] = the tiles whose pixels a fragile Gaussian
  * may reach.
  */
 void or_project(int n, int n_attr, int sh_degree, const double *A, const double *cam, int W,
-                int H, double blur, double eps_g, double *mean2d, double *conic, double *opac,
-                double *rgb, double *depth, int *radius, int *rect, int *fragile, int *frag_rect) {
+                int H, double blur, int tight, double eps_g, double *mean2d, double *conic,
+                double *opac, double *rgb, double *depth, int *radius, int *rect, int *fragile,
+                int *frag_rect) {
     (void)n_attr;
     or_sh_build();
 #pragma omp parallel for schedule(static)
@@ -411,7 +436,7 @@ void or_project(int n, int n_attr, int sh_degree, const double *A, const double 
         or_proj_tmp w;
         double o[10];
         int rad, rc[4], frc[4], fr;
-        or_project_one(i, n, sh_degree, A, cam, W, H, blur, eps_g, &w, o, &rad, rc, frc, &fr);
+        or_project_one(i, n, sh_degree, A, cam, W, H, blur, tight, eps_g, &w, o, &rad, rc, frc, &fr);
         mean2d[i] = o[0]; mean2d[(size_t)n + i] = o[1];
         conic[i] = o[2]; conic[(size_t)n + i] = o[3]; conic[(size_t)2 * n + i] = o[4];
         opac[i] = o[5];
@@ -440,7 +465,7 @@ void or_project_bwd(int n, int n_attr, int sh_degree, const double *A, const dou
         or_proj_tmp w;
         double o[10];
         int rad, rc[4], frc[4], fr;
-        if (!or_project_one(i, n, sh_degree, A, cam, W, H, blur, 0.0, &w, o, &rad, rc, frc, &fr))
+        if (!or_project_one(i, n, sh_degree, A, cam, W, H, blur, 0, 0.0, &w, o, &rad, rc, frc, &fr))
             continue;
         double dp[3] = {0, 0, 0}, dt[3] = {0, 0, 0};
         /* opacity = sigmoid(logit) */

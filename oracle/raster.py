@@ -50,7 +50,7 @@ def _load():
     lib.or_decode_bwd.argtypes = [C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _D, C.c_int, _D, _D,
                                   C.c_double, C.c_double, C.c_double, _D, C.c_double, C.c_void_p,
                                   _D, _D, _D, _D]
-    lib.or_project.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, C.c_double,
+    lib.or_project.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, C.c_double, C.c_int,
                                C.c_double, _D, _D, _D, _D, _D, _I, _I, _I, _I]
     lib.or_project_bwd.argtypes = [C.c_int, C.c_int, C.c_int, _D, _D, C.c_int, C.c_int, C.c_double,
                                    _D, _D, _D, _D, _D]
@@ -156,8 +156,10 @@ def decode_bwd(lat, dec, lp, log_alpha, layout, tau, gamma0, gamma1, d_out, d_lr
     return d_lat, d_dec, d_lp, d_la
 
 
-def project(attrs, cam, sh_degree, blur=0.3, eps_g=0.0):
-    """Eq. 1 + SH colour.  Returns a dict of planes (see queen_oracle.c)."""
+def project(attrs, cam, sh_degree, blur=0.3, eps_g=0.0, tight=False):
+    """Eq. 1 + SH colour.  Returns a dict of planes (see queen_oracle.c).
+    With tight=True the tile rects are limited to the tiles the
+    alpha >= 1/255 ellipse can reach (same rendering, shorter tile lists)."""
     lib = _load()
     oc = cam if isinstance(cam, OracleCamera) else OracleCamera.of(cam)
     A = _d(attrs)
@@ -165,7 +167,7 @@ def project(attrs, cam, sh_degree, blur=0.3, eps_g=0.0):
     r = dict(mean2d=np.zeros((2, n)), conic=np.zeros((3, n)), opac=np.zeros(n), rgb=np.zeros((3, n)),
              depth=np.zeros(n), radius=np.zeros(n, np.int32), rect=np.zeros((4, n), np.int32),
              fragile=np.zeros(n, np.int32), frag_rect=np.zeros((4, n), np.int32))
-    lib.or_project(n, na, sh_degree, A, oc.packed(), oc.width, oc.height, blur, eps_g, r["mean2d"],
+    lib.or_project(n, na, sh_degree, A, oc.packed(), oc.width, oc.height, blur, int(tight), eps_g, r["mean2d"],
                    r["conic"], r["opac"], r["rgb"], r["depth"], r["radius"], r["rect"], r["fragile"],
                    r["frag_rect"])
     r["width"], r["height"] = oc.width, oc.height

@@ -51,7 +51,7 @@ _SIGS = {
     "qn_decode_residuals": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P],
                                 C.c_int),
-    "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P], C.c_int),
+    "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
     "qn_project_bwd": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_workspace_size": ([_I32, _I32, _I32], _SZ),
     "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
@@ -147,9 +147,9 @@ def qn_decode_residuals_bwd(n, n_stride, n_attr, lat, dec, layout, lp, log_alpha
                                          _stream(stream)))
 
 
-def qn_project(n, n_stride, sh_degree, attrs, cam, blur, splats, rects, stream=None):
-    _check(lib().qn_project(n, n_stride, sh_degree, _ptr(attrs), C.byref(cam), float(blur), _ptr(splats),
-                            _ptr(rects), _stream(stream)))
+def qn_project(n, n_stride, sh_degree, attrs, cam, blur, splats, rects, tight_rects=True, stream=None):
+    _check(lib().qn_project(n, n_stride, sh_degree, _ptr(attrs), C.byref(cam), float(blur), int(tight_rects),
+                            _ptr(splats), _ptr(rects), _stream(stream)))
 
 
 def qn_project_bwd(n, n_stride, sh_degree, attrs, cam, blur, d_splats, skip, d_attrs, stream=None):

@@ -90,26 +90,55 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, c
     hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of `count` u32 values in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *__restrict__ v, int count) {
-    __shared__ uint32_t part[1024];
-    const int per = div_up_dev(count, 1024);
-    const int b = threadIdx.x * per, e = min(count, b + per);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += v[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t x = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += x;
-        __syncthreads();
+// Exclusive scan, in place and in digit-major order, of the [RADIX][nb]
+// per-block digit histogram.  One block: warp w owns digits w, w + 32, ...;
+// its lanes walk a digit's blocks 32 at a time (coalesced).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int nb) {
+    __shared__ uint32_t dsum[RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = warp; d < RADIX; d += 32) {
+        uint32_t s = 0;
+        for (int b = lane; b < nb; b += 32) s += hist[(size_t)d * nb + b];
+        s = __reduce_add_sync(FULL, s);
+        if (lane == 0) dsum[d] = s;
     }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int i = b; i < e; ++i) {
-        const uint32_t x = v[i];
-        v[i] = run;
-        run += x;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int PER = RADIX / 32;
+        uint32_t v[PER], t = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            v[i] = dsum[lane * PER + i];
+            t += v[i];
+        }
+        uint32_t incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += x;
+        }
+        uint32_t run = incl - t;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            dsum[lane * PER + i] = run;
+            run += v[i];
+        }
+    }
+    __syncthreads();
+    for (int d = warp; d < RADIX; d += 32) {
+        uint32_t run = dsum[d];
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            const uint32_t v = b < nb ? hist[(size_t)d * nb + b] : 0u;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += x;
+            }
+            if (b < nb) hist[(size_t)d * nb + b] = run + incl - v;
+            run += __shfl_sync(FULL, incl, 31);
+        }
     }
 }
 
@@ -452,7 +481,7 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
         uint32_t *ki = (pass & 1) ? k1 : k0, *vi = (pass & 1) ? v1 : v0;
         uint32_t *ko = (pass & 1) ? k0 : k1, *vo = (pass & 1) ? v0 : v1;
         k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist);
-        k_scan_small<<<1, 1024, 0, s>>>(hist, RADIX * nb);
+        k_radix_scan<<<1, 1024, 0, s>>>(hist, nb);
         k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo);
     }
     // after 4 passes the sorted (depth, index) order is back in k0 / v0

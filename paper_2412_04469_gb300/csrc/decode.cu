@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
             for (int k = 0; k < QN_MAX_LATENT; ++k)
                 if (k < L) l[k] = latent_int(lat[(size_t)(a.lat_off[c] + k) * S + i]);
             const float *D = sD + a.dec_off[c];
+#pragma unroll 8
             for (int r = 0; r < a.ac[c]; ++r) {
                 float acc = 0.f;
 #pragma unroll
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
                 out[o] = prev[o] + acc;                                 // Eq. 4
             }
         }
+#pragma unroll 4
         for (int k = 3; k < a.n_attr; ++k)
             if (!((a.covered >> k) & 1ull)) out[(size_t)k * S + i] = prev[(size_t)k * S + i];
     }
@@ -85,33 +87,58 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
     }
 }
 
-constexpr int BWD_BLOCK = 64;
+// Adjoint, one fused kernel: a block stages 32 Gaussians' residual gradients
+// dr and rounded latents l in shared memory, then writes d_lat = D^T dr per
+// (Gaussian, latent) and accumulates its share of dD = sum dr l^T in
+// registers; one atomic per decoder entry per block at the end.
+constexpr int BWD_THREADS = 256;
+constexpr int BWD_TILE = 32;
+constexpr int BWD_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + BWD_THREADS - 1) / BWD_THREADS;
 
-__global__ void __launch_bounds__(BWD_BLOCK) k_decode_bwd(
+__global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
     DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
     const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
     float d_lreg, const uint8_t *__restrict__ skip, float *__restrict__ d_lat,
     float *__restrict__ d_dec, float *__restrict__ d_lp, float *__restrict__ d_la) {
     __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
-    // rows padded by one word: threads reading different rows at the same
-    // column then fall in different banks
-    __shared__ float s_dr[MAX_RES_PLANES][BWD_BLOCK + 1];
-    __shared__ float s_l[MAX_LAT_TOTAL][BWD_BLOCK + 1];
-    for (int k = threadIdx.x; k < a.n_dec; k += blockDim.x) sD[k] = bf16_to_f32(dec[k]);
-    // each thread owns up to ceil(n_dec / BWD_BLOCK) entries of dD
-    constexpr int MAX_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + BWD_BLOCK - 1) / BWD_BLOCK;
-    float acc[MAX_OWN];
+    __shared__ float s_dr[MAX_RES_PLANES][BWD_TILE + 1];   // +1: different rows, different banks
+    __shared__ float s_l[MAX_LAT_TOTAL][BWD_TILE + 1];
+    __shared__ int s_cat[MAX_LAT_TOTAL];                    // category of each latent plane
+    for (int k = threadIdx.x; k < a.n_dec; k += BWD_THREADS) sD[k] = bf16_to_f32(dec[k]);
+    if (threadIdx.x < a.n_lat) {
+        int c = 0;
+        while (c + 1 < a.n_cat && (int)threadIdx.x >= a.lat_off[c + 1]) ++c;
+        s_cat[threadIdx.x] = c;
+    }
+    // decoder entries owned by this thread: (category, row, latent)
+    int own_c[BWD_OWN], own_r[BWD_OWN], own_k[BWD_OWN];
+    float acc[BWD_OWN];
 #pragma unroll
-    for (int q = 0; q < MAX_OWN; ++q) acc[q] = 0.f;
+    for (int q = 0; q < BWD_OWN; ++q) {
+        const int e = threadIdx.x + q * BWD_THREADS;
+        int c = 0;
+        while (c + 1 < a.n_cat && e >= a.dec_off[c + 1]) ++c;
+        const int L = a.ld[c];
+        own_c[q] = e < a.n_dec ? c : -1;
+        own_r[q] = (e - a.dec_off[c]) / L;
+        own_k[q] = (e - a.dec_off[c]) % L;
+        acc[q] = 0.f;
+    }
     const size_t S = a.stride;
-    const int t = threadIdx.x;
     const int n_res = a.n_attr - 3;
+    const int lane = threadIdx.x & (BWD_TILE - 1), row0 = threadIdx.x / BWD_TILE;
+    constexpr int ROWS_PER_PASS = BWD_THREADS / BWD_TILE;
     __syncthreads();
-    for (int base = blockIdx.x * BWD_BLOCK; base < a.n; base += gridDim.x * BWD_BLOCK) {
-        const int i = base + t;
+    for (int base = blockIdx.x * BWD_TILE; base < a.n; base += gridDim.x * BWD_TILE) {
+        const int i = base + lane;
         const bool valid = i < a.n;
         const bool sk = valid && skip && skip[i];
-        if (valid) {
+        // stage the tile (coalesced: lanes are consecutive Gaussians)
+        for (int r = row0; r < n_res; r += ROWS_PER_PASS)
+            s_dr[r][lane] = (valid && !sk) ? d_out[(size_t)(r + 3) * S + i] : 0.f;
+        for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS)
+            s_l[k][lane] = valid ? latent_int(lat[(size_t)k * S + i]) : 0.f;
+        if (row0 == 0 && valid) {
             const float l_a = la[i];
             const float gh = sigmoidf_(l_a / a.tau);
             const float gt = gh * (a.g1 - a.g0) + a.g0;
@@ -127,43 +154,34 @@ __global__ void __launch_bounds__(BWD_BLOCK) k_decode_bwd(
             const float p = sigmoidf_(l_a - a.shift);
             d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
         }
-        for (int k = 0; k < n_res; ++k)
-            s_dr[k][t] = (valid && !sk) ? d_out[(size_t)(k + 3) * S + i] : 0.f;
-        for (int k = 0; k < a.n_lat; ++k) s_l[k][t] = valid ? latent_int(lat[(size_t)k * S + i]) : 0.f;
         __syncthreads();
+        // STE: d_lat[k] = sum_r D[r][k] dr[r] for this thread's (latent, Gaussian) pairs
         if (valid) {
-            for (int c = 0; c < a.n_cat; ++c) {
-                const int L = a.ld[c], M = a.ac[c];
+            for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) {
+                const int c = s_cat[k], L = a.ld[c], kk = k - a.lat_off[c];
                 const float *D = sD + a.dec_off[c];
-                for (int k = 0; k < L; ++k) {
-                    float s = 0.f;                          // STE: D^T dr
-                    for (int r = 0; r < M; ++r) s = fmaf(D[r * L + k], s_dr[a.ab[c] - 3 + r][t], s);
-                    d_lat[(size_t)(a.lat_off[c] + k) * S + i] = sk ? 0.f : s;
-                }
+                const int rb = a.ab[c] - 3;
+                float sum = 0.f;
+                for (int r = 0; r < a.ac[c]; ++r) sum = fmaf(D[r * L + kk], s_dr[rb + r][lane], sum);
+                d_lat[(size_t)k * S + i] = sk ? 0.f : sum;
             }
         }
-        // dD[c][r][k] += sum over this block of dr[r] l[k]
+        // dD[c][r][k] += sum over the tile of dr[r] l[k]
 #pragma unroll
-        for (int q = 0; q < MAX_OWN; ++q) {
-            const int e = t + q * BWD_BLOCK;
-            if (e >= a.n_dec) break;
-            int c = 0;
-            while (c + 1 < a.n_cat && e >= a.dec_off[c + 1]) ++c;
-            const int L = a.ld[c];
-            const int r = (e - a.dec_off[c]) / L, k = (e - a.dec_off[c]) % L;
-            const float *pr = s_dr[a.ab[c] - 3 + r];
-            const float *pl = s_l[a.lat_off[c] + k];
-            float s = acc[q];
-            for (int j = 0; j < BWD_BLOCK; ++j) s = fmaf(pr[j], pl[j], s);
-            acc[q] = s;
+        for (int q = 0; q < BWD_OWN; ++q) {
+            if (own_c[q] < 0) continue;
+            const float *pr = s_dr[a.ab[own_c[q]] - 3 + own_r[q]];
+            const float *pl = s_l[a.lat_off[own_c[q]] + own_k[q]];
+            float sum = acc[q];
+#pragma unroll 8
+            for (int j = 0; j < BWD_TILE; ++j) sum = fmaf(pr[j], pl[j], sum);
+            acc[q] = sum;
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < MAX_OWN; ++q) {
-        const int e = t + q * BWD_BLOCK;
-        if (e < a.n_dec) atomicAdd(&d_dec[e], acc[q]);
-    }
+    for (int q = 0; q < BWD_OWN; ++q)
+        if (own_c[q] >= 0) atomicAdd(&d_dec[threadIdx.x + q * BWD_THREADS], acc[q]);
 }
 
 int make_args(int32_t n, int32_t n_stride, int32_t n_attr, const qn_decoder_layout *lay,
@@ -244,7 +262,7 @@ extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_at
     if (a.n_dec > 0 && cudaMemsetAsync(d_dec, 0, sizeof(float) * a.n_dec, s) != cudaSuccess)
         return qn::check_launch("decode_bwd memset");
     if (n == 0) return QN_OK;
-    qn::k_decode_bwd<<<qn::grid_for(n, qn::BWD_BLOCK, 4), qn::BWD_BLOCK, 0, s>>>(
+    qn::k_decode_bwd<<<qn::grid_for(n, qn::BWD_TILE, 4), qn::BWD_THREADS, 0, s>>>(
         a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat, d_dec, d_lp, d_log_alpha);
     return qn::check_launch("qn_decode_residuals_bwd");
 }

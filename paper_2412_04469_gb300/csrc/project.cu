@@ -139,7 +139,20 @@ __device__ __forceinline__ bool geometry(const CamArgs &cm, const float *__restr
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_project(int n, int S_, int deg, CamArgs cm, float blur,
+// Bounding box of the region where o exp(-q/2) can reach 1/255, i.e. the
+// ellipse q(d) = d^T conic d <= k, k = 2 ln(255 o); its half-widths are
+// sqrt(k Sigma'_xx) and sqrt(k Sigma'_yy).  k is widened by 0.01 and then 1%,
+// the half-widths by 0.01 px, so that FP32 rounding of alpha outside the box
+// stays far below 1/255.  Returns false when no pixel can pass (o < 0.995/255).
+__device__ __forceinline__ bool alpha_box(float opac, float a, float c, float &hx, float &hy) {
+    const float k = 2.f * logf(255.f * opac) + 0.01f;
+    if (!(k > 0.f)) return false;
+    hx = sqrtf(1.01f * k * a) + 0.01f;
+    hy = sqrtf(1.01f * k * c) + 0.01f;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_project(int n, int S_, int deg, CamArgs cm, float blur, int tight,
                                                  const float *__restrict__ A, float4 *__restrict__ splat,
                                                  int4 *__restrict__ rects) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,12 +179,29 @@ __global__ void __launch_bounds__(256) k_project(int n, int S_, int deg, CamArgs
             rc.y = (int)fminf(fmaxf(fy0, 0.f), (float)cm.TY);
             rc.z = (int)fminf(fmaxf(fx1, 0.f), (float)cm.TX);
             rc.w = (int)fminf(fmaxf(fy1, 0.f), (float)cm.TY);
+            const float opac = 1.f / (1.f + expf(-A[10 * S + i]));
+            if (tight) {
+                // keep only tiles the alpha >= 1/255 ellipse can reach; the
+                // dropped (tile, Gaussian) pairs are skipped by every pixel
+                float hx, hy;
+                if (alpha_box(opac, a, c, hx, hy)) {
+                    const float ex0 = floorf((mx - hx) * (1.f / QN_TILE)), ey0 = floorf((my - hy) * (1.f / QN_TILE));
+                    const float ex1 = floorf((mx + hx) * (1.f / QN_TILE)) + 1.f;
+                    const float ey1 = floorf((my + hy) * (1.f / QN_TILE)) + 1.f;
+                    rc.x = max(rc.x, (int)fminf(fmaxf(ex0, 0.f), (float)cm.TX));
+                    rc.y = max(rc.y, (int)fminf(fmaxf(ey0, 0.f), (float)cm.TY));
+                    rc.z = min(rc.z, (int)fminf(fmaxf(ex1, 0.f), (float)cm.TX));
+                    rc.w = min(rc.w, (int)fminf(fmaxf(ey1, 0.f), (float)cm.TY));
+                } else {
+                    rc = make_int4(0, 0, 0, 0);
+                }
+            }
             vis = rc.z > rc.x && rc.w > rc.y;
             if (vis) {
                 const float id = 1.f / det;
                 s0.x = mx;
                 s0.y = my;
-                s0.z = 1.f / (1.f + expf(-A[10 * S + i]));
+                s0.z = opac;
                 s1 = make_float4(c * id, -b * id, a * id, 0.f);
                 float dx = A[i] - cm.cp[0], dy = A[S + i] - cm.cp[1], dz = A[2 * S + i] - cm.cp[2];
                 const float inv = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
@@ -380,8 +410,8 @@ int cam_args(const qn_camera *cam, CamArgs *c) {
 }  // namespace qn
 
 extern "C" int qn_project(int32_t n, int32_t n_stride, int32_t sh_degree, const float *attrs,
-                          const qn_camera *cam_host, float blur, qn_splat *splats, int32_t *rects,
-                          qn_stream_t stream) {
+                          const qn_camera *cam_host, float blur, int32_t tight_rects, qn_splat *splats,
+                          int32_t *rects, qn_stream_t stream) {
     qn::CamArgs cm;
     int st = qn::cam_args(cam_host, &cm);
     if (st) return st;
@@ -392,7 +422,7 @@ extern "C" int qn_project(int32_t n, int32_t n_stride, int32_t sh_degree, const 
     QN_REQUIRE(((uintptr_t)splats & 15) == 0 && ((uintptr_t)rects & 15) == 0, "splats/rects must be 16-byte aligned");
     if (n == 0) return QN_OK;
     qn::k_project<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(
-        n, n_stride, sh_degree, cm, blur, attrs, reinterpret_cast<float4 *>(splats),
+        n, n_stride, sh_degree, cm, blur, tight_rects != 0, attrs, reinterpret_cast<float4 *>(splats),
         reinterpret_cast<int4 *>(rects));
     return qn::check_launch("qn_project");
 }

@@ -132,8 +132,9 @@ class Rasterizer:
     image size."""
 
     def __init__(self, n: int, n_stride: int, sh_degree: int, width: int, height: int, pair_capacity: int,
-                 device="cuda", keep_keys: bool = False):
+                 device="cuda", keep_keys: bool = False, tight_rects: bool = True):
         dev = torch.device(device)
+        self.tight_rects = tight_rects
         self.n, self.S, self.sh_degree = n, n_stride, sh_degree
         self.W, self.H = width, height
         self.TX, self.TY = (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
@@ -160,7 +161,8 @@ class Rasterizer:
         self.keys = torch.zeros(max(self.capacity, 1), device=dev, dtype=torch.int64) if self.keep_keys else None
 
     def project(self, attrs, cam, blur, stream=None):
-        B.qn_project(self.n, self.S, self.sh_degree, attrs, cam, blur, self.splats, self.rects, stream)
+        B.qn_project(self.n, self.S, self.sh_degree, attrs, cam, blur, self.splats, self.rects, self.tight_rects,
+                     stream)
 
     def bin_sort(self, sync=False, stream=None):
         depth_ptr = self.splats.data_ptr() + 3 * 4

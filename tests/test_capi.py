@@ -46,13 +46,13 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     from paper_2412_04469_gb300 import binding as B
     cam = B.qn_camera()
     cam.width, cam.height, cam.fx, cam.fy, cam.near_plane = 64, 64, 50.0, 50.0, 0.2
-    assert B.lib().qn_project(-1, 4, 0, None, C.byref(cam), 0.3, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_project(-1, 4, 0, None, C.byref(cam), 0.3, 1, None, None, None) == B.QN_ERR_INVALID_ARG
     assert b"n_stride" in B.lib().qn_last_error() or b"n" in B.lib().qn_last_error()
-    assert B.lib().qn_project(8, 8, 4, None, C.byref(cam), 0.3, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_project(8, 8, 4, None, C.byref(cam), 0.3, 1, None, None, None) == B.QN_ERR_INVALID_ARG
     assert b"sh_degree" in B.lib().qn_last_error()
     bad = B.qn_camera()
     bad.width, bad.height = 0, 64
-    assert B.lib().qn_project(8, 8, 0, None, C.byref(bad), 0.3, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_project(8, 8, 0, None, C.byref(bad), 0.3, 1, None, None, None) == B.QN_ERR_INVALID_ARG
     assert B.lib().qn_bin_sort(4, None, 1, None, 300, 2, None, 0, 0, None, None, None, None, None, None) == \
         B.QN_ERR_INVALID_ARG
     lay = B.qn_decoder_layout()

@@ -73,11 +73,11 @@ def close(got, ref, rtol=RTOL, floor_frac=1e-2, what=""):
     return worst
 
 
-def gpu_raster(A, cam, deg, blur, bg=(0.0, 0.0, 0.0), keep_keys=False):
+def gpu_raster(A, cam, deg, blur, bg=(0.0, 0.0, 0.0), keep_keys=False, tight=True):
     from paper_2412_04469_gb300.pipeline import Rasterizer
     n = A.shape[1]
     Sd = stride_of(n)
-    r = Rasterizer(n, Sd, deg, cam.width, cam.height, 1, keep_keys=keep_keys)
+    r = Rasterizer(n, Sd, deg, cam.width, cam.height, 1, keep_keys=keep_keys, tight_rects=tight)
     c = B().make_camera(cam)
     attrs = planes(A, Sd)
     r.project(attrs, c, blur)
@@ -137,7 +137,7 @@ def test_project_matches_oracle(n, W, H, deg, blur, seed):
     r, _, _ = gpu_raster(A, cam, deg, blur)
     sp = r.splats.cpu().numpy()[:n]
     rc = r.rects.cpu().numpy()[:n]
-    ref = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    ref = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G, tight=True)
     ok = ref["fragile"] == 0
     assert (~ok).mean() < 0.01
     vis_ref = ref["radius"] > 0
@@ -158,7 +158,7 @@ def test_project_bwd_matches_oracle(n, W, H, deg, blur, seed):
     A[7:10] += 0.5
     r, c, attrs = gpu_raster(A, cam, deg, blur)
     rng = np.random.default_rng(seed)
-    ref = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    ref = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G, tight=True)
     d = rng.standard_normal((n, 12)).astype(np.float32)
     d[:, [3, 7, 11]] = 0.0
     d[:, 4:7] *= 0.01
@@ -237,7 +237,7 @@ def test_render_forward_matches_oracle(n, W, H, deg, blur, seed):
     A, cam = _scene(n, W, H, deg, seed)
     bg = (0.1, 0.3, 0.2)
     r, _, _ = gpu_raster(A, cam, deg, blur, bg)
-    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G, tight=True)
     img, T, last, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
     ok = frag == 0
     assert (~ok).mean() <= MAX_FRAGILE
@@ -254,7 +254,7 @@ def test_render_backward_matches_oracle(n, W, H, deg, blur, seed):
     A, cam = _scene(n, W, H, deg, seed)
     bg = (0.2, 0.1, 0.05)
     r, c, _ = gpu_raster(A, cam, deg, blur, bg)
-    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G)
+    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G, tight=True)
     _, _, _, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
     d_img = (S.make_image(W, H, seed) - 0.5) * (frag == 0)[None]
     r.d_img.copy_(up(d_img))
@@ -266,6 +266,27 @@ def test_render_backward_matches_oracle(n, W, H, deg, blur, seed):
     close(g[:, 2], ref["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity")
     close(g[:, 4:7].T, ref["d_conic"], floor_frac=GRAD_FLOOR, what="d_conic")
     close(g[:, 8:11].T, ref["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb")
+
+
+@pytest.mark.parametrize("n,W,H,deg,blur,seed", SCENES[:2])
+def test_tight_rects_leave_rendering_unchanged(n, W, H, deg, blur, seed):
+    """The tile lists built from tight rects are a subset of the 3-sigma ones
+    and give the same image, transmittance, last contributor and adjoint."""
+    A, cam = _scene(n, W, H, deg, seed)
+    A[10] += np.linspace(-6, 3, n).astype(np.float32)
+    bg = (0.3, 0.2, 0.1)
+    out = []
+    for tight in (False, True):
+        r, c, _ = gpu_raster(A, cam, deg, blur, bg, tight=tight)
+        r.d_img.copy_(up(S.make_image(W, H, seed) - 0.5))
+        r.render_bwd(c, bg)
+        torch.cuda.synchronize()
+        out.append((r.img.cpu().numpy(), r.T_final.cpu().numpy(), gpu_last_ids(r, W, H),
+                    r.d_splats.cpu().numpy(), int(r.n_pairs.item())))
+    (i0, t0, l0, g0, p0), (i1, t1, l1, g1, p1) = out
+    assert p1 < p0
+    assert np.array_equal(i0, i1) and np.array_equal(t0, t1) and np.array_equal(l0, l1)
+    close(g1, g0, rtol=1e-5, floor_frac=GRAD_FLOOR, what="adjoint")   # atomic order only
 
 
 def test_render_skip_mask_zeroes_skipped():
@@ -389,7 +410,7 @@ def test_end_to_end_gradients_match_oracle_chain():
     f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
     f.decode()
     A_ref, _, _ = oracle.decode(prev.astype(np.float64), res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1)
-    proj = oracle.project(A_ref, cam, deg, blur=0.3, eps_g=EPS_G)
+    proj = oracle.project(A_ref, cam, deg, blur=0.3, eps_g=EPS_G, tight=True)
     img_ref, _, _, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
     _, g_ref = oracle.l1_loss(img_ref, target)
     near = np.abs(img_ref - target).min(axis=0) < 1e-4          # sign of the L1 term could flip

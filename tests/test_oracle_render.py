@@ -169,3 +169,44 @@ def test_backward_matches_finite_differences(seed):
                 assert fd == pytest.approx(grad[row, i], rel=1e-5, abs=1e-6), (key, row, i)
                 checked += 1
     assert checked > 0.9 * 9 * vis.size
+
+
+@pytest.mark.parametrize("seed,grow", [(5, 0.8), (6, 1.4)])
+def test_tight_rects_render_identically(seed, grow):
+    """Limiting tile lists to the tiles the alpha >= 1/255 ellipse reaches
+    drops only pairs every pixel skips: same image, T and adjoint in FP64."""
+    A, oc = _scene(300, 64, 48, seed, degree=1, grow=grow)
+    A[10] += np.linspace(-6, 4, A.shape[1])          # include Gaussians with o < 1/255
+    plain = oracle.project(A, oc, 1)
+    tight = oracle.project(A, oc, 1, tight=True)
+    area = lambda r: np.maximum(r[2] - r[0], 0) * np.maximum(r[3] - r[1], 0)
+    ne = area(tight["rect"]) > 0                                  # non-empty tight rects lie inside
+    t, p = tight["rect"][:, ne], plain["rect"][:, ne]
+    assert np.all(t[0] >= p[0]) and np.all(t[1] >= p[1]) and np.all(t[2] <= p[2]) and np.all(t[3] <= p[3])
+    assert area(tight["rect"]).sum() < 0.9 * area(plain["rect"]).sum()
+    assert np.all(area(tight["rect"])[plain["opac"] < 0.99 / 255] == 0)
+    i1, T1, _, _ = oracle.render_fwd(plain, bg=(0.1, 0.2, 0.3))
+    i2, T2, _, _ = oracle.render_fwd(tight, bg=(0.1, 0.2, 0.3))
+    assert np.array_equal(i1, i2) and np.array_equal(T1, T2)
+    d = S.make_image(64, 48, seed) - 0.5
+    g1 = oracle.render_bwd(plain, d, bg=(0.1, 0.2, 0.3))
+    g2 = oracle.render_bwd(tight, d, bg=(0.1, 0.2, 0.3))
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+
+
+def test_tight_rect_closed_form():
+    W, H, f, z, sig = 256, 256, 100.0, 2.0, 0.1
+    cam = oracle.OracleCamera(np.eye(3), np.zeros(3), f, f, W / 2, H / 2, W, H, 0.2, np.zeros(3))
+    Ahat = np.zeros((14, 1))
+    Ahat[0:3, 0] = [0.3, -0.2, z]
+    Ahat[3, 0] = 1.0
+    Ahat[7:10, 0] = math.log(sig)
+    Ahat[10, 0] = 0.0                                  # o = 1/2
+    r = oracle.project(Ahat, cam, 0, blur=0.0, tight=True)
+    s2 = (f * sig / z) ** 2                            # isotropic footprint, Sigma'_xx = Sigma'_yy
+    k = 2 * math.log(255 * 0.5) + 0.01
+    h = math.sqrt(1.01 * k * s2) + 0.01
+    mx, my = f * 0.3 / z + W / 2, f * -0.2 / z + H / 2
+    assert list(r["rect"][:, 0]) == [math.floor((mx - h) / 16), math.floor((my - h) / 16),
+                                     math.floor((mx + h) / 16) + 1, math.floor((my + h) / 16) + 1]
