@@ -176,8 +176,9 @@ int qn_project(int32_t n, int32_t n_stride, int32_t sh_degree, const float *attr
 /*
  * Adjoint of qn_project: d_attrs[n_attr][n_stride] (overwritten) from the
  * gradient records d_splats[n]; culled Gaussians get zero.  The colour clamp
- * and the Jacobian clamp pass zero gradient.  skip (nullable, [n] u8) zeroes
- * the Gaussians with skip != 0.
+ * and the Jacobian clamp pass zero gradient.  skip (nullable, [n] u8): the
+ * columns of Gaussians with skip != 0 are left unwritten (the decode adjoint
+ * ignores them under the same mask).
  */
 int qn_project_bwd(int32_t n, int32_t n_stride, int32_t sh_degree, const float *attrs,
                    const qn_camera *cam_host, float blur, const qn_splat *d_splats,
@@ -300,6 +301,91 @@ int qn_image_loss(int64_t count, const float *img, const float *target, float w,
 int qn_adam(int32_t rows, int32_t n, int32_t stride, float *param, const float *grad, float *m,
             float *v, int32_t step, float lr, float beta1, float beta2, float eps,
             const uint8_t *skip, uint16_t *param_bf16, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Viewspace gradient difference and gate initialisation -- Sec. 3.3.        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Eq. 9: score[0..1][i] += scale * (d mean2d x, d mean2d y) of d_splats[i].
+ * With d_splats the compositing adjoint of the upstream image
+ * 2 (I_{t-1} - I_t) / (3 H W) at the rendering of A_{t-1} (qn_image_loss with
+ * mse, then qn_render_bwd) and scale = 1 / V, summing over the V views gives
+ * d_t: the MSE is linear in the target, so this single adjoint per view equals
+ * the difference of the two gradients Eq. 9 writes.
+ *   score [2][n_stride] f32 (read-modify-write; zero it before the first view)
+ */
+int qn_viewspace_accum(int32_t n, int32_t n_stride, const qn_splat *d_splats, float scale, float *score,
+                       qn_stream_t stream);
+
+/*
+ * Eq. 10 and Eq. 8 solved for log alpha:
+ *   norms[i] = |d_t,i|, median[0] = lower median of the norms (element
+ *   (m-1)/2 of the m sorted values); with nonzero_median != 0 only the m
+ *   non-zero norms count (median 0 if none), so that Gaussians no view sees do
+ *   not pull the median to 0.  p_i = norms_i / (norms_i + median) (1 or 0 for
+ *   a zero median), clamped to [1e-6, 1 - 1e-6];
+ *   log_alpha[i] = log(p_i / (1 - p_i)) + tau log(-gamma0 / gamma1), so that
+ *   sigmoid(log_alpha_i - tau log(-gamma0/gamma1)) = p_i.
+ *   score [2][n_stride] (read); norms [n], median [1], log_alpha [n] (written).
+ */
+int qn_gate_init(int32_t n, int32_t n_stride, const float *score, const qn_gate_params *gate_host,
+                 int32_t nonzero_median, float *norms, float *median, float *log_alpha, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned static-skip MLP.  Not part of the paper: a per-Gaussian classifier */
+/* trained on the gates that earlier frames of the method produce, whose      */
+/* "static" predictions let the adjoints and the Adam step skip Gaussians.   */
+/* ------------------------------------------------------------------------ */
+
+#define QN_MLP_FEATURES 16
+#define QN_MLP_PARAMS 5313   /* W1[64][16] b1[64] W2[64][64] b2[64] W3[64] b3 */
+
+/*
+ * Features X [16][n_stride] f32 (written) of each Gaussian:
+ *   0 p_i of Eq. 10 (|d| / (|d| + median); 1 or 0 for a zero median)
+ *   1 clip(log(|d| / median + 1e-6), -8, 8) / 4 (0 for a zero median)
+ *   2, 3 direction d / (|d| + 1e-20) of the score d_t (Eq. 9)
+ *   4-6 position of A_{t-1};  7 previous gate g_{t-1} (0 if prev_gate is NULL)
+ *   8 sigmoid(log_alpha_{t-1} - tau log(-gamma0/gamma1)) (Eq. 8; log_alpha 0 if NULL)
+ *   9 opacity;  10-12 (log-scale + 3) / 2
+ *   13 clip(100 |g_{t-1} lp_{t-1}|, 0, 8) (0 if prev_lp is NULL)
+ *   14 the previous frame's label of qn_skip_labels (prev_static != 0), or
+ *      [g_{t-1} == 0] when prev_static is NULL;  15 1
+ *   score [2][n_stride], median [1] (from qn_gate_init), prev [n_attr][n_stride],
+ *   prev_gate [n], prev_log_alpha [n], prev_lp [3][n_stride], prev_static [n] u8
+ *   (last four nullable).
+ */
+int qn_skip_features(int32_t n, int32_t n_stride, int32_t n_attr, const float *score, const float *median,
+                     const float *prev, const float *prev_gate, const float *prev_log_alpha,
+                     const float *prev_lp, const uint8_t *prev_static, const qn_gate_params *gate_host,
+                     float *X, qn_stream_t stream);
+
+/*
+ * logit = W3 relu(W2 relu(W1 x + b1) + b2) + b3 per Gaussian, with the
+ * parameters in bf16 (params, QN_MLP_PARAMS values) and FP32 accumulation.
+ * logits [n] (nullable) and skip [n] u8 = [sigmoid(logit) > threshold]
+ * (nullable; one of the two required).  threshold in (0, 1).
+ */
+int qn_skip_mlp_fwd(int32_t n, int32_t n_stride, const float *X, const uint16_t *params, float threshold,
+                    float *logits, uint8_t *skip, qn_stream_t stream);
+
+/*
+ * Training labels: labels[i] = 1 (static) when Gaussian i's residual of the
+ * finished frame is exactly zero -- gate[i] == 0 and every latent of
+ * lat [n_latent][n_stride] rounds to 0 -- else 0.
+ */
+int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *gate, const float *lat,
+                   uint8_t *labels, qn_stream_t stream);
+
+/*
+ * Gradient of the mean binary cross-entropy between sigmoid(logit) and
+ * labels [n] u8 (1 = static) over the n rows of X: d_params [QN_MLP_PARAMS]
+ * f32 and loss [1] (nullable) are overwritten.  A row range [r0, r0 + n) of a
+ * larger X is passed as X + r0 with the same n_stride, labels + r0.
+ */
+int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, const uint8_t *labels, const uint16_t *params,
+                    float *d_params, float *loss, qn_stream_t stream);
 
 #ifdef __cplusplus
 }

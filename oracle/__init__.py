@@ -19,10 +19,11 @@ docstring says "parity unpinned".
 from .raster import (build, OracleCamera, sh_basis, decode, decode_bwd, project, project_bwd,
                      bin_sort, render_fwd, render_bwd, num_threads)
 from .learn import (l1_loss, mse_grad, viewspace_score, gate_init, adam_step, mlp_forward,
-                    mlp_backward, bce_loss)
+                    mlp_backward, bce_loss, skip_features)
 
 __all__ = [
     "build", "OracleCamera", "sh_basis", "decode", "decode_bwd", "project", "project_bwd",
     "bin_sort", "render_fwd", "render_bwd", "num_threads", "l1_loss", "mse_grad",
     "viewspace_score", "gate_init", "adam_step", "mlp_forward", "mlp_backward", "bce_loss",
+    "skip_features",
 ]

@@ -36,13 +36,16 @@ def viewspace_score(projs, gt_t, gt_prev, bg=(0.0, 0.0, 0.0)):
     return d / len(projs)
 
 
-def gate_init(d, tau, gamma0, gamma1):
+def gate_init(d, tau, gamma0, gamma1, nonzero_median=True):
     """Eq. 10 and Eq. 8 solved for log alpha:
          d_i = |d_i| / (|d_i| + median |d|),  sigmoid(log a_i - tau log(-g0/g1)) = d_i.
-    Median of an even count is the lower median; with a zero median d_i is 1
-    for |d_i| > 0 and 0 otherwise; d_i is clamped to [1e-6, 1 - 1e-6]."""
+    Median of an even count is the lower median; with nonzero_median it is
+    taken over the non-zero |d_i| only (0 if there are none); with a zero
+    median d_i is 1 for |d_i| > 0 and 0 otherwise; d_i is clamped to
+    [1e-6, 1 - 1e-6]."""
     nrm = np.sqrt((np.asarray(d, np.float64) ** 2).sum(axis=0))
-    med = np.sort(nrm)[(nrm.size - 1) // 2]
+    pool = nrm[nrm > 0] if nonzero_median else nrm
+    med = np.sort(pool)[(pool.size - 1) // 2] if pool.size else 0.0
     if med > 0:
         p = nrm / (nrm + med)
     else:
@@ -68,6 +71,53 @@ def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, mas
         m1 = np.where(keep, m, m1)
         v1 = np.where(keep, v, v1)
     return p1, m1, v1
+
+
+# --------------------------------------------------------------------------
+# Static-skip features (16 per Gaussian), written from their definition:
+#   0 p_i of Eq. 10 (|d| / (|d| + median); 1 or 0 for a zero median; the
+#     median as in gate_init)
+#   1 clip(log(|d| / median + 1e-6), -8, 8) / 4  (0 for a zero median)
+#   2, 3 direction of d_t (d / (|d| + 1e-20))
+#   4, 5, 6 position of A_{t-1}
+#   7 previous frame's gate g_{t-1}
+#   8 previous frame's p of Eq. 8: sigmoid(log a_{t-1} - tau log(-g0/g1))
+#   9 opacity sigmoid(logit o)
+#   10, 11, 12 (log-scale + 3) / 2
+#   13 clip(100 |g_{t-1} lp_{t-1}|, 0, 8)  (previous position residual)
+#   14 the previous frame's zero-residual label (prev_static), or
+#      [g_{t-1} == 0] without one
+#   15 1
+# --------------------------------------------------------------------------
+def skip_features(score, prev, prev_gate, prev_log_alpha, prev_lp, tau, gamma0, gamma1, nonzero_median=True,
+                  prev_static=None):
+    """Returns X[16][n] (float64).  score [2][n], prev [n_attr][n] (A_{t-1}),
+    prev_gate [n], prev_log_alpha [n], prev_lp [3][n].  Parity unpinned by the
+    paper (the MLP is not part of it); pinned here by a hand example."""
+    d = np.asarray(score, np.float64)
+    A = np.asarray(prev, np.float64)
+    n = d.shape[1]
+    nrm = np.sqrt((d ** 2).sum(axis=0))
+    pool = nrm[nrm > 0] if nonzero_median else nrm
+    med = np.sort(pool)[(pool.size - 1) // 2] if pool.size else 0.0
+    X = np.zeros((16, n))
+    if med > 0:
+        X[0] = nrm / (nrm + med)
+        X[1] = np.clip(np.log(nrm / med + 1e-6), -8, 8) / 4
+    else:
+        X[0] = (nrm > 0).astype(np.float64)
+    X[2] = d[0] / (nrm + 1e-20)
+    X[3] = d[1] / (nrm + 1e-20)
+    X[4:7] = A[0:3]
+    g = np.asarray(prev_gate, np.float64)
+    X[7] = g
+    X[8] = 1 / (1 + np.exp(-(np.asarray(prev_log_alpha, np.float64) - tau * np.log(-gamma0 / gamma1))))
+    X[9] = 1 / (1 + np.exp(-A[10]))
+    X[10:13] = (A[7:10] + 3) / 2
+    X[13] = np.clip(100 * np.abs(g) * np.sqrt((np.asarray(prev_lp, np.float64) ** 2).sum(axis=0)), 0, 8)
+    X[14] = (g == 0).astype(np.float64) if prev_static is None else (np.asarray(prev_static) != 0).astype(np.float64)
+    X[15] = 1.0
+    return X
 
 
 # --------------------------------------------------------------------------

@@ -59,6 +59,12 @@ _SIGS = {
     "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_bwd": ([_P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
+    "qn_viewspace_accum": ([_I32, _I32, _P, _F32, _P, _P], C.c_int),
+    "qn_gate_init": ([_I32, _I32, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
+    "qn_skip_features": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_skip_mlp_fwd": ([_I32, _I32, _P, _P, _F32, _P, _P, _P], C.c_int),
+    "qn_skip_mlp_bwd": ([_I32, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_skip_labels": ([_I32, _I32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
 }
 
@@ -207,3 +213,37 @@ def qn_adam(rows, n, stride, param, grad, m, v, step, lr, beta1, beta2, eps, ski
             stream=None):
     _check(lib().qn_adam(rows, n, stride, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
                          float(beta1), float(beta2), float(eps), _ptr(skip), _ptr(param_bf16), _stream(stream)))
+
+
+def qn_viewspace_accum(n, n_stride, d_splats, scale, score, stream=None):
+    _check(lib().qn_viewspace_accum(n, n_stride, _ptr(d_splats), float(scale), _ptr(score), _stream(stream)))
+
+
+def qn_gate_init(n, n_stride, score, gate_params, norms, median, log_alpha, nonzero_median=True, stream=None):
+    _check(lib().qn_gate_init(n, n_stride, _ptr(score), C.byref(gate_params), int(nonzero_median), _ptr(norms),
+                              _ptr(median), _ptr(log_alpha), _stream(stream)))
+
+
+QN_MLP_FEATURES = 16
+QN_MLP_PARAMS = 5313
+
+
+def qn_skip_features(n, n_stride, n_attr, score, median, prev, prev_gate, prev_log_alpha, prev_lp, gate_params,
+                     X, prev_static=None, stream=None):
+    _check(lib().qn_skip_features(n, n_stride, n_attr, _ptr(score), _ptr(median), _ptr(prev), _ptr(prev_gate),
+                                  _ptr(prev_log_alpha), _ptr(prev_lp), _ptr(prev_static), C.byref(gate_params),
+                                  _ptr(X), _stream(stream)))
+
+
+def qn_skip_mlp_fwd(n, n_stride, X, params_bf16, threshold, logits=None, skip=None, stream=None):
+    _check(lib().qn_skip_mlp_fwd(n, n_stride, _ptr(X), _ptr(params_bf16), float(threshold), _ptr(logits),
+                                 _ptr(skip), _stream(stream)))
+
+
+def qn_skip_mlp_bwd(n, n_stride, X, labels, params_bf16, d_params, loss=None, stream=None):
+    _check(lib().qn_skip_mlp_bwd(n, n_stride, _ptr(X), _ptr(labels), _ptr(params_bf16), _ptr(d_params),
+                                 _ptr(loss), _stream(stream)))
+
+
+def qn_skip_labels(n, n_stride, n_latent, gate, lat, labels, stream=None):
+    _check(lib().qn_skip_labels(n, n_stride, n_latent, _ptr(gate), _ptr(lat), _ptr(labels), _stream(stream)))

@@ -232,8 +232,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(int n, int S_, int deg, int
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const size_t S = S_;
+    if (skip && skip[i]) return;             // left untouched: the decode adjoint ignores skipped Gaussians
     Fwd f;
-    bool vis = !(skip && skip[i]) && geometry(cm, A, S, i, f);
+    bool vis = geometry(cm, A, S, i, f);
     float a = 0.f, b = 0.f, c = 0.f, det = 0.f;
     if (vis) {
         a = f.a + blur; b = f.b; c = f.c + blur;

@@ -31,6 +31,10 @@ class HParams:
     gamma0: float = -0.5
     gamma1: float = 1.01
     lambda_reg: float = 0.01
+    # Eq. 11 weights Eq. 8's sum by lambda_reg / n (the penalty averaged over
+    # Gaussians): with the L1 term a per-pixel mean, the plain sum closes every
+    # gate within a frame, unlike the few percent of open gates the paper reports.
+    lreg_mean: bool = True
     lr_gate: float = 0.1
     lr_pos: float = 0.00016
     # per decoder category (rotation, scale, opacity, colour)
@@ -96,9 +100,14 @@ class QueenFrame:
         B.qn_decode_residuals(self.n, self.S, self.n_attr, self.prev, self.lat, self.dec_bf16, self.c_layout,
                               self.lp, self.log_alpha, self.c_gate, self.attrs, self.gate, self.lreg, stream)
 
+    @property
+    def d_lreg(self) -> float:
+        """dL_total / dL_reg of Eq. 11."""
+        return self.hp.lambda_reg / max(1, self.n) if self.hp.lreg_mean else self.hp.lambda_reg
+
     def decode_bwd(self, skip=None, stream=None):
         B.qn_decode_residuals_bwd(self.n, self.S, self.n_attr, self.lat, self.dec_bf16, self.c_layout, self.lp,
-                                  self.log_alpha, self.c_gate, self.d_attrs, self.hp.lambda_reg, skip, self.d_lat,
+                                  self.log_alpha, self.c_gate, self.d_attrs, self.d_lreg, skip, self.d_lat,
                                   self.d_dec, self.d_lp, self.d_log_alpha, stream)
 
     def adam(self, skip=None, stream=None):

@@ -181,3 +181,60 @@ def make_bin_inputs(n: int, tiles_x: int, tiles_y: int, seed: int, max_extent: i
     x0[empty] = x1[empty] = y0[empty] = y1[empty] = 0
     rect = np.stack([x0, y0, x1, y1]).astype(np.int32)
     return depth, rect
+
+
+@dataclass
+class Motion:
+    """Ground-truth motion of a synthetic streaming sequence: a random
+    `frac` of the Gaussians rotate rigidly about the world y axis through the
+    origin by `deg_per_frame` per frame and jitter by
+    amp sin(2 pi t / period + phi_i) u_i (u_i uniform on the sphere)."""
+    dynamic: np.ndarray    # [n] bool
+    phase: np.ndarray      # [n]
+    direction: np.ndarray  # [3][n]
+    deg_per_frame: float = 0.5
+    amp: float = 0.01
+    period: float = 30.0
+
+
+def make_motion(n: int, frac: float = 0.1, seed: int = 0, deg_per_frame: float = 0.5, amp: float = 0.01,
+                period: float = 30.0, positions: np.ndarray | None = None,
+                centre=(0.0, 0.0, 1.0)) -> Motion:
+    """With `positions` ([3][n]) the dynamic set is a rigid object: the
+    frac * n Gaussians nearest `centre` (by default the middle of the cube face
+    the cameras look at, so the object is visible); without, a uniformly random
+    subset."""
+    rng = np.random.Generator(np.random.PCG64(seed + 4242))
+    dyn = np.zeros(n, bool)
+    k = int(round(frac * n))
+    if positions is not None:
+        d2 = ((np.asarray(positions, np.float64) - np.asarray(centre, np.float64)[:, None]) ** 2).sum(axis=0)
+        dyn[np.argsort(d2, kind="stable")[:k]] = True
+    else:
+        dyn[rng.choice(n, size=k, replace=False)] = True
+    u = rng.standard_normal((3, n))
+    u /= np.linalg.norm(u, axis=0, keepdims=True)
+    return Motion(dyn, rng.uniform(0, 2 * math.pi, n), u, deg_per_frame, amp, period)
+
+
+def frame_attrs(A0: np.ndarray, motion: Motion, t: int) -> np.ndarray:
+    """Raw attributes of frame t (frame 0 is A0): positions and orientations of
+    the dynamic Gaussians follow the motion, everything else is unchanged."""
+    A = A0.copy()
+    d = motion.dynamic
+    th = math.radians(motion.deg_per_frame * t)
+    c, s = math.cos(th), math.sin(th)
+    x, y, z = A0[0, d].astype(np.float64), A0[1, d].astype(np.float64), A0[2, d].astype(np.float64)
+    jit = motion.amp * (np.sin(2 * math.pi * t / motion.period + motion.phase[d])
+                        - np.sin(motion.phase[d]))[None, :] * motion.direction[:, d]
+    A[0, d] = c * x + s * z + jit[0]
+    A[1, d] = y + jit[1]
+    A[2, d] = -s * x + c * z + jit[2]
+    # orientation: q_t = q_y(th) * q_0 with q_y(th) = (cos th/2, 0, sin th/2, 0)
+    hw, hy = math.cos(th / 2), math.sin(th / 2)
+    w0, x0, y0, z0 = (A0[3 + k, d].astype(np.float64) for k in range(4))
+    A[3, d] = hw * w0 - hy * y0
+    A[4, d] = hw * x0 + hy * z0
+    A[5, d] = hw * y0 + hy * w0
+    A[6, d] = hw * z0 - hy * x0
+    return A

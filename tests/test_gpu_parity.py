@@ -342,14 +342,15 @@ def test_decode_bwd_matches_oracle(n, deg, seed):
     from paper_2412_04469_gb300.pipeline import QueenFrame
     lay, prev, res = _decode_problem(n, deg, seed)
     res.log_alpha[: n // 2] = np.linspace(-1, 1, n // 2)      # inside the open gate interval
-    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    from paper_2412_04469_gb300.pipeline import HParams
+    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha, HParams(lreg_mean=False))
     rng = np.random.default_rng(seed)
     d_out = rng.standard_normal((prev.shape[0], n)).astype(np.float32)
     f.d_attrs[:, :n] = up(d_out)
     skip = (rng.uniform(size=n) < 0.2).astype(np.uint8)
     f.decode_bwd(skip=up(skip, torch.uint8))
     torch.cuda.synchronize()
-    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, d_out, f.hp.lambda_reg,
+    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, d_out, f.d_lreg,
                              skip=skip)
     close(f.d_lat.cpu().numpy()[:, :n], want[0], floor_frac=GRAD_FLOOR, what="d_lat")
     close(f.d_dec.cpu().numpy(), want[1], floor_frac=GRAD_FLOOR, what="d_dec")
@@ -433,7 +434,7 @@ def test_end_to_end_gradients_match_oracle_chain():
     close(r.d_img.cpu().numpy(), g_ref, floor_frac=GRAD_FLOOR, what="d_img")
     g2 = oracle.render_bwd(proj, g_ref, bg)
     dA = oracle.project_bwd(A_ref, cam, deg, g2["d_mean2d"], g2["d_conic"], g2["d_opac"], g2["d_rgb"], blur=0.3)
-    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, dA, f.hp.lambda_reg)
+    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, dA, f.d_lreg)
     close(f.d_attrs.cpu().numpy()[:, :n], dA, floor_frac=GRAD_FLOOR, what="d_attrs")
     close(f.d_lat.cpu().numpy()[:, :n], want[0], floor_frac=GRAD_FLOOR, what="d_lat")
     close(f.d_dec.cpu().numpy(), want[1], floor_frac=GRAD_FLOOR, what="d_dec")

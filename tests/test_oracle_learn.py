@@ -23,13 +23,18 @@ def test_l1_closed_form():
 
 def test_gate_init_median_rule_and_round_trip():
     d = np.array([[3.0, 1.0, 2.0, 0.0], [0.0, 0.0, 0.0, 0.0]])
-    la, nrm, med = oracle.gate_init(d, TAU, G0, G1)
+    la, nrm, med = oracle.gate_init(d, TAU, G0, G1, nonzero_median=False)
     assert med == 1.0                                   # lower median of (0, 1, 2, 3)
     p = 1 / (1 + np.exp(-(la - TAU * math.log(-G0 / G1))))
     assert p == pytest.approx([0.75, 0.5, 2 / 3, 1e-6], rel=1e-9)
-    la0, _, med0 = oracle.gate_init(np.array([[0.0, 0.0, 5.0], [0.0, 0.0, 0.0]]), TAU, G0, G1)
+    la0, _, med0 = oracle.gate_init(np.array([[0.0, 0.0, 5.0], [0.0, 0.0, 0.0]]), TAU, G0, G1, nonzero_median=False)
     p0 = 1 / (1 + np.exp(-(la0 - TAU * math.log(-G0 / G1))))
     assert med0 == 0.0 and p0 == pytest.approx([1e-6, 1e-6, 1 - 1e-6], rel=1e-9)
+    # median over the non-zero scores only: (1, 2, 3) -> 2; zero scores get p = 0 (clamped)
+    la2, _, med2 = oracle.gate_init(d, TAU, G0, G1)
+    p2 = 1 / (1 + np.exp(-(la2 - TAU * math.log(-G0 / G1))))
+    assert med2 == 2.0 and p2 == pytest.approx([0.6, 1 / 3, 0.5, 1e-6], rel=1e-9)
+    assert oracle.gate_init(np.zeros((2, 3)), TAU, G0, G1)[2] == 0.0
 
 
 def test_viewspace_score_linearity_and_zero():
@@ -145,3 +150,27 @@ def test_chain_decode_project_render_finite_differences():
             assert fd == pytest.approx(gx.reshape(-1)[j], rel=1e-4, abs=1e-7), (name, j)
             checked += 1
     assert checked >= 60
+
+
+def test_skip_features_hand_example():
+    # two Gaussians: |d| = (5, 0) -> lower median of (0, 5) is 0 -> p = (1, 0)
+    score = np.array([[3.0, 0.0], [4.0, 0.0]])
+    prev = np.zeros((14, 2))
+    prev[0:3, 0] = [0.1, 0.2, 0.3]
+    prev[7:10, 1] = [-3.0, -1.0, -5.0]
+    prev[10] = [0.0, 100.0]
+    X = oracle.skip_features(score, prev, np.array([0.5, 0.0]), np.array([TAU * math.log(-G0 / G1), 0.0]),
+                             np.array([[0.01, 0.0], [0.0, 0.0], [0.0, 0.0]]), TAU, G0, G1, nonzero_median=False)
+    assert list(X[0]) == [1.0, 0.0] and list(X[1]) == [0.0, 0.0]
+    assert X[2, 0] == pytest.approx(0.6) and X[3, 0] == pytest.approx(0.8) and X[2, 1] == 0.0
+    assert list(X[4:7, 0]) == [0.1, 0.2, 0.3]
+    assert list(X[7]) == [0.5, 0.0] and X[8, 0] == pytest.approx(0.5)
+    assert X[9, 0] == 0.5 and X[9, 1] == pytest.approx(1.0)
+    assert list(X[10:13, 1]) == [0.0, 1.0, -1.0]
+    assert X[13, 0] == pytest.approx(0.5) and X[13, 1] == 0.0
+    assert list(X[14]) == [0.0, 1.0] and list(X[15]) == [1.0, 1.0]
+    # a positive median switches on the log-ratio feature
+    X2 = oracle.skip_features(np.array([[1.0, 2.0, 4.0], [0.0, 0.0, 0.0]]), np.zeros((14, 3)), np.zeros(3),
+                              np.zeros(3), np.zeros((3, 3)), TAU, G0, G1, nonzero_median=False)
+    assert X2[0] == pytest.approx([1 / 3, 0.5, 2 / 3])
+    assert X2[1] == pytest.approx(np.log(np.array([0.5, 1.0, 2.0]) + 1e-6) / 4)
