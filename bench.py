@@ -36,8 +36,8 @@ WORKLOADS = {
 METRIC = "fwd+bwd rasterize it/s @300k Gaussians 1352x1014; s/frame learned vs plain @dPSNR<=.05"
 L2_FLUSH_BYTES = 256 << 20
 # kernels each C-ABI call launches (memsets are not counted)
-KERNELS_PER_CALL = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 1, "render_bwd": 1,
-                    "project_bwd": 1, "decode_bwd": 1}
+KERNELS_PER_CALL = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 2, "render_bwd": 2,
+                    "project_bwd": 1, "decode_bwd": 2}
 STAGES = ["decode", "project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "decode_bwd", "adam"]
 
 

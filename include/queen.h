@@ -48,6 +48,9 @@ enum {
 #define QN_MAX_LATENT 16      /* latent width per category */
 #define QN_MAX_TILES_X 256    /* image width  <= 4096 */
 #define QN_MAX_TILES_Y 256    /* image height <= 4096 */
+#define QN_DECODE_BWD_BLOCKS 512  /* per-block partials of the decoder gradient */
+#define QN_MLP_BWD_BLOCKS 256     /* per-block partials of the MLP gradient */
+#define QN_LOSS_BLOCKS 2048       /* per-block partials of the image loss */
 
 typedef void *qn_stream_t;    /* cudaStream_t */
 
@@ -126,14 +129,16 @@ int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, const float
  * skip (nullable, [n] u8): Gaussians with skip != 0 get zero d_lat, d_lp,
  * d_log_alpha and add nothing to d_dec.
  *   d_lat [sum lat_dim][n_stride], d_dec [sum attr_count*lat_dim], d_lp [3][n_stride],
- *   d_log_alpha [n]: written.  d_dec is zeroed on `stream` first.
+ *   d_log_alpha [n]: written.
+ *   partials [QN_DECODE_BWD_BLOCKS * sum attr_count*lat_dim] f32: scratch for
+ *     per-block partial sums of d_dec, added in block order (reproducible).
  */
 int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_attr, const float *lat,
                             const uint16_t *dec, const qn_decoder_layout *layout_host,
                             const float *lp, const float *log_alpha,
                             const qn_gate_params *gate_host, const float *d_out, float d_lreg,
                             const uint8_t *skip, float *d_lat, float *d_dec, float *d_lp,
-                            float *d_log_alpha, qn_stream_t stream);
+                            float *d_log_alpha, float *partials, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* EWA projection and SH colour -- Sec. 3.1, Eq. 1.                          */
@@ -261,20 +266,39 @@ int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
                   uint32_t *last, uint32_t *n_contrib, qn_stream_t stream);
 
 /*
- * Adjoint of qn_render_fwd for d_img [3][H][W]: walks each pixel's list from
- * its last contributor back to the front, rebuilding T by division by
- * (1 - alpha) and carrying the colour behind each Gaussian:
+ * Adjoint of qn_render_fwd for d_img [3][H][W], first half: walks each
+ * pixel's list from its last contributor back to the front, rebuilding T by
+ * division by (1 - alpha) and carrying the colour behind each Gaussian:
  *   dC/dc_k = alpha_k T_k, dC/dalpha_k = T_k (c_k - B_k), B_last = bg,
  *   B_{k-1} = alpha_k c_k + (1 - alpha_k) B_k; the 0.99 cap passes zero
  *   gradient to opacity, conic and mean.
- * Gradients are summed per Gaussian into d_splats[n] (zeroed first on `stream`,
- * n = number of splats).  skip (nullable, [n] u8): no gradient is written for
- * Gaussians with skip != 0.
+ * Per tile, the gradients of each Gaussian are summed over the tile's pixels
+ * (warp reduce-scatter, then a fixed-order sum over warps; no atomics) and
+ * written as one record per visited list position:
+ *   pair_grads [pair_capacity] qn_splat: record of sorted pair p (written only
+ *     for the visited positions ranges[t][0] .. ranges[t][0] + tile_visited[t] - 1
+ *     of non-skipped Gaussians)
+ *   tile_visited [n_tiles] u32: length of each tile's visited prefix (written)
+ * qn_bin_gather then sums the records per Gaussian.  skip (nullable, [n] u8):
+ * no record is written for Gaussians with skip != 0.
  */
 int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
-                  const qn_splat *splats, int32_t n, const float *bg_host, const float *T_final,
+                  const qn_splat *splats, const float *bg_host, const float *T_final,
                   const uint32_t *last, const float *d_img, const uint8_t *skip,
-                  qn_splat *d_splats, qn_stream_t stream);
+                  qn_splat *pair_grads, uint32_t *tile_visited, qn_stream_t stream);
+
+/*
+ * Second half of the compositing adjoint, the adjoint of the binning scatter:
+ * d_splats[i] = sum over the tiles of Gaussian i's rect (row-major order) of
+ * the record of its pair when that pair lies in the tile's visited prefix;
+ * zero for culled and skipped Gaussians.  The fixed summation order makes the
+ * result reproducible bit for bit.  workspace must still hold the state of the
+ * qn_bin_sort call that produced the pairs (same n, rects, tile grid);
+ * d_splats [n] qn_splat is overwritten.
+ */
+int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, int32_t tiles_y, const void *workspace,
+                  size_t workspace_bytes, const uint32_t *tile_visited, const qn_splat *pair_grads,
+                  const uint8_t *skip, qn_splat *d_splats, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Loss and optimiser steps of the training iteration (Eq. 3, Eq. 11).       */
@@ -285,10 +309,12 @@ int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
  *   loss[0] = w mean |img - target|, d_img = w sign(img - target) / count
  * (both written; sign(0) = 0).  With mse != 0 the squared error is used
  * instead (loss[0] = w mean (img - target)^2, d_img = 2 w (img - target) / count),
- * the loss of Eq. 9.  img, target, d_img: count floats.
+ * the loss of Eq. 9.  img, target, d_img: count floats.  partials
+ * [QN_LOSS_BLOCKS] f32: scratch for per-block sums, added in block order (the
+ * loss is reproducible bit for bit).
  */
 int qn_image_loss(int64_t count, const float *img, const float *target, float w, int32_t mse,
-                  float *loss, float *d_img, qn_stream_t stream);
+                  float *loss, float *d_img, float *partials, qn_stream_t stream);
 
 /*
  * Adam (Kingma & Ba) on `rows` planes of n elements with stride `stride`:
@@ -383,9 +409,11 @@ int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *g
  * labels [n] u8 (1 = static) over the n rows of X: d_params [QN_MLP_PARAMS]
  * f32 and loss [1] (nullable) are overwritten.  A row range [r0, r0 + n) of a
  * larger X is passed as X + r0 with the same n_stride, labels + r0.
+ * partials [QN_MLP_BWD_BLOCKS * (QN_MLP_PARAMS + 1)] f32: scratch for per-block
+ * partial sums, added in block order (reproducible).
  */
 int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, const uint8_t *labels, const uint16_t *params,
-                    float *d_params, float *loss, qn_stream_t stream);
+                    float *d_params, float *loss, float *partials, qn_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -53,8 +53,9 @@ class DecodeGate(torch.autograd.Function):
         d_dec = torch.zeros(ctx.dec_shape, device=lat.device)
         d_lp = torch.zeros_like(lp)
         d_la = torch.zeros_like(log_alpha)
+        partials = torch.zeros(B.QN_DECODE_BWD_BLOCKS * d_dec.numel(), device=lat.device)
         B.qn_decode_residuals_bwd(a.n, a.n_stride, a.n_attr, lat, dec_bf16, a.layout, lp, log_alpha, a.gate, d_out,
-                                  dl, None, d_lat, d_dec, d_lp, d_la)
+                                  dl, None, d_lat, d_dec, d_lp, d_la, partials)
         return None, d_lat, d_dec, d_lp, d_la, None
 
 
@@ -96,9 +97,12 @@ class Rasterize(torch.autograd.Function):
         r = args.rast
         if splat.data_ptr() != r.splats.data_ptr():
             r.splats.copy_(splat)
-        P = r.bin_sort(sync=True) if r.capacity > 0 else 0
-        if P > r.capacity:
-            r.set_capacity(int(P * 1.25) + 1024)
+        try:
+            r.bin_sort(sync=True)
+        except B.QueenError as e:
+            if e.code != B.QN_ERR_CAPACITY:
+                raise
+            r.set_capacity(int(int(r.n_pairs.item()) * 1.25) + 1024)
             r.bin_sort(sync=True)
         r.render_fwd(args.cam, args.bg)
         ctx.args = args

@@ -49,21 +49,22 @@ _SIGS = {
     "qn_last_error": ([], C.c_char_p),
     "qn_version": ([], C.c_char_p),
     "qn_decode_residuals": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P],
-                                C.c_int),
+    "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P,
+                                 _P], C.c_int),
     "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
     "qn_project_bwd": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_workspace_size": ([_I32, _I32, _I32], _SZ),
     "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_noalloc": ([_I32, _P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_render_bwd": ([_P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
+    "qn_render_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_bin_gather": ([_I32, _P, _I32, _I32, _P, _SZ, _P, _P, _P, _P, _P], C.c_int),
+    "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_viewspace_accum": ([_I32, _I32, _P, _F32, _P, _P], C.c_int),
     "qn_gate_init": ([_I32, _I32, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
     "qn_skip_features": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_skip_mlp_fwd": ([_I32, _I32, _P, _P, _F32, _P, _P, _P], C.c_int),
-    "qn_skip_mlp_bwd": ([_I32, _I32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_skip_mlp_bwd": ([_I32, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_skip_labels": ([_I32, _I32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
 }
@@ -145,12 +146,17 @@ def qn_decode_residuals(n, n_stride, n_attr, prev, lat, dec, layout, lp, log_alp
                                      _ptr(lreg), _stream(stream)))
 
 
+QN_DECODE_BWD_BLOCKS = 512
+QN_MLP_BWD_BLOCKS = 256
+
+
 def qn_decode_residuals_bwd(n, n_stride, n_attr, lat, dec, layout, lp, log_alpha, gate_params, d_out, d_lreg,
-                            skip, d_lat, d_dec, d_lp, d_log_alpha, stream=None):
+                            skip, d_lat, d_dec, d_lp, d_log_alpha, partials, stream=None):
+    """partials: QN_DECODE_BWD_BLOCKS * d_dec.numel() floats of scratch."""
     _check(lib().qn_decode_residuals_bwd(n, n_stride, n_attr, _ptr(lat), _ptr(dec), C.byref(layout), _ptr(lp),
                                          _ptr(log_alpha), C.byref(gate_params), _ptr(d_out), float(d_lreg),
                                          _ptr(skip), _ptr(d_lat), _ptr(d_dec), _ptr(d_lp), _ptr(d_log_alpha),
-                                         _stream(stream)))
+                                         _ptr(partials), _stream(stream)))
 
 
 def qn_project(n, n_stride, sh_degree, attrs, cam, blur, splats, rects, tight_rects=True, stream=None):
@@ -199,14 +205,33 @@ def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=N
                                _ptr(T_final), _ptr(last), _ptr(n_contrib), _stream(stream)))
 
 
-def qn_render_bwd(cam, ranges, vals, splats, n, bg, T_final, last, d_img, skip, d_splats, stream=None):
-    _check(lib().qn_render_bwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), n, _bg(bg), _ptr(T_final),
-                               _ptr(last), _ptr(d_img), _ptr(skip), _ptr(d_splats), _stream(stream)))
-
-
-def qn_image_loss(count, img, target, w, mse, loss, d_img, stream=None):
-    _check(lib().qn_image_loss(count, _ptr(img), _ptr(target), float(w), int(mse), _ptr(loss), _ptr(d_img),
+def qn_render_bwd(cam, ranges, vals, splats, bg, T_final, last, d_img, skip, pair_grads, tile_visited,
+                  stream=None):
+    _check(lib().qn_render_bwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg), _ptr(T_final),
+                               _ptr(last), _ptr(d_img), _ptr(skip), _ptr(pair_grads), _ptr(tile_visited),
                                _stream(stream)))
+
+
+def qn_bin_gather(n, rects, tiles_x, tiles_y, workspace, tile_visited, pair_grads, skip, d_splats, stream=None):
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().qn_bin_gather(n, _ptr(rects), tiles_x, tiles_y, _ptr(workspace), ws_bytes, _ptr(tile_visited),
+                               _ptr(pair_grads), _ptr(skip), _ptr(d_splats), _stream(stream)))
+
+
+QN_LOSS_BLOCKS = 2048
+_loss_scratch = {}
+
+
+def qn_image_loss(count, img, target, w, mse, loss, d_img, partials=None, stream=None):
+    """partials: QN_LOSS_BLOCKS floats of scratch (one per device is kept here
+    when not given)."""
+    if partials is None:
+        dev = loss.device
+        if dev not in _loss_scratch:
+            _loss_scratch[dev] = torch.zeros(QN_LOSS_BLOCKS, device=dev)
+        partials = _loss_scratch[dev]
+    _check(lib().qn_image_loss(count, _ptr(img), _ptr(target), float(w), int(mse), _ptr(loss), _ptr(d_img),
+                               _ptr(partials), _stream(stream)))
 
 
 def qn_adam(rows, n, stride, param, grad, m, v, step, lr, beta1, beta2, eps, skip=None, param_bf16=None,
@@ -240,9 +265,10 @@ def qn_skip_mlp_fwd(n, n_stride, X, params_bf16, threshold, logits=None, skip=No
                                  _ptr(skip), _stream(stream)))
 
 
-def qn_skip_mlp_bwd(n, n_stride, X, labels, params_bf16, d_params, loss=None, stream=None):
+def qn_skip_mlp_bwd(n, n_stride, X, labels, params_bf16, d_params, loss, partials, stream=None):
+    """partials: QN_MLP_BWD_BLOCKS * (QN_MLP_PARAMS + 1) floats of scratch."""
     _check(lib().qn_skip_mlp_bwd(n, n_stride, _ptr(X), _ptr(labels), _ptr(params_bf16), _ptr(d_params),
-                                 _ptr(loss), _stream(stream)))
+                                 _ptr(loss), _ptr(partials), _stream(stream)))
 
 
 def qn_skip_labels(n, n_stride, n_latent, gate, lat, labels, stream=None):

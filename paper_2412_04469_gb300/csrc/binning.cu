@@ -198,10 +198,10 @@ struct ChunkSmem {
     int ux0, uy0, ux1, uy1;
 };
 
-// Loads chunk c of the depth-sorted visible Gaussians and builds, per warp,
-// the bitmask of members covering each tile column and each tile row.
-__device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
-                           const int4 *__restrict__ rects, uint32_t n_vis, ChunkSmem &s) {
+// Loads chunk c of the depth-sorted visible Gaussians (ids, rects, union
+// bounding box of the rects).
+__device__ void load_chunk_rects(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
+                                 const int4 *__restrict__ rects, uint32_t n_vis, ChunkSmem &s) {
     const int j = threadIdx.x, warp = j >> 5;
     const uint32_t g = (uint32_t)c * CHUNK + j;
     int4 r = make_int4(0, 0, 0, 0);
@@ -229,6 +229,14 @@ __device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ s
         atomicMin(&s.ux0, x0); atomicMin(&s.uy0, y0);
         atomicMax(&s.ux1, x1); atomicMax(&s.uy1, y1);
     }
+    __syncthreads();
+}
+
+// Builds, per warp, the bitmask of the chunk's members covering each tile
+// column and each tile row (after load_chunk_rects).
+__device__ void build_masks(int TX, int TY, ChunkSmem &s) {
+    const int j = threadIdx.x, warp = j >> 5;
+    const int4 r = s.rect[j];
     for (int tx = 0; tx < TX; ++tx) {
         const unsigned b = __ballot_sync(FULL, r.x <= tx && tx < r.z);
         if ((j & 31) == 0) s.mx[warp][tx] = b;
@@ -238,6 +246,12 @@ __device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ s
         if ((j & 31) == 0) s.my[warp][ty] = b;
     }
     __syncthreads();
+}
+
+__device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
+                           const int4 *__restrict__ rects, uint32_t n_vis, ChunkSmem &s) {
+    load_chunk_rects(c, TX, TY, sorted, rects, n_vis, s);
+    build_masks(TX, TY, s);
 }
 
 __device__ __forceinline__ uint32_t chunk_count(const ChunkSmem &s, int tx, int ty) {
@@ -426,6 +440,82 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
     }
 }
 
+// Adjoint of the pair scatter: each visible Gaussian sums the per-pair
+// gradient records of the visited positions of its tiles, walking its rect in
+// row-major order (one warp per Gaussian, a fixed lane assignment and a fixed
+// butterfly) -- so the sums are reproducible.  Chunks are
+// in depth order and each tile's visited prefix holds its front-most pairs, so
+// most chunks have no visited pair at all: a chunk first marks, in a shared
+// bitmask, the tiles where its first slot lies inside the visited prefix, and
+// returns at once when there are none.
+__global__ void __launch_bounds__(CHUNK) k_bin_gather(int TX, int TY, const uint32_t *__restrict__ sorted,
+                                                      const int4 *__restrict__ rects, const Header *hdr,
+                                                      const uint32_t *__restrict__ gbase,
+                                                      const uint32_t *__restrict__ tile_off,
+                                                      const uint32_t *__restrict__ visited,
+                                                      const float4 *__restrict__ pair_grads,
+                                                      const uint8_t *__restrict__ skip, float4 *__restrict__ out) {
+    __shared__ ChunkSmem s;
+    __shared__ uint32_t active[QN_MAX_TILES_X * QN_MAX_TILES_Y / 32];
+    const int c = blockIdx.x;
+    const uint32_t n_vis = hdr->n_vis;
+    if (hdr->overflow || (uint32_t)c * CHUNK >= n_vis) return;
+    const int n_tiles = TX * TY;
+    const uint32_t *grow = gbase + (size_t)c * n_tiles;
+    load_chunk_rects(c, TX, TY, sorted, rects, n_vis, s);
+    // pass 1: active tiles of the chunk's bounding box, one bit per grid tile;
+    // each warp covers whole 32-tile words with coalesced loads and a ballot
+    const int lane = threadIdx.x & 31;
+    int any = 0;
+    const int w0 = (s.uy0 * TX + s.ux0) >> 5;
+    const int w1 = s.uy1 > s.uy0 ? ((s.uy1 - 1) * TX + s.ux1 - 1) / 32 + 1 : w0;
+    for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += CHUNK / 32) {
+        const int t = w * 32 + lane;
+        const int tx = t % TX, ty = t / TX;
+        const bool in_box = t < n_tiles && tx >= s.ux0 && tx < s.ux1 && ty >= s.uy0 && ty < s.uy1;
+        const unsigned bits = __ballot_sync(FULL, in_box && grow[t] < visited[t]);
+        if (lane == 0) active[w] = bits;
+        any |= bits != 0;
+    }
+    if (!__syncthreads_or(any)) return;
+    build_masks(TX, TY, s);
+    // pass 2: one warp per Gaussian; lane l takes the Gaussian's tiles l, l + 32,
+    // ... in row-major order and a fixed butterfly sums the lanes
+    const int warp = threadIdx.x >> 5;
+    for (int j = warp; j < CHUNK; j += CHUNK / 32) {
+        const uint32_t g = (uint32_t)c * CHUNK + j;
+        if (g >= n_vis) break;
+        const uint32_t id = s.id[j];
+        if (skip && skip[id]) continue;
+        const int4 r = s.rect[j];
+        const int rw = r.z - r.x, area = rw * (r.w - r.y);
+        const int wj = j >> 5;
+        const unsigned below = (1u << (j & 31)) - 1u;
+        float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = lane; k < area; k += 32) {
+            const int tx = r.x + k % rw, ty = r.y + k / rw;
+            const int t = ty * TX + tx;
+            if (!((active[t >> 5] >> (t & 31)) & 1u)) continue;
+            uint32_t rank = __popc(s.mx[wj][tx] & s.my[wj][ty] & below);
+            for (int w = 0; w < wj; ++w) rank += __popc(s.mx[w][tx] & s.my[w][ty]);
+            const uint32_t base = grow[t];
+            if (base + rank >= visited[t]) continue;
+            const float4 *p = pair_grads + 3 * (size_t)(tile_off[t] + base + rank);
+            const float4 b0 = p[0], b1 = p[1], b2 = p[2];
+            acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
+            acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
+            acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+            out[3 * (size_t)id] = make_float4(acc[0], acc[1], acc[2], 0.f);
+            out[3 * (size_t)id + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
+            out[3 * (size_t)id + 2] = make_float4(acc[6], acc[7], acc[8], 0.f);
+        }
+    }
+}
+
 }  // namespace
 }  // namespace qn
 
@@ -504,6 +594,34 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
         }
     }
     return QN_OK;
+}
+
+extern "C" int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, int32_t tiles_y,
+                             const void *workspace, size_t workspace_bytes, const uint32_t *tile_visited,
+                             const qn_splat *pair_grads, const uint8_t *skip, qn_splat *d_splats,
+                             qn_stream_t stream) {
+    using namespace qn;
+    QN_REQUIRE(n >= 0, "n must be >= 0");
+    QN_REQUIRE(tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
+               "tile grid %dx%d out of range", tiles_x, tiles_y);
+    QN_REQUIRE(n == 0 || (rects && workspace && tile_visited && pair_grads && d_splats), "null pointer argument");
+    QN_REQUIRE(((uintptr_t)d_splats & 15) == 0 && ((uintptr_t)pair_grads & 15) == 0 &&
+                   ((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
+               "misaligned pointer argument");
+    const int n_tiles = tiles_x * tiles_y;
+    const Layout L = layout_of(n, n_tiles);
+    QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) return QN_OK;
+    if (cudaMemsetAsync(d_splats, 0, sizeof(qn_splat) * (size_t)n, s) != cudaSuccess)
+        return check_launch("qn_bin_gather memset");
+    const char *ws = static_cast<const char *>(workspace);
+    k_bin_gather<<<div_up(n, CHUNK), CHUNK, 0, s>>>(
+        tiles_x, tiles_y, reinterpret_cast<const uint32_t *>(ws + L.vals0), reinterpret_cast<const int4 *>(rects),
+        reinterpret_cast<const Header *>(ws + L.hdr), reinterpret_cast<const uint32_t *>(ws + L.counts),
+        reinterpret_cast<const uint32_t *>(ws + L.tile_off), tile_visited,
+        reinterpret_cast<const float4 *>(pair_grads), skip, reinterpret_cast<float4 *>(d_splats));
+    return check_launch("qn_bin_gather");
 }
 
 // ---------------------------------------------------------------- no-allocation variant

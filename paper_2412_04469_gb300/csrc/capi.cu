@@ -28,6 +28,18 @@ int check_launch(const char *what) {
     return QN_OK;
 }
 
+__global__ void k_sum_partials(int count, int blocks, const float *__restrict__ partials, float *__restrict__ out) {
+    // one warp per entry: lane l adds blocks l, l + 32, ... in order, then a
+    // fixed butterfly combines the lanes
+    const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= count) return;
+    float s = 0.f;
+    for (int b = lane; b < blocks; b += 32) s += partials[(size_t)b * count + e];
+    s = warp_sum(s);
+    if (lane == 0) out[e] = s;
+}
+
 }  // namespace qn
 
 extern "C" const char *qn_last_error(void) { return g_err; }

@@ -35,6 +35,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// out[e] = sum over b < blocks of partials[b * count + e] in a fixed order
+// (a reproducible reduction of per-block partial sums); launch with
+// 32 * count threads.
+__global__ void k_sum_partials(int count, int blocks, const float *__restrict__ partials, float *__restrict__ out);
+
+inline int sum_partials_grid(int count) { return (int)(((int64_t)count * 32 + 255) / 256); }
+
 __device__ __forceinline__ int div_up_dev(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace qn

@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
 // Adjoint, one fused kernel: a block stages 32 Gaussians' residual gradients
 // dr and rounded latents l in shared memory, then writes d_lat = D^T dr per
 // (Gaussian, latent) and accumulates its share of dD = sum dr l^T in
-// registers; one atomic per decoder entry per block at the end.
+// registers; each block writes its partial dD, and a second kernel sums the
+// partials in block order (no atomics: reproducible).
 constexpr int BWD_THREADS = 256;
 constexpr int BWD_TILE = 32;
 constexpr int BWD_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + BWD_THREADS - 1) / BWD_THREADS;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
     DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
     const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
     float d_lreg, const uint8_t *__restrict__ skip, float *__restrict__ d_lat,
-    float *__restrict__ d_dec, float *__restrict__ d_lp, float *__restrict__ d_la) {
+    float *__restrict__ partials, float *__restrict__ d_lp, float *__restrict__ d_la) {
     __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
     __shared__ float s_dr[MAX_RES_PLANES][BWD_TILE + 1];   // +1: different rows, different banks
     __shared__ float s_l[MAX_LAT_TOTAL][BWD_TILE + 1];
@@ -179,9 +180,10 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
         }
         __syncthreads();
     }
+    // this block's partial dD; summed over blocks in block order afterwards
 #pragma unroll
     for (int q = 0; q < BWD_OWN; ++q)
-        if (own_c[q] >= 0) atomicAdd(&d_dec[threadIdx.x + q * BWD_THREADS], acc[q]);
+        if (own_c[q] >= 0) partials[(size_t)blockIdx.x * a.n_dec + threadIdx.x + q * BWD_THREADS] = acc[q];
 }
 
 int make_args(int32_t n, int32_t n_stride, int32_t n_attr, const qn_decoder_layout *lay,
@@ -252,17 +254,23 @@ extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_at
                                        const float *lp, const float *log_alpha,
                                        const qn_gate_params *gate_host, const float *d_out,
                                        float d_lreg, const uint8_t *skip, float *d_lat, float *d_dec,
-                                       float *d_lp, float *d_log_alpha, qn_stream_t stream) {
+                                       float *d_lp, float *d_log_alpha, float *partials, qn_stream_t stream) {
     qn::DecodeArgs a;
     int st = qn::make_args(n, n_stride, n_attr, layout_host, gate_host, &a);
     if (st) return st;
     QN_REQUIRE(n == 0 || (d_out && lp && log_alpha && d_lp && d_log_alpha), "null pointer argument");
-    QN_REQUIRE(a.n_cat == 0 || (d_dec && (n == 0 || (lat && dec && d_lat))), "null latent/decoder pointer");
+    QN_REQUIRE(a.n_cat == 0 || (d_dec && (n == 0 || (lat && dec && d_lat && partials))),
+               "null latent/decoder/partials pointer");
     cudaStream_t s = qn::as_stream(stream);
-    if (a.n_dec > 0 && cudaMemsetAsync(d_dec, 0, sizeof(float) * a.n_dec, s) != cudaSuccess)
-        return qn::check_launch("decode_bwd memset");
-    if (n == 0) return QN_OK;
-    qn::k_decode_bwd<<<qn::grid_for(n, qn::BWD_TILE, 4), qn::BWD_THREADS, 0, s>>>(
-        a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat, d_dec, d_lp, d_log_alpha);
+    if (n == 0) {
+        if (a.n_dec > 0 && cudaMemsetAsync(d_dec, 0, sizeof(float) * a.n_dec, s) != cudaSuccess)
+            return qn::check_launch("decode_bwd memset");
+        return QN_OK;
+    }
+    int grid = qn::grid_for(n, qn::BWD_TILE, 4);
+    if (grid > QN_DECODE_BWD_BLOCKS) grid = QN_DECODE_BWD_BLOCKS;
+    qn::k_decode_bwd<<<grid, qn::BWD_THREADS, 0, s>>>(a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat,
+                                                      partials, d_lp, d_log_alpha);
+    if (a.n_dec > 0) qn::k_sum_partials<<<qn::sum_partials_grid(a.n_dec), 256, 0, s>>>(a.n_dec, grid, partials, d_dec);
     return qn::check_launch("qn_decode_residuals_bwd");
 }

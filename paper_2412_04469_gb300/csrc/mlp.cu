@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(256) k_skip_mlp_fwd(int n, int S, const float 
 
 // Fused backward of the mean BCE over rows [0, n): each block walks 32-row
 // tiles, recomputes the forward in shared memory, forms the layer adjoints
-// and accumulates every weight gradient in registers; one atomic per
-// parameter per block at the end.
+// and accumulates every weight gradient in registers; each block writes its
+// partial gradient, summed over blocks in block order by a second kernel.
 constexpr int R = 32;            // rows per tile
 constexpr int BT = 256;          // threads
 constexpr int LD = HID + 1;      // padded row stride
@@ -109,7 +109,7 @@ constexpr int SMEM_FLOATS = QN_MLP_PARAMS + 3 + R * XLD + 4 * R * LD + 2 * R + 8
 __global__ void __launch_bounds__(BT) k_skip_mlp_bwd(int n, int S, const float *__restrict__ X,
                                                      const uint8_t *__restrict__ labels,
                                                      const uint16_t *__restrict__ P, float inv_n,
-                                                     float *__restrict__ dP, float *__restrict__ loss) {
+                                                     float *__restrict__ partials, float *__restrict__ lpart) {
     extern __shared__ float sm[];
     float *w = sm;                                   // QN_MLP_PARAMS (+3 pad)
     float *xs = w + QN_MLP_PARAMS + 3;               // [R][XLD]
@@ -216,21 +216,23 @@ __global__ void __launch_bounds__(BT) k_skip_mlp_bwd(int n, int S, const float *
         }
         __syncthreads();
     }
+    // this block's partial gradient (and loss); summed in block order afterwards
+    float *dP = partials + (size_t)blockIdx.x * QN_MLP_PARAMS;
     {
         const int o = t / 4, jb = t % 4;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) atomicAdd(&dP[OFF_W2 + o * HID + jb + 4 * q], gW2[q]);
+        for (int q = 0; q < 16; ++q) dP[OFF_W2 + o * HID + jb + 4 * q] = gW2[q];
         const int jj = t / 4, mb = t % 4;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) atomicAdd(&dP[OFF_W1 + jj * F + mb + 4 * q], gW1[q]);
+        for (int q = 0; q < 4; ++q) dP[OFF_W1 + jj * F + mb + 4 * q] = gW1[q];
         if (t < HID) {
-            atomicAdd(&dP[OFF_W3 + t], gW3);
-            atomicAdd(&dP[OFF_B2 + t], gb2);
-            atomicAdd(&dP[OFF_B1 + t], gb1);
+            dP[OFF_W3 + t] = gW3;
+            dP[OFF_B2 + t] = gb2;
+            dP[OFF_B1 + t] = gb1;
         }
         if (t == 0) {
-            atomicAdd(&dP[OFF_B3], gb3);
-            if (loss) atomicAdd(loss, lacc * inv_n);
+            dP[OFF_B3] = gb3;
+            lpart[blockIdx.x] = lacc * inv_n;
         }
     }
 }
@@ -285,20 +287,22 @@ extern "C" int qn_skip_mlp_fwd(int32_t n, int32_t n_stride, const float *X, cons
 }
 
 extern "C" int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, const uint8_t *labels,
-                               const uint16_t *params, float *d_params, float *loss, qn_stream_t stream) {
+                               const uint16_t *params, float *d_params, float *loss, float *partials,
+                               qn_stream_t stream) {
     QN_REQUIRE(n >= 1 && n_stride >= n, "bad n / n_stride");
-    QN_REQUIRE(X && labels && params && d_params, "null pointer argument");
+    QN_REQUIRE(X && labels && params && d_params && partials, "null pointer argument");
     cudaStream_t s = qn::as_stream(stream);
-    if (cudaMemsetAsync(d_params, 0, sizeof(float) * QN_MLP_PARAMS, s) != cudaSuccess ||
-        (loss && cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess))
-        return qn::check_launch("qn_skip_mlp_bwd memset");
     const size_t smem = sizeof(float) * qn::SMEM_FLOATS;
     if (cudaFuncSetAttribute(qn::k_skip_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return qn::check_launch("qn_skip_mlp_bwd attribute");
     const int tiles = qn::div_up(n, qn::R);
-    const int grid = tiles < qn::sm_count() ? tiles : qn::sm_count();
-    qn::k_skip_mlp_bwd<<<grid, qn::BT, smem, s>>>(n, n_stride, X, labels, params, 1.f / (float)n, d_params, loss);
+    int grid = tiles < qn::sm_count() ? tiles : qn::sm_count();
+    if (grid > QN_MLP_BWD_BLOCKS) grid = QN_MLP_BWD_BLOCKS;
+    float *lpart = partials + (size_t)QN_MLP_BWD_BLOCKS * QN_MLP_PARAMS;
+    qn::k_skip_mlp_bwd<<<grid, qn::BT, smem, s>>>(n, n_stride, X, labels, params, 1.f / (float)n, partials, lpart);
+    qn::k_sum_partials<<<qn::sum_partials_grid(QN_MLP_PARAMS), 256, 0, s>>>(QN_MLP_PARAMS, grid, partials, d_params);
+    if (loss) qn::k_sum_partials<<<1, 32, 0, s>>>(1, grid, lpart, loss);
     return qn::check_launch("qn_skip_mlp_bwd");
 }
 

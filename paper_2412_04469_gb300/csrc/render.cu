@@ -148,19 +148,20 @@ __global__ void __launch_bounds__(THREADS) k_render_bwd(int W, int H, int TX, co
                                                         const uint32_t *__restrict__ last,
                                                         const float *__restrict__ dimg,
                                                         const uint8_t *__restrict__ skip,
-                                                        float4 *__restrict__ dsp) {
+                                                        float4 *__restrict__ pair_grads,
+                                                        uint32_t *__restrict__ visited) {
     constexpr int BATCH = THREADS;
+    constexpr int WARPS = THREADS / 32;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
-    __shared__ uint32_t sid[BATCH];
     __shared__ int sskip[BATCH];
-    __shared__ float sg[BATCH][9];
+    __shared__ float sg[WARPS][BATCH][9];       // one slot per warp: summed in a fixed order
     __shared__ uint32_t smax;
     const int tile = blockIdx.x;
     const int px = (tile % TX) * QN_TILE + (threadIdx.x % QN_TILE);
     const int py0 = (tile / TX) * QN_TILE + (threadIdx.x / QN_TILE) * PPT;
     const uint32_t beg = ranges[2 * tile];
     const float fx = px + 0.5f;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float T[PPT], dc0[PPT], dc1[PPT], dc2[PPT], B0[PPT], B1[PPT], B2[PPT];
     uint32_t lastp[PPT];
     uint32_t mymax = 0;
@@ -181,17 +182,17 @@ __global__ void __launch_bounds__(THREADS) k_render_bwd(int W, int H, int TX, co
         mymax = max(mymax, lastp[q]);
     }
     if (threadIdx.x == 0) smax = 0;
-    for (int k = threadIdx.x; k < BATCH * 9; k += THREADS) (&sg[0][0])[k] = 0.f;
     __syncthreads();
     const uint32_t wmax = __reduce_max_sync(FULL, mymax);
     if (lane == 0) atomicMax(&smax, wmax);
     __syncthreads();
     const int n = (int)smax;
+    if (threadIdx.x == 0) visited[tile] = (uint32_t)n;
     for (int hi = n; hi > 0; hi -= BATCH) {
         const int lo = max(0, hi - BATCH);
+        for (int k = threadIdx.x; k < WARPS * BATCH * 9; k += THREADS) (&sg[0][0][0])[k] = 0.f;
         if (threadIdx.x < hi - lo) {
             const uint32_t id = vals[beg + lo + threadIdx.x];
-            sid[threadIdx.x] = id;
             sskip[threadIdx.x] = skip ? (int)skip[id] : 0;
             s0[threadIdx.x] = sp[3 * (size_t)id];
             s1[threadIdx.x] = sp[3 * (size_t)id + 1];
@@ -233,19 +234,25 @@ __global__ void __launch_bounds__(THREADS) k_render_bwd(int W, int H, int TX, co
             if (sk || !__any_sync(FULL, any)) continue;
             const float v = reduce_scatter8(g, lane);
             const float last_v = warp_sum(g[8]);
-            if ((lane & 3) == 0) atomicAdd(&sg[j][(lane >> 2) & 7], v);
-            if (lane == 0) atomicAdd(&sg[j][8], last_v);
+            if ((lane & 3) == 0) sg[warp][j][(lane >> 2) & 7] = v;
+            if (lane == 0) sg[warp][j][8] = last_v;
         }
         __syncthreads();
+        // one record per visited list position: the tile's sum for that Gaussian
         if (threadIdx.x < hi - lo && !sskip[threadIdx.x]) {
-            const float *vv = sg[threadIdx.x];
-            float4 *d = dsp + 3 * (size_t)sid[threadIdx.x];
-            atomicAdd(d, make_float4(vv[0], vv[1], vv[2], 0.f));
-            atomicAdd(d + 1, make_float4(vv[3], vv[4], vv[5], 0.f));
-            atomicAdd(d + 2, make_float4(vv[6], vv[7], vv[8], 0.f));
+            float r[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                float a = 0.f;
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) a += sg[w][threadIdx.x][q];
+                r[q] = a;
+            }
+            float4 *d = pair_grads + 3 * (size_t)(beg + lo + threadIdx.x);
+            d[0] = make_float4(r[0], r[1], r[2], 0.f);
+            d[1] = make_float4(r[3], r[4], r[5], 0.f);
+            d[2] = make_float4(r[6], r[7], r[8], 0.f);
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < BATCH * 9; k += THREADS) (&sg[0][0])[k] = 0.f;
         __syncthreads();
     }
 }
@@ -277,21 +284,16 @@ extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, 
 }
 
 extern "C" int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
-                             const qn_splat *splats, int32_t n, const float *bg_host, const float *T_final,
+                             const qn_splat *splats, const float *bg_host, const float *T_final,
                              const uint32_t *last, const float *d_img, const uint8_t *skip,
-                             qn_splat *d_splats, qn_stream_t stream) {
+                             qn_splat *pair_grads, uint32_t *tile_visited, qn_stream_t stream) {
     int st = qn::check_render_args(cam_host, ranges, splats);
     if (st) return st;
-    QN_REQUIRE(n >= 0, "n must be >= 0");
-    QN_REQUIRE(T_final && last && d_img && bg_host && (n == 0 || d_splats), "null pointer argument");
-    QN_REQUIRE(((uintptr_t)d_splats & 15) == 0, "d_splats must be 16-byte aligned");
-    cudaStream_t s = qn::as_stream(stream);
-    if (n > 0 && cudaMemsetAsync(d_splats, 0, sizeof(qn_splat) * (size_t)n, s) != cudaSuccess)
-        return qn::check_launch("qn_render_bwd memset");
+    QN_REQUIRE(T_final && last && d_img && bg_host && pair_grads && tile_visited, "null pointer argument");
+    QN_REQUIRE(((uintptr_t)pair_grads & 15) == 0, "pair_grads must be 16-byte aligned");
     const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
-    qn::k_render_bwd<<<TX * TY, qn::THREADS, 0, s>>>(cam_host->width, cam_host->height, TX, ranges, vals,
-                                                    reinterpret_cast<const float4 *>(splats), bg_host[0],
-                                                    bg_host[1], bg_host[2], T_final, last, d_img, skip,
-                                                    reinterpret_cast<float4 *>(d_splats));
+    qn::k_render_bwd<<<TX * TY, qn::THREADS, 0, qn::as_stream(stream)>>>(
+        cam_host->width, cam_host->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg_host[0],
+        bg_host[1], bg_host[2], T_final, last, d_img, skip, reinterpret_cast<float4 *>(pair_grads), tile_visited);
     return qn::check_launch("qn_render_bwd");
 }

@@ -9,7 +9,7 @@ namespace {
 
 __global__ void __launch_bounds__(256) k_image_loss(long long count, const float *__restrict__ img,
                                                     const float *__restrict__ tgt, float scale, int mse,
-                                                    float *__restrict__ loss, float *__restrict__ dimg) {
+                                                    float *__restrict__ partials, float *__restrict__ dimg) {
     __shared__ float red[8];
     float acc = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256) k_image_loss(long long count, const float
     if (threadIdx.x == 0) {
         float s = 0.f;
         for (int w = 0; w < 8; ++w) s += red[w];
-        atomicAdd(loss, s * scale);
+        partials[blockIdx.x] = s * scale;      // summed in block order afterwards
     }
 }
 
@@ -38,10 +38,8 @@ __global__ void __launch_bounds__(256) k_adam(int rows, int n, int stride, float
                                               float *__restrict__ v, float lr, float b1, float b2, float eps,
                                               float ibc1, float ibc2, const uint8_t *__restrict__ skip,
                                               uint16_t *__restrict__ pb) {
-    const long long total = (long long)rows * n;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n), i = (int)(e % n);
+    const int r = blockIdx.y;                      // one grid row per parameter plane
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const size_t o = (size_t)r * stride + i;
         if (skip && skip[i]) continue;
         const float gr = g[o];
@@ -69,14 +67,20 @@ int grid_cap(long long work, int block) {
 }  // namespace qn
 
 extern "C" int qn_image_loss(int64_t count, const float *img, const float *target, float w, int32_t mse,
-                             float *loss, float *d_img, qn_stream_t stream) {
+                             float *loss, float *d_img, float *partials, qn_stream_t stream) {
     QN_REQUIRE(count >= 0, "count must be >= 0");
     QN_REQUIRE(loss && (count == 0 || (img && target && d_img)), "null pointer argument");
     cudaStream_t s = qn::as_stream(stream);
-    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("qn_image_loss memset");
-    if (count == 0) return QN_OK;
+    if (count == 0) {
+        if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("qn_image_loss memset");
+        return QN_OK;
+    }
+    QN_REQUIRE(partials, "partials is required");
     const float scale = (float)((double)w / (double)count);
-    qn::k_image_loss<<<qn::grid_cap(count, 256), 256, 0, s>>>(count, img, target, scale, mse, loss, d_img);
+    int grid = qn::grid_cap(count, 256);
+    if (grid > QN_LOSS_BLOCKS) grid = QN_LOSS_BLOCKS;
+    qn::k_image_loss<<<grid, 256, 0, s>>>(count, img, target, scale, mse, partials, d_img);
+    qn::k_sum_partials<<<1, 32, 0, s>>>(1, grid, partials, loss);
     return qn::check_launch("qn_image_loss");
 }
 
@@ -90,7 +94,10 @@ extern "C" int qn_adam(int32_t rows, int32_t n, int32_t stride, float *param, co
     QN_REQUIRE(param && grad && m && v, "null pointer argument");
     const float ibc1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
     const float ibc2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
-    qn::k_adam<<<qn::grid_cap((long long)rows * n, 256), 256, 0, qn::as_stream(stream)>>>(
+    int gx = qn::grid_cap(n, 256);
+    const int per_row = qn::div_up((int64_t)gx, rows);      // keep the total near the grid cap
+    gx = per_row < 1 ? 1 : per_row;
+    qn::k_adam<<<dim3(gx, rows), 256, 0, qn::as_stream(stream)>>>(
         rows, n, stride, param, grad, m, v, lr, beta1, beta2, eps, ibc1, ibc2, skip, param_bf16);
     return qn::check_launch("qn_adam");
 }

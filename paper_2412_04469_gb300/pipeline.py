@@ -92,6 +92,7 @@ class QueenFrame:
         self.d_dec = torch.zeros_like(self.dec)
         self.d_lp = torch.zeros_like(self.lp)
         self.d_log_alpha = torch.zeros_like(self.log_alpha)
+        self.dec_partials = torch.zeros(B.QN_DECODE_BWD_BLOCKS * max(1, layout.n_dec), device=dev)
         self.opt = {k: _Adam(getattr(self, k).shape, dev) for k in ("lat", "dec", "lp", "log_alpha")}
         self.step_count = 0
 
@@ -108,7 +109,7 @@ class QueenFrame:
     def decode_bwd(self, skip=None, stream=None):
         B.qn_decode_residuals_bwd(self.n, self.S, self.n_attr, self.lat, self.dec_bf16, self.c_layout, self.lp,
                                   self.log_alpha, self.c_gate, self.d_attrs, self.d_lreg, skip, self.d_lat,
-                                  self.d_dec, self.d_lp, self.d_log_alpha, stream)
+                                  self.d_dec, self.d_lp, self.d_log_alpha, self.dec_partials, stream)
 
     def adam(self, skip=None, stream=None):
         self.step_count += 1
@@ -155,6 +156,7 @@ class Rasterizer:
         self.workspace = torch.zeros(max(ws, 256), device=dev, dtype=torch.uint8)
         self.ranges = torch.zeros((self.TX * self.TY, 2), device=dev, dtype=torch.int32)
         self.n_pairs = torch.zeros(1, device=dev, dtype=torch.int64)
+        self.tile_visited = torch.zeros(self.TX * self.TY, device=dev, dtype=torch.int32)
         self.keep_keys = keep_keys
         self.set_capacity(pair_capacity)
         self.img = torch.zeros((3, height, width), device=dev)
@@ -167,6 +169,7 @@ class Rasterizer:
         dev = self.splats.device
         self.capacity = int(cap)
         self.vals = torch.zeros(max(self.capacity, 1), device=dev, dtype=torch.int32)
+        self.pair_grads = torch.zeros((max(self.capacity, 1), 12), device=dev)
         self.keys = torch.zeros(max(self.capacity, 1), device=dev, dtype=torch.int64) if self.keep_keys else None
 
     def project(self, attrs, cam, blur, stream=None):
@@ -186,7 +189,10 @@ class Rasterizer:
         B.qn_image_loss(self.img.numel(), self.img, target, w, mse, self.loss, self.d_img, stream)
 
     def render_bwd(self, cam, bg, skip=None, stream=None):
-        B.qn_render_bwd(cam, self.ranges, self.vals, self.splats, self.n, bg, self.T_final, self.last, self.d_img,
+        """Compositing adjoint: per-pair records, then the per-Gaussian gather."""
+        B.qn_render_bwd(cam, self.ranges, self.vals, self.splats, bg, self.T_final, self.last, self.d_img, skip,
+                        self.pair_grads, self.tile_visited, stream)
+        B.qn_bin_gather(self.n, self.rects, self.TX, self.TY, self.workspace, self.tile_visited, self.pair_grads,
                         skip, self.d_splats, stream)
 
     def project_bwd(self, attrs, cam, blur, d_attrs, skip=None, stream=None):

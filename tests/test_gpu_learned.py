@@ -170,7 +170,8 @@ def test_skip_mlp_forward_and_backward_match_oracle(n):
     B().qn_skip_mlp_fwd(n, Sd, Xd, pb, 0.9, logits, skip)
     dP = torch.zeros(B().QN_MLP_PARAMS, device="cuda")
     loss = torch.zeros(1, device="cuda")
-    B().qn_skip_mlp_bwd(n, Sd, Xd, up(y, torch.uint8), pb, dP, loss)
+    part = torch.zeros(B().QN_MLP_BWD_BLOCKS * (B().QN_MLP_PARAMS + 1), device="cuda")
+    B().qn_skip_mlp_bwd(n, Sd, Xd, up(y, torch.uint8), pb, dP, loss, part)
     torch.cuda.synchronize()
     z_ref, cache = oracle.mlp_forward(X.T, P)
     close(logits.cpu().numpy(), z_ref, floor_frac=0.01, what="logits")
