@@ -35,10 +35,10 @@ WORKLOADS = {
 }
 METRIC = "fwd+bwd rasterize it/s @300k Gaussians 1352x1014; s/frame learned vs plain @dPSNR<=.05"
 L2_FLUSH_BYTES = 256 << 20
-# kernels each C-ABI call launches (memsets are not counted)
-KERNELS_PER_CALL = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 2, "render_bwd": 2,
-                    "project_bwd": 1, "decode_bwd": 2}
-STAGES = ["decode", "project", "bin_sort", "render_fwd", "loss", "render_bwd", "project_bwd", "decode_bwd", "adam"]
+# kernels each stage launches (memsets are not counted)
+KERNELS_PER_STAGE = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 2, "render_bwd": 1,
+                     "gather": 1, "project_bwd": 1, "decode_bwd": 2, "adam": 2}
+STAGES = list(KERNELS_PER_STAGE)
 
 
 def workload_name(name):
@@ -148,7 +148,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_2412_04469_gb300 import build as pbuild
-    from paper_2412_04469_gb300.pipeline import training_iteration
+    from paper_2412_04469_gb300.pipeline import IterationGraph, training_iteration
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -170,80 +170,88 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step_timed(v, ev):
+    def max_over_ranks(x):
+        t = torch.tensor([x], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def staged_step(v, ev):
+        """One iteration issued stage by stage with an event between stages."""
         c = cams[v]
-        ev[0].record(stream)
-        frame.decode()
-        ev[1].record(stream)
-        rast.project(frame.attrs, c, hp.blur)
-        ev[2].record(stream)
-        rast.bin_sort(False)
-        ev[3].record(stream)
-        rast.render_fwd(c, hp.bg)
-        ev[4].record(stream)
-        rast.loss_grad(targets[v])
-        ev[5].record(stream)
-        rast.render_bwd(c, hp.bg)
-        ev[6].record(stream)
-        rast.project_bwd(frame.attrs, c, hp.blur, frame.d_attrs)
-        ev[7].record(stream)
-        frame.decode_bwd()
-        ev[8].record(stream)
-        frame.adam()
-        ev[9].record(stream)
+        calls = (lambda: frame.decode(), lambda: rast.project(frame.attrs, c, hp.blur), lambda: rast.bin_sort(False),
+                 lambda: rast.render_fwd(c, hp.bg), lambda: rast.loss_grad(targets[v]),
+                 lambda: rast.render_bwd_pairs(c, hp.bg), lambda: rast.gather(),
+                 lambda: rast.project_bwd(frame.attrs, c, hp.blur, frame.d_attrs), lambda: frame.decode_bwd(),
+                 lambda: frame.adam())
+        for i, f in enumerate(calls):
+            ev[i].record(stream)
+            f()
+        ev[len(calls)].record(stream)
 
     for w in range(args.warmup):
         training_iteration(frame, rast, cams[w % V], targets[w % V])
     torch.cuda.synchronize()
     assert int(rast.n_pairs.item()) <= rast.capacity, "pair buffer overflow during warm-up"
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(10)] for _ in range(args.steps)]
+
+    # ---- per-stage breakdown: eager launches, CUDA events between stages
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (outside the step events)
+        staged_step((args.warmup + k) % V, evs[k])
+    barrier()
+    stage_ms = {s: [e[i].elapsed_time(e[i + 1]) for e in evs] for i, s in enumerate(STAGES)}
+    staged_ms = max_over_ranks(float(sum(e[0].elapsed_time(e[-1]) for e in evs)))
+
+    # ---- headline: the iteration replayed as one CUDA graph per view
+    graphs = IterationGraph(frame, rast)
+    for w in range(V + 1):                  # warm-up: the eager step, then one capture per view
+        graphs.run(w % V, cams[w % V], targets[w % V])
+    for w in range(args.warmup):
+        graphs.run(w % V, cams[w % V], targets[w % V])
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
     t_wall = time.perf_counter()
     for k in range(args.steps):
-        flush.zero_()                       # L2 flush between timed steps (outside the step events)
-        step_timed((args.warmup + k) % V, evs[k])
+        v = (args.warmup + k) % V
+        flush.zero_()
+        gev[k][0].record(stream)
+        graphs.run(v, cams[v], targets[v])
+        gev[k][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     overflow = int(rast.n_pairs.item()) > rast.capacity
-    stage_ms = {s: [] for s in STAGES}
-    step_ms = []
-    for e in evs:
-        for i, s in enumerate(STAGES):
-            stage_ms[s].append(e[i].elapsed_time(e[i + 1]))
-        step_ms.append(e[0].elapsed_time(e[9]))
-    total_ms = float(sum(step_ms))
-    t = torch.tensor([total_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in gev)))
     if args.quick:
         if rank == 0:
             print(json.dumps({"quick": True, "ms_per_step": max_ms / args.steps,
+                              "staged_ms_per_step": staged_ms / args.steps,
                               "stage_ms": {s: float(np.mean(stage_ms[s])) for s in STAGES}}), flush=True)
         return
 
     # ---- end to end through the public API with host buffers: H2D of the
-    # view's target from pinned memory and D2H of the loss every step
+    # view's target from pinned memory into the graphs' target buffer and D2H
+    # of the loss every step
     loss_host = torch.zeros(1).pin_memory()
     tgt_dev = torch.empty_like(targets[0])
+    for v in range(V):
+        tgt_dev.copy_(targets_host[v], non_blocking=True)
+        graphs.run(("e2e", v), cams[v], tgt_dev)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
         v = (args.warmup + k) % V
         tgt_dev.copy_(targets_host[v], non_blocking=True)
-        training_iteration(frame, rast, cams[v], tgt_dev)
+        graphs.run(("e2e", v), cams[v], tgt_dev)
         loss_host.copy_(rast.loss, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
 
     # ---- work counts for the roofline (after timing; one forward per view)
     P_list, Pvis_list, last_sum, contrib_sum = [], [], [], []
@@ -268,10 +276,11 @@ def run_gpu(args):
     Pvis = float(np.mean(Pvis_list))
     n_vis = int((rast.rects[:, 2] > rast.rects[:, 0]).sum().item())
     px = W * H
+    # algorithmic bytes per launch: what each stage must read and write once
     algo_bytes = {
         "decode": 620.0 * n, "project": 300.0 * n, "bin_sort": 20.0 * n + 36.0 * P,
         "render_fwd": 40.0 * Pvis + 20.0 * px, "loss": 36.0 * px,
-        "render_bwd": 32.0 * px + 40.0 * Pvis + 36.0 * n_vis,
+        "render_bwd": 32.0 * px + 40.0 * Pvis + 36.0 * Pvis, "gather": 36.0 * Pvis + 36.0 * n_vis,
         "project_bwd": 508.0 * n, "decode_bwd": 524.0 * n,
         "adam": 28.0 * ((lay.n_latent + 4) * n + lay.n_dec),
     }
@@ -282,9 +291,10 @@ def run_gpu(args):
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
             "traffic": None, "algorithmic_bytes": algo_bytes[dom]}
-    # FP32 arithmetic estimate for the compositing adjoint:
-    # 12 flop per alpha evaluation, 41 per contributing evaluation, and a
-    # 45-flop warp reduction per 32 contributions.
+    # FP32 arithmetic of the compositing adjoint as the method defines it:
+    # 12 flop per alpha evaluation (every pixel up to its last contributor),
+    # 41 more per contributing evaluation, and a 45-flop reduction of the
+    # nine per-Gaussian sums per 32 contributions
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     flops_bwd = 12.0 * np.mean(last_sum) + 41.0 * np.mean(contrib_sum) + 45.0 * np.mean(contrib_sum) / 32.0
@@ -300,7 +310,7 @@ def run_gpu(args):
         roof["alu_render_bwd"] = alu
 
     value = world * args.steps / (max_ms * 1e-3)
-    launches = args.steps * (sum(KERNELS_PER_CALL.values()) + 2 * lay.n_cat + 2)
+    launches = args.steps * sum(KERNELS_PER_STAGE.values())
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "it/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
@@ -309,8 +319,10 @@ def run_gpu(args):
         "config": {"workload": workload_name(name), "n_gaussians": n, "sh_degree": deg, "width": W, "height": H,
                    "views": V, "latent_dim": L, "pairs_per_view": round(P), "visited_pairs_per_view": round(Pvis),
                    "visible_gaussians": n_vis, "l2": "flushed between timed steps (256 MB write outside step events)",
+                   "launch": "one CUDA graph replay per step (iteration captured once per view)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "stage_ms": {s: round(avg[s], 4) for s in STAGES},
+        "staged_ms_per_step": round(staged_ms / args.steps, 4),
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": round(world * args.steps / (e2e_ms * 1e-3), 3), "unit": "it/s",
@@ -319,6 +331,10 @@ def run_gpu(args):
         "pair_overflow": overflow,
         "wall_s": round(t_wall, 3),
     }
+    if not args.no_seq and name == "full":
+        del graphs, frame, rast, targets, flush
+        torch.cuda.empty_cache()
+        out["sequence"] = run_sequence(args)
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
     if world > 1:
@@ -326,6 +342,34 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_sequence(args):
+    """The learned static-skip comparison on the full workload's scene and
+    cameras: plain gated training and learned skip over the same streamed
+    frames (the MLP trains on the first 10, skips from frame 11 on)."""
+    from paper_2412_04469_gb300.sequence import SequenceConfig, compare
+
+    cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
+    t0 = time.perf_counter()
+    out = compare(cfg)
+    learned = out["learned"]
+    skip = [r for r in learned if r.t > cfg.train_frames]
+    return {"config": {"n_gaussians": cfg.n, "sh_degree": cfg.sh_degree, "width": cfg.width, "height": cfg.height,
+                       "views": cfg.views, "frames": cfg.frames, "iters_per_frame": cfg.iters,
+                       "frac_dynamic": cfg.frac_dynamic, "mlp_train_frames": cfg.train_frames,
+                       "threshold": cfg.threshold, "max_dpsnr": cfg.max_dpsnr,
+                       "launch": "CUDA graph replays" if cfg.graphs else "eager"},
+            "s_per_frame_plain": round(out["s_per_frame_plain_skip_frames"], 4),
+            "s_per_frame_learned": round(out["s_per_frame_learned_skip_frames"], 4),
+            "speedup": round(out["s_per_frame_plain_skip_frames"] / out["s_per_frame_learned_skip_frames"], 4),
+            "skip_frames": len(skip),
+            "mean_skipped_fraction": round(out["mean_skipped"], 4),
+            "min_dpsnr_vs_same_state_plain": round(out["min_dpsnr_skip_frames"], 4),
+            "fallbacks": out["fallbacks"],
+            "psnr_learned": [round(r.psnr, 3) for r in skip],
+            "psnr_same_state_plain": [round(r.psnr_plain, 3) for r in skip],
+            "wall_s": round(time.perf_counter() - t0, 1)}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -422,6 +466,9 @@ def main():
     ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-seq", action="store_true", help="skip the learned-skip sequence comparison")
+    ap.add_argument("--seq-frames", type=int, default=16, help="frames of the learned-skip sequence comparison")
+    ap.add_argument("--seq-iters", type=int, default=250, help="training iterations per frame in that comparison")
     ap.add_argument("--quick", action="store_true",
                     help="one view, timed steps only (for profiler captures); prints stage times")
     args = ap.parse_args()

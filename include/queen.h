@@ -328,6 +328,33 @@ int qn_adam(int32_t rows, int32_t n, int32_t stride, float *param, const float *
             float *v, int32_t step, float lr, float beta1, float beta2, float eps,
             const uint8_t *skip, uint16_t *param_bf16, qn_stream_t stream);
 
+#define QN_ADAM_MAX_GROUPS 16
+
+/* One parameter group of qn_adam_groups: `rows` planes of n elements with
+ * stride `stride` (device pointers; param_bf16 nullable as in qn_adam), its
+ * learning rate, and whether the skip mask applies (use_skip != 0). */
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    uint16_t *param_bf16;
+    int32_t rows, n, stride;
+    float lr;
+    int32_t use_skip;
+} qn_adam_group;
+
+/*
+ * One Adam step (as qn_adam) over n_groups <= QN_ADAM_MAX_GROUPS parameter
+ * groups in a single launch, with the step count on the device: *step
+ * (device int32) is incremented first and the bias corrections use the new
+ * value, so repeated calls -- also replays of a captured CUDA graph -- count
+ * steps without the host.  groups_host is read during the call only.
+ * skip ([n] u8, nullable) applies to the groups with use_skip.
+ */
+int qn_adam_groups(int32_t n_groups, const qn_adam_group *groups_host, int32_t *step, float beta1, float beta2,
+                   float eps, const uint8_t *skip, qn_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Viewspace gradient difference and gate initialisation -- Sec. 3.3.        */
 /* ------------------------------------------------------------------------ */

@@ -41,6 +41,15 @@ class qn_gate_params(C.Structure):
     _fields_ = [("tau", C.c_float), ("gamma0", C.c_float), ("gamma1", C.c_float)]
 
 
+QN_ADAM_MAX_GROUPS = 16
+
+
+class qn_adam_group(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("param_bf16", C.c_void_p), ("rows", C.c_int32), ("n", C.c_int32), ("stride", C.c_int32),
+                ("lr", C.c_float), ("use_skip", C.c_int32)]
+
+
 _lib = None
 _P = C.c_void_p
 _I32, _I64, _F32, _SZ = C.c_int32, C.c_int64, C.c_float, C.c_size_t
@@ -67,6 +76,7 @@ _SIGS = {
     "qn_skip_mlp_bwd": ([_I32, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_skip_labels": ([_I32, _I32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
+    "qn_adam_groups": ([_I32, _P, _P, _F32, _F32, _F32, _P, _P], C.c_int),
 }
 
 
@@ -238,6 +248,21 @@ def qn_adam(rows, n, stride, param, grad, m, v, step, lr, beta1, beta2, eps, ski
             stream=None):
     _check(lib().qn_adam(rows, n, stride, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
                          float(beta1), float(beta2), float(eps), _ptr(skip), _ptr(param_bf16), _stream(stream)))
+
+
+def adam_group(param, grad, m, v, lr, rows, n, stride, param_bf16=None, use_skip=True):
+    """One qn_adam_group over device tensors (views are fine: their data
+    pointers are taken)."""
+    return qn_adam_group(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), _ptr(param_bf16), int(rows), int(n), int(stride),
+                         float(lr), int(bool(use_skip)))
+
+
+def qn_adam_groups(groups, step, beta1, beta2, eps, skip=None, stream=None):
+    """groups: a sequence of qn_adam_group, or a ctypes array of them."""
+    if not isinstance(groups, C.Array):
+        groups = (qn_adam_group * len(groups))(*groups)
+    _check(lib().qn_adam_groups(len(groups), groups, _ptr(step), float(beta1), float(beta2), float(eps), _ptr(skip),
+                                _stream(stream)))
 
 
 def qn_viewspace_accum(n, n_stride, d_splats, scale, score, stream=None):

@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(CHUNK) k_bin_gather(int TX, int TY, const uint
     if (!__syncthreads_or(any)) return;
     build_masks(TX, TY, s);
     // pass 2: one warp per Gaussian; lane l takes the Gaussian's tiles l, l + 32,
-    // ... in row-major order and a fixed butterfly sums the lanes
+    // ... in row-major order and a fixed shuffle pattern sums the lanes
     const int warp = threadIdx.x >> 5;
     for (int j = warp; j < CHUNK; j += CHUNK / 32) {
         const uint32_t g = (uint32_t)c * CHUNK + j;
@@ -492,8 +492,19 @@ __global__ void __launch_bounds__(CHUNK) k_bin_gather(int TX, int TY, const uint
         const int wj = j >> 5;
         const unsigned below = (1u << (j & 31)) - 1u;
         float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool found = false;
+        // lane l walks tiles l, l + 32, ... of the rect in row-major order,
+        // stepping its (column, row) without a division per tile
+        int cx = rw > 0 ? lane % rw : 0, cy = rw > 0 ? lane / rw : 0;
+        const int dq = rw > 0 ? 32 / rw : 0, dr = rw > 0 ? 32 % rw : 0;
         for (int k = lane; k < area; k += 32) {
-            const int tx = r.x + k % rw, ty = r.y + k / rw;
+            const int tx = r.x + cx, ty = r.y + cy;
+            cx += dr;
+            cy += dq;
+            if (cx >= rw) {
+                cx -= rw;
+                ++cy;
+            }
             const int t = ty * TX + tx;
             if (!((active[t >> 5] >> (t & 31)) & 1u)) continue;
             uint32_t rank = __popc(s.mx[wj][tx] & s.my[wj][ty] & below);
@@ -505,13 +516,22 @@ __global__ void __launch_bounds__(CHUNK) k_bin_gather(int TX, int TY, const uint
             acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
             acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
             acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
+            found = true;
         }
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc[q] = warp_sum(acc[q]);
+        float *o = reinterpret_cast<float *>(out + 3 * (size_t)id);
+        if (!__any_sync(FULL, found)) {                 // no visited pair: a zero gradient
+            if (lane < 12) o[lane] = 0.f;
+            continue;
+        }
+        const float red = reduce_scatter8(acc, lane);   // lane 4q holds the sum of value q
+        const float red8 = warp_sum(acc[8]);
+        if ((lane & 3) == 0) {
+            const int q = lane >> 2;
+            o[(q / 3) * 4 + q % 3] = red;
+        }
         if (lane == 0) {
-            out[3 * (size_t)id] = make_float4(acc[0], acc[1], acc[2], 0.f);
-            out[3 * (size_t)id + 1] = make_float4(acc[3], acc[4], acc[5], 0.f);
-            out[3 * (size_t)id + 2] = make_float4(acc[6], acc[7], acc[8], 0.f);
+            o[10] = red8;
+            o[3] = o[7] = o[11] = 0.f;
         }
     }
 }

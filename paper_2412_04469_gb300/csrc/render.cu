@@ -162,30 +162,6 @@ __global__ void __launch_bounds__(32 * WARPS) k_render_fwd(int W, int H, int TX,
     }
 }
 
-// Sum over the warp of v[0..7] scattered across lanes (lane l ends up with
-// the total of value (l >> 2) & 7): 9 shuffles instead of the 40 of eight
-// independent butterflies.
-__device__ __forceinline__ float reduce_scatter8(float v[8], int lane) {
-    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
-    float a[4], b[2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = h4 ? v[i] : v[i + 4];
-        const float keep = h4 ? v[i + 4] : v[i];
-        a[i] = keep + __shfl_xor_sync(FULL, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = h3 ? a[i] : a[i + 2];
-        const float keep = h3 ? a[i + 2] : a[i];
-        b[i] = keep + __shfl_xor_sync(FULL, send, 8);
-    }
-    float c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(FULL, h2 ? b[0] : b[1], 4);
-    c += __shfl_xor_sync(FULL, c, 2);
-    c += __shfl_xor_sync(FULL, c, 1);
-    return c;
-}
-
 // Adjoint of k_render_fwd for one tile, walking its list back to front from
 // the last contributor of any of its pixels.  Per (lane, Gaussian) the lane
 // accumulates, over its pixels, s = dL/dpower and the moments

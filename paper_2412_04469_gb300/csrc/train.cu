@@ -53,6 +53,46 @@ __global__ void __launch_bounds__(256) k_adam(int rows, int n, int stride, float
     }
 }
 
+struct AdamGroups {
+    qn_adam_group g[QN_ADAM_MAX_GROUPS];
+    int row_start[QN_ADAM_MAX_GROUPS + 1];       // first grid row of each group
+    int n_groups;
+};
+
+__global__ void k_step_increment(int32_t *step) { *step += 1; }
+
+// Grid row y updates row y - row_start[g] of the group g that holds it.
+__global__ void __launch_bounds__(256) k_adam_groups(const __grid_constant__ AdamGroups G,
+                                                     const int32_t *__restrict__ step, float b1, float b2,
+                                                     float eps, const uint8_t *__restrict__ skip) {
+    __shared__ float ibc[2];
+    if (threadIdx.x == 0) {
+        const double t = (double)*step;
+        ibc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
+        ibc[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
+    }
+    __syncthreads();
+    const int y = blockIdx.y;
+    int gi = 0;
+    while (gi + 1 < G.n_groups && G.row_start[gi + 1] <= y) ++gi;
+    const qn_adam_group &P = G.g[gi];
+    const int r = y - G.row_start[gi];
+    const uint8_t *sk = P.use_skip ? skip : nullptr;
+    const float ibc1 = ibc[0], ibc2 = ibc[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const size_t o = (size_t)r * P.stride + i;
+        if (sk && sk[i]) continue;
+        const float gr = P.grad[o];
+        const float mm = fmaf(b1, P.m[o], (1.f - b1) * gr);
+        const float vv = fmaf(b2, P.v[o], (1.f - b2) * gr * gr);
+        P.m[o] = mm;
+        P.v[o] = vv;
+        const float np = P.param[o] - P.lr * (mm * ibc1) / (sqrtf(vv * ibc2) + eps);
+        P.param[o] = np;
+        if (P.param_bf16) P.param_bf16[o] = __bfloat16_as_ushort(__float2bfloat16_rn(np));
+    }
+}
+
 int grid_cap(long long work, int block) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -100,4 +140,33 @@ extern "C" int qn_adam(int32_t rows, int32_t n, int32_t stride, float *param, co
     qn::k_adam<<<dim3(gx, rows), 256, 0, qn::as_stream(stream)>>>(
         rows, n, stride, param, grad, m, v, lr, beta1, beta2, eps, ibc1, ibc2, skip, param_bf16);
     return qn::check_launch("qn_adam");
+}
+
+extern "C" int qn_adam_groups(int32_t n_groups, const qn_adam_group *groups_host, int32_t *step, float beta1,
+                              float beta2, float eps, const uint8_t *skip, qn_stream_t stream) {
+    QN_REQUIRE(n_groups >= 1 && n_groups <= QN_ADAM_MAX_GROUPS, "n_groups must be in 1..%d", QN_ADAM_MAX_GROUPS);
+    QN_REQUIRE(groups_host && step, "null pointer argument");
+    QN_REQUIRE(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f, "bad Adam constants");
+    qn::AdamGroups G{};
+    G.n_groups = n_groups;
+    int rows = 0, nmax = 0;
+    for (int k = 0; k < n_groups; ++k) {
+        const qn_adam_group &g = groups_host[k];
+        QN_REQUIRE(g.rows >= 0 && g.n >= 0 && g.stride >= g.n, "group %d: bad rows / n / stride", k);
+        QN_REQUIRE((long long)g.rows * g.n == 0 || (g.param && g.grad && g.m && g.v), "group %d: null pointer", k);
+        G.g[k] = g;
+        G.row_start[k] = rows;
+        rows += g.rows;
+        nmax = g.n > nmax ? g.n : nmax;
+    }
+    G.row_start[n_groups] = rows;
+    QN_REQUIRE(rows <= 65535, "too many rows (%d)", rows);
+    cudaStream_t s = qn::as_stream(stream);
+    qn::k_step_increment<<<1, 1, 0, s>>>(step);
+    if (rows == 0 || nmax == 0) return qn::check_launch("qn_adam_groups");
+    int gx = qn::grid_cap(nmax, 256);
+    const int per_row = qn::div_up((int64_t)gx, rows);      // keep the total near the grid cap
+    gx = per_row < 1 ? 1 : per_row;
+    qn::k_adam_groups<<<dim3(gx, rows), 256, 0, s>>>(G, step, beta1, beta2, eps, skip);
+    return qn::check_launch("qn_adam_groups");
 }

@@ -94,7 +94,41 @@ class QueenFrame:
         self.d_log_alpha = torch.zeros_like(self.log_alpha)
         self.dec_partials = torch.zeros(B.QN_DECODE_BWD_BLOCKS * max(1, layout.n_dec), device=dev)
         self.opt = {k: _Adam(getattr(self, k).shape, dev) for k in ("lat", "dec", "lp", "log_alpha")}
-        self.step_count = 0
+        self.step = torch.zeros(1, device=dev, dtype=torch.int32)     # Adam step count, on the device
+        self._adam_groups = self._make_adam_groups()
+
+    def _make_adam_groups(self):
+        """Every trainable tensor as qn_adam groups: latents and decoders per
+        category (each its own learning rate), position residuals and gate
+        parameters; the decoders also refresh their bf16 copy."""
+        hp, n, S, lay = self.hp, self.n, self.S, self.layout
+        groups = []
+        lo, dofs = 0, 0
+        o = self.opt["lat"]
+        for c in range(lay.n_cat):
+            L = lay.lat_dim[c]
+            groups.append(B.adam_group(self.lat[lo:lo + L], self.d_lat[lo:lo + L], o.m[lo:lo + L], o.v[lo:lo + L],
+                                       hp.lr_latent[min(c, len(hp.lr_latent) - 1)], L, n, S))
+            lo += L
+        o = self.opt["dec"]
+        for c in range(lay.n_cat):
+            k = lay.attr_count[c] * lay.lat_dim[c]
+            groups.append(B.adam_group(self.dec[dofs:dofs + k], self.d_dec[dofs:dofs + k], o.m[dofs:dofs + k],
+                                       o.v[dofs:dofs + k], hp.lr_decoder[min(c, len(hp.lr_decoder) - 1)], 1, k, k,
+                                       param_bf16=self.dec_bf16[dofs:dofs + k], use_skip=False))
+            dofs += k
+        o = self.opt["lp"]
+        groups.append(B.adam_group(self.lp, self.d_lp, o.m, o.v, hp.lr_pos, 3, n, S))
+        o = self.opt["log_alpha"]
+        groups.append(B.adam_group(self.log_alpha, self.d_log_alpha, o.m, o.v, hp.lr_gate, 1, n, S))
+        return (B.qn_adam_group * len(groups))(*groups)
+
+    def reset_optimizer(self):
+        """Clears Adam's moments and step count (device work, no sync)."""
+        for o in self.opt.values():
+            o.m.zero_()
+            o.v.zero_()
+        self.step.zero_()
 
     # ---------------------------------------------------------------- steps
     def decode(self, stream=None):
@@ -112,29 +146,10 @@ class QueenFrame:
                                   self.d_dec, self.d_lp, self.d_log_alpha, self.dec_partials, stream)
 
     def adam(self, skip=None, stream=None):
-        self.step_count += 1
-        t, hp, n, S = self.step_count, self.hp, self.n, self.S
-        lay = self.layout
-        lo = 0
-        for c in range(lay.n_cat):
-            L = lay.lat_dim[c]
-            o = self.opt["lat"]
-            B.qn_adam(L, n, S, self.lat[lo:lo + L], self.d_lat[lo:lo + L], o.m[lo:lo + L], o.v[lo:lo + L], t,
-                      hp.lr_latent[min(c, len(hp.lr_latent) - 1)], hp.beta1, hp.beta2, hp.eps, skip, None, stream)
-            lo += L
-        dofs = 0
-        for c in range(lay.n_cat):
-            k = lay.attr_count[c] * lay.lat_dim[c]
-            o = self.opt["dec"]
-            B.qn_adam(1, k, k, self.dec[dofs:dofs + k], self.d_dec[dofs:dofs + k], o.m[dofs:dofs + k],
-                      o.v[dofs:dofs + k], t, hp.lr_decoder[min(c, len(hp.lr_decoder) - 1)], hp.beta1, hp.beta2,
-                      hp.eps, None, self.dec_bf16[dofs:dofs + k], stream)
-            dofs += k
-        o = self.opt["lp"]
-        B.qn_adam(3, n, S, self.lp, self.d_lp, o.m, o.v, t, hp.lr_pos, hp.beta1, hp.beta2, hp.eps, skip, None, stream)
-        o = self.opt["log_alpha"]
-        B.qn_adam(1, n, S, self.log_alpha, self.d_log_alpha, o.m, o.v, t, hp.lr_gate, hp.beta1, hp.beta2, hp.eps,
-                  skip, None, stream)
+        """One Adam step on every trainable tensor: a single launch (after
+        the device step counter's increment)."""
+        hp = self.hp
+        B.qn_adam_groups(self._adam_groups, self.step, hp.beta1, hp.beta2, hp.eps, skip, stream)
 
 
 class Rasterizer:
@@ -190,8 +205,14 @@ class Rasterizer:
 
     def render_bwd(self, cam, bg, skip=None, stream=None):
         """Compositing adjoint: per-pair records, then the per-Gaussian gather."""
+        self.render_bwd_pairs(cam, bg, skip, stream)
+        self.gather(skip, stream)
+
+    def render_bwd_pairs(self, cam, bg, skip=None, stream=None):
         B.qn_render_bwd(cam, self.ranges, self.vals, self.splats, bg, self.T_final, self.last, self.d_img, skip,
                         self.pair_grads, self.tile_visited, stream)
+
+    def gather(self, skip=None, stream=None):
         B.qn_bin_gather(self.n, self.rects, self.TX, self.TY, self.workspace, self.tile_visited, self.pair_grads,
                         skip, self.d_splats, stream)
 
@@ -221,3 +242,48 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
     frame.decode_bwd(skip, stream)
     frame.adam(skip, stream)
+
+
+class IterationGraph:
+    """training_iteration captured as CUDA graphs and replayed: one graph per
+    key (normally the view index and whether a skip mask is used), captured
+    on first use.  A replay issues the whole iteration with one host call, so
+    the loop's speed is the GPU's.  Everything an iteration reads is bound at
+    capture: the camera, and the addresses of the target, the skip mask and
+    the frame's and rasterizer's buffers; a graph is captured again when one
+    of those addresses changes (e.g. after Rasterizer.set_capacity).  The
+    Adam step count lives on the device, so replays keep counting."""
+
+    def __init__(self, frame: QueenFrame, rast: Rasterizer):
+        self.frame, self.rast = frame, rast
+        self.graphs = {}
+        self.pool = None
+        self.warm = False
+
+    def _signature(self, target, skip):
+        r = self.rast
+        return (target.data_ptr(), None if skip is None else skip.data_ptr(), r.vals.data_ptr(),
+                r.pair_grads.data_ptr(), r.workspace.data_ptr())
+
+    def run(self, key, cam, target, skip=None):
+        sig = self._signature(target, skip)
+        ent = self.graphs.get(key)
+        if ent is None or ent[1] != sig:
+            if not self.warm:
+                # one eager iteration first: lazily allocated scratch must
+                # exist before capture; it is a real training step
+                training_iteration(self.frame, self.rast, cam, target, skip)
+                self.warm = True
+                return
+            if self.pool is None:
+                self.pool = torch.cuda.graph_pool_handle()
+            g = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, pool=self.pool):
+                training_iteration(self.frame, self.rast, cam, target, skip)
+            ent = (g, sig, cam, target, skip)           # keep what the graph points at alive
+            self.graphs[key] = ent
+        ent[0].replay()
+
+    def clear(self):
+        self.graphs.clear()

@@ -71,3 +71,10 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert B.lib().qn_adam(1, 4, 4, None, None, None, None, 0, 0.1, 0.9, 0.999, 1e-8, None, None, None) == \
         B.QN_ERR_INVALID_ARG
     assert B.lib().qn_bin_sort_workspace_size(-1, 4, 4) == 0
+    groups = (B.qn_adam_group * 1)()
+    assert B.lib().qn_adam_groups(0, groups, None, 0.9, 0.999, 1e-8, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_adam_groups(B.QN_ADAM_MAX_GROUPS + 1, groups, None, 0.9, 0.999, 1e-8, None, None) == \
+        B.QN_ERR_INVALID_ARG
+    groups[0].rows, groups[0].n, groups[0].stride = 1, 8, 4                  # stride < n
+    assert B.lib().qn_adam_groups(1, groups, 16, 0.9, 0.999, 1e-8, None, None) == B.QN_ERR_INVALID_ARG
+    assert b"stride" in B.lib().qn_last_error()
