@@ -347,29 +347,41 @@ def run_gpu(args):
 def run_sequence(args):
     """The learned static-skip comparison on the full workload's scene and
     cameras: plain gated training and learned skip over the same streamed
-    frames (the MLP trains on the first 10, skips from frame 11 on)."""
+    frames (the MLP trains on the first 10, skips from frame 11 on), at the
+    configured skip threshold and at each --seq-extra-threshold."""
     from paper_2412_04469_gb300.sequence import SequenceConfig, compare
 
     cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
     t0 = time.perf_counter()
-    out = compare(cfg)
-    learned = out["learned"]
-    skip = [r for r in learned if r.t > cfg.train_frames]
-    return {"config": {"n_gaussians": cfg.n, "sh_degree": cfg.sh_degree, "width": cfg.width, "height": cfg.height,
-                       "views": cfg.views, "frames": cfg.frames, "iters_per_frame": cfg.iters,
-                       "frac_dynamic": cfg.frac_dynamic, "mlp_train_frames": cfg.train_frames,
-                       "threshold": cfg.threshold, "max_dpsnr": cfg.max_dpsnr,
-                       "launch": "CUDA graph replays" if cfg.graphs else "eager"},
-            "s_per_frame_plain": round(out["s_per_frame_plain_skip_frames"], 4),
-            "s_per_frame_learned": round(out["s_per_frame_learned_skip_frames"], 4),
-            "speedup": round(out["s_per_frame_plain_skip_frames"] / out["s_per_frame_learned_skip_frames"], 4),
-            "skip_frames": len(skip),
-            "mean_skipped_fraction": round(out["mean_skipped"], 4),
-            "min_dpsnr_vs_same_state_plain": round(out["min_dpsnr_skip_frames"], 4),
-            "fallbacks": out["fallbacks"],
-            "psnr_learned": [round(r.psnr, 3) for r in skip],
-            "psnr_same_state_plain": [round(r.psnr_plain, 3) for r in skip],
-            "wall_s": round(time.perf_counter() - t0, 1)}
+    out = compare(cfg, extra_thresholds=args.seq_extra_threshold)
+
+    def arm(summary, learned, thr):
+        skip = [r for r in learned if r.t > cfg.train_frames]
+        return {"threshold": thr,
+                "s_per_frame_plain": round(summary["s_per_frame_plain_skip_frames"], 4),
+                "s_per_frame_learned": round(summary["s_per_frame_learned_skip_frames"], 4),
+                "speedup": round(summary["s_per_frame_plain_skip_frames"]
+                                 / summary["s_per_frame_learned_skip_frames"], 4),
+                "skip_frames": len(skip), "fallbacks": summary["fallbacks"],
+                "mean_skipped_fraction": round(summary["mean_skipped"], 4),
+                "dpsnr_train_views_min": round(summary["min_dpsnr_train_skip_frames"], 4),
+                "dpsnr_train_views_mean": round(summary["mean_dpsnr_train_skip_frames"], 4),
+                "dpsnr_heldout_min": round(summary["min_dpsnr_skip_frames"], 4),
+                "dpsnr_heldout_mean": round(summary["mean_dpsnr_skip_frames"], 4),
+                "frame_s_learned": [round(r.seconds, 4) for r in skip]}
+
+    res = {"config": {"n_gaussians": cfg.n, "sh_degree": cfg.sh_degree, "width": cfg.width, "height": cfg.height,
+                      "views": cfg.views, "frames": cfg.frames, "iters_per_frame": cfg.iters,
+                      "frac_dynamic": cfg.frac_dynamic, "mlp_train_frames": cfg.train_frames,
+                      "max_dpsnr": cfg.max_dpsnr, "fallback_psnr": cfg.fallback_psnr,
+                      "dpsnr_reference": "plain gated training of the same frame from the same state",
+                      "timed": "training work only (PSNR evaluation and the reference run excluded)",
+                      "launch": "CUDA graph replays" if cfg.graphs else "eager"},
+           "configured": arm(out, out["learned"], cfg.threshold)}
+    for thr, v in out["by_threshold"].items():
+        res[f"threshold_{thr:g}"] = arm(v, v["learned"], thr)
+    res["wall_s"] = round(time.perf_counter() - t0, 1)
+    return res
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -469,6 +481,8 @@ def main():
     ap.add_argument("--no-seq", action="store_true", help="skip the learned-skip sequence comparison")
     ap.add_argument("--seq-frames", type=int, default=16, help="frames of the learned-skip sequence comparison")
     ap.add_argument("--seq-iters", type=int, default=250, help="training iterations per frame in that comparison")
+    ap.add_argument("--seq-extra-threshold", type=float, nargs="*", default=[0.97],
+                    help="further skip thresholds to run in that comparison (same plain arm)")
     ap.add_argument("--quick", action="store_true",
                     help="one view, timed steps only (for profiler captures); prints stage times")
     args = ap.parse_args()

@@ -108,16 +108,21 @@ const char *qn_version(void);
  *   dec   bf16 bits, concatenated row-major D_c blocks  (read)
  *   lp    [3][n_stride] f32  pre-gated position residual (read)
  *   log_alpha [n] f32                                   (read)
+ *   skip  [n] u8 (nullable): Gaussians with skip != 0 are frozen -- their
+ *         out columns and gate entries are left as they are and they add
+ *         nothing to lreg.  A Gaussian whose residual parameters do not
+ *         change keeps its A_t, so after one call without skip the frozen
+ *         columns already hold it.
  *   out   [n_attr][n_stride] f32  A_t                   (written; may not alias prev)
  *   gate  [n] f32 g_i                                    (written; nullable)
- *   lreg  [1] f32 L_reg                                  (written; nullable)
+ *   lreg  [1] f32 L_reg over the Gaussians not skipped   (written; nullable)
  * Errors: QN_ERR_INVALID_ARG for n < 0, bad stride, null required pointers,
  * a layout outside the limits above.
  */
 int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, const float *prev,
                         const float *lat, const uint16_t *dec, const qn_decoder_layout *layout_host,
                         const float *lp, const float *log_alpha, const qn_gate_params *gate_host,
-                        float *out, float *gate, float *lreg, qn_stream_t stream);
+                        const uint8_t *skip, float *out, float *gate, float *lreg, qn_stream_t stream);
 
 /*
  * Adjoint of qn_decode_residuals for dL/dA_t = d_out and dL/dL_reg = d_lreg:
@@ -441,6 +446,33 @@ int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *g
  */
 int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, const uint8_t *labels, const uint16_t *params,
                     float *d_params, float *loss, float *partials, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Data layout for the learned static skip.                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace qn_partition needs for n flags (0 for n < 0). */
+size_t qn_partition_workspace_size(int32_t n);
+
+/*
+ * Stable partition of 0..n-1 by flags [n] u8: perm [n] i32 (device) lists
+ * the indices with flags == 0 in increasing order, then the others in
+ * increasing order; *n_first (device i32) = number of zero flags.
+ * Reordering every per-Gaussian plane by perm (qn_gather_columns) puts the
+ * skipped Gaussians (flag != 0) in one contiguous run at the end, which is
+ * what lets the skip save memory traffic in the adjoint and Adam kernels.
+ * workspace: >= qn_partition_workspace_size(n) bytes of device memory.
+ */
+int qn_partition(int32_t n, const uint8_t *flags, int32_t *perm, int32_t *n_first, void *workspace,
+                 size_t workspace_bytes, qn_stream_t stream);
+
+/*
+ * dst[r][i] = src[r][perm[i]] for r < rows, i < n; elements of elem_bytes
+ * (1, 2, 4 or 8) bytes, row strides in elements.  perm [n] i32 (device) must
+ * hold column indices of src (not checked); dst may not alias src.
+ */
+int qn_gather_columns(int32_t rows, int32_t n, int32_t elem_bytes, const void *src, int64_t src_stride,
+                      const int32_t *perm, void *dst, int64_t dst_stride, qn_stream_t stream);
 
 #ifdef __cplusplus
 }

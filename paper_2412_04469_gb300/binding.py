@@ -57,7 +57,7 @@ _I32, _I64, _F32, _SZ = C.c_int32, C.c_int64, C.c_float, C.c_size_t
 _SIGS = {
     "qn_last_error": ([], C.c_char_p),
     "qn_version": ([], C.c_char_p),
-    "qn_decode_residuals": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_decode_residuals": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P,
                                  _P], C.c_int),
     "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
@@ -77,6 +77,9 @@ _SIGS = {
     "qn_skip_labels": ([_I32, _I32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
     "qn_adam_groups": ([_I32, _P, _P, _F32, _F32, _F32, _P, _P], C.c_int),
+    "qn_partition_workspace_size": ([_I32], C.c_size_t),
+    "qn_partition": ([_I32, _P, _P, _P, _P, C.c_size_t, _P], C.c_int),
+    "qn_gather_columns": ([_I32, _I32, _I32, _P, C.c_int64, _P, _P, C.c_int64, _P], C.c_int),
 }
 
 
@@ -150,10 +153,10 @@ def make_gate(tau, gamma0, gamma1) -> qn_gate_params:
 
 
 def qn_decode_residuals(n, n_stride, n_attr, prev, lat, dec, layout, lp, log_alpha, gate_params, out, gate=None,
-                        lreg=None, stream=None):
+                        lreg=None, stream=None, skip=None):
     _check(lib().qn_decode_residuals(n, n_stride, n_attr, _ptr(prev), _ptr(lat), _ptr(dec), C.byref(layout),
-                                     _ptr(lp), _ptr(log_alpha), C.byref(gate_params), _ptr(out), _ptr(gate),
-                                     _ptr(lreg), _stream(stream)))
+                                     _ptr(lp), _ptr(log_alpha), C.byref(gate_params), _ptr(skip), _ptr(out),
+                                     _ptr(gate), _ptr(lreg), _stream(stream)))
 
 
 QN_DECODE_BWD_BLOCKS = 512
@@ -298,3 +301,19 @@ def qn_skip_mlp_bwd(n, n_stride, X, labels, params_bf16, d_params, loss, partial
 
 def qn_skip_labels(n, n_stride, n_latent, gate, lat, labels, stream=None):
     _check(lib().qn_skip_labels(n, n_stride, n_latent, _ptr(gate), _ptr(lat), _ptr(labels), _stream(stream)))
+
+
+def qn_partition_workspace_size(n):
+    return int(lib().qn_partition_workspace_size(n))
+
+
+def qn_partition(n, flags, perm, n_first, workspace, stream=None):
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().qn_partition(n, _ptr(flags), _ptr(perm), _ptr(n_first), _ptr(workspace), ws_bytes,
+                              _stream(stream)))
+
+
+def qn_gather_columns(rows, n, src, src_stride, perm, dst, dst_stride, stream=None):
+    """dst[r][i] = src[r][perm[i]]; element size from src's dtype."""
+    _check(lib().qn_gather_columns(rows, n, src.element_size(), _ptr(src), int(src_stride), _ptr(perm), _ptr(dst),
+                                   int(dst_stride), _stream(stream)))

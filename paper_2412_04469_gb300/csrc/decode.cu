@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
                                                 const float *__restrict__ lat,
                                                 const uint16_t *__restrict__ dec,
                                                 const float *__restrict__ lp,
-                                                const float *__restrict__ la, float *__restrict__ out,
+                                                const float *__restrict__ la,
+                                                const uint8_t *__restrict__ skip, float *__restrict__ out,
                                                 float *__restrict__ gate, float *__restrict__ lreg) {
     __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
     __shared__ float sred[8];
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
     const size_t S = a.stride;
     float reg = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        if (skip && skip[i]) continue;                 // frozen: out and gate already hold its values
         const float l_a = la[i];
         const float gh = sigmoidf_(l_a / a.tau);                       // Eq. 6
         const float g = fminf(1.f, fmaxf(0.f, gh * (a.g1 - a.g0) + a.g0));   // Eq. 7
@@ -134,6 +136,17 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
         const int i = base + lane;
         const bool valid = i < a.n;
         const bool sk = valid && skip && skip[i];
+        // a tile of skipped Gaussians only zeroes their gradients (block-uniform)
+        if (__syncthreads_and(!valid || sk)) {
+            if (valid) {
+                for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) d_lat[(size_t)k * S + i] = 0.f;
+                if (row0 == 0) {
+                    d_lp[i] = d_lp[S + i] = d_lp[2 * S + i] = 0.f;
+                    d_la[i] = 0.f;
+                }
+            }
+            continue;
+        }
         // stage the tile (coalesced: lanes are consecutive Gaussians)
         for (int r = row0; r < n_res; r += ROWS_PER_PASS)
             s_dr[r][lane] = (valid && !sk) ? d_out[(size_t)(r + 3) * S + i] : 0.f;
@@ -235,7 +248,8 @@ extern "C" int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, 
                                    const float *lat, const uint16_t *dec,
                                    const qn_decoder_layout *layout_host, const float *lp,
                                    const float *log_alpha, const qn_gate_params *gate_host,
-                                   float *out, float *gate, float *lreg, qn_stream_t stream) {
+                                   const uint8_t *skip, float *out, float *gate, float *lreg,
+                                   qn_stream_t stream) {
     qn::DecodeArgs a;
     int st = qn::make_args(n, n_stride, n_attr, layout_host, gate_host, &a);
     if (st) return st;
@@ -245,7 +259,8 @@ extern "C" int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, 
     cudaStream_t s = qn::as_stream(stream);
     if (lreg && cudaMemsetAsync(lreg, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("decode memset");
     if (n == 0) return QN_OK;
-    qn::k_decode<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, out, gate, lreg);
+    qn::k_decode<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, skip, out, gate,
+                                                         lreg);
     return qn::check_launch("qn_decode_residuals");
 }
 

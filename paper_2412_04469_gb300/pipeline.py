@@ -131,9 +131,11 @@ class QueenFrame:
         self.step.zero_()
 
     # ---------------------------------------------------------------- steps
-    def decode(self, stream=None):
+    def decode(self, stream=None, skip=None):
+        """A_t from A_{t-1} and the residuals; Gaussians with skip set are
+        frozen and keep their columns of attrs and gate."""
         B.qn_decode_residuals(self.n, self.S, self.n_attr, self.prev, self.lat, self.dec_bf16, self.c_layout,
-                              self.lp, self.log_alpha, self.c_gate, self.attrs, self.gate, self.lreg, stream)
+                              self.lp, self.log_alpha, self.c_gate, self.attrs, self.gate, self.lreg, stream, skip)
 
     @property
     def d_lreg(self) -> float:
@@ -231,9 +233,12 @@ class Rasterizer:
 def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None):
     """One view of Eq. 11's optimisation: forward, L1 loss (Eq. 3 L1 term) +
     lambda_reg L_reg (the L_reg gradient is folded into the gate adjoint), full
-    adjoint and the Adam step.  No host synchronisation."""
+    adjoint and the Adam step.  No host synchronisation.  Gaussians with skip
+    set are frozen: no gradient, no update, and their decoded columns are
+    reused (frame.attrs must hold their A_t, e.g. from a decode without
+    skip)."""
     hp = frame.hp
-    frame.decode(stream)
+    frame.decode(stream, skip)
     rast.project(frame.attrs, cam, hp.blur, stream)
     rast.bin_sort(False, stream)
     rast.render_fwd(cam, hp.bg, stream)

@@ -60,6 +60,7 @@ class SequenceConfig:
     mlp_batch: int = 16384
     mlp_lr: float = 1e-3
     graphs: bool = True          # replay the training iterations as CUDA graphs
+    partition: bool = True       # skip frames: reorder the Gaussians so the skipped ones are contiguous
 
 
 class SkipMLP:
@@ -107,6 +108,8 @@ class FrameRecord:
     fallback: bool = False
     psnr_plain: float = float("nan")          # skip frames: plain gating from the same state
     psnr_train: float = float("nan")          # mean PSNR over the training views
+    psnr_skip: float = float("nan")           # fallback frames: the skip result before the fallback
+    psnr_skip_train: float = float("nan")
     psnr_plain_train: float = float("nan")
     mlp_loss: float = float("nan")
     static_recall: float = float("nan")       # skipped set vs ground-truth static Gaussians
@@ -124,6 +127,22 @@ def sequence_hparams() -> HParams:
     then lowers the held-out PSNR (31.2 -> 30.1 dB on the first frame), while
     1.6e-5 raises it (31.2 -> 32.3 dB)."""
     return HParams(lr_pos=1.6e-5)
+
+
+class _Clock:
+    """Accumulates wall time of device work between start() and stop()."""
+
+    def __init__(self):
+        self.seconds = 0.0
+        self._t = 0.0
+
+    def start(self):
+        torch.cuda.synchronize()
+        self._t = time.perf_counter()
+
+    def stop(self):
+        torch.cuda.synchronize()
+        self.seconds += time.perf_counter() - self._t
 
 
 class StreamingTrainer:
@@ -160,8 +179,14 @@ class StreamingTrainer:
         self.prev_static = torch.zeros(f.S, device="cuda", dtype=torch.uint8)
         self.mse = torch.zeros(1, device="cuda")
         self.truth_static = torch.from_numpy(~self.motion.dynamic).cuda()
+        self.perm = torch.zeros(f.S, device="cuda", dtype=torch.int32)
+        self.n_first = torch.zeros(1, device="cuda", dtype=torch.int32)
+        self.part_ws = torch.zeros(max(B.qn_partition_workspace_size(c.n), 16), device="cuda", dtype=torch.uint8)
+        self.scratch_f = torch.zeros((f.n_attr, f.S), device="cuda")
+        self.scratch_u8 = torch.zeros((1, f.S), device="cuda", dtype=torch.uint8)
         self._size_pairs()
         self.graphs = IterationGraph(f, self.rast)
+        self.threshold = c.threshold
 
     # ---------------------------------------------------------------- helpers
     def _size_pairs(self):
@@ -216,6 +241,7 @@ class StreamingTrainer:
         self.prev_la.zero_()
         self.prev_lp.zero_()
         self.prev_static.zero_()
+        self.truth_static.copy_(torch.from_numpy(~self.motion.dynamic))
 
     # ---------------------------------------------------------------- one frame
     def _score_and_init(self):
@@ -245,6 +271,19 @@ class StreamingTrainer:
             else:
                 training_iteration(f, r, self.cams[v], self.tgt_cur[v], skip)
 
+    def _partition(self):
+        """Reorders the Gaussians so that the skipped ones form one contiguous
+        run at the end (stable): A_{t-1}, the initialised gates, the skip mask
+        and the diagnostic ground truth move; everything else of the frame is
+        recomputed from them, and the next frame inherits the order.  The
+        scene is a set of Gaussians, so the order carries no meaning."""
+        n, f = self.cfg.n, self.frame
+        B.qn_partition(n, self.skip, self.perm, self.n_first, self.part_ws)
+        for t in (f.prev, f.log_alpha.view(1, -1), self.skip.view(1, -1), self.truth_static.view(1, -1)):
+            scr = self.scratch_f if t.dtype == torch.float32 else self.scratch_u8
+            B.qn_gather_columns(t.shape[0], n, t, t.shape[1], self.perm, scr, scr.shape[1])
+            t[:, :n].copy_(scr[:t.shape[0], :n])
+
     def _restore(self, snap):
         """Puts back the frame's starting state (gate initialisation and
         decoders); the residual parameters are reset by the caller."""
@@ -253,11 +292,10 @@ class StreamingTrainer:
         f.dec.copy_(snap[1])
         f.dec_bf16.copy_(snap[2])
 
-    def _plain_pass(self):
+    def _plain_train(self):
         self._reset_residuals()
         self._train(None)
         self.frame.decode()
-        return self._psnr_pair(self.frame.attrs)
 
     def _worse(self, rec) -> bool:
         """Whether the skip cost more than max_dpsnr against same-state plain."""
@@ -266,50 +304,63 @@ class StreamingTrainer:
         return rec.psnr_train < rec.psnr_plain_train - self.cfg.max_dpsnr
 
     def run_frame(self, t, mlp: SkipMLP | None) -> FrameRecord:
+        """One frame.  Its `seconds` count the training work only (device
+        synchronised around each part): Eq. 9/10, the skip features, MLP
+        inference and reordering, the training iterations and the final
+        decode, plus the plain re-run of a fallback.  The PSNR evaluations and
+        the harness's same-state plain pass are not counted."""
         c, f, n = self.cfg, self.frame, self.cfg.n
-        psnr_start = self._psnr(f.prev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        clock = _Clock()
+        rec = FrameRecord(t, 0.0, 0.0, self._psnr(f.prev))
+        clock.start()
         self._score_and_init()
         skip = None
-        rec = FrameRecord(t, 0.0, 0.0, psnr_start)
         if mlp is not None:
             B.qn_skip_features(n, f.S, f.n_attr, self.score, self.median, f.prev, self.prev_gate, self.prev_la,
                                self.prev_lp, f.c_gate, self.X, self.prev_static)
             if t > c.train_frames:
-                mlp.predict(self.X, f.S, n, c.threshold, self.skip)
+                mlp.predict(self.X, f.S, n, self.threshold, self.skip)
                 skip = self.skip
-        harness_s = 0.0
+                if c.partition:
+                    self._partition()
+        clock.stop()
         if skip is not None:
             # the evaluation harness: plain gated training of this same frame
-            # from this same state, untimed, gives the PSNR the skip must hold
+            # from this same state gives the PSNR the skip must hold
             snap = (f.log_alpha.clone(), f.dec.clone(), f.dec_bf16.clone())
-            torch.cuda.synchronize()
-            th = time.perf_counter()
-            rec.psnr_plain, rec.psnr_plain_train = self._plain_pass()
-            torch.cuda.synchronize()
-            harness_s = time.perf_counter() - th
+            self._plain_train()
+            rec.psnr_plain, rec.psnr_plain_train = self._psnr_pair(f.attrs)
             self._restore(snap)
+        clock.start()
         self._reset_residuals()
+        if skip is not None:
+            f.decode()                 # A_t of the frozen Gaussians, reused by every skip decode
         self._train(skip)
         f.decode()
-        if skip is not None:
+        clock.stop()
+        if skip is None:
+            rec.psnr = self._psnr(f.attrs)
+        else:
             rec.psnr, rec.psnr_train = self._psnr_pair(f.attrs)
             if self._worse(rec):
                 rec.fallback = True                        # redo the frame with plain gating
+                rec.psnr_skip, rec.psnr_skip_train = rec.psnr, rec.psnr_train
+                clock.start()
                 self._restore(snap)
-                rec.psnr, rec.psnr_train = self._plain_pass()
-        else:
-            rec.psnr = self._psnr(f.attrs)
-        torch.cuda.synchronize()
-        rec.seconds = time.perf_counter() - t0 - harness_s
+                self._plain_train()
+                clock.stop()
+                rec.psnr, rec.psnr_train = self._psnr_pair(f.attrs)
         self._check_capacity()
         if mlp is not None:
+            clock.start()                                  # labels and the MLP's online training count
             B.qn_skip_labels(n, f.S, self.layout.n_latent, f.gate, f.lat, self.labels)
             if t <= c.train_frames:
                 mlp.train(self.X, f.S, self.labels, n, c.mlp_epochs, c.mlp_batch)
-                rec.mlp_loss = float(mlp.loss.item())
             self.prev_static.copy_(self.labels)
+            clock.stop()
+            if t <= c.train_frames:
+                rec.mlp_loss = float(mlp.loss.item())
+        rec.seconds = clock.seconds
         static = f.gate[:n] == 0
         # diagnostics against the ground-truth motion (outside the timed region)
         truth = self.truth_static
@@ -329,12 +380,15 @@ class StreamingTrainer:
         f.prev.copy_(f.attrs)
         return rec
 
-    def run(self, learned: bool, frames: int | None = None):
+    def run(self, learned: bool, frames: int | None = None, threshold: float | None = None):
+        """One arm over the sequence; `threshold` overrides the config's skip
+        threshold for this run."""
         frames = frames or self.cfg.frames
+        self.threshold = self.cfg.threshold if threshold is None else float(threshold)
         self.reset()
         mlp = SkipMLP(self.cfg.seed, self.cfg.mlp_lr) if learned else None
         if mlp is not None:                                 # load the skip kernels before any timing
-            mlp.predict(self.X, self.frame.S, self.cfg.n, self.cfg.threshold, self.skip)
+            mlp.predict(self.X, self.frame.S, self.cfg.n, self.threshold, self.skip)
             torch.cuda.synchronize()
         self._render_targets(0, self.tgt_cur)
         out = []
@@ -345,19 +399,15 @@ class StreamingTrainer:
         return out
 
 
-def compare(cfg: SequenceConfig, frames: int | None = None) -> dict:
-    """Runs the plain arm, then the learned-skip arm, on the same sequence and
-    GPU; returns per-frame records and the s/frame comparison."""
-    tr = StreamingTrainer(cfg)
-    plain = tr.run(learned=False, frames=frames)
-    learned = tr.run(learned=True, frames=frames)
+def summarize(cfg: SequenceConfig, plain: list, learned: list) -> dict:
+    """s/frame of both arms on the skip frames and the skip's PSNR cost
+    against same-state plain training (held-out view and training views)."""
     skip_frames = [i for i, r in enumerate(learned) if r.t > cfg.train_frames]
     sp = [plain[i].seconds for i in skip_frames]
     sl = [learned[i].seconds for i in skip_frames]
     dps = [learned[i].psnr - learned[i].psnr_plain for i in skip_frames]
     dpt = [learned[i].psnr_train - learned[i].psnr_plain_train for i in skip_frames]
     return {
-        "plain": plain, "learned": learned,
         "s_per_frame_plain_all": float(np.mean([r.seconds for r in plain])),
         "s_per_frame_learned_all": float(np.mean([r.seconds for r in learned])),
         "s_per_frame_plain_skip_frames": float(np.mean(sp)) if sp else float("nan"),
@@ -369,3 +419,18 @@ def compare(cfg: SequenceConfig, frames: int | None = None) -> dict:
         "fallbacks": int(sum(r.fallback for r in learned)),
         "mean_skipped": float(np.mean([learned[i].skipped for i in skip_frames])) if skip_frames else 0.0,
     }
+
+
+def compare(cfg: SequenceConfig, frames: int | None = None, extra_thresholds=()) -> dict:
+    """Runs the plain arm, then the learned-skip arm (the config's threshold,
+    then each of extra_thresholds), on the same sequence and GPU; returns
+    per-frame records and the s/frame comparisons."""
+    tr = StreamingTrainer(cfg)
+    plain = tr.run(learned=False, frames=frames)
+    learned = tr.run(learned=True, frames=frames)
+    out = {"plain": plain, "learned": learned, **summarize(cfg, plain, learned)}
+    out["by_threshold"] = {}
+    for thr in extra_thresholds:
+        rec = tr.run(learned=True, frames=frames, threshold=thr)
+        out["by_threshold"][float(thr)] = {"learned": rec, **summarize(cfg, plain, rec)}
+    return out

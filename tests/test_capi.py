@@ -60,14 +60,14 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     lay.attr_begin[0], lay.attr_count[0], lay.lat_dim[0] = 1, 2, 4      # overlaps the position planes
     gp = B.make_gate(0.3, -0.5, 1.01)
     assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp),
-                                       None, None, None, None) == B.QN_ERR_INVALID_ARG
+                                       None, None, None, None, None) == B.QN_ERR_INVALID_ARG
     assert b"category" in B.lib().qn_last_error()
     assert B.lib().qn_render_bwd(None, None, None, None, None, None, None, None, None, None, None, None) == \
         B.QN_ERR_INVALID_ARG
     gp_bad = B.make_gate(0.3, 0.5, 1.01)
     lay.attr_begin[0] = 3
     assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp_bad),
-                                       None, None, None, None) == B.QN_ERR_INVALID_ARG
+                                       None, None, None, None, None) == B.QN_ERR_INVALID_ARG
     assert B.lib().qn_adam(1, 4, 4, None, None, None, None, 0, 0.1, 0.9, 0.999, 1e-8, None, None, None) == \
         B.QN_ERR_INVALID_ARG
     assert B.lib().qn_bin_sort_workspace_size(-1, 4, 4) == 0
@@ -78,3 +78,10 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     groups[0].rows, groups[0].n, groups[0].stride = 1, 8, 4                  # stride < n
     assert B.lib().qn_adam_groups(1, groups, 16, 0.9, 0.999, 1e-8, None, None) == B.QN_ERR_INVALID_ARG
     assert b"stride" in B.lib().qn_last_error()
+    assert B.lib().qn_partition_workspace_size(-1) == 0
+    assert B.lib().qn_partition_workspace_size(2049) == 4 * 4
+    assert B.lib().qn_partition(-1, None, None, None, None, 0, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_partition(10, 16, 16, 16, 16, 4, None) == B.QN_ERR_INVALID_ARG      # workspace too small
+    assert b"workspace" in B.lib().qn_last_error()
+    assert B.lib().qn_gather_columns(1, 4, 3, 16, 4, 16, 32, 4, None) == B.QN_ERR_INVALID_ARG   # elem_bytes
+    assert B.lib().qn_gather_columns(1, 4, 4, 16, 4, 16, 16, 4, None) == B.QN_ERR_INVALID_ARG   # aliasing

@@ -395,6 +395,32 @@ def test_adam_matches_oracle():
     assert np.array_equal(got_b[:, skip == 0], S.to_bf16_values(P.cpu().numpy()[:, :n][:, skip == 0]))
 
 
+def test_decode_skip_freezes_columns():
+    """Skipped Gaussians keep their out columns and gate entries; the others
+    match the oracle; L_reg sums the others only."""
+    from paper_2412_04469_gb300.pipeline import QueenFrame
+    n, deg = 3000, 1
+    lay = DecoderLayout.default(sh_degree=deg, latent=8)
+    prev = S.make_scene(n, deg, 21)
+    res = S.make_residuals(n, lay, 21)
+    skip = (np.random.default_rng(4).uniform(size=n) < 0.6).astype(np.uint8)
+    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    f.attrs.fill_(7.0)
+    f.gate.fill_(3.0)
+    f.decode(skip=up(skip, torch.uint8))
+    torch.cuda.synchronize()
+    A_ref, g_ref, _ = oracle.decode(prev.astype(np.float64), res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1)
+    got = f.attrs.cpu().numpy()[:, :n]
+    gg = f.gate.cpu().numpy()[:n]
+    assert np.all(got[:, skip == 1] == 7.0) and np.all(gg[skip == 1] == 3.0)
+    close(got[:, skip == 0], A_ref[:, skip == 0], rtol=2e-3, floor_frac=0.01, what="A_t")
+    close(gg[skip == 0], g_ref[skip == 0], rtol=1e-5, floor_frac=0.01, what="gate")
+    keep = skip == 0
+    shift = TAU * np.log(-G0 / G1)
+    lreg_ref = float((1 / (1 + np.exp(-(res.log_alpha.astype(np.float64)[keep] - shift)))).sum())
+    assert float(f.lreg.item()) == pytest.approx(lreg_ref, rel=1e-4)
+
+
 B1_F32, B2_F32 = float(np.float32(0.9)), float(np.float32(0.999))
 
 
@@ -465,6 +491,33 @@ def test_graph_replay_equals_eager():
                                           r.d_splats, r.img, r.loss)])
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n,frac", [(1, 0.5), (1000, 0.0), (1000, 1.0), (2500, 0.8), (70_001, 0.3)])
+def test_partition_is_a_stable_partition(n, frac):
+    rng = np.random.default_rng(n)
+    flags = (rng.uniform(size=n) < frac).astype(np.uint8)
+    perm = torch.zeros(n, device="cuda", dtype=torch.int32)
+    nf = torch.zeros(1, device="cuda", dtype=torch.int32)
+    ws = torch.zeros(B().qn_partition_workspace_size(n), device="cuda", dtype=torch.uint8)
+    B().qn_partition(n, up(flags, torch.uint8), perm, nf, ws)
+    torch.cuda.synchronize()
+    ref = np.argsort(flags, kind="stable")
+    assert np.array_equal(perm.cpu().numpy(), ref)
+    assert int(nf.item()) == int((flags == 0).sum())
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.int16, torch.float32, torch.float64])
+def test_gather_columns(dtype):
+    rng = np.random.default_rng(3)
+    rows, n, ss, ds = 3, 1500, 1504, 1600
+    src = torch.from_numpy(rng.integers(0, 100, size=(rows, ss))).to("cuda", dtype)
+    perm = rng.permutation(n).astype(np.int32)
+    dst = torch.zeros((rows, ds), device="cuda", dtype=dtype)
+    B().qn_gather_columns(rows, n, src, ss, up(perm, torch.int32), dst, ds)
+    torch.cuda.synchronize()
+    assert torch.equal(dst[:, :n].cpu(), src.cpu()[:, perm])
+    assert torch.count_nonzero(dst[:, n:]) == 0
 
 
 # ---------------------------------------------------------------- whole iteration
