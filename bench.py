@@ -39,6 +39,26 @@ L2_FLUSH_BYTES = 256 << 20
 KERNELS_PER_STAGE = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 2, "render_bwd": 1,
                      "gather": 1, "project_bwd": 1, "decode_bwd": 2, "adam": 2}
 STAGES = list(KERNELS_PER_STAGE)
+# DRAM bytes per launch of a kernel on the full workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); valid while the sources it
+# was built from are unchanged (their SHA-256 is checked), else reported null
+NCU_TRAFFIC = {
+    "render_bwd": {"bytes": 37.969664e6 + 10.111488e6,
+                   "sources": ("paper_2412_04469_gb300/csrc/render.cu", "paper_2412_04469_gb300/csrc/common.cuh"),
+                   "sha256": "8ea8042485ce8bc3aa7f5dd3178beec519d092b52dbcbe8170f52f90062036f1"},
+}
+
+
+def ncu_traffic(stage):
+    import hashlib
+    rec = NCU_TRAFFIC.get(stage)
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest() == rec["sha256"] else None
 
 
 def workload_name(name):
@@ -277,10 +297,11 @@ def run_gpu(args):
     n_vis = int((rast.rects[:, 2] > rast.rects[:, 0]).sum().item())
     px = W * H
     # algorithmic bytes per launch: what each stage must read and write once
+    # (a projected record or a pair's gradient record is 48 bytes)
     algo_bytes = {
         "decode": 620.0 * n, "project": 300.0 * n, "bin_sort": 20.0 * n + 36.0 * P,
-        "render_fwd": 40.0 * Pvis + 20.0 * px, "loss": 36.0 * px,
-        "render_bwd": 32.0 * px + 40.0 * Pvis + 36.0 * Pvis, "gather": 36.0 * Pvis + 36.0 * n_vis,
+        "render_fwd": 20.0 * px + 4.0 * Pvis + 48.0 * n_vis, "loss": 36.0 * px,
+        "render_bwd": 20.0 * px + 52.0 * Pvis + 48.0 * n_vis, "gather": 48.0 * Pvis + 48.0 * n_vis,
         "project_bwd": 508.0 * n, "decode_bwd": 524.0 * n,
         "adam": 28.0 * ((lay.n_latent + 4) * n + lay.n_dec),
     }
@@ -290,7 +311,7 @@ def run_gpu(args):
     achieved = algo_bytes[dom] / (avg[dom] * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-            "traffic": None, "algorithmic_bytes": algo_bytes[dom]}
+            "traffic": ncu_traffic(dom), "algorithmic_bytes": algo_bytes[dom]}
     # FP32 arithmetic of the compositing adjoint as the method defines it:
     # 12 flop per alpha evaluation (every pixel up to its last contributor),
     # 41 more per contributing evaluation, and a 45-flop reduction of the
@@ -305,7 +326,8 @@ def run_gpu(args):
         roof_alu = dict(roof)
         roof = {"bound": "alu", "kernel": dom, "achieved": alu["achieved"], "peak": alu["peak"],
                 "unit": "TFLOP/s", "frac": alu["frac"], "peak_source": "152 SM x 128 FP32 lanes x 2 x median SM clock",
-                "traffic": None, "hbm": {k: roof_alu[k] for k in ("achieved", "peak", "unit", "frac")}}
+                "traffic": ncu_traffic(dom), "algorithmic_bytes": algo_bytes[dom],
+                "hbm": {k: roof_alu[k] for k in ("achieved", "peak", "unit", "frac")}}
     else:
         roof["alu_render_bwd"] = alu
 
