@@ -35,7 +35,7 @@ struct Header {
 };
 
 struct Layout {
-    size_t hdr, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, total;
+    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, total;
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
@@ -45,7 +45,8 @@ Layout layout_of(int n, int n_tiles) {
     const size_t nb = (size_t)div_up(n > 0 ? n : 1, SORT_TILE);
     const size_t chunks = (size_t)div_up(n > 0 ? n : 1, CHUNK);
     size_t o = 0;
-    L.hdr = o; o = align_up(o + sizeof(Header));
+    L.hdr = o; o = o + sizeof(Header);
+    L.dtot = o; o = align_up(o + 4 * 4 * (size_t)RADIX);      // digit totals of the 4 passes
     L.keys0 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
     L.vals0 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
     L.keys1 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
@@ -76,7 +77,8 @@ __global__ void k_bin_prep(int n, const float *__restrict__ depth, int dstride,
 
 // ---------------------------------------------------------------- step 1: radix sort of depth keys
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, const uint32_t *__restrict__ keys,
-                                                             uint32_t *__restrict__ hist) {
+                                                             uint32_t *__restrict__ hist,
+                                                             uint32_t *__restrict__ dtot) {
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -87,58 +89,38 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, c
         if (i < n) atomicAdd(&h[(keys[i] >> shift) & (RADIX - 1)], 1u);
     }
     __syncthreads();
-    hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+    const uint32_t c = h[threadIdx.x];
+    hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = c;
+    if (c) atomicAdd(&dtot[threadIdx.x], c);              // integer: the total is order-independent
 }
 
 // Exclusive scan, in place and in digit-major order, of the [RADIX][nb]
-// per-block digit histogram.  One block: warp w owns digits w, w + 32, ...;
-// its lanes walk a digit's blocks 32 at a time (coalesced).
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int nb) {
-    __shared__ uint32_t dsum[RADIX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = warp; d < RADIX; d += 32) {
-        uint32_t s = 0;
-        for (int b = lane; b < nb; b += 32) s += hist[(size_t)d * nb + b];
-        s = __reduce_add_sync(FULL, s);
-        if (lane == 0) dsum[d] = s;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        constexpr int PER = RADIX / 32;
-        uint32_t v[PER], t = 0;
+// per-block digit histogram: one warp per digit (RADIX / 32 blocks of 32
+// warps).  Warp d starts from the count of all smaller digits (from the digit
+// totals) and walks its digit's blocks 32 at a time (coalesced).
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int nb,
+                                                     const uint32_t *__restrict__ dtot) {
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * 32 + (threadIdx.x >> 5);
+    constexpr int PER = RADIX / 32;
+    uint32_t below = 0;
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            v[i] = dsum[lane * PER + i];
-            t += v[i];
-        }
-        uint32_t incl = t;
+    for (int q = 0; q < PER; ++q) {
+        const int e = lane * PER + q;
+        below += e < d ? dtot[e] : 0u;
+    }
+    uint32_t run = __reduce_add_sync(FULL, below);
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        const uint32_t v = b < nb ? hist[(size_t)d * nb + b] : 0u;
+        uint32_t incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += x;
         }
-        uint32_t run = incl - t;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            dsum[lane * PER + i] = run;
-            run += v[i];
-        }
-    }
-    __syncthreads();
-    for (int d = warp; d < RADIX; d += 32) {
-        uint32_t run = dsum[d];
-        for (int b0 = 0; b0 < nb; b0 += 32) {
-            const int b = b0 + lane;
-            const uint32_t v = b < nb ? hist[(size_t)d * nb + b] : 0u;
-            uint32_t incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t x = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += x;
-            }
-            if (b < nb) hist[(size_t)d * nb + b] = run + incl - v;
-            run += __shfl_sync(FULL, incl, 31);
-        }
+        if (b < nb) hist[(size_t)d * nb + b] = run + incl - v;
+        run += __shfl_sync(FULL, incl, 31);
     }
 }
 
@@ -202,7 +184,7 @@ struct ChunkSmem {
 // bounding box of the rects).
 __device__ void load_chunk_rects(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
                                  const int4 *__restrict__ rects, uint32_t n_vis, ChunkSmem &s) {
-    const int j = threadIdx.x, warp = j >> 5;
+    const int j = threadIdx.x;
     const uint32_t g = (uint32_t)c * CHUNK + j;
     int4 r = make_int4(0, 0, 0, 0);
     uint32_t id = 0;
@@ -583,15 +565,17 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     uint32_t *tile_off = reinterpret_cast<uint32_t *>(ws + L.tile_off);
     const int4 *r4 = reinterpret_cast<const int4 *>(rects);
 
-    if (cudaMemsetAsync(hdr, 0, sizeof(Header), s) != cudaSuccess) return check_launch("qn_bin_sort memset");
+    uint32_t *dtot = reinterpret_cast<uint32_t *>(ws + L.dtot);
+    if (cudaMemsetAsync(hdr, 0, L.keys0 - L.hdr, s) != cudaSuccess)      // header and digit totals
+        return check_launch("qn_bin_sort memset");
     k_bin_prep<<<div_up(n, 256), 256, 0, s>>>(n, depth, depth_stride, r4, k0, v0, hdr);
     const int nb = div_up(n, SORT_TILE);
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         uint32_t *ki = (pass & 1) ? k1 : k0, *vi = (pass & 1) ? v1 : v0;
         uint32_t *ko = (pass & 1) ? k0 : k1, *vo = (pass & 1) ? v0 : v1;
-        k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist);
-        k_radix_scan<<<1, 1024, 0, s>>>(hist, nb);
+        k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist, dtot + pass * RADIX);
+        k_radix_scan<<<RADIX / 32, 1024, 0, s>>>(hist, nb, dtot + pass * RADIX);
         k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo);
     }
     // after 4 passes the sorted (depth, index) order is back in k0 / v0

@@ -34,6 +34,9 @@ __device__ __forceinline__ float latent_int(float v) {
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + __expf(-x)); }
 
+// LT > 0: every category has latent width LT (compile-time loops, D rows
+// read as float4 broadcasts); LT == 0: any layout within the limits.
+template <int LT>
 __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__restrict__ prev,
                                                 const float *__restrict__ lat,
                                                 const uint16_t *__restrict__ dec,
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
                                                 const float *__restrict__ la,
                                                 const uint8_t *__restrict__ skip, float *__restrict__ out,
                                                 float *__restrict__ gate, float *__restrict__ lreg) {
-    __shared__ float sD[MAX_RES_PLANES * QN_MAX_LATENT];
+    __shared__ __align__(16) float sD[MAX_RES_PLANES * QN_MAX_LATENT];
     __shared__ float sred[8];
     for (int k = threadIdx.x; k < a.n_dec; k += blockDim.x) sD[k] = bf16_to_f32(dec[k]);
     __syncthreads();
@@ -57,20 +60,41 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
 #pragma unroll
         for (int d = 0; d < 3; ++d) out[d * S + i] = prev[d * S + i] + g * lp[d * S + i];
         for (int c = 0; c < a.n_cat; ++c) {
-            float l[QN_MAX_LATENT];
-            const int L = a.ld[c];
-#pragma unroll
-            for (int k = 0; k < QN_MAX_LATENT; ++k)
-                if (k < L) l[k] = latent_int(lat[(size_t)(a.lat_off[c] + k) * S + i]);
             const float *D = sD + a.dec_off[c];
-#pragma unroll 8
-            for (int r = 0; r < a.ac[c]; ++r) {
-                float acc = 0.f;
+            if (LT > 0) {
+                float l[LT > 0 ? LT : 1];
+#pragma unroll
+                for (int k = 0; k < LT; ++k) l[k] = latent_int(lat[(size_t)(a.lat_off[c] + k) * S + i]);
+#pragma unroll 4
+                for (int r = 0; r < a.ac[c]; ++r) {
+                    const float4 *Dr = reinterpret_cast<const float4 *>(D + r * LT);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k4 = 0; k4 < LT / 4; ++k4) {
+                        const float4 w = Dr[k4];
+                        acc = fmaf(w.x, l[4 * k4], acc);                // Eq. 5
+                        acc = fmaf(w.y, l[4 * k4 + 1], acc);
+                        acc = fmaf(w.z, l[4 * k4 + 2], acc);
+                        acc = fmaf(w.w, l[4 * k4 + 3], acc);
+                    }
+                    const size_t o = (size_t)(a.ab[c] + r) * S + i;
+                    out[o] = prev[o] + acc;                             // Eq. 4
+                }
+            } else {
+                float l[QN_MAX_LATENT];
+                const int L = a.ld[c];
 #pragma unroll
                 for (int k = 0; k < QN_MAX_LATENT; ++k)
-                    if (k < L) acc = fmaf(D[r * L + k], l[k], acc);     // Eq. 5
-                const size_t o = (size_t)(a.ab[c] + r) * S + i;
-                out[o] = prev[o] + acc;                                 // Eq. 4
+                    if (k < L) l[k] = latent_int(lat[(size_t)(a.lat_off[c] + k) * S + i]);
+#pragma unroll 8
+                for (int r = 0; r < a.ac[c]; ++r) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < QN_MAX_LATENT; ++k)
+                        if (k < L) acc = fmaf(D[r * L + k], l[k], acc);     // Eq. 5
+                    const size_t o = (size_t)(a.ab[c] + r) * S + i;
+                    out[o] = prev[o] + acc;                             // Eq. 4
+                }
             }
         }
 #pragma unroll 4
@@ -89,6 +113,14 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
     }
 }
 
+// Latent width shared by every category, if it is 8 (the layout with a
+// compile-time kernel), else 0.
+int uniform_width8(const DecodeArgs &a) {
+    for (int c = 0; c < a.n_cat; ++c)
+        if (a.ld[c] != 8) return 0;
+    return 8;
+}
+
 // Adjoint, one fused kernel: a block stages 32 Gaussians' residual gradients
 // dr and rounded latents l in shared memory, then writes d_lat = D^T dr per
 // (Gaussian, latent) and accumulates its share of dD = sum dr l^T in
@@ -98,6 +130,53 @@ constexpr int BWD_THREADS = 256;
 constexpr int BWD_TILE = 32;
 constexpr int BWD_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + BWD_THREADS - 1) / BWD_THREADS;
 
+constexpr int ROWS_PER_PASS = BWD_THREADS / BWD_TILE;
+constexpr int PF_DR = (MAX_RES_PLANES + ROWS_PER_PASS - 1) / ROWS_PER_PASS;   // residual rows per thread
+constexpr int PF_L = MAX_LAT_TOTAL / ROWS_PER_PASS;                            // latent rows per thread
+
+// The global values one thread stages for one tile: residual gradients of
+// rows row0 + 8m, latents of rows row0 + 8m, and (row0 == 0) the gate inputs.
+struct TileRegs {
+    float dr[PF_DR], l[PF_L];
+    float la, dp[3], lp[3];
+    bool valid, sk;
+};
+
+__device__ __forceinline__ void load_tile(const DecodeArgs &a, int base, int lane, int row0,
+                                          const float *__restrict__ lat, const float *__restrict__ lp,
+                                          const float *__restrict__ la, const float *__restrict__ d_out,
+                                          const uint8_t *__restrict__ skip, TileRegs &t) {
+    const size_t S = a.stride;
+    const int i = base + lane;
+    const int n_res = a.n_attr - 3;
+    t.valid = i < a.n;
+    t.sk = t.valid && skip && skip[i];
+    const bool use = t.valid && !t.sk;
+#pragma unroll
+    for (int m = 0; m < PF_DR; ++m) {
+        const int r = row0 + m * ROWS_PER_PASS;
+        t.dr[m] = (use && r < n_res) ? d_out[(size_t)(r + 3) * S + i] : 0.f;
+    }
+#pragma unroll
+    for (int m = 0; m < PF_L; ++m) {
+        const int k = row0 + m * ROWS_PER_PASS;
+        t.l[m] = (use && k < a.n_lat) ? lat[(size_t)k * S + i] : 0.f;
+    }
+    if (row0 == 0 && use) {
+        t.la = la[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            t.dp[d] = d_out[d * S + i];
+            t.lp[d] = lp[d * S + i];
+        }
+    }
+}
+
+// LT > 0: every category has latent width LT, so thread row0 computes latent
+// row0 of each category (compile-time indexing); LT == 0: any layout.
+// Software-pipelined: while a tile is computed from shared memory, the next
+// tile's values are already being loaded into registers.
+template <int LT>
 __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
     DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
     const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
@@ -130,14 +209,14 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
     const size_t S = a.stride;
     const int n_res = a.n_attr - 3;
     const int lane = threadIdx.x & (BWD_TILE - 1), row0 = threadIdx.x / BWD_TILE;
-    constexpr int ROWS_PER_PASS = BWD_THREADS / BWD_TILE;
-    __syncthreads();
-    for (int base = blockIdx.x * BWD_TILE; base < a.n; base += gridDim.x * BWD_TILE) {
+    const int step = gridDim.x * BWD_TILE;
+    TileRegs t;
+    load_tile(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
+    for (int base = blockIdx.x * BWD_TILE; base < a.n; base += step) {
         const int i = base + lane;
-        const bool valid = i < a.n;
-        const bool sk = valid && skip && skip[i];
-        // a tile of skipped Gaussians only zeroes their gradients (block-uniform)
-        if (__syncthreads_and(!valid || sk)) {
+        const bool valid = t.valid, sk = t.sk;
+        // the barrier also keeps the previous tile's readers ahead of the stores below
+        if (__syncthreads_and(!valid || sk)) {            // a tile of skipped Gaussians only zeroes them
             if (valid) {
                 for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) d_lat[(size_t)k * S + i] = 0.f;
                 if (row0 == 0) {
@@ -145,39 +224,57 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
                     d_la[i] = 0.f;
                 }
             }
+            load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
             continue;
         }
-        // stage the tile (coalesced: lanes are consecutive Gaussians)
-        for (int r = row0; r < n_res; r += ROWS_PER_PASS)
-            s_dr[r][lane] = (valid && !sk) ? d_out[(size_t)(r + 3) * S + i] : 0.f;
-        for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS)
-            s_l[k][lane] = valid ? latent_int(lat[(size_t)k * S + i]) : 0.f;
+#pragma unroll
+        for (int m = 0; m < PF_DR; ++m) {
+            const int r = row0 + m * ROWS_PER_PASS;
+            if (r < n_res) s_dr[r][lane] = t.dr[m];
+        }
+#pragma unroll
+        for (int m = 0; m < PF_L; ++m) {
+            const int k = row0 + m * ROWS_PER_PASS;
+            if (k < a.n_lat) s_l[k][lane] = latent_int(t.l[m]);
+        }
         if (row0 == 0 && valid) {
-            const float l_a = la[i];
-            const float gh = sigmoidf_(l_a / a.tau);
+            const float gh = sigmoidf_(t.la / a.tau);
             const float gt = gh * (a.g1 - a.g0) + a.g0;
             const float g = fminf(1.f, fmaxf(0.f, gt));
             const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
             float dot = 0.f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const float dp = d_out[d * S + i];
-                d_lp[d * S + i] = sk ? 0.f : g * dp;
-                dot = fmaf(dp, lp[d * S + i], dot);
+                d_lp[d * S + i] = sk ? 0.f : g * t.dp[d];
+                dot = fmaf(t.dp[d], t.lp[d], dot);
             }
-            const float p = sigmoidf_(l_a - a.shift);
+            const float p = sigmoidf_(t.la - a.shift);
             d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
         }
+        load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
         __syncthreads();
         // STE: d_lat[k] = sum_r D[r][k] dr[r] for this thread's (latent, Gaussian) pairs
         if (valid) {
-            for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) {
-                const int c = s_cat[k], L = a.ld[c], kk = k - a.lat_off[c];
-                const float *D = sD + a.dec_off[c];
-                const int rb = a.ab[c] - 3;
-                float sum = 0.f;
-                for (int r = 0; r < a.ac[c]; ++r) sum = fmaf(D[r * L + kk], s_dr[rb + r][lane], sum);
-                d_lat[(size_t)k * S + i] = sk ? 0.f : sum;
+            if (LT > 0) {
+#pragma unroll
+                for (int c = 0; c < QN_MAX_CATEGORIES; ++c) {
+                    if (c >= a.n_cat) break;
+                    const float *D = sD + a.dec_off[c] + row0;
+                    const float *dr = &s_dr[a.ab[c] - 3][lane];
+                    float sum = 0.f;
+#pragma unroll 4
+                    for (int r = 0; r < a.ac[c]; ++r) sum = fmaf(D[r * LT], dr[r * (BWD_TILE + 1)], sum);
+                    d_lat[(size_t)(a.lat_off[c] + row0) * S + i] = sk ? 0.f : sum;
+                }
+            } else {
+                for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) {
+                    const int c = s_cat[k], L = a.ld[c], kk = k - a.lat_off[c];
+                    const float *D = sD + a.dec_off[c];
+                    const int rb = a.ab[c] - 3;
+                    float sum = 0.f;
+                    for (int r = 0; r < a.ac[c]; ++r) sum = fmaf(D[r * L + kk], s_dr[rb + r][lane], sum);
+                    d_lat[(size_t)k * S + i] = sk ? 0.f : sum;
+                }
             }
         }
         // dD[c][r][k] += sum over the tile of dr[r] l[k]
@@ -191,7 +288,6 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
             for (int j = 0; j < BWD_TILE; ++j) sum = fmaf(pr[j], pl[j], sum);
             acc[q] = sum;
         }
-        __syncthreads();
     }
     // this block's partial dD; summed over blocks in block order afterwards
 #pragma unroll
@@ -259,8 +355,8 @@ extern "C" int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, 
     cudaStream_t s = qn::as_stream(stream);
     if (lreg && cudaMemsetAsync(lreg, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("decode memset");
     if (n == 0) return QN_OK;
-    qn::k_decode<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, skip, out, gate,
-                                                         lreg);
+    auto kern = qn::uniform_width8(a) ? qn::k_decode<8> : qn::k_decode<0>;
+    kern<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, skip, out, gate, lreg);
     return qn::check_launch("qn_decode_residuals");
 }
 
@@ -284,7 +380,8 @@ extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_at
     }
     int grid = qn::grid_for(n, qn::BWD_TILE, 4);
     if (grid > QN_DECODE_BWD_BLOCKS) grid = QN_DECODE_BWD_BLOCKS;
-    qn::k_decode_bwd<<<grid, qn::BWD_THREADS, 0, s>>>(a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat,
+    auto kern = qn::uniform_width8(a) ? qn::k_decode_bwd<8> : qn::k_decode_bwd<0>;
+    kern<<<grid, qn::BWD_THREADS, 0, s>>>(a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat,
                                                       partials, d_lp, d_log_alpha);
     if (a.n_dec > 0) qn::k_sum_partials<<<qn::sum_partials_grid(a.n_dec), 256, 0, s>>>(a.n_dec, grid, partials, d_dec);
     return qn::check_launch("qn_decode_residuals_bwd");

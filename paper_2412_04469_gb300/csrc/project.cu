@@ -152,9 +152,13 @@ __device__ __forceinline__ bool alpha_box(float opac, float a, float c, float &h
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_project(int n, int S_, int deg, CamArgs cm, float blur, int tight,
+// DEG: the SH degree, a template parameter so the basis and its loops are
+// unrolled into registers.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project(int n, int S_, CamArgs cm, float blur, int tight,
                                                  const float *__restrict__ A, float4 *__restrict__ splat,
                                                  int4 *__restrict__ rects) {
+    constexpr int deg = DEG;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const size_t S = S_;
@@ -208,8 +212,9 @@ __global__ void __launch_bounds__(256) k_project(int n, int S_, int deg, CamArgs
                 dx *= inv; dy *= inv; dz *= inv;
                 float Y[16];
                 sh_basis(deg, dx, dy, dz, Y);
-                const int K = (deg + 1) * (deg + 1);
+                constexpr int K = (deg + 1) * (deg + 1);
                 float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
                 for (int k = 0; k < K; ++k)
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(A[(11 + 3 * k + ch) * S + i], Y[k], col[ch]);
@@ -224,11 +229,14 @@ __global__ void __launch_bounds__(256) k_project(int n, int S_, int deg, CamArgs
     rects[i] = rc;
 }
 
-__global__ void __launch_bounds__(128) k_project_bwd(int n, int S_, int deg, int n_attr, CamArgs cm,
-                                                     float blur, const float *__restrict__ A,
+template <int DEG>
+__global__ void __launch_bounds__(128) k_project_bwd(int n, int S_, CamArgs cm, float blur,
+                                                     const float *__restrict__ A,
                                                      const float4 *__restrict__ dsp,
                                                      const uint8_t *__restrict__ skip,
                                                      float *__restrict__ dA) {
+    constexpr int deg = DEG;
+    constexpr int n_attr = 11 + 3 * (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const size_t S = S_;
@@ -252,6 +260,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(int n, int S_, int deg, int
         }
     }
     if (!vis) {
+#pragma unroll
         for (int k = 0; k < n_attr; ++k) dA[k * S + i] = 0.f;
         return;
     }
@@ -268,13 +277,15 @@ __global__ void __launch_bounds__(128) k_project_bwd(int n, int S_, int deg, int
         const float x = vx * inv, y = vy * inv, z = vz * inv;
         float Y[16];
         sh_basis(deg, x, y, z, Y);
-        const int K = (deg + 1) * (deg + 1);
+        constexpr int K = (deg + 1) * (deg + 1);
         float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
         for (int k = 0; k < K; ++k)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(A[(11 + 3 * k + ch) * S + i], Y[k], col[ch]);
         const float gr[3] = {col[0] > 0.f ? g2.x : 0.f, col[1] > 0.f ? g2.y : 0.f, col[2] > 0.f ? g2.z : 0.f};
         float w[16];
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             float s = 0.f;
 #pragma unroll
@@ -422,8 +433,10 @@ extern "C" int qn_project(int32_t n, int32_t n_stride, int32_t sh_degree, const 
     QN_REQUIRE(n == 0 || (attrs && splats && rects), "null pointer argument");
     QN_REQUIRE(((uintptr_t)splats & 15) == 0 && ((uintptr_t)rects & 15) == 0, "splats/rects must be 16-byte aligned");
     if (n == 0) return QN_OK;
-    qn::k_project<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(
-        n, n_stride, sh_degree, cm, blur, tight_rects != 0, attrs, reinterpret_cast<float4 *>(splats),
+    decltype(&qn::k_project<0>) kern[4] = {qn::k_project<0>, qn::k_project<1>, qn::k_project<2>,
+                                            qn::k_project<3>};
+    kern[sh_degree]<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(
+        n, n_stride, cm, blur, tight_rects != 0, attrs, reinterpret_cast<float4 *>(splats),
         reinterpret_cast<int4 *>(rects));
     return qn::check_launch("qn_project");
 }
@@ -440,9 +453,10 @@ extern "C" int qn_project_bwd(int32_t n, int32_t n_stride, int32_t sh_degree, co
     QN_REQUIRE(n == 0 || (attrs && d_splats && d_attrs), "null pointer argument");
     QN_REQUIRE(((uintptr_t)d_splats & 15) == 0, "d_splats must be 16-byte aligned");
     if (n == 0) return QN_OK;
-    const int n_attr = 11 + 3 * (sh_degree + 1) * (sh_degree + 1);
-    qn::k_project_bwd<<<qn::div_up(n, 128), 128, 0, qn::as_stream(stream)>>>(
-        n, n_stride, sh_degree, n_attr, cm, blur, attrs, reinterpret_cast<const float4 *>(d_splats), skip,
+    decltype(&qn::k_project_bwd<0>) kern[4] = {qn::k_project_bwd<0>, qn::k_project_bwd<1>,
+                                                qn::k_project_bwd<2>, qn::k_project_bwd<3>};
+    kern[sh_degree]<<<qn::div_up(n, 128), 128, 0, qn::as_stream(stream)>>>(
+        n, n_stride, cm, blur, attrs, reinterpret_cast<const float4 *>(d_splats), skip,
         d_attrs);
     return qn::check_launch("qn_project_bwd");
 }

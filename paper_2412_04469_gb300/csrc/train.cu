@@ -56,10 +56,21 @@ __global__ void __launch_bounds__(256) k_adam(int rows, int n, int stride, float
 struct AdamGroups {
     qn_adam_group g[QN_ADAM_MAX_GROUPS];
     int row_start[QN_ADAM_MAX_GROUPS + 1];       // first grid row of each group
+    int vec[QN_ADAM_MAX_GROUPS];                 // 16-byte aligned planes: four elements per thread
     int n_groups;
 };
 
 __global__ void k_step_increment(int32_t *step) { *step += 1; }
+
+struct AdamConst {
+    float b1, b2, eps, ibc1, ibc2, lr;
+};
+
+__device__ __forceinline__ float adam_update(const AdamConst &c, float p, float g, float &m, float &v) {
+    m = fmaf(c.b1, m, (1.f - c.b1) * g);
+    v = fmaf(c.b2, v, (1.f - c.b2) * g * g);
+    return p - c.lr * (m * c.ibc1) / (sqrtf(v * c.ibc2) + c.eps);
+}
 
 // Grid row y updates row y - row_start[g] of the group g that holds it.
 __global__ void __launch_bounds__(256) k_adam_groups(const __grid_constant__ AdamGroups G,
@@ -78,16 +89,46 @@ __global__ void __launch_bounds__(256) k_adam_groups(const __grid_constant__ Ada
     const qn_adam_group &P = G.g[gi];
     const int r = y - G.row_start[gi];
     const uint8_t *sk = P.use_skip ? skip : nullptr;
-    const float ibc1 = ibc[0], ibc2 = ibc[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const size_t o = (size_t)r * P.stride + i;
+    const AdamConst c{b1, b2, eps, ibc[0], ibc[1], P.lr};
+    const size_t row = (size_t)r * P.stride;
+    const int stride = gridDim.x * blockDim.x;
+    int done = 0;                                      // elements covered by the vector loop
+    if (G.vec[gi]) {
+        const int nq = P.n / 4;
+        done = nq * 4;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+            const int i = 4 * q;
+            uchar4 s4 = make_uchar4(0, 0, 0, 0);
+            if (sk) s4 = *reinterpret_cast<const uchar4 *>(sk + i);
+            if (s4.x && s4.y && s4.z && s4.w) continue;
+            const float4 g4 = *reinterpret_cast<const float4 *>(P.grad + row + i);
+            float4 m4 = *reinterpret_cast<const float4 *>(P.m + row + i);
+            float4 v4 = *reinterpret_cast<const float4 *>(P.v + row + i);
+            float4 p4 = *reinterpret_cast<const float4 *>(P.param + row + i);
+            if (!s4.x) p4.x = adam_update(c, p4.x, g4.x, m4.x, v4.x);
+            if (!s4.y) p4.y = adam_update(c, p4.y, g4.y, m4.y, v4.y);
+            if (!s4.z) p4.z = adam_update(c, p4.z, g4.z, m4.z, v4.z);
+            if (!s4.w) p4.w = adam_update(c, p4.w, g4.w, m4.w, v4.w);
+            *reinterpret_cast<float4 *>(P.param + row + i) = p4;
+            *reinterpret_cast<float4 *>(P.m + row + i) = m4;
+            *reinterpret_cast<float4 *>(P.v + row + i) = v4;
+            if (P.param_bf16) {
+                uint16_t *pb = P.param_bf16 + row + i;
+                const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+                const uint8_t sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (!sv[e]) pb[e] = __bfloat16_as_ushort(__float2bfloat16_rn(pv[e]));
+            }
+        }
+    }
+    for (int i = done + blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
         if (sk && sk[i]) continue;
-        const float gr = P.grad[o];
-        const float mm = fmaf(b1, P.m[o], (1.f - b1) * gr);
-        const float vv = fmaf(b2, P.v[o], (1.f - b2) * gr * gr);
-        P.m[o] = mm;
-        P.v[o] = vv;
-        const float np = P.param[o] - P.lr * (mm * ibc1) / (sqrtf(vv * ibc2) + eps);
+        const size_t o = row + i;
+        float m = P.m[o], v = P.v[o];
+        const float np = adam_update(c, P.param[o], P.grad[o], m, v);
+        P.m[o] = m;
+        P.v[o] = v;
         P.param[o] = np;
         if (P.param_bf16) P.param_bf16[o] = __bfloat16_as_ushort(__float2bfloat16_rn(np));
     }
@@ -156,17 +197,27 @@ extern "C" int qn_adam_groups(int32_t n_groups, const qn_adam_group *groups_host
         QN_REQUIRE((long long)g.rows * g.n == 0 || (g.param && g.grad && g.m && g.v), "group %d: null pointer", k);
         G.g[k] = g;
         G.row_start[k] = rows;
+        auto a16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+        G.vec[k] = a16(g.param) && a16(g.grad) && a16(g.m) && a16(g.v) && g.stride % 4 == 0 &&
+                   (!g.param_bf16 || ((uintptr_t)g.param_bf16 & 7) == 0);
         rows += g.rows;
         nmax = g.n > nmax ? g.n : nmax;
     }
     G.row_start[n_groups] = rows;
+    if (skip && ((uintptr_t)skip & 3))                      // the vector loop reads the mask as uchar4
+        for (int k = 0; k < n_groups; ++k)
+            if (G.g[k].use_skip) G.vec[k] = 0;
     QN_REQUIRE(rows <= 65535, "too many rows (%d)", rows);
     cudaStream_t s = qn::as_stream(stream);
     qn::k_step_increment<<<1, 1, 0, s>>>(step);
     if (rows == 0 || nmax == 0) return qn::check_launch("qn_adam_groups");
-    int gx = qn::grid_cap(nmax, 256);
-    const int per_row = qn::div_up((int64_t)gx, rows);      // keep the total near the grid cap
-    gx = per_row < 1 ? 1 : per_row;
+    // blocks per row: enough for the longest row's quads, with all rows
+    // together near the grid cap (8 blocks per SM)
+    const int cap = qn::grid_cap(1LL << 40, 256);
+    int gx = qn::div_up((int64_t)cap, rows);
+    const int need = qn::div_up((int64_t)((nmax + 3) / 4), 256);
+    gx = gx > need ? need : gx;
+    gx = gx < 1 ? 1 : gx;
     qn::k_adam_groups<<<dim3(gx, rows), 256, 0, s>>>(G, step, beta1, beta2, eps, skip);
     return qn::check_launch("qn_adam_groups");
 }
