@@ -28,9 +28,17 @@ constexpr int BATCH = 32;                       // records staged per round by e
 
 // Staged record: (mean x, mean y, opacity, -) and the conic scaled for a
 // base-2 exponential, log2(e) * power = A dx^2 + B dx dy + C dy^2 with
-// A = -a log2(e) / 2, B = -b log2(e), C = -c log2(e) / 2.
-__device__ __forceinline__ float4 scaled_conic(float4 g1) {
-    return make_float4(__fmul_rn(-0.5f * LOG2E, g1.x), __fmul_rn(-LOG2E, g1.y), __fmul_rn(-0.5f * LOG2E, g1.z), 0.f);
+// A = -a log2(e) / 2, B = -b log2(e), C = -c log2(e) / 2, plus a cull bound:
+// alpha >= 1/255 needs o 2^e >= 1/255, i.e. e >= -log2(255 o); a band whose
+// pixels all have e below that bound minus a margin (far wider than the
+// rounding of ex2 and log2) cannot pass the alpha test anywhere and skips the
+// Gaussian, so the cull never changes a result.
+constexpr float CULL_MARGIN = 1e-3f;
+
+__device__ __forceinline__ float4 scaled_conic(float4 g1, float opacity) {
+    const float bound = opacity > 0.f ? -log2f(255.f * opacity) - CULL_MARGIN : INFINITY;
+    return make_float4(__fmul_rn(-0.5f * LOG2E, g1.x), __fmul_rn(-LOG2E, g1.y), __fmul_rn(-0.5f * LOG2E, g1.z),
+                       bound);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -57,14 +65,19 @@ struct PixelAlpha {
     bool capped, ok;
 };
 
-// alpha = min(0.99, o 2^(log2(e) power)) at one pixel of the lane's column,
-// with explicit round-to-nearest operations so that the forward pass and the
-// adjoint evaluate bit-identical alphas and take identical skip decisions.
+// log2(e) * power at one pixel of the lane's column; dy = y - mean_y.
+__device__ __forceinline__ float pixel_e2(const float4 &g0, const float4 &k, const RowTerms &r, float fy, float &dy) {
+    dy = __fsub_rn(fy, g0.y);
+    return __fmaf_rn(dy, __fmaf_rn(k.z, dy, r.bdx), r.p0);
+}
+
+// alpha = min(0.99, o 2^(log2(e) power)) from the exponent, with explicit
+// round-to-nearest operations so that the forward pass and the adjoint
+// evaluate bit-identical alphas and take identical skip decisions.
 // ok: power <= 0 and alpha >= 1/255.
-__device__ __forceinline__ PixelAlpha pixel_alpha(const float4 &g0, const float4 &k, const RowTerms &r, float fy) {
+__device__ __forceinline__ PixelAlpha pixel_alpha(const float4 &g0, float e2, float dy) {
     PixelAlpha p;
-    p.dy = __fsub_rn(fy, g0.y);
-    const float e2 = __fmaf_rn(p.dy, __fmaf_rn(k.z, p.dy, r.bdx), r.p0);
+    p.dy = dy;
     p.G = ex2_approx(e2);
     const float v = __fmul_rn(g0.z, p.G);
     p.capped = v > ALPHA_MAX;
@@ -117,8 +130,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_render_fwd(int W, int H, int TX,
         if (!__any_sync(FULL, live)) break;
         if (b0 + lane < n) {
             const size_t id = vals[beg + b0 + lane];
-            s.g0[lane] = sp[3 * id];
-            s.k[lane] = scaled_conic(sp[3 * id + 1]);
+            const float4 g0 = sp[3 * id];
+            s.g0[lane] = g0;
+            s.k[lane] = scaled_conic(sp[3 * id + 1], g0.z);
             s.c[lane] = sp[3 * id + 2];
         }
         __syncwarp();
@@ -127,10 +141,18 @@ __global__ void __launch_bounds__(32 * WARPS) k_render_fwd(int W, int H, int TX,
             if (!__any_sync(FULL, live)) break;
             const float4 g0 = s.g0[j], k = s.k[j], c = s.c[j];
             const RowTerms r = row_terms(g0, k, fx);
+            float e2[PPT], dy[PPT];
+            bool near = false;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                e2[q] = pixel_e2(g0, k, r, fy0 + (float)q, dy[q]);
+                near |= e2[q] >= k.w;
+            }
+            if (!__any_sync(FULL, near)) continue;      // alpha < 1/255 on every pixel of the band
             const uint32_t pos1 = (uint32_t)(b0 + j + 1);
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
-                const PixelAlpha p = pixel_alpha(g0, k, r, fy0 + (float)q);
+                const PixelAlpha p = pixel_alpha(g0, e2[q], dy[q]);
                 const bool ok = ((live >> q) & 1u) && p.ok;
                 const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, p.alpha));
                 const bool stop = Tn < T_MIN;
@@ -233,9 +255,10 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
         if (t < cnt) {
             const uint32_t id = vals[beg + lo + t];
             my_skip = skip ? skip[id] != 0 : false;
-            s.g0[t] = sp[3 * (size_t)id];
+            const float4 g0 = sp[3 * (size_t)id];
+            s.g0[t] = g0;
             conic = sp[3 * (size_t)id + 1];
-            s.k[t] = scaled_conic(conic);
+            s.k[t] = scaled_conic(conic, g0.z);
             s.c[t] = sp[3 * (size_t)id + 2];
             sskip[t] = my_skip;
         }
@@ -248,11 +271,22 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
             }
             const float4 g0 = s.g0[j], k = s.k[j], c = s.c[j];
             const RowTerms r = row_terms(g0, k, fx);
+            float e2[PPT], dy[PPT];
+            bool near = false;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                e2[q] = pixel_e2(g0, k, r, fy0 + (float)q, dy[q]);
+                near |= e2[q] >= k.w && pos < lastp[q];
+            }
+            if (!__any_sync(FULL, near)) {              // no pixel of the band can take j
+                if (lane == 0) hit[warp][j] = 0;
+                continue;
+            }
             float S0 = 0.f, S1 = 0.f, S2 = 0.f, So = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
             bool any = false;
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
-                const PixelAlpha p = pixel_alpha(g0, k, r, fy0 + (float)q);
+                const PixelAlpha p = pixel_alpha(g0, e2[q], dy[q]);
                 const bool valid = pos < lastp[q] && p.ok;
                 any |= valid;
                 const float Tq = valid ? __fdividef(T[q], 1.f - p.alpha) : T[q];   // in front of j
