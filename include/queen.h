@@ -225,7 +225,7 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
                 int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream);
 
 /* Size of the device array that qn_bin_sort_noalloc uses as its workspace. */
-#define QN_BIN_SORT_STATIC_BYTES (32u << 20)
+#define QN_BIN_SORT_STATIC_BYTES (40u << 20)
 
 /*
  * qn_bin_sort without a caller-provided workspace, for callers that cannot
@@ -236,10 +236,10 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
  *
  * Arguments, results and errors are those of qn_bin_sort, minus `workspace`
  * and `workspace_bytes`.  The scratch space is a fixed file-scope device
- * array of QN_BIN_SORT_STATIC_BYTES (32 MiB), which every GPU that loads this
+ * array of QN_BIN_SORT_STATIC_BYTES (40 MiB), which every GPU that loads this
  * library keeps until the process exits.  A problem whose
  * qn_bin_sort_workspace_size exceeds that is rejected with
- * QN_ERR_INVALID_ARG before any launch (32 MiB covers 300,000 Gaussians on a
+ * QN_ERR_INVALID_ARG before any launch (40 MiB covers 300,000 Gaussians on a
  * 1352 x 1014 image).
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
@@ -284,13 +284,16 @@ int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
  *     for the visited positions ranges[t][0] .. ranges[t][0] + tile_visited[t] - 1
  *     of non-skipped Gaussians)
  *   tile_visited [n_tiles] u32: length of each tile's visited prefix (written)
+ *   gauss_hit [n] u8 (nullable): set to 1 for every Gaussian that some pixel
+ *     composited (a record with a contribution); never cleared -- zero it
+ *     before the call.  qn_bin_gather uses it to skip the others.
  * qn_bin_gather then sums the records per Gaussian.  skip (nullable, [n] u8):
  * no record is written for Gaussians with skip != 0.
  */
 int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
                   const qn_splat *splats, const float *bg_host, const float *T_final,
                   const uint32_t *last, const float *d_img, const uint8_t *skip,
-                  qn_splat *pair_grads, uint32_t *tile_visited, qn_stream_t stream);
+                  qn_splat *pair_grads, uint32_t *tile_visited, uint8_t *gauss_hit, qn_stream_t stream);
 
 /*
  * Second half of the compositing adjoint, the adjoint of the binning scatter:
@@ -299,11 +302,13 @@ int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
  * zero for culled and skipped Gaussians.  The fixed summation order makes the
  * result reproducible bit for bit.  workspace must still hold the state of the
  * qn_bin_sort call that produced the pairs (same n, rects, tile grid);
- * d_splats [n] qn_splat is overwritten.
+ * d_splats [n] qn_splat is overwritten.  gauss_hit (nullable): qn_render_bwd's
+ * marks; an unmarked Gaussian has only zero records, so its sum is 0 without
+ * walking its tiles (the result is the same).
  */
 int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, int32_t tiles_y, const void *workspace,
                   size_t workspace_bytes, const uint32_t *tile_visited, const qn_splat *pair_grads,
-                  const uint8_t *skip, qn_splat *d_splats, qn_stream_t stream);
+                  const uint8_t *skip, const uint8_t *gauss_hit, qn_splat *d_splats, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Loss and optimiser steps of the training iteration (Eq. 3, Eq. 11).       */

@@ -66,8 +66,8 @@ _SIGS = {
     "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_noalloc": ([_I32, _P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_render_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_bin_gather": ([_I32, _P, _I32, _I32, _P, _SZ, _P, _P, _P, _P, _P], C.c_int),
+    "qn_render_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_bin_gather": ([_I32, _P, _I32, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_viewspace_accum": ([_I32, _I32, _P, _F32, _P, _P], C.c_int),
     "qn_gate_init": ([_I32, _I32, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
@@ -219,16 +219,17 @@ def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=N
 
 
 def qn_render_bwd(cam, ranges, vals, splats, bg, T_final, last, d_img, skip, pair_grads, tile_visited,
-                  stream=None):
+                  stream=None, gauss_hit=None):
     _check(lib().qn_render_bwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg), _ptr(T_final),
                                _ptr(last), _ptr(d_img), _ptr(skip), _ptr(pair_grads), _ptr(tile_visited),
-                               _stream(stream)))
+                               _ptr(gauss_hit), _stream(stream)))
 
 
-def qn_bin_gather(n, rects, tiles_x, tiles_y, workspace, tile_visited, pair_grads, skip, d_splats, stream=None):
+def qn_bin_gather(n, rects, tiles_x, tiles_y, workspace, tile_visited, pair_grads, skip, d_splats, stream=None,
+                  gauss_hit=None):
     ws_bytes = workspace.numel() * workspace.element_size()
     _check(lib().qn_bin_gather(n, _ptr(rects), tiles_x, tiles_y, _ptr(workspace), ws_bytes, _ptr(tile_visited),
-                               _ptr(pair_grads), _ptr(skip), _ptr(d_splats), _stream(stream)))
+                               _ptr(pair_grads), _ptr(skip), _ptr(gauss_hit), _ptr(d_splats), _stream(stream)))
 
 
 QN_LOSS_BLOCKS = 2048

@@ -12,6 +12,7 @@
 // Every pair of one Gaussian shares its depth bits, so sorting the depth
 // digits on the Gaussians first and then the tile digit stably on the pairs is
 // exactly the LSD order of the 64-bit key; the output equals the stable sort.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -35,12 +36,16 @@ struct Header {
 };
 
 struct Layout {
-    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, total;
+    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, total;
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-Layout layout_of(int n, int n_tiles) {
+// masks: per chunk, the column words mx[CHUNK_WARPS][TX] then the row words
+// my[CHUNK_WARPS][TY] (built once by k_chunk_counts, read by the scatter and
+// the gather).
+Layout layout_of(int n, int TX, int TY) {
+    const int n_tiles = TX * TY;
     Layout L;
     const size_t nb = (size_t)div_up(n > 0 ? n : 1, SORT_TILE);
     const size_t chunks = (size_t)div_up(n > 0 ? n : 1, CHUNK);
@@ -55,6 +60,7 @@ Layout layout_of(int n, int n_tiles) {
     L.counts = o; o = align_up(o + 4 * chunks * (size_t)n_tiles);
     L.tile_total = o; o = align_up(o + 4 * (size_t)n_tiles);
     L.tile_off = o; o = align_up(o + 4 * (size_t)(n_tiles + 1));
+    L.masks = o; o = align_up(o + 4 * chunks * CHUNK_WARPS * (size_t)(TX + TY));
     L.total = o;
     return L;
 }
@@ -230,6 +236,23 @@ __device__ void build_masks(int TX, int TY, ChunkSmem &s) {
     __syncthreads();
 }
 
+// Copies the chunk's masks between shared memory and their workspace slot;
+// warp w moves its own rows mx[w][..] and my[w][..].
+__device__ void store_masks(int TX, int TY, const ChunkSmem &s, uint32_t *__restrict__ gm) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int tx = lane; tx < TX; tx += 32) gm[w * TX + tx] = s.mx[w][tx];
+    uint32_t *gy = gm + CHUNK_WARPS * TX;
+    for (int ty = lane; ty < TY; ty += 32) gy[w * TY + ty] = s.my[w][ty];
+}
+
+__device__ void fetch_masks(int TX, int TY, const uint32_t *__restrict__ gm, ChunkSmem &s) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int tx = lane; tx < TX; tx += 32) s.mx[w][tx] = gm[w * TX + tx];
+    const uint32_t *gy = gm + CHUNK_WARPS * TX;
+    for (int ty = lane; ty < TY; ty += 32) s.my[w][ty] = gy[w * TY + ty];
+    __syncthreads();
+}
+
 __device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
                            const int4 *__restrict__ rects, uint32_t n_vis, ChunkSmem &s) {
     load_chunk_rects(c, TX, TY, sorted, rects, n_vis, s);
@@ -245,7 +268,8 @@ __device__ __forceinline__ uint32_t chunk_count(const ChunkSmem &s, int tx, int 
 
 __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const uint32_t *__restrict__ sorted,
                                                         const int4 *__restrict__ rects, const Header *hdr,
-                                                        uint32_t *__restrict__ counts) {
+                                                        uint32_t *__restrict__ counts,
+                                                        uint32_t *__restrict__ masks) {
     __shared__ ChunkSmem s;
     const int c = blockIdx.x;
     const uint32_t n_vis = hdr->n_vis;
@@ -256,6 +280,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
         return;
     }
     load_chunk(c, TX, TY, sorted, rects, n_vis, s);
+    store_masks(TX, TY, s, masks + (size_t)c * CHUNK_WARPS * (TX + TY));
     for (int t = threadIdx.x; t < n_tiles; t += CHUNK) {
         const int tx = t % TX, ty = t / TX;
         row[t] = (tx >= s.ux0 && tx < s.ux1 && ty >= s.uy0 && ty < s.uy1) ? chunk_count(s, tx, ty) : 0u;
@@ -343,6 +368,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
                                                          const float *__restrict__ depth, int dstride,
                                                          const Header *hdr, const uint32_t *__restrict__ gbase,
                                                          const uint32_t *__restrict__ tile_off,
+                                                         const uint32_t *__restrict__ masks,
                                                          uint32_t *__restrict__ vals,
                                                          unsigned long long *__restrict__ keys) {
     __shared__ ChunkSmem s;
@@ -351,7 +377,8 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
     const int c = blockIdx.x;
     const uint32_t n_vis = hdr->n_vis;
     if (hdr->overflow || (uint32_t)c * CHUNK >= n_vis) return;
-    load_chunk(c, TX, TY, sorted, rects, n_vis, s);
+    load_chunk_rects(c, TX, TY, sorted, rects, n_vis, s);
+    fetch_masks(TX, TY, masks + (size_t)c * CHUNK_WARPS * (TX + TY), s);
     const int n_tiles = TX * TY;
     const int uw = s.ux1 - s.ux0;
     if (uw <= 0) return;
@@ -425,95 +452,103 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
 // Adjoint of the pair scatter: each visible Gaussian sums the per-pair
 // gradient records of the visited positions of its tiles, walking its rect in
 // row-major order (one warp per Gaussian, a fixed lane assignment and a fixed
-// butterfly) -- so the sums are reproducible.  Chunks are
-// in depth order and each tile's visited prefix holds its front-most pairs, so
-// most chunks have no visited pair at all: a chunk first marks, in a shared
-// bitmask, the tiles where its first slot lies inside the visited prefix, and
-// returns at once when there are none.
-__global__ void __launch_bounds__(CHUNK) k_bin_gather(int TX, int TY, const uint32_t *__restrict__ sorted,
-                                                      const int4 *__restrict__ rects, const Header *hdr,
-                                                      const uint32_t *__restrict__ gbase,
-                                                      const uint32_t *__restrict__ tile_off,
-                                                      const uint32_t *__restrict__ visited,
-                                                      const float4 *__restrict__ pair_grads,
-                                                      const uint8_t *__restrict__ skip, float4 *__restrict__ out) {
-    __shared__ ChunkSmem s;
-    __shared__ uint32_t active[QN_MAX_TILES_X * QN_MAX_TILES_Y / 32];
-    const int c = blockIdx.x;
-    const uint32_t n_vis = hdr->n_vis;
-    if (hdr->overflow || (uint32_t)c * CHUNK >= n_vis) return;
+// shuffle pattern) -- so the sums are reproducible.  The warps run over the
+// depth-sorted Gaussians across the whole grid: the Gaussians with visited
+// pairs are the front-most, i.e. they crowd the first chunks, and a warp per
+// Gaussian spreads them over every SM.  A Gaussian's rank in a tile's list
+// comes from its chunk's row/column bitmasks (stored by k_chunk_counts); a
+// tile is skipped when the chunk starts beyond the tile's visited prefix.
+// One Gaussian: sum its visited records (a whole warp; g is its depth-sorted
+// index, id its index in the scene).
+__device__ __forceinline__ void gather_one(int TX, int TY, uint32_t g, uint32_t id, int lane,
+                                           const int4 *__restrict__ rects, const uint32_t *__restrict__ gbase,
+                                           const uint32_t *__restrict__ tile_off,
+                                           const uint32_t *__restrict__ visited,
+                                           const float4 *__restrict__ pair_grads,
+                                           const uint32_t *__restrict__ masks, float4 *__restrict__ out) {
+    const int4 r = rects[id];
     const int n_tiles = TX * TY;
+    const int c = (int)(g / CHUNK), j = (int)(g % CHUNK), wj = j >> 5;
+    const unsigned below = (1u << (j & 31)) - 1u;
+    const uint32_t *mx = masks + (size_t)c * CHUNK_WARPS * (TX + TY);
+    const uint32_t *my = mx + CHUNK_WARPS * TX;
     const uint32_t *grow = gbase + (size_t)c * n_tiles;
-    load_chunk_rects(c, TX, TY, sorted, rects, n_vis, s);
-    // pass 1: active tiles of the chunk's bounding box, one bit per grid tile;
-    // each warp covers whole 32-tile words with coalesced loads and a ballot
-    const int lane = threadIdx.x & 31;
-    int any = 0;
-    const int w0 = (s.uy0 * TX + s.ux0) >> 5;
-    const int w1 = s.uy1 > s.uy0 ? ((s.uy1 - 1) * TX + s.ux1 - 1) / 32 + 1 : w0;
-    for (int w = w0 + (int)(threadIdx.x >> 5); w < w1; w += CHUNK / 32) {
-        const int t = w * 32 + lane;
-        const int tx = t % TX, ty = t / TX;
-        const bool in_box = t < n_tiles && tx >= s.ux0 && tx < s.ux1 && ty >= s.uy0 && ty < s.uy1;
-        const unsigned bits = __ballot_sync(FULL, in_box && grow[t] < visited[t]);
-        if (lane == 0) active[w] = bits;
-        any |= bits != 0;
+    const int rw = r.z - r.x, area = rw * (r.w - r.y);
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool found = false;
+    // lane l walks tiles l, l + 32, ... of the rect in row-major order,
+    // stepping its (column, row) without a division per tile
+    int cx = rw > 0 ? lane % rw : 0, cy = rw > 0 ? lane / rw : 0;
+    const int dq = rw > 0 ? 32 / rw : 0, dr = rw > 0 ? 32 % rw : 0;
+    for (int k = lane; k < area; k += 32) {
+        const int tx = r.x + cx, ty = r.y + cy;
+        cx += dr;
+        cy += dq;
+        if (cx >= rw) {
+            cx -= rw;
+            ++cy;
+        }
+        const int t = ty * TX + tx;
+        const uint32_t base = grow[t], vis = visited[t];
+        if (base >= vis) continue;                       // the chunk starts past the visited prefix
+        uint32_t rank = __popc(mx[wj * TX + tx] & my[wj * TY + ty] & below);
+        for (int w = 0; w < wj; ++w) rank += __popc(mx[w * TX + tx] & my[w * TY + ty]);
+        if (base + rank >= vis) continue;
+        const float4 *p = pair_grads + 3 * (size_t)(tile_off[t] + base + rank);
+        const float4 b0 = p[0], b1 = p[1], b2 = p[2];
+        acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
+        acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
+        acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
+        found = true;
     }
-    if (!__syncthreads_or(any)) return;
-    build_masks(TX, TY, s);
-    // pass 2: one warp per Gaussian; lane l takes the Gaussian's tiles l, l + 32,
-    // ... in row-major order and a fixed shuffle pattern sums the lanes
-    const int warp = threadIdx.x >> 5;
-    for (int j = warp; j < CHUNK; j += CHUNK / 32) {
-        const uint32_t g = (uint32_t)c * CHUNK + j;
-        if (g >= n_vis) break;
-        const uint32_t id = s.id[j];
-        if (skip && skip[id]) continue;
-        const int4 r = s.rect[j];
-        const int rw = r.z - r.x, area = rw * (r.w - r.y);
-        const int wj = j >> 5;
-        const unsigned below = (1u << (j & 31)) - 1u;
-        float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        bool found = false;
-        // lane l walks tiles l, l + 32, ... of the rect in row-major order,
-        // stepping its (column, row) without a division per tile
-        int cx = rw > 0 ? lane % rw : 0, cy = rw > 0 ? lane / rw : 0;
-        const int dq = rw > 0 ? 32 / rw : 0, dr = rw > 0 ? 32 % rw : 0;
-        for (int k = lane; k < area; k += 32) {
-            const int tx = r.x + cx, ty = r.y + cy;
-            cx += dr;
-            cy += dq;
-            if (cx >= rw) {
-                cx -= rw;
-                ++cy;
-            }
-            const int t = ty * TX + tx;
-            if (!((active[t >> 5] >> (t & 31)) & 1u)) continue;
-            uint32_t rank = __popc(s.mx[wj][tx] & s.my[wj][ty] & below);
-            for (int w = 0; w < wj; ++w) rank += __popc(s.mx[w][tx] & s.my[w][ty]);
-            const uint32_t base = grow[t];
-            if (base + rank >= visited[t]) continue;
-            const float4 *p = pair_grads + 3 * (size_t)(tile_off[t] + base + rank);
-            const float4 b0 = p[0], b1 = p[1], b2 = p[2];
-            acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
-            acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
-            acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
-            found = true;
+    if (!__any_sync(FULL, found)) return;               // no visited pair: stays 0
+    float *o = reinterpret_cast<float *>(out + 3 * (size_t)id);
+    const float red = reduce_scatter8(acc, lane);       // lane 4q holds the sum of value q
+    const float red8 = warp_sum(acc[8]);
+    if ((lane & 3) == 0) {
+        const int q = lane >> 2;
+        o[(q / 3) * 4 + q % 3] = red;
+    }
+    if (lane == 0) {
+        o[10] = red8;
+        o[3] = o[7] = o[11] = 0.f;
+    }
+}
+
+// Warp w of W takes the depth-sorted Gaussians w, w + W, w + 2W, ...: its
+// lanes test 32 of them at once (skipped, or without a composited record ->
+// nothing to do), then the warp sums the wanted ones one after another.  The
+// stride spreads the front-most Gaussians, which own nearly all visited pairs,
+// over every warp.
+__global__ void __launch_bounds__(256) k_bin_gather(int TX, int TY, const uint32_t *__restrict__ sorted,
+                                                    const int4 *__restrict__ rects, const Header *hdr,
+                                                    const uint32_t *__restrict__ gbase,
+                                                    const uint32_t *__restrict__ tile_off,
+                                                    const uint32_t *__restrict__ visited,
+                                                    const float4 *__restrict__ pair_grads,
+                                                    const uint8_t *__restrict__ skip,
+                                                    const uint8_t *__restrict__ ghit,
+                                                    const uint32_t *__restrict__ masks, float4 *__restrict__ out) {
+    if (hdr->overflow) return;
+    const uint32_t n_vis = hdr->n_vis;
+    const uint32_t W = (uint32_t)((gridDim.x * (size_t)blockDim.x) >> 5);
+    const uint32_t w = (uint32_t)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t k0 = 0; w + (size_t)k0 * W < n_vis; k0 += 32) {
+        const size_t gl = w + (size_t)(k0 + lane) * W;
+        uint32_t id = 0;
+        bool wanted = false;
+        if (gl < n_vis) {
+            id = sorted[gl];
+            wanted = !(skip && skip[id]) && !(ghit && !ghit[id]);
         }
-        float *o = reinterpret_cast<float *>(out + 3 * (size_t)id);
-        if (!__any_sync(FULL, found)) {                 // no visited pair: a zero gradient
-            if (lane < 12) o[lane] = 0.f;
-            continue;
-        }
-        const float red = reduce_scatter8(acc, lane);   // lane 4q holds the sum of value q
-        const float red8 = warp_sum(acc[8]);
-        if ((lane & 3) == 0) {
-            const int q = lane >> 2;
-            o[(q / 3) * 4 + q % 3] = red;
-        }
-        if (lane == 0) {
-            o[10] = red8;
-            o[3] = o[7] = o[11] = 0.f;
+        unsigned m = __ballot_sync(FULL, wanted);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t gid = __shfl_sync(FULL, id, l);
+            gather_one(TX, TY, (uint32_t)(w + (size_t)(k0 + l) * W), gid, lane, rects, gbase, tile_off, visited,
+                       pair_grads, masks, out);
         }
     }
 }
@@ -523,7 +558,7 @@ __global__ void __launch_bounds__(CHUNK) k_bin_gather(int TX, int TY, const uint
 
 extern "C" size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y) {
     if (n < 0 || tiles_x <= 0 || tiles_y <= 0) return 0;
-    return qn::layout_of(n, tiles_x * tiles_y).total;
+    return qn::layout_of(n, tiles_x, tiles_y).total;
 }
 
 extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
@@ -542,7 +577,7 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     QN_REQUIRE(((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
                "rects must be 16-byte and workspace 256-byte aligned");
     const int n_tiles = tiles_x * tiles_y;
-    const Layout L = layout_of(n, n_tiles);
+    const Layout L = layout_of(n, tiles_x, tiles_y);
     QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
     cudaStream_t s = as_stream(stream);
     if (n == 0) {
@@ -580,12 +615,13 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     }
     // after 4 passes the sorted (depth, index) order is back in k0 / v0
     const int n_chunks = div_up(n, CHUNK);
-    k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts);
+    uint32_t *masks = reinterpret_cast<uint32_t *>(ws + L.masks);
+    k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts, masks);
     k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total);
     k_tile_offsets<<<1, 1024, 0, s>>>(n_tiles, tile_total, tile_off, ranges, hdr,
                                       (unsigned long long)pair_capacity, reinterpret_cast<long long *>(n_pairs));
     k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
-                                               tile_off, vals, reinterpret_cast<unsigned long long *>(keys));
+                                               tile_off, masks, vals, reinterpret_cast<unsigned long long *>(keys));
     int st = check_launch("qn_bin_sort");
     if (st) return st;
     if (n_pairs_host) {
@@ -602,8 +638,8 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
 
 extern "C" int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, int32_t tiles_y,
                              const void *workspace, size_t workspace_bytes, const uint32_t *tile_visited,
-                             const qn_splat *pair_grads, const uint8_t *skip, qn_splat *d_splats,
-                             qn_stream_t stream) {
+                             const qn_splat *pair_grads, const uint8_t *skip, const uint8_t *gauss_hit,
+                             qn_splat *d_splats, qn_stream_t stream) {
     using namespace qn;
     QN_REQUIRE(n >= 0, "n must be >= 0");
     QN_REQUIRE(tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
@@ -612,19 +648,23 @@ extern "C" int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, i
     QN_REQUIRE(((uintptr_t)d_splats & 15) == 0 && ((uintptr_t)pair_grads & 15) == 0 &&
                    ((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
                "misaligned pointer argument");
-    const int n_tiles = tiles_x * tiles_y;
-    const Layout L = layout_of(n, n_tiles);
+    const Layout L = layout_of(n, tiles_x, tiles_y);
     QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
     cudaStream_t s = as_stream(stream);
     if (n == 0) return QN_OK;
     if (cudaMemsetAsync(d_splats, 0, sizeof(qn_splat) * (size_t)n, s) != cudaSuccess)
         return check_launch("qn_bin_gather memset");
     const char *ws = static_cast<const char *>(workspace);
-    k_bin_gather<<<div_up(n, CHUNK), CHUNK, 0, s>>>(
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = std::min(div_up((int64_t)n * 32, 256), sms * 8);   // 8 warps per block
+    k_bin_gather<<<blocks, 256, 0, s>>>(
         tiles_x, tiles_y, reinterpret_cast<const uint32_t *>(ws + L.vals0), reinterpret_cast<const int4 *>(rects),
         reinterpret_cast<const Header *>(ws + L.hdr), reinterpret_cast<const uint32_t *>(ws + L.counts),
         reinterpret_cast<const uint32_t *>(ws + L.tile_off), tile_visited,
-        reinterpret_cast<const float4 *>(pair_grads), skip, reinterpret_cast<float4 *>(d_splats));
+        reinterpret_cast<const float4 *>(pair_grads), skip, gauss_hit,
+        reinterpret_cast<const uint32_t *>(ws + L.masks), reinterpret_cast<float4 *>(d_splats));
     return check_launch("qn_bin_gather");
 }
 

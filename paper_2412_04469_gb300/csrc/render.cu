@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
                                                         const float *__restrict__ dimg,
                                                         const uint8_t *__restrict__ skip,
                                                         float4 *__restrict__ pair_grads,
-                                                        uint32_t *__restrict__ visited) {
+                                                        uint32_t *__restrict__ visited,
+                                                        uint8_t *__restrict__ ghit) {
     __shared__ StageBuf<BWD_BATCH> s;
     __shared__ float rec[WARPS][BWD_BATCH][9];
     __shared__ int hit[WARPS][BWD_BATCH];
@@ -252,8 +253,9 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
         const int t = threadIdx.x;
         float4 conic = make_float4(0.f, 0.f, 0.f, 0.f);   // thread t: raw conic of record lo + t
         bool my_skip = true;
+        uint32_t id = 0;
         if (t < cnt) {
-            const uint32_t id = vals[beg + lo + t];
+            id = vals[beg + lo + t];
             my_skip = skip ? skip[id] != 0 : false;
             const float4 g0 = sp[3 * (size_t)id];
             s.g0[t] = g0;
@@ -323,12 +325,15 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
         // one record per visited list position: the tile's sum for that Gaussian
         if (t < cnt && !my_skip) {
             float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool contributed = false;
 #pragma unroll
             for (int w = 0; w < WARPS; ++w) {
                 if (!hit[w][t]) continue;
+                contributed = true;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) m[q] += rec[w][t][q];
             }
+            if (ghit && contributed) ghit[id] = 1;
             float4 *d = pair_grads + 3 * (size_t)(beg + lo + t);
             d[0] = make_float4(conic.x * m[0] + conic.y * m[1], conic.y * m[0] + conic.z * m[1], m[5], 0.f);
             d[1] = make_float4(-0.5f * m[2], -m[3], -0.5f * m[4], 0.f);
@@ -368,7 +373,8 @@ extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, 
 extern "C" int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
                              const qn_splat *splats, const float *bg_host, const float *T_final,
                              const uint32_t *last, const float *d_img, const uint8_t *skip,
-                             qn_splat *pair_grads, uint32_t *tile_visited, qn_stream_t stream) {
+                             qn_splat *pair_grads, uint32_t *tile_visited, uint8_t *gauss_hit,
+                             qn_stream_t stream) {
     int st = qn::check_render_args(cam_host, ranges, splats);
     if (st) return st;
     QN_REQUIRE(T_final && last && d_img && bg_host && pair_grads && tile_visited, "null pointer argument");
@@ -376,6 +382,7 @@ extern "C" int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, 
     const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
     qn::k_render_bwd<<<TX * TY, qn::BWD_THREADS, 0, qn::as_stream(stream)>>>(
         cam_host->width, cam_host->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg_host[0],
-        bg_host[1], bg_host[2], T_final, last, d_img, skip, reinterpret_cast<float4 *>(pair_grads), tile_visited);
+        bg_host[1], bg_host[2], T_final, last, d_img, skip, reinterpret_cast<float4 *>(pair_grads), tile_visited,
+        gauss_hit);
     return qn::check_launch("qn_render_bwd");
 }

@@ -174,6 +174,7 @@ class Rasterizer:
         self.ranges = torch.zeros((self.TX * self.TY, 2), device=dev, dtype=torch.int32)
         self.n_pairs = torch.zeros(1, device=dev, dtype=torch.int64)
         self.tile_visited = torch.zeros(self.TX * self.TY, device=dev, dtype=torch.int32)
+        self.gauss_hit = torch.zeros(nn, device=dev, dtype=torch.uint8)      # Gaussians some pixel composited
         self.keep_keys = keep_keys
         self.set_capacity(pair_capacity)
         self.img = torch.zeros((3, height, width), device=dev)
@@ -211,12 +212,13 @@ class Rasterizer:
         self.gather(skip, stream)
 
     def render_bwd_pairs(self, cam, bg, skip=None, stream=None):
+        self.gauss_hit.zero_()
         B.qn_render_bwd(cam, self.ranges, self.vals, self.splats, bg, self.T_final, self.last, self.d_img, skip,
-                        self.pair_grads, self.tile_visited, stream)
+                        self.pair_grads, self.tile_visited, stream, gauss_hit=self.gauss_hit)
 
     def gather(self, skip=None, stream=None):
         B.qn_bin_gather(self.n, self.rects, self.TX, self.TY, self.workspace, self.tile_visited, self.pair_grads,
-                        skip, self.d_splats, stream)
+                        skip, self.d_splats, stream, gauss_hit=self.gauss_hit)
 
     def project_bwd(self, attrs, cam, blur, d_attrs, skip=None, stream=None):
         B.qn_project_bwd(self.n, self.S, self.sh_degree, attrs, cam, blur, self.d_splats, skip, d_attrs, stream)

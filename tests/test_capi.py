@@ -62,7 +62,7 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp),
                                        None, None, None, None, None) == B.QN_ERR_INVALID_ARG
     assert b"category" in B.lib().qn_last_error()
-    assert B.lib().qn_render_bwd(None, None, None, None, None, None, None, None, None, None, None, None) == \
+    assert B.lib().qn_render_bwd(None, None, None, None, None, None, None, None, None, None, None, None, None) == \
         B.QN_ERR_INVALID_ARG
     gp_bad = B.make_gate(0.3, 0.5, 1.01)
     lay.attr_begin[0] = 3

@@ -66,7 +66,7 @@ def test_noalloc_matches_workspace_version_twice():
 def test_noalloc_rejects_oversized_problems():
     from paper_2412_04469_gb300 import binding as B
     n, tx, ty = 4_000_000, 256, 256
-    assert B.qn_bin_sort_workspace_size(n, tx, ty) > (32 << 20)
+    assert B.qn_bin_sort_workspace_size(n, tx, ty) > (40 << 20)
     v, k, r, p = _outs(1, tx * ty)
     with pytest.raises(B.QueenError) as e:
         B.qn_bin_sort_noalloc(n, 0, 12, 0, tx, ty, 1, v, k, r, p)
