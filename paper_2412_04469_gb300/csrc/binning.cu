@@ -26,7 +26,6 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per block per pas
 constexpr int RADIX = 256;
 constexpr int CHUNK = 256;                             // Gaussians per binning chunk
 constexpr int CHUNK_WARPS = CHUNK / 32;
-constexpr int LOCAL_MAX = 6144;                        // tiles per band in the scatter (static smem < 48 KB)
 constexpr uint32_t KEY_CULLED = 0xffffffffu;
 
 struct Header {
@@ -357,12 +356,10 @@ __global__ void __launch_bounds__(1024) k_tile_offsets(int n_tiles, const uint32
     }
 }
 
-struct BandSmem {
-    uint32_t off[LOCAL_MAX + 1];
-};
-
-// Writes chunk c's members tile by tile: slot k of a band is the r-th member
-// (in depth order) of its tile; consecutive slots go to consecutive addresses.
+// Writes chunk c's members tile by tile: one thread per tile of the chunk's
+// bounding box writes the tile's members in depth order (the set bits of the
+// per-warp words, warp by warp) to consecutive slots from the chunk's first
+// slot in that tile.
 __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const uint32_t *__restrict__ sorted,
                                                          const int4 *__restrict__ rects,
                                                          const float *__restrict__ depth, int dstride,
@@ -372,80 +369,40 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
                                                          uint32_t *__restrict__ vals,
                                                          unsigned long long *__restrict__ keys) {
     __shared__ ChunkSmem s;
-    __shared__ BandSmem band;
-    __shared__ uint32_t wsum[CHUNK_WARPS];
+    __shared__ uint32_t dbits[CHUNK];                   // depth bits of the members (for keys)
     const int c = blockIdx.x;
     const uint32_t n_vis = hdr->n_vis;
     if (hdr->overflow || (uint32_t)c * CHUNK >= n_vis) return;
     load_chunk_rects(c, TX, TY, sorted, rects, n_vis, s);
+    if (keys) dbits[threadIdx.x] = __float_as_uint(depth[(size_t)s.id[threadIdx.x] * dstride]);
     fetch_masks(TX, TY, masks + (size_t)c * CHUNK_WARPS * (TX + TY), s);
     const int n_tiles = TX * TY;
-    const int uw = s.ux1 - s.ux0;
-    if (uw <= 0) return;
-    const int rows_per_band = max(1, LOCAL_MAX / uw);
+    const int uw = s.ux1 - s.ux0, uh = s.uy1 - s.uy0;
+    if (uw <= 0 || uh <= 0) return;
     const uint32_t *grow = gbase + (size_t)c * n_tiles;
-    for (int yb = s.uy0; yb < s.uy1; yb += rows_per_band) {
-        const int ye = min(s.uy1, yb + rows_per_band);
-        const int nloc = (ye - yb) * uw;
-        // local counts -> exclusive offsets (per-thread serial segments + block scan)
-        const int per = div_up_dev(nloc, CHUNK);
-        const int b0 = threadIdx.x * per, b1 = min(nloc, b0 + per);
-        uint32_t sum = 0;
-        for (int q = b0; q < b1; ++q) {
-            const uint32_t v = chunk_count(s, s.ux0 + q % uw, yb + q / uw);
-            band.off[q] = v;
-            sum += v;
-        }
-        uint32_t incl = sum;
+    for (int q = threadIdx.x; q < uw * uh; q += CHUNK) {
+        const int tx = s.ux0 + q % uw, ty = s.uy0 + q / uw;
+        uint32_t m[CHUNK_WARPS];
+        bool any = false;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(FULL, incl, o);
-            if ((threadIdx.x & 31) >= (unsigned)o) incl += x;
+        for (int w = 0; w < CHUNK_WARPS; ++w) {
+            m[w] = s.mx[w][tx] & s.my[w][ty];
+            any |= m[w] != 0;
         }
-        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = incl;
-        __syncthreads();
-        uint32_t wbase = 0;
-        for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) wbase += wsum[w];
-        uint32_t run = wbase + incl - sum;
-        for (int q = b0; q < b1; ++q) {
-            const uint32_t v = band.off[q];
-            band.off[q] = run;
-            run += v;
-        }
-        __syncthreads();
-        uint32_t total = 0;
-        for (int w = 0; w < CHUNK_WARPS; ++w) total += wsum[w];
-        if (threadIdx.x == 0) band.off[nloc] = total;
-        __syncthreads();
-        for (uint32_t k = threadIdx.x; k < total; k += CHUNK) {
-            int lo = 0, hi = nloc;               // largest q with off[q] <= k
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (band.off[mid] <= k) lo = mid; else hi = mid;
+        if (!any) continue;
+        const int t = ty * TX + tx;
+        uint32_t pos = tile_off[t] + grow[t];
+#pragma unroll
+        for (int w = 0; w < CHUNK_WARPS; ++w) {
+            uint32_t b = m[w];
+            while (b) {
+                const int jj = w * 32 + __ffs(b) - 1;
+                b &= b - 1;
+                vals[pos] = s.id[jj];
+                if (keys) keys[pos] = ((unsigned long long)(uint32_t)t << 32) | (unsigned long long)dbits[jj];
+                ++pos;
             }
-            const int tx = s.ux0 + lo % uw, ty = yb + lo / uw;
-            const uint32_t rank = k - band.off[lo];
-            uint32_t r = rank;
-            int jj = 0;
-            for (int w = 0; w < CHUNK_WARPS; ++w) {
-                uint32_t m = s.mx[w][tx] & s.my[w][ty];
-                const uint32_t cnt = __popc(m);
-                if (r < cnt) {
-                    for (uint32_t q = 0; q < r; ++q) m &= m - 1;
-                    jj = w * 32 + (__ffs(m) - 1);
-                    break;
-                }
-                r -= cnt;
-            }
-            const int t = ty * TX + tx;
-            const uint32_t pos = tile_off[t] + grow[t] + rank;
-            const uint32_t id = s.id[jj];
-            vals[pos] = id;
-            if (keys)
-                keys[pos] = ((unsigned long long)(uint32_t)t << 32) |
-                            (unsigned long long)__float_as_uint(depth[(size_t)id * dstride]);
         }
-        __syncthreads();
     }
 }
 
