@@ -379,6 +379,7 @@ def run_sequence(args):
 
     def arm(summary, learned, thr):
         skip = [r for r in learned if r.t > cfg.train_frames]
+        kept = [r.seconds for r in skip if not r.fallback]
         return {"threshold": thr,
                 "s_per_frame_plain": round(summary["s_per_frame_plain_skip_frames"], 4),
                 "s_per_frame_learned": round(summary["s_per_frame_learned_skip_frames"], 4),
@@ -390,7 +391,10 @@ def run_sequence(args):
                 "dpsnr_train_views_mean": round(summary["mean_dpsnr_train_skip_frames"], 4),
                 "dpsnr_heldout_min": round(summary["min_dpsnr_skip_frames"], 4),
                 "dpsnr_heldout_mean": round(summary["mean_dpsnr_skip_frames"], 4),
-                "frame_s_learned": [round(r.seconds, 4) for r in skip]}
+                "frame_s_learned": [round(r.seconds, 4) for r in skip],
+                "s_per_frame_learned_kept": round(float(np.mean(kept)), 4) if kept else None,
+                "fallback_dpsnr_train_before": [round(r.psnr_skip_train - r.psnr_plain_train, 4)
+                                                for r in skip if r.fallback]}
 
     res = {"config": {"n_gaussians": cfg.n, "sh_degree": cfg.sh_degree, "width": cfg.width, "height": cfg.height,
                       "views": cfg.views, "frames": cfg.frames, "iters_per_frame": cfg.iters,

@@ -48,7 +48,7 @@ enum {
 #define QN_MAX_LATENT 16      /* latent width per category */
 #define QN_MAX_TILES_X 256    /* image width  <= 4096 */
 #define QN_MAX_TILES_Y 256    /* image height <= 4096 */
-#define QN_DECODE_BWD_BLOCKS 512  /* per-block partials of the decoder gradient */
+#define QN_DECODE_BWD_BLOCKS 1216 /* per-block partials of the decoder gradient */
 #define QN_MLP_BWD_BLOCKS 256     /* per-block partials of the MLP gradient */
 #define QN_LOSS_BLOCKS 2048       /* per-block partials of the image loss */
 

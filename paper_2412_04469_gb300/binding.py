@@ -159,7 +159,7 @@ def qn_decode_residuals(n, n_stride, n_attr, prev, lat, dec, layout, lp, log_alp
                                      _ptr(gate), _ptr(lreg), _stream(stream)))
 
 
-QN_DECODE_BWD_BLOCKS = 512
+QN_DECODE_BWD_BLOCKS = 1216
 QN_MLP_BWD_BLOCKS = 256
 
 

@@ -295,6 +295,131 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
         if (own_c[q] >= 0) partials[(size_t)blockIdx.x * a.n_dec + threadIdx.x + q * BWD_THREADS] = acc[q];
 }
 
+// The adjoint for layouts of at most 4 categories, each of latent width 8
+// (the configured layout).  Per tile of 32 Gaussians:
+//  - STE product d_lat = D^T dr: warp (c, h) of the 8 takes latents 4h..4h+3
+//    of category c for its 32 Gaussians (lane = Gaussian); a decoder row is
+//    read as one float4 broadcast, so 4 FMAs cost 2 shared loads;
+//  - dD += dr l^T: thread (row R, half h, tile half jh) accumulates the 4
+//    entries of row R for latents 4h..4h+3 over 16 Gaussians, the latents
+//    staged transposed (one float4 per Gaussian); the two tile halves are
+//    added at the end, in a fixed order.
+constexpr int LT8_STRIDE = 36;                 // s_lT row: 32 latents + 4 (rows stay 16-byte aligned)
+constexpr int DD_ITEMS = 2 * MAX_RES_PLANES;    // (row, half) items of dD
+
+__global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
+    DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
+    const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
+    float d_lreg, const uint8_t *__restrict__ skip, float *__restrict__ d_lat,
+    float *__restrict__ partials, float *__restrict__ d_lp, float *__restrict__ d_la) {
+    __shared__ __align__(16) float sD[MAX_RES_PLANES * 8];
+    __shared__ float s_dr[MAX_RES_PLANES][BWD_TILE + 1];
+    __shared__ __align__(16) float s_lT[BWD_TILE][LT8_STRIDE];
+    __shared__ float s_part[2][MAX_RES_PLANES * 8];
+    for (int k = threadIdx.x; k < a.n_dec; k += BWD_THREADS) sD[k] = bf16_to_f32(dec[k]);
+    const size_t S = a.stride;
+    const int n_res = a.n_attr - 3;
+    const int lane = threadIdx.x & (BWD_TILE - 1), row0 = threadIdx.x / BWD_TILE;
+    // d_lat role of this warp
+    const int lc = row0 >> 1, lh = row0 & 1;
+    // dD role of this thread: row R (of the residual planes), half h, tile half jh
+    const int item = threadIdx.x % DD_ITEMS, jh = threadIdx.x / DD_ITEMS;
+    const int R = item % MAX_RES_PLANES, dh = item / MAX_RES_PLANES;
+    int dc = -1;
+    for (int c = 0; c < a.n_cat; ++c)
+        if (R >= a.ab[c] - 3 && R < a.ab[c] - 3 + a.ac[c]) dc = c;
+    const bool dd_on = jh < 2 && dc >= 0;
+    const int d_e = dd_on ? a.dec_off[dc] + (R - (a.ab[dc] - 3)) * 8 + 4 * dh : 0;   // first of the 4 entries
+    const int d_l = dd_on ? a.lat_off[dc] + 4 * dh : 0;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int step = gridDim.x * BWD_TILE;
+    TileRegs t;
+    load_tile(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
+    for (int base = blockIdx.x * BWD_TILE; base < a.n; base += step) {
+        const int i = base + lane;
+        const bool valid = t.valid, sk = t.sk;
+        // the barrier also keeps the previous tile's readers ahead of the stores below
+        if (__syncthreads_and(!valid || sk)) {            // a tile of skipped Gaussians only zeroes them
+            if (valid) {
+                for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) d_lat[(size_t)k * S + i] = 0.f;
+                if (row0 == 0) {
+                    d_lp[i] = d_lp[S + i] = d_lp[2 * S + i] = 0.f;
+                    d_la[i] = 0.f;
+                }
+            }
+            load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
+            continue;
+        }
+#pragma unroll
+        for (int m = 0; m < PF_DR; ++m) {
+            const int r = row0 + m * ROWS_PER_PASS;
+            if (r < n_res) s_dr[r][lane] = t.dr[m];
+        }
+#pragma unroll
+        for (int m = 0; m < PF_L; ++m) {
+            const int k = row0 + m * ROWS_PER_PASS;
+            if (k < a.n_lat) s_lT[lane][k] = latent_int(t.l[m]);
+        }
+        if (row0 == 0 && valid) {
+            const float gh = sigmoidf_(t.la / a.tau);
+            const float gt = gh * (a.g1 - a.g0) + a.g0;
+            const float g = fminf(1.f, fmaxf(0.f, gt));
+            const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
+            float dot = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                d_lp[d * S + i] = sk ? 0.f : g * t.dp[d];
+                dot = fmaf(t.dp[d], t.lp[d], dot);
+            }
+            const float p = sigmoidf_(t.la - a.shift);
+            d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
+        }
+        load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
+        __syncthreads();
+        // STE: d_lat of latents 4 lh .. 4 lh + 3 of category lc
+        if (valid && lc < a.n_cat) {
+            const float *D = sD + a.dec_off[lc] + 4 * lh;
+            const float *dr = &s_dr[a.ab[lc] - 3][lane];
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll 4
+            for (int r = 0; r < a.ac[lc]; ++r) {
+                const float d = dr[r * (BWD_TILE + 1)];
+                const float4 w = *reinterpret_cast<const float4 *>(D + r * 8);
+                o0 = fmaf(w.x, d, o0);
+                o1 = fmaf(w.y, d, o1);
+                o2 = fmaf(w.z, d, o2);
+                o3 = fmaf(w.w, d, o3);
+            }
+            float *dl = d_lat + (size_t)(a.lat_off[lc] + 4 * lh) * S + i;
+            dl[0] = sk ? 0.f : o0;
+            dl[S] = sk ? 0.f : o1;
+            dl[2 * S] = sk ? 0.f : o2;
+            dl[3 * S] = sk ? 0.f : o3;
+        }
+        // dD: row R, latents d_l .. d_l + 3, Gaussians 16 jh .. 16 jh + 15 of the tile
+        if (dd_on) {
+#pragma unroll 4
+            for (int j = 16 * jh; j < 16 * jh + 16; ++j) {
+                const float d = s_dr[R][j];
+                const float4 l4 = *reinterpret_cast<const float4 *>(&s_lT[j][d_l]);
+                acc[0] = fmaf(d, l4.x, acc[0]);
+                acc[1] = fmaf(d, l4.y, acc[1]);
+                acc[2] = fmaf(d, l4.z, acc[2]);
+                acc[3] = fmaf(d, l4.w, acc[3]);
+            }
+        }
+    }
+    // this block's partial dD (tile halves added in order); summed over blocks afterwards
+    __syncthreads();
+    if (dd_on) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s_part[jh][d_e + q] = acc[q];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.n_dec; e += BWD_THREADS)
+        partials[(size_t)blockIdx.x * a.n_dec + e] = s_part[0][e] + s_part[1][e];
+}
+
 int make_args(int32_t n, int32_t n_stride, int32_t n_attr, const qn_decoder_layout *lay,
               const qn_gate_params *gp, DecodeArgs *a) {
     QN_REQUIRE(n >= 0, "n must be >= 0 (got %d)", n);
@@ -378,9 +503,9 @@ extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_at
             return qn::check_launch("decode_bwd memset");
         return QN_OK;
     }
-    int grid = qn::grid_for(n, qn::BWD_TILE, 4);
+    int grid = qn::grid_for(n, qn::BWD_TILE, 8);
     if (grid > QN_DECODE_BWD_BLOCKS) grid = QN_DECODE_BWD_BLOCKS;
-    auto kern = qn::uniform_width8(a) ? qn::k_decode_bwd<8> : qn::k_decode_bwd<0>;
+    auto kern = (qn::uniform_width8(a) && a.n_cat <= 4) ? qn::k_decode_bwd8 : qn::k_decode_bwd<0>;
     kern<<<grid, qn::BWD_THREADS, 0, s>>>(a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat,
                                                       partials, d_lp, d_log_alpha);
     if (a.n_dec > 0) qn::k_sum_partials<<<qn::sum_partials_grid(a.n_dec), 256, 0, s>>>(a.n_dec, grid, partials, d_dec);

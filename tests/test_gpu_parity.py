@@ -322,10 +322,10 @@ def _decode_problem(n, deg, seed, latent=8):
     return lay, prev, res
 
 
-@pytest.mark.parametrize("n,deg,seed", [(1000, 3, 0), (37, 1, 1), (1, 0, 2)])
-def test_decode_matches_oracle(n, deg, seed):
+@pytest.mark.parametrize("n,deg,seed,latent", [(1000, 3, 0, 8), (37, 1, 1, 8), (1, 0, 2, 8), (1000, 2, 5, 4)])
+def test_decode_matches_oracle(n, deg, seed, latent):
     from paper_2412_04469_gb300.pipeline import QueenFrame
-    lay, prev, res = _decode_problem(n, deg, seed)
+    lay, prev, res = _decode_problem(n, deg, seed, latent)
     f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
     f.decode()
     torch.cuda.synchronize()
@@ -337,10 +337,13 @@ def test_decode_matches_oracle(n, deg, seed):
     assert float(f.lreg.item()) == pytest.approx(lreg, rel=1e-5)
 
 
-@pytest.mark.parametrize("n,deg,seed", [(1000, 3, 0), (37, 1, 1)])
-def test_decode_bwd_matches_oracle(n, deg, seed):
+@pytest.mark.parametrize("n,deg,seed,latent", [(1000, 3, 0, 8), (37, 1, 1, 8), (1000, 3, 0, 4), (40_000, 3, 3, 8),
+                                               (40_000, 1, 4, 4)])
+def test_decode_bwd_matches_oracle(n, deg, seed, latent):
+    """Latent width 8 takes the specialised adjoint, width 4 the general one;
+    the 40k cases span many tiles per block, with a contiguous skipped run."""
     from paper_2412_04469_gb300.pipeline import QueenFrame
-    lay, prev, res = _decode_problem(n, deg, seed)
+    lay, prev, res = _decode_problem(n, deg, seed, latent)
     res.log_alpha[: n // 2] = np.linspace(-1, 1, n // 2)      # inside the open gate interval
     from paper_2412_04469_gb300.pipeline import HParams
     f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha, HParams(lreg_mean=False))
@@ -348,6 +351,8 @@ def test_decode_bwd_matches_oracle(n, deg, seed):
     d_out = rng.standard_normal((prev.shape[0], n)).astype(np.float32)
     f.d_attrs[:, :n] = up(d_out)
     skip = (rng.uniform(size=n) < 0.2).astype(np.uint8)
+    if n > 10_000:
+        skip[n // 3: 2 * n // 3] = 1                            # whole tiles of skipped Gaussians
     f.decode_bwd(skip=up(skip, torch.uint8))
     torch.cuda.synchronize()
     want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, d_out, f.d_lreg,
