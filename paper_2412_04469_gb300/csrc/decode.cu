@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
                 float l[LT > 0 ? LT : 1];
 #pragma unroll
                 for (int k = 0; k < LT; ++k) l[k] = latent_int(lat[(size_t)(a.lat_off[c] + k) * S + i]);
-#pragma unroll 4
+#pragma unroll 8
                 for (int r = 0; r < a.ac[c]; ++r) {
                     const float4 *Dr = reinterpret_cast<const float4 *>(D + r * LT);
                     float acc = 0.f;
