@@ -477,7 +477,7 @@ __device__ __forceinline__ void gather_one(int TX, int TY, uint32_t g, uint32_t 
 // nothing to do), then the warp sums the wanted ones one after another.  The
 // stride spreads the front-most Gaussians, which own nearly all visited pairs,
 // over every warp.
-__global__ void __launch_bounds__(256) k_bin_gather(int TX, int TY, const uint32_t *__restrict__ sorted,
+__global__ void __launch_bounds__(256, 6) k_bin_gather(int TX, int TY, const uint32_t *__restrict__ sorted,
                                                     const int4 *__restrict__ rects, const Header *hdr,
                                                     const uint32_t *__restrict__ gbase,
                                                     const uint32_t *__restrict__ tile_off,

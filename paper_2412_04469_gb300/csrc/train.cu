@@ -76,20 +76,18 @@ __device__ __forceinline__ float adam_update(const AdamConst &c, float p, float 
 __global__ void __launch_bounds__(256) k_adam_groups(const __grid_constant__ AdamGroups G,
                                                      const int32_t *__restrict__ step, float b1, float b2,
                                                      float eps, const uint8_t *__restrict__ skip) {
-    __shared__ float ibc[2];
-    if (threadIdx.x == 0) {
-        const double t = (double)*step;
-        ibc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
-        ibc[1] = (float)(1.0 / (1.0 - pow((double)b2, t)));
-    }
-    __syncthreads();
+    // bias corrections 1 / (1 - b^t), each thread on its own (no barrier):
+    // 1 - b^t = -expm1(t log1p(b - 1)) has no cancellation, and b - 1 is exact
+    const float t = (float)*step;
+    const float ibc1 = -1.f / expm1f(t * log1pf(b1 - 1.f));
+    const float ibc2 = -1.f / expm1f(t * log1pf(b2 - 1.f));
     const int y = blockIdx.y;
     int gi = 0;
     while (gi + 1 < G.n_groups && G.row_start[gi + 1] <= y) ++gi;
     const qn_adam_group &P = G.g[gi];
     const int r = y - G.row_start[gi];
     const uint8_t *sk = P.use_skip ? skip : nullptr;
-    const AdamConst c{b1, b2, eps, ibc[0], ibc[1], P.lr};
+    const AdamConst c{b1, b2, eps, ibc1, ibc2, P.lr};
     const size_t row = (size_t)r * P.stride;
     const int stride = gridDim.x * blockDim.x;
     int done = 0;                                      // elements covered by the vector loop
