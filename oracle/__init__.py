@@ -8,8 +8,8 @@ Two halves:
   raster  -- ctypes front-end to queen_oracle.c (decode, gate, projection,
              binning, compositing and their analytic adjoints), Sec. 3.1-3.2.
   learn   -- numpy FP64 code for the loss, the viewspace gradient difference
-             and gate initialisation (Sec. 3.3, Eq. 9-10), Adam, and the
-             static-skip MLP.
+             and gate initialisation (Sec. 3.3, Eq. 9-10), the adaptive
+             training mask (Sec. 3.3), Adam, and the static-skip MLP.
 
 Parity status per function is recorded in each function's docstring; every
 function listed here is pinned by tests/test_oracle_*.py (closed forms,
@@ -19,11 +19,13 @@ docstring says "parity unpinned".
 from .raster import (build, OracleCamera, sh_basis, decode, decode_bwd, project, project_bwd,
                      bin_sort, render_fwd, render_bwd, num_threads)
 from .learn import (l1_loss, mse_grad, viewspace_score, gate_init, adam_step, mlp_forward,
-                    mlp_backward, bce_loss, skip_features)
+                    mlp_backward, bce_loss, skip_features, dynamic_flags, dynamic_pixels, dilate, tile_mask,
+                    masked_l1_loss, MASK_T_D, MASK_KERNEL)
 
 __all__ = [
     "build", "OracleCamera", "sh_basis", "decode", "decode_bwd", "project", "project_bwd",
     "bin_sort", "render_fwd", "render_bwd", "num_threads", "l1_loss", "mse_grad",
     "viewspace_score", "gate_init", "adam_step", "mlp_forward", "mlp_backward", "bce_loss",
-    "skip_features",
+    "skip_features", "dynamic_flags", "dynamic_pixels", "dilate", "tile_mask", "masked_l1_loss",
+    "MASK_T_D", "MASK_KERNEL",
 ]

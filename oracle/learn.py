@@ -155,3 +155,68 @@ def mlp_backward(d_logit, params, cache):
     g["W1"] = d1.T @ X
     g["b1"] = d1.sum(axis=0)
     return g
+
+
+# --------------------------------------------------------------------------
+# Adaptive masked training (Sec. 3.3; App. B: t_d = 0.001, a 48 x 48
+# dilation, masked iterations for a fraction of the frame's iterations).
+MASK_T_D = 0.001
+MASK_KERNEL = 48
+
+
+def dynamic_flags(norms, t_d=MASK_T_D):
+    """Dynamic Gaussians: |d_t| above the threshold t_d."""
+    return np.asarray(norms, np.float64) > t_d
+
+
+def dynamic_pixels(proj, flags, bg=(0.0, 0.0, 0.0)):
+    """Pixels where the dynamic Gaussians rendered alone produce a contributor:
+    the oracle rendering with every other Gaussian's tile rect emptied, and
+    last > 0 (the first Gaussian that passes the alpha test at a pixel always
+    contributes, so this is the union of the dynamic Gaussians' alpha >= 1/255
+    footprints).  Returns bool [H][W]."""
+    p = dict(proj)
+    rect = np.array(proj["rect"], copy=True)
+    rect[:, ~np.asarray(flags, bool)] = 0
+    p["rect"] = rect
+    _, _, last, _ = raster.render_fwd(p, bg)
+    return last > 0
+
+
+def dilate(mask, k=MASK_KERNEL):
+    """Box dilation with a k x k kernel: out[y][x] is set when some input
+    pixel (x', y') has x in [x' - k/2, x' + k/2 - 1] and y likewise, i.e. the
+    input window of out[y][x] is [x - k/2 + 1, x + k/2] (k even)."""
+    m = np.asarray(mask, bool)
+    H, W = m.shape
+    lo, hi = k // 2 - 1, k // 2
+    cs = np.zeros((H + 1, W + 1), np.int64)
+    cs[1:, 1:] = np.cumsum(np.cumsum(m, axis=0), axis=1)
+    y0 = np.clip(np.arange(H) - lo, 0, H)
+    y1 = np.clip(np.arange(H) + hi + 1, 0, H)
+    x0 = np.clip(np.arange(W) - lo, 0, W)
+    x1 = np.clip(np.arange(W) + hi + 1, 0, W)
+    s = cs[y1][:, x1] - cs[y0][:, x1] - cs[y1][:, x0] + cs[y0][:, x0]
+    return s > 0
+
+
+def tile_mask(pixel_mask, tile=16):
+    """Tiles (row-major over the tile grid) holding at least one masked pixel."""
+    m = np.asarray(pixel_mask, bool)
+    H, W = m.shape
+    TX, TY = (W + tile - 1) // tile, (H + tile - 1) // tile
+    pad = np.zeros((TY * tile, TX * tile), bool)
+    pad[:H, :W] = m
+    return pad.reshape(TY, tile, TX, tile).any(axis=(1, 3)).reshape(-1)
+
+
+def masked_l1_loss(img, target, pixel_mask):
+    """L1 term of Eq. 3 restricted to the masked pixels: the mean of |img -
+    target| over the C x (masked pixels) values; dL/dimg = sign / that count on
+    masked pixels and 0 elsewhere (both 0 for an empty mask)."""
+    d = np.asarray(img, np.float64) - np.asarray(target, np.float64)
+    m = np.broadcast_to(np.asarray(pixel_mask, bool)[None], d.shape)
+    cnt = int(m.sum())
+    if cnt == 0:
+        return 0.0, np.zeros_like(d)
+    return float(np.abs(d[m]).sum() / cnt), np.where(m, np.sign(d), 0.0) / cnt
