@@ -370,12 +370,14 @@ def run_sequence(args):
     """The learned static-skip comparison on the full workload's scene and
     cameras: plain gated training and learned skip over the same streamed
     frames (the MLP trains on the first 10, skips from frame 11 on), at the
-    configured skip threshold and at each --seq-extra-threshold."""
+    configured skip threshold and at each --seq-extra-threshold; then plain
+    gated training with Sec. 3.3's masked training on each --seq-masked
+    fraction of the iterations, against the plain arm.
     from paper_2412_04469_gb300.sequence import SequenceConfig, compare
 
     cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
     t0 = time.perf_counter()
-    out = compare(cfg, extra_thresholds=args.seq_extra_threshold)
+    out = compare(cfg, extra_thresholds=args.seq_extra_threshold, masked_fractions=args.seq_masked)
 
     def arm(summary, learned, thr):
         skip = [r for r in learned if r.t > cfg.train_frames]
@@ -406,6 +408,16 @@ def run_sequence(args):
            "configured": arm(out, out["learned"], cfg.threshold)}
     for thr, v in out["by_threshold"].items():
         res[f"threshold_{thr:g}"] = arm(v, v["learned"], thr)
+    plain = out["plain"]
+    for mf, recs in out["masked"].items():
+        res[f"masked_{mf:g}"] = {
+            "masked_fraction": mf, "t_d_ndc": cfg.mask_t_d, "dilation": 48,
+            "s_per_frame_plain": round(float(np.mean([r.seconds for r in plain])), 4),
+            "s_per_frame_masked": round(float(np.mean([r.seconds for r in recs])), 4),
+            "speedup": round(float(np.mean([r.seconds for r in plain]) / np.mean([r.seconds for r in recs])), 4),
+            "dpsnr_heldout_mean": round(float(np.mean([m.psnr - p.psnr for m, p in zip(recs, plain)])), 4),
+            "dpsnr_heldout_min": round(float(np.min([m.psnr - p.psnr for m, p in zip(recs, plain)])), 4),
+            "mask_tile_fraction_mean": round(float(np.mean([r.mask_tiles for r in recs])), 4)}
     res["wall_s"] = round(time.perf_counter() - t0, 1)
     return res
 
@@ -507,6 +519,8 @@ def main():
     ap.add_argument("--no-seq", action="store_true", help="skip the learned-skip sequence comparison")
     ap.add_argument("--seq-frames", type=int, default=16, help="frames of the learned-skip sequence comparison")
     ap.add_argument("--seq-iters", type=int, default=250, help="training iterations per frame in that comparison")
+    ap.add_argument("--seq-masked", type=float, nargs="*", default=[0.3],
+                    help="fractions of iterations trained on Sec. 3.3's adaptive masks (plain gating otherwise)")
     ap.add_argument("--seq-extra-threshold", type=float, nargs="*", default=[0.97],
                     help="further skip thresholds to run in that comparison (same plain arm)")
     ap.add_argument("--quick", action="store_true",

@@ -453,6 +453,57 @@ int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, const uint8_t *
                     float *d_params, float *loss, float *partials, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Adaptive masked training -- Sec. 3.3; App. B (t_d = 0.001, 48 x 48).      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * rects_out[i] = rects[i] for a dynamic Gaussian, else an empty rect:
+ * dynamic when |(ndc_x score[0][i], ndc_y score[1][i])| > t_d, the score
+ * being d_t of Eq. 9 in pixel units (qn_viewspace_accum) and ndc_x, ndc_y
+ * the factors to the units t_d is stated in (W/2 and H/2 for normalised
+ * device coordinates; 1 for pixels).  Binning and compositing with rects_out
+ * render the dynamic Gaussians alone.  rects, rects_out [n] int4 (16-byte
+ * aligned), score [2][n_stride] f32.
+ */
+int qn_select_rects(int32_t n, int32_t n_stride, const int32_t *rects, const float *score, float ndc_x,
+                    float ndc_y, float t_d, int32_t *rects_out, qn_stream_t stream);
+
+/*
+ * The mask of one view from the dynamic-only rendering: a pixel is dynamic
+ * when its last contributor is > 0 (last [H][W] u32 of qn_render_fwd; the
+ * first Gaussian passing the alpha test always contributes, so these are the
+ * pixels some dynamic Gaussian covers with alpha >= 1/255).  Dilated with a
+ * k x k box (k even): pixel_mask[y][x] = 1 when a dynamic pixel lies in
+ * [x - k/2 + 1, x + k/2] x [y - k/2 + 1, y + k/2].  tile_mask [tiles] u8
+ * marks the 16 x 16 tiles holding a masked pixel; *n_masked (device i32) =
+ * number of masked pixels.  tmp [H][W] u8 scratch.  All outputs written.
+ */
+int qn_dilate_mask(int32_t width, int32_t height, const uint32_t *last, int32_t k, uint8_t *tmp,
+                   uint8_t *pixel_mask, uint8_t *tile_mask, int32_t *n_masked, qn_stream_t stream);
+
+/*
+ * ranges_out[t] = ranges[t] for tiles with tile_mask[t] != 0, else the empty
+ * range [ranges[t][0], ranges[t][0]): qn_render_fwd, qn_render_bwd and
+ * qn_bin_gather given ranges_out skip the unmasked tiles.
+ */
+int qn_mask_ranges(int32_t n_tiles, const uint32_t *ranges, const uint8_t *tile_mask, uint32_t *ranges_out,
+                   qn_stream_t stream);
+
+/*
+ * The loss of qn_image_loss restricted to the masked pixels: over the
+ * channels x *n_masked values with pixel_mask[p] != 0 (pixel p of each
+ * channel plane of hw pixels), loss[0] = w mean |img - target| (or the mean
+ * square with mse != 0); d_img = w sign(img - target) / (channels n_masked)
+ * (or 2 w (img - target) / ...) on masked values and 0 elsewhere; both 0 when
+ * *n_masked == 0.  n_masked is read on the device (as qn_dilate_mask leaves
+ * it), so the call can be captured in a CUDA graph.  partials
+ * [QN_LOSS_BLOCKS] f32 scratch, summed in block order.
+ */
+int qn_masked_image_loss(int64_t hw, int32_t channels, const float *img, const float *target,
+                         const uint8_t *pixel_mask, const int32_t *n_masked, float w, int32_t mse, float *loss,
+                         float *d_img, float *partials, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Data layout for the learned static skip.                                  */
 /* ------------------------------------------------------------------------ */
 

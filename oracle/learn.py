@@ -164,9 +164,14 @@ MASK_T_D = 0.001
 MASK_KERNEL = 48
 
 
-def dynamic_flags(norms, t_d=MASK_T_D):
-    """Dynamic Gaussians: |d_t| above the threshold t_d."""
-    return np.asarray(norms, np.float64) > t_d
+def dynamic_flags(d, width, height, t_d=MASK_T_D):
+    """Dynamic Gaussians: |d_t| above the threshold t_d, with d_t (Eq. 9,
+    [2][n], pixel units) taken in normalised device coordinates -- the units
+    of the 3D-GS rasterizer's viewspace gradients that t_d refers to: a
+    position in NDC moves W/2 (H/2) pixels per unit, so the gradient w.r.t.
+    it is the pixel-unit gradient times W/2 (H/2)."""
+    d = np.asarray(d, np.float64)
+    return np.hypot(d[0] * (width / 2.0), d[1] * (height / 2.0)) > t_d
 
 
 def dynamic_pixels(proj, flags, bg=(0.0, 0.0, 0.0)):

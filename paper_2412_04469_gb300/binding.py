@@ -78,6 +78,10 @@ _SIGS = {
     "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
     "qn_adam_groups": ([_I32, _P, _P, _F32, _F32, _F32, _P, _P], C.c_int),
     "qn_partition_workspace_size": ([_I32], C.c_size_t),
+    "qn_select_rects": ([_I32, _I32, _P, _P, _F32, _F32, _F32, _P, _P], C.c_int),
+    "qn_dilate_mask": ([_I32, _I32, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
+    "qn_mask_ranges": ([_I32, _P, _P, _P, _P], C.c_int),
+    "qn_masked_image_loss": ([_I64, _I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_partition": ([_I32, _P, _P, _P, _P, C.c_size_t, _P], C.c_int),
     "qn_gather_columns": ([_I32, _I32, _I32, _P, C.c_int64, _P, _P, C.c_int64, _P], C.c_int),
 }
@@ -236,14 +240,17 @@ QN_LOSS_BLOCKS = 2048
 _loss_scratch = {}
 
 
+def _loss_partials(dev):
+    if dev not in _loss_scratch:
+        _loss_scratch[dev] = torch.zeros(QN_LOSS_BLOCKS, device=dev)
+    return _loss_scratch[dev]
+
+
 def qn_image_loss(count, img, target, w, mse, loss, d_img, partials=None, stream=None):
     """partials: QN_LOSS_BLOCKS floats of scratch (one per device is kept here
     when not given)."""
     if partials is None:
-        dev = loss.device
-        if dev not in _loss_scratch:
-            _loss_scratch[dev] = torch.zeros(QN_LOSS_BLOCKS, device=dev)
-        partials = _loss_scratch[dev]
+        partials = _loss_partials(loss.device)
     _check(lib().qn_image_loss(count, _ptr(img), _ptr(target), float(w), int(mse), _ptr(loss), _ptr(d_img),
                                _ptr(partials), _stream(stream)))
 
@@ -318,3 +325,24 @@ def qn_gather_columns(rows, n, src, src_stride, perm, dst, dst_stride, stream=No
     """dst[r][i] = src[r][perm[i]]; element size from src's dtype."""
     _check(lib().qn_gather_columns(rows, n, src.element_size(), _ptr(src), int(src_stride), _ptr(perm), _ptr(dst),
                                    int(dst_stride), _stream(stream)))
+
+
+def qn_select_rects(n, n_stride, rects, score, ndc_x, ndc_y, t_d, rects_out, stream=None):
+    _check(lib().qn_select_rects(n, n_stride, _ptr(rects), _ptr(score), float(ndc_x), float(ndc_y), float(t_d),
+                                 _ptr(rects_out), _stream(stream)))
+
+
+def qn_dilate_mask(width, height, last, k, tmp, pixel_mask, tile_mask, n_masked, stream=None):
+    _check(lib().qn_dilate_mask(width, height, _ptr(last), int(k), _ptr(tmp), _ptr(pixel_mask), _ptr(tile_mask),
+                                _ptr(n_masked), _stream(stream)))
+
+
+def qn_mask_ranges(n_tiles, ranges, tile_mask, ranges_out, stream=None):
+    _check(lib().qn_mask_ranges(n_tiles, _ptr(ranges), _ptr(tile_mask), _ptr(ranges_out), _stream(stream)))
+
+
+def qn_masked_image_loss(hw, channels, img, target, pixel_mask, n_masked, w, mse, loss, d_img, stream=None):
+    part = _loss_partials(img.device)
+    _check(lib().qn_masked_image_loss(int(hw), int(channels), _ptr(img), _ptr(target), _ptr(pixel_mask),
+                                      _ptr(n_masked), float(w), int(bool(mse)), _ptr(loss), _ptr(d_img), _ptr(part),
+                                      _stream(stream)))

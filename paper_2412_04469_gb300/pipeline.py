@@ -18,6 +18,8 @@ from . import binding as B
 from .synthetic import DecoderLayout, n_attr as n_attr_of, bf16_bits
 
 TILE = B.QN_TILE
+MASK_T_D = 0.001          # Sec. 3.3 threshold on |d_t| (App. B)
+MASK_KERNEL = 48          # dilation of the mask (App. B)
 
 
 def _stride(n: int) -> int:
@@ -174,6 +176,9 @@ class Rasterizer:
         self.ranges = torch.zeros((self.TX * self.TY, 2), device=dev, dtype=torch.int32)
         self.n_pairs = torch.zeros(1, device=dev, dtype=torch.int64)
         self.tile_visited = torch.zeros(self.TX * self.TY, device=dev, dtype=torch.int32)
+        self.ranges_masked = torch.zeros_like(self.ranges)         # masked iterations: inactive tiles emptied
+        self.rects_sel = torch.zeros_like(self.rects)              # mask building: dynamic Gaussians' rects
+        self.mask_tmp = torch.zeros((height, width), device=dev, dtype=torch.uint8)
         self.gauss_hit = torch.zeros(nn, device=dev, dtype=torch.uint8)      # Gaussians some pixel composited
         self.keep_keys = keep_keys
         self.set_capacity(pair_capacity)
@@ -194,27 +199,29 @@ class Rasterizer:
         B.qn_project(self.n, self.S, self.sh_degree, attrs, cam, blur, self.splats, self.rects, self.tight_rects,
                      stream)
 
-    def bin_sort(self, sync=False, stream=None):
+    def bin_sort(self, sync=False, stream=None, rects=None):
         depth_ptr = self.splats.data_ptr() + 3 * 4
-        return B.qn_bin_sort(self.n, depth_ptr, 12, self.rects, self.TX, self.TY, self.workspace, self.capacity,
-                             self.vals, self.keys, self.ranges, self.n_pairs, sync, stream)
+        return B.qn_bin_sort(self.n, depth_ptr, 12, self.rects if rects is None else rects, self.TX, self.TY,
+                             self.workspace, self.capacity, self.vals, self.keys, self.ranges, self.n_pairs, sync,
+                             stream)
 
-    def render_fwd(self, cam, bg, n_contrib=None, stream=None):
-        B.qn_render_fwd(cam, self.ranges, self.vals, self.splats, bg, self.img, self.T_final, self.last, n_contrib,
-                        stream)
+    def render_fwd(self, cam, bg, n_contrib=None, stream=None, ranges=None):
+        B.qn_render_fwd(cam, self.ranges if ranges is None else ranges, self.vals, self.splats, bg, self.img,
+                        self.T_final, self.last, n_contrib, stream)
 
     def loss_grad(self, target, w=1.0, mse=False, stream=None):
         B.qn_image_loss(self.img.numel(), self.img, target, w, mse, self.loss, self.d_img, stream)
 
-    def render_bwd(self, cam, bg, skip=None, stream=None):
+    def render_bwd(self, cam, bg, skip=None, stream=None, ranges=None):
         """Compositing adjoint: per-pair records, then the per-Gaussian gather."""
-        self.render_bwd_pairs(cam, bg, skip, stream)
+        self.render_bwd_pairs(cam, bg, skip, stream, ranges)
         self.gather(skip, stream)
 
-    def render_bwd_pairs(self, cam, bg, skip=None, stream=None):
+    def render_bwd_pairs(self, cam, bg, skip=None, stream=None, ranges=None):
         self.gauss_hit.zero_()
-        B.qn_render_bwd(cam, self.ranges, self.vals, self.splats, bg, self.T_final, self.last, self.d_img, skip,
-                        self.pair_grads, self.tile_visited, stream, gauss_hit=self.gauss_hit)
+        B.qn_render_bwd(cam, self.ranges if ranges is None else ranges, self.vals, self.splats, bg, self.T_final,
+                        self.last, self.d_img, skip, self.pair_grads, self.tile_visited, stream,
+                        gauss_hit=self.gauss_hit)
 
     def gather(self, skip=None, stream=None):
         B.qn_bin_gather(self.n, self.rects, self.TX, self.TY, self.workspace, self.tile_visited, self.pair_grads,
@@ -222,6 +229,27 @@ class Rasterizer:
 
     def project_bwd(self, attrs, cam, blur, d_attrs, skip=None, stream=None):
         B.qn_project_bwd(self.n, self.S, self.sh_degree, attrs, cam, blur, self.d_splats, skip, d_attrs, stream)
+
+    # ------------------------------------------------------------ masked training
+    def build_mask(self, attrs, cam, blur, score, vm: "ViewMask", t_d=MASK_T_D, k=MASK_KERNEL, bg=(0.0, 0.0, 0.0),
+                   stream=None):
+        """Sec. 3.3's mask of one view: the dynamic Gaussians (|d_t| > t_d,
+        d_t = score [2][S] in pixel units, compared in normalised device
+        coordinates) rendered alone, their pixels dilated with a k x k box,
+        the tiles holding a masked pixel marked.  Overwrites the rasterizer's
+        projection, binning and image buffers."""
+        self.project(attrs, cam, blur, stream)
+        B.qn_select_rects(self.n, self.S, self.rects, score, self.W / 2.0, self.H / 2.0, t_d, self.rects_sel, stream)
+        self.bin_sort(False, stream, rects=self.rects_sel)
+        self.render_fwd(cam, bg, stream=stream)
+        B.qn_dilate_mask(self.W, self.H, self.last, k, self.mask_tmp, vm.pixel, vm.tiles, vm.count, stream)
+
+    def mask_ranges(self, vm: "ViewMask", stream=None):
+        B.qn_mask_ranges(self.TX * self.TY, self.ranges, vm.tiles, self.ranges_masked, stream)
+
+    def masked_loss_grad(self, target, vm: "ViewMask", w=1.0, mse=False, stream=None):
+        B.qn_masked_image_loss(self.W * self.H, 3, self.img, target, vm.pixel, vm.count, w, mse, self.loss,
+                               self.d_img, stream)
 
     def ensure_capacity(self, margin: float = 1.25):
         """Synchronising: re-runs the binning with a larger buffer if it overflowed."""
@@ -232,20 +260,45 @@ class Rasterizer:
         return P
 
 
-def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None):
+@dataclass
+class ViewMask:
+    """The adaptive training mask of one view (Sec. 3.3): pixel mask [H][W]
+    u8, tile mask [tiles] u8, number of masked pixels [1] i32 (device)."""
+    pixel: torch.Tensor
+    tiles: torch.Tensor
+    count: torch.Tensor
+
+    @classmethod
+    def empty(cls, width, height, device="cuda"):
+        tx, ty = (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
+        return cls(torch.zeros((height, width), device=device, dtype=torch.uint8),
+                   torch.zeros(tx * ty, device=device, dtype=torch.uint8),
+                   torch.zeros(1, device=device, dtype=torch.int32))
+
+
+def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None,
+                       mask: ViewMask | None = None):
     """One view of Eq. 11's optimisation: forward, L1 loss (Eq. 3 L1 term) +
     lambda_reg L_reg (the L_reg gradient is folded into the gate adjoint), full
     adjoint and the Adam step.  No host synchronisation.  Gaussians with skip
     set are frozen: no gradient, no update, and their decoded columns are
     reused (frame.attrs must hold their A_t, e.g. from a decode without
-    skip)."""
+    skip).  With a mask (Sec. 3.3's masked training) only the masked tiles
+    are composited and the loss is the mean over the masked pixels."""
     hp = frame.hp
     frame.decode(stream, skip)
     rast.project(frame.attrs, cam, hp.blur, stream)
     rast.bin_sort(False, stream)
-    rast.render_fwd(cam, hp.bg, stream)
-    rast.loss_grad(target, 1.0, False, stream)
-    rast.render_bwd(cam, hp.bg, skip, stream)
+    ranges = None
+    if mask is not None:
+        rast.mask_ranges(mask, stream)
+        ranges = rast.ranges_masked
+    rast.render_fwd(cam, hp.bg, stream=stream, ranges=ranges)
+    if mask is None:
+        rast.loss_grad(target, 1.0, False, stream)
+    else:
+        rast.masked_loss_grad(target, mask, 1.0, False, stream)
+    rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges)
     rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
     frame.decode_bwd(skip, stream)
     frame.adam(skip, stream)
@@ -267,19 +320,19 @@ class IterationGraph:
         self.pool = None
         self.warm = False
 
-    def _signature(self, target, skip):
+    def _signature(self, target, skip, mask):
         r = self.rast
         return (target.data_ptr(), None if skip is None else skip.data_ptr(), r.vals.data_ptr(),
-                r.pair_grads.data_ptr(), r.workspace.data_ptr())
+                r.pair_grads.data_ptr(), r.workspace.data_ptr(), None if mask is None else mask.pixel.data_ptr())
 
-    def run(self, key, cam, target, skip=None):
-        sig = self._signature(target, skip)
+    def run(self, key, cam, target, skip=None, mask=None):
+        sig = self._signature(target, skip, mask)
         ent = self.graphs.get(key)
         if ent is None or ent[1] != sig:
             if not self.warm:
                 # one eager iteration first: lazily allocated scratch must
                 # exist before capture; it is a real training step
-                training_iteration(self.frame, self.rast, cam, target, skip)
+                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask)
                 self.warm = True
                 return
             if self.pool is None:
@@ -287,8 +340,8 @@ class IterationGraph:
             g = torch.cuda.CUDAGraph()
             torch.cuda.synchronize()
             with torch.cuda.graph(g, pool=self.pool):
-                training_iteration(self.frame, self.rast, cam, target, skip)
-            ent = (g, sig, cam, target, skip)           # keep what the graph points at alive
+                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask)
+            ent = (g, sig, cam, target, skip, mask)     # keep what the graph points at alive
             self.graphs[key] = ent
         ent[0].replay()
 

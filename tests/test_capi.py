@@ -85,3 +85,12 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert b"workspace" in B.lib().qn_last_error()
     assert B.lib().qn_gather_columns(1, 4, 3, 16, 4, 16, 32, 4, None) == B.QN_ERR_INVALID_ARG   # elem_bytes
     assert B.lib().qn_gather_columns(1, 4, 4, 16, 4, 16, 16, 4, None) == B.QN_ERR_INVALID_ARG   # aliasing
+    assert B.lib().qn_dilate_mask(64, 64, 16, 47, 16, 16, 16, 16, None) == B.QN_ERR_INVALID_ARG     # odd k
+    assert b"k must be even" in B.lib().qn_last_error()
+    assert B.lib().qn_dilate_mask(0, 64, 16, 48, 16, 16, 16, 16, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_mask_ranges(4, 16, 32, 16, None) == B.QN_ERR_INVALID_ARG                      # aliasing
+    assert B.lib().qn_select_rects(4, 4, 8, 32, 1.0, 1.0, 0.001, 48, None) == B.QN_ERR_INVALID_ARG  # misaligned
+    assert B.lib().qn_select_rects(4, 2, 16, 32, 1.0, 1.0, 0.001, 48, None) == B.QN_ERR_INVALID_ARG  # stride < n
+    assert B.lib().qn_select_rects(4, 4, 16, 32, 1.0, 1.0, -1.0, 48, None) == B.QN_ERR_INVALID_ARG   # t_d < 0
+    assert B.lib().qn_masked_image_loss(16, 0, None, None, None, None, 1.0, 0, None, None, None, None) == \
+        B.QN_ERR_INVALID_ARG

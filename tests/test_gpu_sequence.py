@@ -42,3 +42,23 @@ def test_learned_skip_on_short_sequence():
     assert out["min_dpsnr_train_skip_frames"] >= -cfg.max_dpsnr
     losses = [r.mlp_loss for r in learned[:cfg.train_frames]]
     assert losses[-1] < 0.7 * losses[0]
+
+
+def test_masked_training_on_short_sequence():
+    """Sec. 3.3's masked training for the first 30% of each frame's
+    iterations: every view's mask is non-empty (the moving object is in view)
+    and leaves some tiles out, the masked iterations are reproducible, and
+    the held-out PSNR stays close to full-image training."""
+    from paper_2412_04469_gb300.sequence import SequenceConfig, StreamingTrainer
+    cfg = SequenceConfig(n=20_000, sh_degree=1, width=160, height=120, views=6, frames=5, iters=80, seed=3)
+    tr = StreamingTrainer(cfg)
+    plain = tr.run(learned=False)
+    tr.cfg.masked_fraction = 0.3
+    masked = tr.run(learned=False)
+    again = tr.run(learned=False)
+    for p, m, a in zip(plain, masked, again):
+        assert 0.0 < m.mask_tiles < 1.0
+        assert m.psnr == a.psnr
+        assert m.psnr >= p.psnr - 0.3
+    for vm in tr.masks:
+        assert 0 < int(vm.count.item()) == int(vm.pixel.sum().item())

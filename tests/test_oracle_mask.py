@@ -89,4 +89,6 @@ def test_dynamic_pixels_are_the_union_of_dynamic_footprints():
     assert want.any() and not want.all()
     assert np.array_equal(got, want)
     assert not oracle.dynamic_pixels(proj, np.zeros(n, bool)).any()
-    assert np.array_equal(oracle.dynamic_flags(np.array([0.0, 0.001, 0.0011, 2.0])), [False, False, True, True])
+    d = np.array([[0.0, 0.001 / 50, 0.0011 / 50, 0.0, 0.0006 / 50], [0.0, 0.0, 0.0, 0.0011 / 20, 0.0008 / 20]])
+    assert np.array_equal(oracle.dynamic_flags(d, 100, 40), [False, False, True, True, False])   # NDC: x W/2, y H/2
+    assert oracle.dynamic_flags(np.array([[0.0006 / 50], [0.00081 / 20]]), 100, 40)[0]               # |(6, 8.1)| e-4 > 1e-3
