@@ -36,7 +36,7 @@ WORKLOADS = {
 METRIC = "fwd+bwd rasterize it/s @300k Gaussians 1352x1014; s/frame learned vs plain @dPSNR<=.05"
 L2_FLUSH_BYTES = 256 << 20
 # kernels each stage launches (memsets are not counted)
-KERNELS_PER_STAGE = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 2, "render_bwd": 1,
+KERNELS_PER_STAGE = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 4, "render_bwd": 1,
                      "gather": 1, "project_bwd": 1, "decode_bwd": 2, "adam": 2}
 STAGES = list(KERNELS_PER_STAGE)
 # DRAM bytes per launch of a kernel on the full workload, from one ncu capture
@@ -200,7 +200,7 @@ def run_gpu(args):
         """One iteration issued stage by stage with an event between stages."""
         c = cams[v]
         calls = (lambda: frame.decode(), lambda: rast.project(frame.attrs, c, hp.blur), lambda: rast.bin_sort(False),
-                 lambda: rast.render_fwd(c, hp.bg), lambda: rast.loss_grad(targets[v]),
+                 lambda: rast.render_fwd(c, hp.bg), lambda: rast.photometric_loss(targets[v], hp.lambda_dssim),
                  lambda: rast.render_bwd_pairs(c, hp.bg), lambda: rast.gather(),
                  lambda: rast.project_bwd(frame.attrs, c, hp.blur, frame.d_attrs), lambda: frame.decode_bwd(),
                  lambda: frame.adam())
@@ -300,7 +300,9 @@ def run_gpu(args):
     # (a projected record or a pair's gradient record is 48 bytes)
     algo_bytes = {
         "decode": 620.0 * n, "project": 300.0 * n, "bin_sort": 20.0 * n + 36.0 * P,
-        "render_fwd": 20.0 * px + 4.0 * Pvis + 48.0 * n_vis, "loss": 36.0 * px,
+        "render_fwd": 20.0 * px + 4.0 * Pvis + 48.0 * n_vis,
+        # L1: img, target, d_img; D-SSIM: img, target, 3 maps out, 3 maps in, img, target, d_img += (3 channels)
+        "loss": 36.0 * px + (144.0 * px if hp.lambda_dssim > 0 else 0.0),
         "render_bwd": 20.0 * px + 52.0 * Pvis + 48.0 * n_vis, "gather": 48.0 * Pvis + 48.0 * n_vis,
         "project_bwd": 508.0 * n, "decode_bwd": 524.0 * n,
         "adam": 28.0 * ((lay.n_latent + 4) * n + lay.n_dec),
@@ -332,7 +334,7 @@ def run_gpu(args):
         roof["alu_render_bwd"] = alu
 
     value = world * args.steps / (max_ms * 1e-3)
-    launches = args.steps * sum(KERNELS_PER_STAGE.values())
+    launches = args.steps * (sum(KERNELS_PER_STAGE.values()) - (2 if hp.lambda_dssim == 0 else 0))
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "it/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
@@ -340,6 +342,7 @@ def run_gpu(args):
         "data": "synthetic (seeded scene, residuals and target images; no dataset)",
         "config": {"workload": workload_name(name), "n_gaussians": n, "sh_degree": deg, "width": W, "height": H,
                    "views": V, "latent_dim": L, "pairs_per_view": round(P), "visited_pairs_per_view": round(Pvis),
+                   "loss": f"{1 - hp.lambda_dssim:g} L1 + {hp.lambda_dssim:g} D-SSIM (Eq. 3) + lambda_reg L_reg",
                    "visible_gaussians": n_vis, "l2": "flushed between timed steps (256 MB write outside step events)",
                    "launch": "one CUDA graph replay per step (iteration captured once per view)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -372,7 +375,7 @@ def run_sequence(args):
     frames (the MLP trains on the first 10, skips from frame 11 on), at the
     configured skip threshold and at each --seq-extra-threshold; then plain
     gated training with Sec. 3.3's masked training on each --seq-masked
-    fraction of the iterations, against the plain arm.
+    fraction of the iterations, against the plain arm."""
     from paper_2412_04469_gb300.sequence import SequenceConfig, compare
 
     cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
@@ -446,16 +449,32 @@ def oracle_iteration(name, n_tiles_sample, seed=0, view=0):
     proj = oracle.project(A, cam, deg, blur=0.3)
     t1 = time.perf_counter()
     img, _, _, _ = oracle.render_fwd(proj, tiles=tiles)
+    t2a = time.perf_counter()
+    lam = 0.2                                       # Eq. 3 weights, as the GPU step uses them
     _, g = oracle.l1_loss(img, target)
+    g *= 1 - lam
+    t2b = time.perf_counter()
+    crop_px = 0
+    for t in tiles:
+        # D-SSIM's gradient inside a tile depends on pixels up to 10 away: the
+        # oracle on the tile plus that margin gives it exactly (rescaled from
+        # the crop's mean to the image's)
+        y0, x0 = (t // TX) * 16, (t % TX) * 16
+        y1, x1 = min(H, y0 + 16), min(W, x0 + 16)
+        cy0, cx0, cy1, cx1 = max(0, y0 - 10), max(0, x0 - 10), min(H, y1 + 10), min(W, x1 + 10)
+        _, gc = oracle.dssim_loss(img[:, cy0:cy1, cx0:cx1], target[:, cy0:cy1, cx0:cx1])
+        g[:, y0:y1, x0:x1] += lam * gc[:, y0 - cy0:y1 - cy0, x0 - cx0:x1 - cx0] * (gc.size / img.size)
+        crop_px += (cy1 - cy0) * (cx1 - cx0)
     t2 = time.perf_counter()
     gr = oracle.render_bwd(proj, g, tiles=tiles)
     t3 = time.perf_counter()
     dA = oracle.project_bwd(A, cam, deg, gr["d_mean2d"], gr["d_conic"], gr["d_opac"], gr["d_rgb"], blur=0.3)
     oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, tau, g0, g1, dA, 0.01)
     t4 = time.perf_counter()
-    per_gauss = (t1 - t0) + (t4 - t3)
-    per_tile = (t2 - t1) + (t3 - t2)
-    full = per_gauss + per_tile * (TX * TY) / len(tiles)
+    per_image = (t1 - t0) + (t2b - t2a) + (t4 - t3)   # per-Gaussian work and the L1 term
+    per_tile = (t2a - t1) + (t3 - t2)
+    dssim = (t2 - t2b) * (W * H) / max(crop_px, 1)    # D-SSIM per cropped pixel, scaled to the image
+    full = per_image + per_tile * (TX * TY) / len(tiles) + dssim
     return t4 - t0, full, len(tiles)
 
 
@@ -468,9 +487,10 @@ def cpu_baseline(name, budget_s=20.0):
     k = int(min(5440, max(32, budget_s / per_tile / 2)))
     sampled, full, k = oracle_iteration(name, k)
     return {"value": round(1.0 / full, 6), "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one iteration of the workload with compositing and its adjoint on {k} random tiles of "
-                      f"{(WORKLOADS[name][2] + 15) // 16 * ((WORKLOADS[name][3] + 15) // 16)}; per-tile time "
-                      f"scaled to all tiles; sampled run {sampled:.1f} s"}
+            "sample": f"one iteration of the workload with compositing, its adjoint and the D-SSIM gradient (tile "
+                      f"plus a 10-pixel margin) on {k} random tiles of "
+                      f"{(WORKLOADS[name][2] + 15) // 16 * ((WORKLOADS[name][3] + 15) // 16)}; per-tile and "
+                      f"per-pixel times scaled to the whole image; sampled run {sampled:.1f} s"}
 
 
 def run_reference(args):
@@ -501,8 +521,9 @@ def run_reference(args):
                                            "height": H, "views": V, "sh_degree": deg},
            "cpu_baseline": {"value": round(value, 6), "unit": "it/s", "cores": oracle.num_threads(),
                             "kind": "oracle",
-                            "sample": f"per step one iteration with compositing on {k} random tiles of {ntiles}, "
-                                      f"per-tile time scaled to all tiles; sampled time {sampled:.1f} s"},
+                            "sample": f"per step one iteration with compositing, its adjoint and the D-SSIM "
+                                      f"gradient on {k} random tiles of {ntiles}, per-tile and per-pixel times "
+                                      f"scaled to the whole image; sampled time {sampled:.1f} s"},
            "e2e": {"value": round(value, 6), "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

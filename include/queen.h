@@ -504,6 +504,32 @@ int qn_masked_image_loss(int64_t hw, int32_t channels, const float *img, const f
                          float *d_img, float *partials, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* D-SSIM term of Eq. 3 (Sec. 3.1).                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace qn_dssim_loss needs (0 for sizes it rejects). */
+size_t qn_dssim_workspace_size(int32_t width, int32_t height, int32_t channels);
+
+/*
+ * Adds the D-SSIM term of Eq. 3 with weight w to a loss and its image
+ * gradient:  loss[0] += w (1 - mean SSIM),  d_img += w dD-SSIM/d img.
+ * SSIM per channel and pixel from the local means, variances and covariance
+ * of img and target under an 11 x 11 Gaussian window (sigma 1.5; taps outside
+ * the image read zero), C1 = 0.01^2, C2 = 0.03^2 (values in [0, 1]).  With
+ * pixel_mask [H][W] u8 and n_masked (device i32, the number of non-zero mask
+ * entries, as qn_dilate_mask leaves it) the mean runs over the masked pixels
+ * only (the windows still read every pixel) and both additions are 0 when
+ * *n_masked == 0; pass both NULL for the whole image.  img, target, d_img
+ * [channels][H][W] f32 planes; d_img may not alias img or target; loss and
+ * d_img must hold values already (e.g. qn_image_loss's L1 term weighted
+ * 1 - w).  workspace: >= qn_dssim_workspace_size bytes, 16-byte aligned.
+ * The loss is summed in a fixed order (reproducible).
+ */
+int qn_dssim_loss(int32_t width, int32_t height, int32_t channels, const float *img, const float *target,
+                  const uint8_t *pixel_mask, const int32_t *n_masked, float w, float *loss, float *d_img,
+                  void *workspace, size_t workspace_bytes, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Data layout for the learned static skip.                                  */
 /* ------------------------------------------------------------------------ */
 

@@ -82,16 +82,23 @@ def ssim_map(img, target) -> np.ndarray:
     return out
 
 
-def dssim_loss(img, target):
+def dssim_loss(img, target, mask=None):
     """D-SSIM = 1 - mean SSIM of img against target ([C][H][W]); returns
     (loss, dD/dimg).  The gradient is the chain rule through the three window
     statistics that depend on img -- mu_x, E[x^2] and E[xy] under the window --
     followed by the transpose of the window filter:
       dD/dx = F^T(a) + 2 x F^T(b) + y F^T(c),
-    a, b, c = -1/(C H W) times dSSIM/dmu_x, dSSIM/dE[x^2], dSSIM/dE[xy]."""
+    a, b, c = -1/(C H W) times dSSIM/dmu_x, dSSIM/dE[x^2], dSSIM/dE[xy].
+    With mask ([H][W] bool, Sec. 3.3's masked training) the mean runs over the
+    C x (masked pixels) values only, the windows still reading every pixel;
+    (0, 0) for an empty mask."""
     x, y = np.asarray(img, np.float64), np.asarray(target, np.float64)
     w = ssim_window()
-    scale = -1.0 / x.size
+    sel = np.ones(x.shape[1:], bool) if mask is None else np.asarray(mask, bool)
+    count = x.shape[0] * int(sel.sum())
+    if count == 0:
+        return 0.0, np.zeros(x.shape)
+    scale = np.where(sel, -1.0 / count, 0.0)
     total = 0.0
     grad = np.zeros(x.shape)
     for c in range(x.shape[0]):
@@ -101,7 +108,7 @@ def dssim_loss(img, target):
         B1 = mx * mx + my * my + SSIM_C1
         B2 = vx + vy + SSIM_C2
         S = A1 * A2 / (B1 * B2)
-        total += S.sum()
+        total += S[sel].sum()
         # E[x^2] and E[xy] enter through the variance and covariance only;
         # mu_x also enters both of those (s_x^2 = E[x^2] - mu_x^2, s_xy = E[xy] - mu_x mu_y)
         dS_dmx = (2 * my * A2 - 2 * my * A1) / (B1 * B2) - S * (2 * mx / B1 - 2 * mx / B2)
@@ -110,4 +117,4 @@ def dssim_loss(img, target):
         grad[c] = (window_filter_adjoint(scale * dS_dmx, w)
                    + 2 * x[c] * window_filter_adjoint(scale * dS_dexx, w)
                    + y[c] * window_filter_adjoint(scale * dS_dexy, w))
-    return 1.0 - total / x.size, grad
+    return 1.0 - total / count, grad

@@ -82,6 +82,8 @@ _SIGS = {
     "qn_dilate_mask": ([_I32, _I32, _P, _I32, _P, _P, _P, _P, _P], C.c_int),
     "qn_mask_ranges": ([_I32, _P, _P, _P, _P], C.c_int),
     "qn_masked_image_loss": ([_I64, _I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P, _P], C.c_int),
+    "qn_dssim_workspace_size": ([_I32, _I32, _I32], _SZ),
+    "qn_dssim_loss": ([_I32, _I32, _I32, _P, _P, _P, _P, _F32, _P, _P, _P, _SZ, _P], C.c_int),
     "qn_partition": ([_I32, _P, _P, _P, _P, C.c_size_t, _P], C.c_int),
     "qn_gather_columns": ([_I32, _I32, _I32, _P, C.c_int64, _P, _P, C.c_int64, _P], C.c_int),
 }
@@ -346,3 +348,15 @@ def qn_masked_image_loss(hw, channels, img, target, pixel_mask, n_masked, w, mse
     _check(lib().qn_masked_image_loss(int(hw), int(channels), _ptr(img), _ptr(target), _ptr(pixel_mask),
                                       _ptr(n_masked), float(w), int(bool(mse)), _ptr(loss), _ptr(d_img), _ptr(part),
                                       _stream(stream)))
+
+
+def qn_dssim_workspace_size(width, height, channels):
+    return int(lib().qn_dssim_workspace_size(width, height, channels))
+
+
+def qn_dssim_loss(width, height, channels, img, target, w, loss, d_img, workspace, pixel_mask=None, n_masked=None,
+                  stream=None):
+    """loss += w (1 - mean SSIM), d_img += w dD/dimg (Eq. 3's D-SSIM term)."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check(lib().qn_dssim_loss(width, height, channels, _ptr(img), _ptr(target), _ptr(pixel_mask), _ptr(n_masked),
+                               float(w), _ptr(loss), _ptr(d_img), _ptr(workspace), ws_bytes, _stream(stream)))

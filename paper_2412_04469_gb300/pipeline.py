@@ -33,6 +33,9 @@ class HParams:
     gamma0: float = -0.5
     gamma1: float = 1.01
     lambda_reg: float = 0.01
+    # weight of the D-SSIM term of Eq. 3 (L = (1 - lambda) L1 + lambda D-SSIM);
+    # the paper does not give it: 0.2, the value of the 3D-GS training it builds on
+    lambda_dssim: float = 0.2
     # Eq. 11 weights Eq. 8's sum by lambda_reg / n (the penalty averaged over
     # Gaussians): with the L1 term a per-pixel mean, the plain sum closes every
     # gate within a frame, unlike the few percent of open gates the paper reports.
@@ -187,6 +190,7 @@ class Rasterizer:
         self.last = torch.zeros((height, width), device=dev, dtype=torch.int32)
         self.d_img = torch.zeros((3, height, width), device=dev)
         self.loss = torch.zeros(1, device=dev)
+        self.dssim_ws = torch.zeros(B.qn_dssim_workspace_size(width, height, 3), device=dev, dtype=torch.uint8)
 
     def set_capacity(self, cap: int):
         dev = self.splats.device
@@ -211,6 +215,22 @@ class Rasterizer:
 
     def loss_grad(self, target, w=1.0, mse=False, stream=None):
         B.qn_image_loss(self.img.numel(), self.img, target, w, mse, self.loss, self.d_img, stream)
+
+    def dssim_grad(self, target, w, mask: "ViewMask | None" = None, stream=None):
+        """Adds w D-SSIM (Eq. 3) to the loss and its gradient to d_img; with a
+        mask, over the masked pixels."""
+        B.qn_dssim_loss(self.W, self.H, 3, self.img, target, w, self.loss, self.d_img, self.dssim_ws,
+                        None if mask is None else mask.pixel, None if mask is None else mask.count, stream)
+
+    def photometric_loss(self, target, lambda_dssim, mask: "ViewMask | None" = None, stream=None):
+        """Eq. 3: (1 - lambda) L1 + lambda D-SSIM, into loss and d_img (both
+        over the masked pixels when a mask is given)."""
+        if mask is None:
+            self.loss_grad(target, 1.0 - lambda_dssim, False, stream)
+        else:
+            self.masked_loss_grad(target, mask, 1.0 - lambda_dssim, False, stream)
+        if lambda_dssim > 0:
+            self.dssim_grad(target, lambda_dssim, mask, stream)
 
     def render_bwd(self, cam, bg, skip=None, stream=None, ranges=None):
         """Compositing adjoint: per-pair records, then the per-Gaussian gather."""
@@ -278,8 +298,9 @@ class ViewMask:
 
 def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None,
                        mask: ViewMask | None = None):
-    """One view of Eq. 11's optimisation: forward, L1 loss (Eq. 3 L1 term) +
-    lambda_reg L_reg (the L_reg gradient is folded into the gate adjoint), full
+    """One view of Eq. 11's optimisation: forward, Eq. 3's loss ((1 - lambda)
+    L1 + lambda D-SSIM) + lambda_reg L_reg (the L_reg gradient is folded into
+    the gate adjoint), full
     adjoint and the Adam step.  No host synchronisation.  Gaussians with skip
     set are frozen: no gradient, no update, and their decoded columns are
     reused (frame.attrs must hold their A_t, e.g. from a decode without
@@ -294,10 +315,7 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
         rast.mask_ranges(mask, stream)
         ranges = rast.ranges_masked
     rast.render_fwd(cam, hp.bg, stream=stream, ranges=ranges)
-    if mask is None:
-        rast.loss_grad(target, 1.0, False, stream)
-    else:
-        rast.masked_loss_grad(target, mask, 1.0, False, stream)
+    rast.photometric_loss(target, hp.lambda_dssim, mask, stream)
     rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges)
     rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
     frame.decode_bwd(skip, stream)

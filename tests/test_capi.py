@@ -94,3 +94,16 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert B.lib().qn_select_rects(4, 4, 16, 32, 1.0, 1.0, -1.0, 48, None) == B.QN_ERR_INVALID_ARG   # t_d < 0
     assert B.lib().qn_masked_image_loss(16, 0, None, None, None, None, 1.0, 0, None, None, None, None) == \
         B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_dssim_workspace_size(0, 8, 3) == 0
+    ws = B.lib().qn_dssim_workspace_size(40, 20, 3)
+    assert ws >= 3 * 3 * 40 * 20 * 4
+    assert B.lib().qn_dssim_loss(40, 20, 0, 16, 32, None, None, 0.2, 48, 64, 128, ws, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_dssim_loss(40, 20, 3, 16, 32, None, None, 0.2, 48, 64, 128, ws - 4, None) == \
+        B.QN_ERR_INVALID_ARG                                                                          # workspace
+    assert b"workspace too small" in B.lib().qn_last_error()
+    assert B.lib().qn_dssim_loss(40, 20, 3, 16, 32, 80, None, 0.2, 48, 64, 128, ws, None) == \
+        B.QN_ERR_INVALID_ARG                                                                          # mask, no count
+    assert B.lib().qn_dssim_loss(40, 20, 3, 16, 32, None, None, 0.2, 48, 16, 128, ws, None) == \
+        B.QN_ERR_INVALID_ARG                                                                          # aliasing
+    assert B.lib().qn_dssim_loss(40, 20, 3, 16, 32, None, None, 0.2, 48, 64, 136, ws, None) == \
+        B.QN_ERR_INVALID_ARG                                                                          # misaligned

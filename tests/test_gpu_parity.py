@@ -526,9 +526,11 @@ def test_gather_columns(dtype):
 
 
 # ---------------------------------------------------------------- whole iteration
-def test_end_to_end_gradients_match_oracle_chain():
-    """decode -> project -> bin -> composite -> L1 -> every adjoint, against the
-    oracle's chain on the same inputs (the small config's camera, SH degree 1)."""
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_end_to_end_gradients_match_oracle_chain(lam):
+    """decode -> project -> bin -> composite -> Eq. 3's loss ((1 - lam) L1 +
+    lam D-SSIM) -> every adjoint, against the oracle's chain on the same inputs
+    (the small config's camera, SH degree 1)."""
     from paper_2412_04469_gb300.pipeline import QueenFrame, Rasterizer
     n, deg, W, H = 1500, 1, 96, 80
     lay = DecoderLayout.default(sh_degree=deg, latent=4)
@@ -544,8 +546,13 @@ def test_end_to_end_gradients_match_oracle_chain():
     proj = oracle.project(A_ref, cam, deg, blur=0.3, eps_g=EPS_G, tight=True)
     img_ref, _, _, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
     _, g_ref = oracle.l1_loss(img_ref, target)
+    g_ref = (1 - lam) * g_ref
     near = np.abs(img_ref - target).min(axis=0) < 1e-4          # sign of the L1 term could flip
     mask = (frag == 0) & ~near
+    if lam > 0:
+        g_ref = g_ref + lam * oracle.dssim_loss(img_ref, target)[1]
+        mask &= ~oracle.dilate(frag != 0, 22)                   # D-SSIM's gradient reads 10 pixels around
+        assert mask.mean() > 0.5
     g_ref = g_ref * mask[None]
     r = Rasterizer(n, f.S, deg, W, H, 1)
     c = B().make_camera(cam)
@@ -555,7 +562,7 @@ def test_end_to_end_gradients_match_oracle_chain():
     r.set_capacity(int(r.n_pairs.item()) + 16)
     r.bin_sort(sync=True)
     r.render_fwd(c, bg)
-    r.loss_grad(up(target))
+    r.photometric_loss(up(target), lam)
     r.d_img.mul_(up(mask.astype(np.float32))[None])
     r.render_bwd(c, bg)
     r.project_bwd(f.attrs, c, 0.3, f.d_attrs)

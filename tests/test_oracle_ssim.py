@@ -95,3 +95,23 @@ def test_dssim_gradient_matches_central_differences():
         xm[c, py, px] -= h
         fd = (oracle.dssim_loss(xp, y)[0] - oracle.dssim_loss(xm, y)[0]) / (2 * h)
         assert g[c, py, px] == pytest.approx(fd, rel=1e-6, abs=1e-10)
+
+
+def test_masked_dssim():
+    rng = np.random.default_rng(5)
+    C, H, W = 2, 13, 11
+    x, y = rng.uniform(size=(C, H, W)), rng.uniform(size=(C, H, W))
+    full = oracle.dssim_loss(x, y)
+    ones = oracle.dssim_loss(x, y, np.ones((H, W), bool))
+    assert ones[0] == full[0] and np.array_equal(ones[1], full[1])
+    assert oracle.dssim_loss(x, y, np.zeros((H, W), bool))[0] == 0.0
+    m = rng.uniform(size=(H, W)) < 0.3
+    loss, g = oracle.dssim_loss(x, y, m)
+    assert loss == pytest.approx(1.0 - oracle.ssim_map(x, y)[:, m].mean(), rel=1e-14)
+    h = 1e-6
+    for c, py, px in [(0, 0, 0), (1, 6, 5), (0, 12, 10), (1, 3, 9)]:
+        xp, xm = x.copy(), x.copy()
+        xp[c, py, px] += h
+        xm[c, py, px] -= h
+        fd = (oracle.dssim_loss(xp, y, m)[0] - oracle.dssim_loss(xm, y, m)[0]) / (2 * h)
+        assert g[c, py, px] == pytest.approx(fd, rel=1e-6, abs=1e-10)
