@@ -11,6 +11,8 @@ Two halves:
              and gate initialisation (Sec. 3.3, Eq. 9-10), the adaptive
              training mask (Sec. 3.3), Adam, and the static-skip MLP.
   ssim    -- numpy FP64 D-SSIM term of Eq. 3 and its gradient.
+  packet  -- the compressed per-frame packet (entropy-coded latents, decoders,
+             COO position residuals; App. B storage) and its rANS coder.
 
 Parity status per function is recorded in each function's docstring; every
 function listed here is pinned by tests/test_oracle_*.py (closed forms,
@@ -22,6 +24,7 @@ from .raster import (build, OracleCamera, sh_basis, decode, decode_bwd, project,
 from .learn import (l1_loss, mse_grad, viewspace_score, gate_init, adam_step, mlp_forward,
                     mlp_backward, bce_loss, skip_features, dynamic_flags, dynamic_pixels, dilate, tile_mask,
                     masked_l1_loss, MASK_T_D, MASK_KERNEL)
+from . import packet
 from .ssim import (ssim_window, window_filter, window_filter_adjoint, ssim_map, dssim_loss, SSIM_WINDOW,
                    SSIM_SIGMA, SSIM_C1, SSIM_C2)
 
@@ -31,5 +34,5 @@ __all__ = [
     "viewspace_score", "gate_init", "adam_step", "mlp_forward", "mlp_backward", "bce_loss",
     "skip_features", "dynamic_flags", "dynamic_pixels", "dilate", "tile_mask", "masked_l1_loss",
     "MASK_T_D", "MASK_KERNEL", "ssim_window", "window_filter", "window_filter_adjoint", "ssim_map", "dssim_loss",
-    "SSIM_WINDOW", "SSIM_SIGMA", "SSIM_C1", "SSIM_C2",
+    "SSIM_WINDOW", "SSIM_SIGMA", "SSIM_C1", "SSIM_C2", "packet",
 ]
