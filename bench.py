@@ -412,6 +412,13 @@ def run_sequence(args):
     for thr, v in out["by_threshold"].items():
         res[f"threshold_{thr:g}"] = arm(v, v["learned"], thr)
     plain = out["plain"]
+    if cfg.packet:
+        res["packet"] = {
+            "mb_per_frame": round(float(np.mean([r.packet_bytes for r in plain])) / 1e6, 4),
+            "mb_per_frame_each": [round(r.packet_bytes / 1e6, 4) for r in plain],
+            "pack_unpack_s": round(float(np.mean([r.packet_s for r in plain])), 4),
+            "dpsnr_gate_binarised_mean": round(float(np.mean([r.psnr_packet - r.psnr for r in plain])), 4),
+            "contents": "rANS-coded integer latents, bf16 decoders, COO position residuals (gate binarised)"}
     for mf, recs in out["masked"].items():
         res[f"masked_{mf:g}"] = {
             "masked_fraction": mf, "t_d_ndc": cfg.mask_t_d, "dilation": 48,

@@ -530,6 +530,70 @@ int qn_dssim_loss(int32_t width, int32_t height, int32_t channels, const float *
                   void *workspace, size_t workspace_bytes, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Compressed per-frame packet -- Sec. 3.2.1 and App. B (storage).           */
+/* ------------------------------------------------------------------------ */
+
+#define QN_PACKET_STREAM_SYMBOLS 8192   /* symbols per independently coded rANS stream */
+#define QN_PACKET_SCALE_BITS 12         /* model frequencies sum to 2^12 */
+
+/* Bytes of device workspace qn_pack_frame needs (0 for a bad layout). */
+size_t qn_pack_workspace_size(int32_t n, const qn_decoder_layout *layout);
+/* Upper bound on the size of a packet for n Gaussians and this layout. */
+size_t qn_packet_max_bytes(int32_t n, const qn_decoder_layout *layout);
+
+/*
+ * The packet of one frame's residual R_t, written to packet (device) with its
+ * size in *packet_bytes (host).  Contents (little-endian):
+ *   header: u32 magic 0x46504E51, version 1, n, n_cat, 8192, 12; per category
+ *     u32 lat_dim, attr_count, n_streams, payload bytes; per category u16
+ *     freq[256]; per category u32 stream_bytes[n_streams];
+ *   per category the rANS streams (zero-padded to 4 bytes): the integer
+ *     latents (Eq. 5: round half to even, saturate to int8) + 128 of the
+ *     category, flattened latent-major (dimension k, then Gaussian i) and
+ *     cut into streams of 8192 symbols, each coded on its own under the
+ *     category's frequencies (counts quantised to sum 2^12: f = max(1,
+ *     floor(count 2^12 / total)); a shortfall goes to the most frequent
+ *     symbol, smallest on ties; an excess is taken back in one pass by
+ *     decreasing f, then increasing symbol, each giving up to f - 1).  rANS
+ *     with a 32-bit state in [2^23, 2^31), byte renormalisation, coding the
+ *     symbols last to first; a stream is the final state (4 bytes) followed
+ *     by the emitted bytes in reverse order of emission;
+ *   per category the decoder's bf16 bits, row-major (zero-padded to 4);
+ *   u32 n_coo, u32 index[n_coo] (increasing) of the Gaussians with
+ *     gate != 0, f32 lp[3][n_coo] their pre-gated position residuals: the
+ *     gate is binarised for storage (taken as 1 where it is not 0).
+ * lat [sum lat_dim][n_stride] f32 continuous latents; dec the concatenated
+ * bf16 decoder blocks (as for qn_decode_residuals); lp [3][n_stride] f32;
+ * gate [n] f32 (qn_decode_residuals' gate output).  workspace (256-byte
+ * aligned) >= qn_pack_workspace_size; packet (4-byte aligned) >= the packet's
+ * size (qn_packet_max_bytes bounds it; QN_ERR_INVALID_ARG if too small).
+ * Synchronises the stream (the frequency tables and the layout are built on
+ * the host from device counts).
+ */
+int qn_pack_frame(int32_t n, int32_t n_stride, const qn_decoder_layout *layout, const float *lat,
+                  const uint16_t *dec, const float *lp, const float *gate, void *workspace, size_t workspace_bytes,
+                  uint8_t *packet, size_t packet_capacity, size_t *packet_bytes, qn_stream_t stream);
+
+/* Bytes of device workspace qn_unpack_frame needs for a packet of that size. */
+size_t qn_unpack_workspace_size(int32_t n, int32_t n_stride, const qn_decoder_layout *layout,
+                                size_t packet_bytes);
+
+/*
+ * A_t = A_{t-1} + R_t from a packet (host memory): the streams decoded on
+ * the GPU into latents, the decoders and the COO position residuals (gate 1
+ * on the listed Gaussians, 0 elsewhere) through qn_decode_residuals, so the
+ * result is what that call gives for the same integer latents, decoders and
+ * binarised gates.  prev, out [n_attr][n_stride] f32 (device).  The header is
+ * checked against n and the layout, and the sections against the size;
+ * stream bytes read past their end or out-of-range COO indices are detected
+ * on the device: QN_ERR_INVALID_ARG ("corrupt packet") in every such case.
+ * Synchronises the stream.
+ */
+int qn_unpack_frame(const uint8_t *packet_host, size_t packet_bytes, int32_t n, int32_t n_stride, int32_t n_attr,
+                    const qn_decoder_layout *layout, const float *prev, float *out, void *workspace,
+                    size_t workspace_bytes, qn_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Data layout for the learned static skip.                                  */
 /* ------------------------------------------------------------------------ */
 

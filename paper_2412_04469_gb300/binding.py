@@ -84,6 +84,11 @@ _SIGS = {
     "qn_masked_image_loss": ([_I64, _I32, _P, _P, _P, _P, _F32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_dssim_workspace_size": ([_I32, _I32, _I32], _SZ),
     "qn_dssim_loss": ([_I32, _I32, _I32, _P, _P, _P, _P, _F32, _P, _P, _P, _SZ, _P], C.c_int),
+    "qn_pack_workspace_size": ([_I32, _P], _SZ),
+    "qn_packet_max_bytes": ([_I32, _P], _SZ),
+    "qn_pack_frame": ([_I32, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P, _SZ, _P, _P], C.c_int),
+    "qn_unpack_workspace_size": ([_I32, _I32, _P, _SZ], _SZ),
+    "qn_unpack_frame": ([_P, _SZ, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P], C.c_int),
     "qn_partition": ([_I32, _P, _P, _P, _P, C.c_size_t, _P], C.c_int),
     "qn_gather_columns": ([_I32, _I32, _I32, _P, C.c_int64, _P, _P, C.c_int64, _P], C.c_int),
 }
@@ -360,3 +365,32 @@ def qn_dssim_loss(width, height, channels, img, target, w, loss, d_img, workspac
     ws_bytes = workspace.numel() * workspace.element_size()
     _check(lib().qn_dssim_loss(width, height, channels, _ptr(img), _ptr(target), _ptr(pixel_mask), _ptr(n_masked),
                                float(w), _ptr(loss), _ptr(d_img), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def qn_pack_workspace_size(n, layout):
+    return int(lib().qn_pack_workspace_size(n, C.byref(layout)))
+
+
+def qn_packet_max_bytes(n, layout):
+    return int(lib().qn_packet_max_bytes(n, C.byref(layout)))
+
+
+def qn_pack_frame(n, n_stride, layout, lat, dec_bf16, lp, gate, workspace, packet, stream=None):
+    """Writes the frame's packet into packet (device uint8); returns its size."""
+    size = C.c_size_t(0)
+    _check(lib().qn_pack_frame(n, n_stride, C.byref(layout), _ptr(lat), _ptr(dec_bf16), _ptr(lp), _ptr(gate),
+                               _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(packet),
+                               packet.numel(), C.byref(size), _stream(stream)))
+    return int(size.value)
+
+
+def qn_unpack_workspace_size(n, n_stride, layout, packet_bytes):
+    return int(lib().qn_unpack_workspace_size(n, n_stride, C.byref(layout), packet_bytes))
+
+
+def qn_unpack_frame(packet: bytes, n, n_stride, n_attr, layout, prev, out, workspace, stream=None):
+    """A_t = prev + R_t from a packet held in host memory (bytes)."""
+    buf = C.create_string_buffer(bytes(packet), len(packet))
+    _check(lib().qn_unpack_frame(C.cast(buf, C.c_void_p), len(packet), n, n_stride, n_attr, C.byref(layout),
+                                 _ptr(prev), _ptr(out), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                 _stream(stream)))

@@ -142,6 +142,29 @@ class QueenFrame:
         B.qn_decode_residuals(self.n, self.S, self.n_attr, self.prev, self.lat, self.dec_bf16, self.c_layout,
                               self.lp, self.log_alpha, self.c_gate, self.attrs, self.gate, self.lreg, stream, skip)
 
+    def pack(self, stream=None) -> bytes:
+        """The frame's compressed packet (App. B storage; layout in the C
+        header): entropy-coded integer latents, bf16 decoders, COO position
+        residuals of the Gaussians whose gate is on.  Reads the gate of the
+        last decode."""
+        if getattr(self, "_pack_ws", None) is None:
+            self._pack_ws = torch.zeros(max(B.qn_pack_workspace_size(self.n, self.c_layout), 256), device=self.dev,
+                                        dtype=torch.uint8)
+            self._packet = torch.zeros(B.qn_packet_max_bytes(self.n, self.c_layout), device=self.dev,
+                                       dtype=torch.uint8)
+        size = B.qn_pack_frame(self.n, self.S, self.c_layout, self.lat, self.dec_bf16, self.lp, self.gate,
+                               self._pack_ws, self._packet, stream)
+        return bytes(self._packet[:size].cpu().numpy().tobytes())
+
+    def unpack(self, packet: bytes, out, stream=None):
+        """out = A_{t-1} + R_t decoded from a packet (what a receiver holding
+        A_{t-1} reconstructs)."""
+        need = B.qn_unpack_workspace_size(self.n, self.S, self.c_layout, len(packet))
+        ws = getattr(self, "_unpack_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = self._unpack_ws = torch.zeros(need, device=self.dev, dtype=torch.uint8)
+        B.qn_unpack_frame(packet, self.n, self.S, self.n_attr, self.c_layout, self.prev, out, ws, stream)
+
     @property
     def d_lreg(self) -> float:
         """dL_total / dL_reg of Eq. 11."""

@@ -71,6 +71,10 @@ class SequenceConfig:
     # set for real captures, whose frame-to-frame changes are far larger than
     # this synthetic sequence's
     mask_t_d: float = 1e-6
+    # carry A_t forward through the frame's compressed packet (App. B
+    # storage: entropy-coded latents, COO positions with the gate binarised),
+    # so the trainer holds exactly what a receiver of the packets decodes
+    packet: bool = True
 
 
 class SkipMLP:
@@ -128,6 +132,9 @@ class FrameRecord:
     gate0_precision: float = float("nan")     # gate == 0 vs ground-truth static
     gate0_recall: float = float("nan")
     mask_tiles: float = float("nan")          # masked training: mean fraction of active tiles over the views
+    packet_bytes: int = 0                     # size of the frame's compressed packet
+    packet_s: float = float("nan")            # packing and unpacking time (not in `seconds`)
+    psnr_packet: float = float("nan")         # held-out PSNR of the packet's A_t (gate binarised)
 
 
 def sequence_hparams() -> HParams:
@@ -399,6 +406,16 @@ class StreamingTrainer:
             rec.skipped = float(pred.float().mean().item())
             rec.static_recall = float((pred & truth).sum().item() / nt)
             rec.static_precision = float((pred & truth).sum().item() / max(1, int(pred.sum().item())))
+        if c.packet:
+            # A_t as a receiver rebuilds it from the frame's packet
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pkt = f.pack()
+            f.unpack(pkt, f.attrs)
+            torch.cuda.synchronize()
+            rec.packet_s = time.perf_counter() - t0
+            rec.packet_bytes = len(pkt)
+            rec.psnr_packet = self._psnr(f.attrs)
         # carry the frame's state forward: A_t becomes A_{t-1}
         self.prev_gate.copy_(f.gate)
         self.prev_la.copy_(f.log_alpha)

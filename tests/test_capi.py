@@ -94,6 +94,10 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert B.lib().qn_select_rects(4, 4, 16, 32, 1.0, 1.0, -1.0, 48, None) == B.QN_ERR_INVALID_ARG   # t_d < 0
     assert B.lib().qn_masked_image_loss(16, 0, None, None, None, None, 1.0, 0, None, None, None, None) == \
         B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_pack_workspace_size(10, None) == 0 and B.lib().qn_packet_max_bytes(-1, None) == 0
+    assert B.lib().qn_pack_frame(10, 12, None, 16, 16, 16, 16, 256, 1 << 20, 16, 64, 16, None) == \
+        B.QN_ERR_INVALID_ARG                                                                          # no layout
+    assert B.lib().qn_unpack_frame(None, 0, 10, 12, 59, None, 16, 16, 256, 1 << 20, None) == B.QN_ERR_INVALID_ARG
     assert B.lib().qn_dssim_workspace_size(0, 8, 3) == 0
     ws = B.lib().qn_dssim_workspace_size(40, 20, 3)
     assert ws >= 3 * 3 * 40 * 20 * 4
