@@ -52,6 +52,14 @@ class HParams:
     eps: float = 1e-15
 
 
+def n3dv_hparams() -> HParams:
+    """HParams for DecoderLayout.paper_n3dv: the latent learning rates of the
+    paper's quantisation table for N3DV (rotation, scale, opacity, colour
+    base, colour frequency) and App. B's decoder rates (1e-3 for colour and
+    rotation, 1e-4 for opacity and scale)."""
+    return HParams(lr_latent=(0.025, 0.01, 0.05, 0.0125, 0.000625), lr_decoder=(1e-3, 1e-4, 1e-4, 1e-3, 1e-3))
+
+
 class _Adam:
     def __init__(self, shape, dev):
         self.m = torch.zeros(shape, device=dev, dtype=torch.float32)

@@ -52,6 +52,17 @@ class DecoderLayout:
     def default(sh_degree: int = 3, latent: int = 8) -> "DecoderLayout":
         return DecoderLayout([3, 7, 10, 11], [4, 3, 1, 3 * n_sh(sh_degree)], [latent] * 4)
 
+    @staticmethod
+    def paper_n3dv(sh_degree: int = 2) -> "DecoderLayout":
+        """The N3DV decoders of the paper's quantisation table (App. B):
+        rotation (latent width 6), scale (8), opacity (3), colour base = the
+        SH DC coefficients (8) and colour frequency = the higher SH
+        coefficients (4); N3DV trains SH degree 2."""
+        K = n_sh(sh_degree)
+        if K < 2:
+            raise ValueError("the colour-frequency decoder needs SH degree >= 1")
+        return DecoderLayout([3, 7, 10, 11, 14], [4, 3, 1, 3, 3 * (K - 1)], [6, 8, 3, 8, 4])
+
     @property
     def n_cat(self) -> int:
         return len(self.attr_begin)

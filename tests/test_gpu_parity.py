@@ -121,6 +121,7 @@ SCENES = [  # n, W, H, sh degree, blur, seed
     (2000, 128, 128, 0, 0.3, 0),     # the small plain config: 2,000 Gaussians, 128 x 128
     (900, 97, 61, 3, 0.3, 1),        # SH degree 3, ragged tiles
     (64, 17, 33, 1, 0.0, 2),         # tiny, no blur, partial tiles
+    (700, 80, 72, 2, 0.3, 3),        # SH degree 2 (the paper's N3DV setting)
 ]
 
 
