@@ -163,6 +163,24 @@ def setup(name, seed=0, quick=False):
     return frame, rast, ccams, targets, targets_host, lay, prev, res, cams
 
 
+def reduce_max(x, world, device):
+    """The maximum of x over the ranks of the process group (x itself for one
+    rank): every rank's timed region is bracketed by barriers, so the slowest
+    rank's time is the job's."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, max_ms):
+    """Whole-job throughput: the iterations all ranks ran (each rank a replica
+    running `steps` of them) over the slowest rank's time."""
+    return world * steps / (max_ms * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -191,10 +209,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        t = torch.tensor([x], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     def staged_step(v, ev):
         """One iteration issued stage by stage with an event between stages."""
@@ -333,7 +348,7 @@ def run_gpu(args):
     else:
         roof["alu_render_bwd"] = alu
 
-    value = world * args.steps / (max_ms * 1e-3)
+    value = job_rate(world, args.steps, max_ms)
     launches = args.steps * (sum(KERNELS_PER_STAGE.values()) - (2 if hp.lambda_dssim == 0 else 0))
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "it/s", "n_gpus": world, "steps": args.steps,
@@ -350,7 +365,7 @@ def run_gpu(args):
         "staged_ms_per_step": round(staged_ms / args.steps, 4),
         "roofline": roof,
         "clocks": clocks,
-        "e2e": {"value": round(world * args.steps / (e2e_ms * 1e-3), 3), "unit": "it/s",
+        "e2e": {"value": round(job_rate(world, args.steps, e2e_ms), 3), "unit": "it/s",
                 "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
         "gpu_launches": launches,
         "pair_overflow": overflow,
