@@ -11,6 +11,7 @@ Two halves:
              and gate initialisation (Sec. 3.3, Eq. 9-10), the adaptive
              training mask (Sec. 3.3), Adam, and the static-skip MLP.
   ssim    -- numpy FP64 D-SSIM term of Eq. 3 and its gradient.
+  rng     -- Philox4x32-10 gate noise for the stochastic hard-concrete gate.
   packet  -- the compressed per-frame packet (entropy-coded latents, decoders,
              COO position residuals; App. B storage) and its rANS coder.
 
@@ -24,7 +25,7 @@ from .raster import (build, OracleCamera, sh_basis, decode, decode_bwd, project,
 from .learn import (l1_loss, mse_grad, viewspace_score, gate_init, adam_step, mlp_forward,
                     mlp_backward, bce_loss, skip_features, dynamic_flags, dynamic_pixels, dilate, tile_mask,
                     masked_l1_loss, MASK_T_D, MASK_KERNEL)
-from . import packet
+from . import packet, rng
 from .ssim import (ssim_window, window_filter, window_filter_adjoint, ssim_map, dssim_loss, SSIM_WINDOW,
                    SSIM_SIGMA, SSIM_C1, SSIM_C2)
 
@@ -34,5 +35,5 @@ __all__ = [
     "viewspace_score", "gate_init", "adam_step", "mlp_forward", "mlp_backward", "bce_loss",
     "skip_features", "dynamic_flags", "dynamic_pixels", "dilate", "tile_mask", "masked_l1_loss",
     "MASK_T_D", "MASK_KERNEL", "ssim_window", "window_filter", "window_filter_adjoint", "ssim_map", "dssim_loss",
-    "SSIM_WINDOW", "SSIM_SIGMA", "SSIM_C1", "SSIM_C2", "packet",
+    "SSIM_WINDOW", "SSIM_SIGMA", "SSIM_C1", "SSIM_C2", "packet", "rng",
 ]

@@ -121,10 +121,30 @@ def _layout_arrays(layout):
     return (_i(layout.attr_begin), _i(layout.attr_count), _i(layout.lat_dim))
 
 
-def decode(prev, lat, dec, lp, log_alpha, layout, tau, gamma0, gamma1, round_latents=True):
+def _noise_shift(log_alpha, noise):
+    """log alpha + logit(u): the stochastic hard-concrete sample is Eq. 6 with
+    log alpha shifted by the logistic noise log u - log(1 - u)."""
+    u = np.asarray(noise, np.float64)
+    return _d(log_alpha) + (np.log(u) - np.log1p(-u))
+
+
+def _lreg(log_alpha, tau, gamma0, gamma1):
+    """Eq. 8 (independent of the noise)."""
+    z = _d(log_alpha) - tau * np.log(-gamma0 / gamma1)
+    return 1.0 / (1.0 + np.exp(-z))
+
+
+def decode(prev, lat, dec, lp, log_alpha, layout, tau, gamma0, gamma1, round_latents=True, noise=None):
     """Eq. 4-8: A_t = A_{t-1} + R_t with r = D float(round(l_hat)) and
-    dp = g l_p; returns (A_t, gate, L_reg).  Pinned: hand example, closed-form
-    gate values, rounding/saturation cases."""
+    dp = g l_p; returns (A_t, gate, L_reg).  With noise (u [n] in (0, 1)) the
+    gate is the stochastic hard-concrete sample sigmoid((log alpha + log u -
+    log(1 - u)) / tau), stretched and clipped as in Eq. 7; L_reg (Eq. 8) stays
+    on log alpha.  Pinned: hand example, closed-form gate values,
+    rounding/saturation cases; the noisy gate against its closed form."""
+    if noise is not None:
+        out, gate, _ = decode(prev, lat, dec, lp, _noise_shift(log_alpha, noise), layout, tau, gamma0, gamma1,
+                              round_latents)
+        return out, gate, float(_lreg(log_alpha, tau, gamma0, gamma1).sum())
     lib = _load()
     prev = _d(prev)
     na, n = prev.shape
@@ -138,9 +158,19 @@ def decode(prev, lat, dec, lp, log_alpha, layout, tau, gamma0, gamma1, round_lat
 
 
 def decode_bwd(lat, dec, lp, log_alpha, layout, tau, gamma0, gamma1, d_out, d_lreg=0.0, skip=None,
-               round_latents=True):
+               round_latents=True, noise=None):
     """Adjoint of decode (STE for the latents).  Returns (d_lat, d_dec, d_lp,
-    d_log_alpha).  Pinned: finite differences with rounding switched off."""
+    d_log_alpha).  With noise, the gate's path takes the shifted log alpha
+    and the L_reg path the plain one.  Pinned: finite differences with
+    rounding switched off (also with noise)."""
+    if noise is not None:
+        d_lat, d_dec, d_lp, d_la = decode_bwd(lat, dec, lp, _noise_shift(log_alpha, noise), layout, tau, gamma0,
+                                              gamma1, d_out, 0.0, skip, round_latents)
+        p = _lreg(log_alpha, tau, gamma0, gamma1)
+        d_la = d_la + float(d_lreg) * p * (1.0 - p)
+        if skip is not None:
+            d_la = np.where(np.asarray(skip) != 0, 0.0, d_la)
+        return d_lat, d_dec, d_lp, d_la
     lib = _load()
     d_out = _d(d_out)
     na, n = d_out.shape
