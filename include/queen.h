@@ -80,9 +80,14 @@ typedef struct {
 } qn_decoder_layout;
 
 /* Hard-concrete gate hyper-parameters (Eq. 6-8): temperature tau, stretch
- * interval (gamma0, gamma1) with gamma0 < 0 < 1 < gamma1. */
+ * interval (gamma0, gamma1) with gamma0 < 0 < 1 < gamma1.  noise (nullable,
+ * device [n] f32, u in (0, 1), e.g. from qn_gate_uniform): the stochastic
+ * hard-concrete sample of the cited gate formulation, g-hat =
+ * sigmoid((log alpha + log u - log(1 - u)) / tau), for training; NULL gives
+ * Eq. 6 as written.  L_reg (Eq. 8) does not depend on the noise. */
 typedef struct {
     float tau, gamma0, gamma1;
+    const float *noise;
 } qn_gate_params;
 
 /* Message of the last error on this host thread ("" if none). */
@@ -451,6 +456,17 @@ int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *g
  */
 int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, const uint8_t *labels, const uint16_t *params,
                     float *d_params, float *loss, float *partials, qn_stream_t stream);
+
+/*
+ * Gate noise for the stochastic hard-concrete sample: u[i] for i < n from
+ * Philox4x32-10 (Salmon et al., SC 2011; 10 rounds, multipliers 0xD2511F53,
+ * 0xCD9E8D57, key increments 0x9E3779B9, 0xBB67AE85) with counter
+ * (i, *step, 0, 0) and key (seed mod 2^32, seed >> 32): the first output
+ * word x, as u = ((x >> 9) + 1/2) / 2^23 in (0, 1).  step (device i32) is
+ * read on the device, so a captured graph draws fresh noise whenever the
+ * step advances (e.g. the Adam step of qn_adam_groups).  u [n] f32.
+ */
+int qn_gate_uniform(int32_t n, uint64_t seed, const int32_t *step, float *u, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Adaptive masked training -- Sec. 3.3; App. B (t_d = 0.001, 48 x 48).      */

@@ -38,7 +38,7 @@ class qn_decoder_layout(C.Structure):
 
 
 class qn_gate_params(C.Structure):
-    _fields_ = [("tau", C.c_float), ("gamma0", C.c_float), ("gamma1", C.c_float)]
+    _fields_ = [("tau", C.c_float), ("gamma0", C.c_float), ("gamma1", C.c_float), ("noise", C.c_void_p)]
 
 
 QN_ADAM_MAX_GROUPS = 16
@@ -89,6 +89,7 @@ _SIGS = {
     "qn_pack_frame": ([_I32, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P, _SZ, _P, _P], C.c_int),
     "qn_unpack_workspace_size": ([_I32, _I32, _P, _SZ], _SZ),
     "qn_unpack_frame": ([_P, _SZ, _I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P], C.c_int),
+    "qn_gate_uniform": ([_I32, C.c_uint64, _P, _P, _P], C.c_int),
     "qn_partition": ([_I32, _P, _P, _P, _P, C.c_size_t, _P], C.c_int),
     "qn_gather_columns": ([_I32, _I32, _I32, _P, C.c_int64, _P, _P, C.c_int64, _P], C.c_int),
 }
@@ -159,8 +160,10 @@ def make_layout(layout) -> qn_decoder_layout:
     return L
 
 
-def make_gate(tau, gamma0, gamma1) -> qn_gate_params:
-    return qn_gate_params(tau, gamma0, gamma1)
+def make_gate(tau, gamma0, gamma1, noise=None) -> qn_gate_params:
+    """Gate parameters; noise (device float tensor [n], u in (0, 1)) selects
+    the stochastic hard-concrete sample, None the gate of Eq. 6."""
+    return qn_gate_params(tau, gamma0, gamma1, _ptr(noise))
 
 
 def qn_decode_residuals(n, n_stride, n_attr, prev, lat, dec, layout, lp, log_alpha, gate_params, out, gate=None,
@@ -394,3 +397,8 @@ def qn_unpack_frame(packet: bytes, n, n_stride, n_attr, layout, prev, out, works
     _check(lib().qn_unpack_frame(C.cast(buf, C.c_void_p), len(packet), n, n_stride, n_attr, C.byref(layout),
                                  _ptr(prev), _ptr(out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                  _stream(stream)))
+
+
+def qn_gate_uniform(n, seed, step, u, stream=None):
+    """u[i] = Philox4x32-10 uniform of counter (i, *step) under seed."""
+    _check(lib().qn_gate_uniform(n, int(seed) & ((1 << 64) - 1), _ptr(step), _ptr(u), _stream(stream)))

@@ -22,6 +22,7 @@ struct DecodeArgs {
     int lat_off[QN_MAX_CATEGORIES], dec_off[QN_MAX_CATEGORIES];
     unsigned long long covered;        // bit k: attribute plane k receives a residual
     float tau, g0, g1, shift;          // shift = tau log(-gamma0 / gamma1)
+    const float *noise;                // nullable: u of the stochastic gate
 };
 
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) {
@@ -34,9 +35,18 @@ __device__ __forceinline__ float latent_int(float v) {
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + __expf(-x)); }
 
+// The gate's argument: log alpha, plus the logistic noise log u - log(1 - u)
+// of the stochastic hard-concrete sample when a noise array is given.
+template <bool NOISE>
+__device__ __forceinline__ float gate_logit(const DecodeArgs &a, float l_a, int i) {
+    if (!NOISE) return l_a;
+    const float u = a.noise[i];
+    return l_a + (logf(u) - log1pf(-u));
+}
+
 // LT > 0: every category has latent width LT (compile-time loops, D rows
 // read as float4 broadcasts); LT == 0: any layout within the limits.
-template <int LT>
+template <int LT, bool NOISE>
 __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__restrict__ prev,
                                                 const float *__restrict__ lat,
                                                 const uint16_t *__restrict__ dec,
@@ -53,7 +63,7 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         if (skip && skip[i]) continue;                 // frozen: out and gate already hold its values
         const float l_a = la[i];
-        const float gh = sigmoidf_(l_a / a.tau);                       // Eq. 6
+        const float gh = sigmoidf_(gate_logit<NOISE>(a, l_a, i) / a.tau);   // Eq. 6
         const float g = fminf(1.f, fmaxf(0.f, gh * (a.g1 - a.g0) + a.g0));   // Eq. 7
         if (gate) gate[i] = g;
         reg += sigmoidf_(l_a - a.shift);                                // Eq. 8
@@ -138,10 +148,11 @@ constexpr int PF_L = MAX_LAT_TOTAL / ROWS_PER_PASS;                            /
 // rows row0 + 8m, latents of rows row0 + 8m, and (row0 == 0) the gate inputs.
 struct TileRegs {
     float dr[PF_DR], l[PF_L];
-    float la, dp[3], lp[3];
+    float la, lz, dp[3], lp[3];            // lz: the gate's argument (log alpha + noise)
     bool valid, sk;
 };
 
+template <bool NOISE>
 __device__ __forceinline__ void load_tile(const DecodeArgs &a, int base, int lane, int row0,
                                           const float *__restrict__ lat, const float *__restrict__ lp,
                                           const float *__restrict__ la, const float *__restrict__ d_out,
@@ -164,6 +175,7 @@ __device__ __forceinline__ void load_tile(const DecodeArgs &a, int base, int lan
     }
     if (row0 == 0 && use) {
         t.la = la[i];
+        t.lz = gate_logit<NOISE>(a, t.la, i);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             t.dp[d] = d_out[d * S + i];
@@ -176,7 +188,7 @@ __device__ __forceinline__ void load_tile(const DecodeArgs &a, int base, int lan
 // row0 of each category (compile-time indexing); LT == 0: any layout.
 // Software-pipelined: while a tile is computed from shared memory, the next
 // tile's values are already being loaded into registers.
-template <int LT>
+template <int LT, bool NOISE>
 __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
     DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
     const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
     const int lane = threadIdx.x & (BWD_TILE - 1), row0 = threadIdx.x / BWD_TILE;
     const int step = gridDim.x * BWD_TILE;
     TileRegs t;
-    load_tile(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
+    load_tile<NOISE>(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
     for (int base = blockIdx.x * BWD_TILE; base < a.n; base += step) {
         const int i = base + lane;
         const bool valid = t.valid, sk = t.sk;
@@ -224,7 +236,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
                     d_la[i] = 0.f;
                 }
             }
-            load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
+            load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
             continue;
         }
 #pragma unroll
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
             if (k < a.n_lat) s_l[k][lane] = latent_int(t.l[m]);
         }
         if (row0 == 0 && valid) {
-            const float gh = sigmoidf_(t.la / a.tau);
+            const float gh = sigmoidf_(t.lz / a.tau);
             const float gt = gh * (a.g1 - a.g0) + a.g0;
             const float g = fminf(1.f, fmaxf(0.f, gt));
             const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
@@ -251,7 +263,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
             const float p = sigmoidf_(t.la - a.shift);
             d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
         }
-        load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
+        load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
         __syncthreads();
         // STE: d_lat[k] = sum_r D[r][k] dr[r] for this thread's (latent, Gaussian) pairs
         if (valid) {
@@ -307,6 +319,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
 constexpr int LT8_STRIDE = 36;                 // s_lT row: 32 latents + 4 (rows stay 16-byte aligned)
 constexpr int DD_ITEMS = 2 * MAX_RES_PLANES;    // (row, half) items of dD
 
+template <bool NOISE>
 __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
     DecodeArgs a, const float *__restrict__ lat, const uint16_t *__restrict__ dec,
     const float *__restrict__ lp, const float *__restrict__ la, const float *__restrict__ d_out,
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int step = gridDim.x * BWD_TILE;
     TileRegs t;
-    load_tile(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
+    load_tile<NOISE>(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
     for (int base = blockIdx.x * BWD_TILE; base < a.n; base += step) {
         const int i = base + lane;
         const bool valid = t.valid, sk = t.sk;
@@ -347,7 +360,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
                     d_la[i] = 0.f;
                 }
             }
-            load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
+            load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
             continue;
         }
 #pragma unroll
@@ -361,7 +374,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
             if (k < a.n_lat) s_lT[lane][k] = latent_int(t.l[m]);
         }
         if (row0 == 0 && valid) {
-            const float gh = sigmoidf_(t.la / a.tau);
+            const float gh = sigmoidf_(t.lz / a.tau);
             const float gt = gh * (a.g1 - a.g0) + a.g0;
             const float g = fminf(1.f, fmaxf(0.f, gt));
             const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
             const float p = sigmoidf_(t.la - a.shift);
             d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
         }
-        load_tile(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
+        load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
         __syncthreads();
         // STE: d_lat of latents 4 lh .. 4 lh + 3 of category lc
         if (valid && lc < a.n_cat) {
@@ -448,6 +461,7 @@ int make_args(int32_t n, int32_t n_stride, int32_t n_attr, const qn_decoder_layo
     a->n_lat = lo;
     a->n_dec = dofs;
     a->tau = gp->tau; a->g0 = gp->gamma0; a->g1 = gp->gamma1;
+    a->noise = gp->noise;
     a->shift = (float)(gp->tau * std::log(-(double)gp->gamma0 / (double)gp->gamma1));
     return QN_OK;
 }
@@ -480,7 +494,9 @@ extern "C" int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, 
     cudaStream_t s = qn::as_stream(stream);
     if (lreg && cudaMemsetAsync(lreg, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("decode memset");
     if (n == 0) return QN_OK;
-    auto kern = qn::uniform_width8(a) ? qn::k_decode<8> : qn::k_decode<0>;
+    const bool w8 = qn::uniform_width8(a), noise = a.noise != nullptr;
+    auto kern = w8 ? (noise ? qn::k_decode<8, true> : qn::k_decode<8, false>)
+                   : (noise ? qn::k_decode<0, true> : qn::k_decode<0, false>);
     kern<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, skip, out, gate, lreg);
     return qn::check_launch("qn_decode_residuals");
 }
@@ -505,7 +521,9 @@ extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_at
     }
     int grid = qn::grid_for(n, qn::BWD_TILE, 8);
     if (grid > QN_DECODE_BWD_BLOCKS) grid = QN_DECODE_BWD_BLOCKS;
-    auto kern = (qn::uniform_width8(a) && a.n_cat <= 4) ? qn::k_decode_bwd8 : qn::k_decode_bwd<0>;
+    const bool w8 = qn::uniform_width8(a) && a.n_cat <= 4, noise = a.noise != nullptr;
+    auto kern = w8 ? (noise ? qn::k_decode_bwd8<true> : qn::k_decode_bwd8<false>)
+                   : (noise ? qn::k_decode_bwd<0, true> : qn::k_decode_bwd<0, false>);
     kern<<<grid, qn::BWD_THREADS, 0, s>>>(a, lat, dec, lp, log_alpha, d_out, d_lreg, skip, d_lat,
                                                       partials, d_lp, d_log_alpha);
     if (a.n_dec > 0) qn::k_sum_partials<<<qn::sum_partials_grid(a.n_dec), 256, 0, s>>>(a.n_dec, grid, partials, d_dec);

@@ -36,6 +36,11 @@ class HParams:
     # weight of the D-SSIM term of Eq. 3 (L = (1 - lambda) L1 + lambda D-SSIM);
     # the paper does not give it: 0.2, the value of the 3D-GS training it builds on
     lambda_dssim: float = 0.2
+    # the stochastic hard-concrete sample (noise on log alpha) during training
+    # iterations instead of Eq. 6's deterministic gate; decodes outside
+    # training (A_t, the packet) keep Eq. 6
+    gate_noise: bool = False
+    gate_seed: int = 0
     # Eq. 11 weights Eq. 8's sum by lambda_reg / n (the penalty averaged over
     # Gaussians): with the L1 term a per-pixel mean, the plain sum closes every
     # gate within a frame, unlike the few percent of open gates the paper reports.
@@ -96,6 +101,9 @@ class QueenFrame:
         self.dec_bf16 = torch.from_numpy(bf16_bits(dec).view(np.int16)).to(dev).view(torch.bfloat16)
         self.c_layout = B.make_layout(layout)
         self.c_gate = B.make_gate(self.hp.tau, self.hp.gamma0, self.hp.gamma1)
+        self.noise = torch.zeros(S, device=dev) if self.hp.gate_noise else None
+        self.c_gate_train = (B.make_gate(self.hp.tau, self.hp.gamma0, self.hp.gamma1, self.noise)
+                             if self.hp.gate_noise else self.c_gate)
         # outputs and gradients
         self.attrs = torch.zeros((self.n_attr, S), device=dev)
         self.gate = torch.zeros(S, device=dev)
@@ -144,11 +152,17 @@ class QueenFrame:
         self.step.zero_()
 
     # ---------------------------------------------------------------- steps
-    def decode(self, stream=None, skip=None):
+    def decode(self, stream=None, skip=None, train=False):
         """A_t from A_{t-1} and the residuals; Gaussians with skip set are
-        frozen and keep their columns of attrs and gate."""
+        frozen and keep their columns of attrs and gate.  train: the
+        iteration's gate (with HParams.gate_noise, fresh noise drawn for the
+        current Adam step first)."""
+        gate = self.c_gate
+        if train and self.noise is not None:
+            B.qn_gate_uniform(self.n, self.hp.gate_seed, self.step, self.noise, stream)
+            gate = self.c_gate_train
         B.qn_decode_residuals(self.n, self.S, self.n_attr, self.prev, self.lat, self.dec_bf16, self.c_layout,
-                              self.lp, self.log_alpha, self.c_gate, self.attrs, self.gate, self.lreg, stream, skip)
+                              self.lp, self.log_alpha, gate, self.attrs, self.gate, self.lreg, stream, skip)
 
     def pack(self, stream=None) -> bytes:
         """The frame's compressed packet (App. B storage; layout in the C
@@ -180,7 +194,7 @@ class QueenFrame:
 
     def decode_bwd(self, skip=None, stream=None):
         B.qn_decode_residuals_bwd(self.n, self.S, self.n_attr, self.lat, self.dec_bf16, self.c_layout, self.lp,
-                                  self.log_alpha, self.c_gate, self.d_attrs, self.d_lreg, skip, self.d_lat,
+                                  self.log_alpha, self.c_gate_train, self.d_attrs, self.d_lreg, skip, self.d_lat,
                                   self.d_dec, self.d_lp, self.d_log_alpha, self.dec_partials, stream)
 
     def adam(self, skip=None, stream=None):
@@ -338,7 +352,7 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     skip).  With a mask (Sec. 3.3's masked training) only the masked tiles
     are composited and the loss is the mean over the masked pixels."""
     hp = frame.hp
-    frame.decode(stream, skip)
+    frame.decode(stream, skip, train=True)
     rast.project(frame.attrs, cam, hp.blur, stream)
     rast.bin_sort(False, stream)
     ranges = None

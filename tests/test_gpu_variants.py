@@ -1,9 +1,12 @@
-"""The paper's own N3DV configuration as a variant of the path: five decoders
+"""Variants of the path.  The paper's own N3DV configuration: five decoders
 (rotation, scale, opacity, colour base, colour frequency with latent widths
-6, 8, 3, 8, 4 from the quantisation table) on SH degree 2.  The decode and its
-adjoint against the oracle, a training iteration (eager and graph-replayed,
-bit-identical) with the table's learning rates, and the packet against the
-oracle's bytes."""
+6, 8, 3, 8, 4 from the quantisation table) on SH degree 2 -- the decode and
+its adjoint against the oracle, a training iteration (eager and
+graph-replayed, bit-identical) with the table's learning rates, and the packet
+against the oracle's bytes.  The stochastic hard-concrete gate: the Philox
+noise bit-identical to the oracle's, the noisy decode and its adjoint against
+the oracle, and training iterations that draw fresh noise per step and still
+replay bit-identically."""
 import numpy as np
 import pytest
 import torch
@@ -108,3 +111,77 @@ def test_paper_layout_packet():
     size = B.qn_pack_frame(n, Sd, L, up(lat), up(dec.view(np.int16), torch.int16), up(lp), up(gate), ws, pkt)
     got = bytes(pkt[:size].cpu().numpy().tobytes())
     assert got == OP.pack_frame(n, lat, lay.lat_dim, lay.attr_count, dec, lp, gate)
+
+
+@pytest.mark.parametrize("n,seed,step", [(1, 0, 0), (1000, 7, 5), (300_001, (3 << 40) + 11, 123_456)])
+def test_gate_noise_matches_oracle_philox(n, seed, step):
+    from oracle import rng
+    from paper_2412_04469_gb300 import binding as B
+    u = torch.zeros(n, device="cuda")
+    st = torch.tensor([step], device="cuda", dtype=torch.int32)
+    B.qn_gate_uniform(n, seed, st, u)
+    torch.cuda.synchronize()
+    assert np.array_equal(u.cpu().numpy(), rng.gate_uniform(n, seed, step))
+
+
+@pytest.mark.parametrize("n,latent", [(1000, 8), (40_000, 8), (3000, 4)])
+def test_noisy_gate_decode_and_adjoint(n, latent):
+    from oracle import rng
+    from paper_2412_04469_gb300 import binding as B
+    from paper_2412_04469_gb300.pipeline import HParams, QueenFrame
+    deg = 1
+    lay = S.DecoderLayout.default(sh_degree=deg, latent=latent)
+    prev = S.make_scene(n, deg, 13)
+    res = S.make_residuals(n, lay, 13)
+    res.log_alpha[:] = np.random.default_rng(13).uniform(-1.5, 1.5, n).astype(np.float32)
+    f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha, HParams(lreg_mean=False))
+    u = rng.gate_uniform(n, 99, 3)
+    noise = torch.zeros(f.S, device="cuda")
+    noise[:n] = up(u)
+    f.c_gate = f.c_gate_train = B.make_gate(TAU, G0, G1, noise)
+    f.decode()
+    torch.cuda.synchronize()
+    out, gate, lreg = oracle.decode(prev.astype(np.float64), res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0,
+                                    G1, noise=u)
+    got = f.attrs.cpu().numpy()[:, :n]
+    close(got[:3], out[:3], 1e-4, 1e-2, "position")
+    close(f.gate.cpu().numpy()[:n], gate, 1e-4, 1e-2, "gate")
+    assert float(f.lreg.item()) == pytest.approx(lreg, rel=1e-5)
+    d_out = np.random.default_rng(14).standard_normal((prev.shape[0], n)).astype(np.float32)
+    f.d_attrs[:, :n] = up(d_out)
+    f.decode_bwd()
+    torch.cuda.synchronize()
+    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, d_out, f.d_lreg, noise=u)
+    close(f.d_lp.cpu().numpy()[:, :n], want[2], 1e-4, 0.05, "d_lp")
+    close(f.d_log_alpha.cpu().numpy()[:n], want[3], 1e-4, 0.05, "d_log_alpha")
+
+
+def test_noisy_gate_training_draws_per_step_and_replays():
+    from paper_2412_04469_gb300 import binding as B
+    from paper_2412_04469_gb300.pipeline import HParams, IterationGraph, QueenFrame, Rasterizer, training_iteration
+    n, deg, W, H = 5000, 1, 96, 80
+    lay = S.DecoderLayout.default(sh_degree=deg, latent=8)
+    prev = S.make_scene(n, deg, 6)
+    res = S.make_residuals(n, lay, 6)
+    cams = [B.make_camera(c) for c in S.make_arc_cameras(2, W, H)]
+    tg = [up(S.make_image(W, H, 60 + v)) for v in range(2)]
+    outs, noises = [], []
+    for graphs in (False, True):
+        f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha, HParams(gate_noise=True, gate_seed=5))
+        r = Rasterizer(n, f.S, deg, W, H, 1 << 20)
+        g = IterationGraph(f, r) if graphs else None
+        seen = []
+        for it in range(6):
+            if g is None:
+                training_iteration(f, r, cams[it % 2], tg[it % 2])
+            else:
+                g.run(it % 2, cams[it % 2], tg[it % 2])
+            seen.append(f.noise[:n].clone())
+        torch.cuda.synchronize()
+        outs.append([t.clone() for t in (f.lat, f.dec, f.lp, f.log_alpha, r.loss)])
+        noises.append(seen)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    for a, b in zip(*noises):
+        assert torch.equal(a, b)
+    assert not torch.equal(noises[0][0], noises[0][1])          # fresh noise every step
