@@ -283,7 +283,9 @@ typedef struct {
 
 /* Projection of one Gaussian; returns 1 if visible.  fr gets fragility bits
  * (a decision that FP32 rounding could flip, within eps_g relative):
- *   1 near plane, 2 radius ceil, 4 rect floor, 8 det sign.
+ *   1 near plane, 2 radius ceil, 4 rect floor, 8 det sign, 16 opacity bound,
+ *   and 32 << k for the rect edges k (x0, y0, x1, y1) such a flip can move
+ *   (a radius flip moves all four).
  * out2d = (mx, my, conic a, b, c, opacity, r, g, b, depth); for a fragile
  * Gaussian the 2D footprint is filled in even when it is culled, so that the
  * renderer can tell which pixels the flipped decision could reach. */
@@ -355,11 +357,11 @@ static int or_project_one(int i, int n, int sh_degree, const double *A, const do
     double lam = mid + sqrt(fmax(0.1, mid * mid - w->det));
     double r3 = 3.0 * sqrt(lam);
     int rad = (int)ceil(r3);
-    if (or_near_int(r3, eps_g)) *fr |= 2;
+    if (or_near_int(r3, eps_g)) *fr |= 2 | (15 << 5);
     double ex[4] = {(mx - rad) / OR_TILE, (my - rad) / OR_TILE, (mx + rad + OR_TILE - 1) / OR_TILE,
                     (my + rad + OR_TILE - 1) / OR_TILE};
     for (int k = 0; k < 4; ++k)
-        if (or_near_int(ex[k], eps_g)) *fr |= 4;
+        if (or_near_int(ex[k], eps_g)) *fr |= 4 | (32 << k);
     int rc[4] = {or_clampi((int)floor(ex[0]), 0, TX), or_clampi((int)floor(ex[1]), 0, TY),
                  or_clampi((int)floor(ex[2]), 0, TX), or_clampi((int)floor(ex[3]), 0, TY)};
     if (tight) {
@@ -375,7 +377,7 @@ static int or_project_one(int i, int n, int sh_degree, const double *A, const do
             double hx = sqrt(1.01 * k * w->a) + 0.01, hy = sqrt(1.01 * k * w->c) + 0.01;
             double tb[4] = {(mx - hx) / OR_TILE, (my - hy) / OR_TILE, (mx + hx) / OR_TILE, (my + hy) / OR_TILE};
             for (int q = 0; q < 4; ++q)
-                if (or_near_int(tb[q], eps_g)) *fr |= 4;
+                if (or_near_int(tb[q], eps_g)) *fr |= 4 | (32 << q);
             int t0 = or_clampi((int)floor(tb[0]), 0, TX), t1 = or_clampi((int)floor(tb[1]), 0, TY);
             int t2 = or_clampi((int)floor(tb[2]) + 1, 0, TX), t3 = or_clampi((int)floor(tb[3]) + 1, 0, TY);
             rc[0] = rc[0] > t0 ? rc[0] : t0;
@@ -749,9 +751,14 @@ static int or_max_list(int n, const int *rect, int TX, int TY) {
  * tiles (nullable): composite only these n_tiles_sel tile indices (a bounded
  * sample); other pixels are left untouched.
  * img: [3][H][W]; T_final, last, fragile: [H][W].  fragile pixel bits: see
- * or_pixel, plus 8 when a fragile Gaussian (frag_g != 0) whose frag_rect
- * covers the pixel's tile reaches alpha >= (1 - eps)/255 there, i.e. when an
- * FP32-flippable projection decision could change the pixel.
+ * or_pixel, plus 8 when a fragile Gaussian (frag_g != 0) could change the
+ * pixel: it reaches alpha >= (1 - eps)/255 there, and the pixel's tile lies in
+ * its frag_rect when the flippable decision is the near plane, the
+ * determinant's sign or the opacity bound, or when the Gaussian is culled (the
+ * whole footprint can appear or vanish), or else (rect and radius decisions of
+ * a visible Gaussian) in the band of tiles a flippable rect edge can add or
+ * remove: columns x0 - 1, x0 or x1 - 1, x1 (rows y0 - 1 .. y1) for a vertical
+ * edge, likewise rows for a horizontal one.
  */
 void or_render_fwd(int n, const double *mean2d, const double *conic, const double *opac,
                    const double *rgb, const double *depth, const int *rect, const int *frag_g,
@@ -789,6 +796,19 @@ void or_render_fwd(int n, const double *mean2d, const double *conic, const doubl
                               ty >= frag_rect[(size_t)n + i] && ty < frag_rect[(size_t)3 * n + i]))
                             continue;
                         if (frag_g[i] & 8) { fr |= 8; continue; }
+                        const int x0 = rect[i], y0 = rect[(size_t)n + i], x1 = rect[(size_t)2 * n + i],
+                                  y1 = rect[(size_t)3 * n + i];
+                        if (!(frag_g[i] & (1 | 16)) && x1 > x0 && y1 > y0) {
+                            /* rect or radius decisions of a visible Gaussian only: the edge bands
+                             * (a culled one keeps the whole frag_rect) */
+                            const int g = frag_g[i];
+                            const int iny = ty >= y0 - 1 && ty <= y1, inx = tx >= x0 - 1 && tx <= x1;
+                            const int band = ((g & 32) && iny && (tx == x0 - 1 || tx == x0)) ||
+                                             ((g & 128) && iny && (tx == x1 - 1 || tx == x1)) ||
+                                             ((g & 64) && inx && (ty == y0 - 1 || ty == y0)) ||
+                                             ((g & 256) && inx && (ty == y1 - 1 || ty == y1));
+                            if (!band) continue;
+                        }
                         double dx = u + 0.5 - mean2d[i], dy = v + 0.5 - mean2d[(size_t)n + i];
                         double power = -0.5 * (conic[i] * dx * dx + conic[(size_t)2 * n + i] * dy * dy) -
                                        conic[(size_t)n + i] * dx * dy;

@@ -1,0 +1,170 @@
+"""The whole path at the benchmark's full sizes -- 300k Gaussians at 1352 x 1014
+and 1M at 1920 x 1080, SH degree 3, set up by bench.py's own setup (same
+buffers, capacities and launch configuration as the timed step) -- against
+the oracle on sampled outputs the oracle computes one by one: the decode of
+sampled Gaussians, the projection of sampled Gaussians, the rendered pixels
+and last contributors of sampled tiles (corner and ragged-edge tiles
+included), the compositing adjoint and gather for an upstream image gradient
+that lives on those tiles only (every per-Gaussian gradient is then the
+oracle's sum over the sampled tiles), and the projection and decode adjoints
+of all Gaussians fed the oracle's upstream gradients."""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+EPS_A, EPS_D, EPS_G = 2e-5, 1e-6, 2e-6
+TAU, G0, G1 = 0.3, -0.5, 1.01
+GRAD_FLOOR = 0.05
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_04469_gb300 import build
+    build.build()
+
+
+def up(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def close(got, ref, rtol=1e-4, floor_frac=1e-2, what=""):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    if ref.size == 0:
+        return
+    den = np.maximum(np.abs(ref), floor_frac * np.abs(ref).max())
+    err = np.abs(got - ref) / den
+    at = np.unravel_index(err.argmax(), err.shape)
+    assert err.max() <= rtol, f"{what}: {err.max():.3e} at {at}: got {got[at]:.9g} ref {ref[at]:.9g} den {den[at]:.3g}"
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+@pytest.mark.parametrize("name", ["full", "large"])
+def test_full_size_path_on_sampled_outputs(name):
+    bench = _bench()
+    frame, rast, ccams, _, _, lay, prev, res, cams = bench.setup(name, quick=True)
+    n, deg, W, H, V, L = bench.WORKLOADS[name]
+    hp = frame.hp
+    cam, c = cams[0], ccams[0]
+    bg = hp.bg
+    # GPU forward, as the training step issues it
+    frame.decode()
+    rast.project(frame.attrs, c, hp.blur)
+    P = rast.bin_sort(sync=True)
+    assert 0 < P <= rast.capacity
+    rast.render_fwd(c, bg)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    # decode and projection of sampled Gaussians
+    A_ref, gate_ref, _ = oracle.decode(prev.astype(np.float64), res.lat, res.dec, res.lp, res.log_alpha, lay, TAU,
+                                       G0, G1)
+    idx = np.sort(rng.choice(n, 4000, replace=False))
+    got_A = frame.attrs[:, :n].cpu().numpy()
+    close(got_A[:3, idx], A_ref[:3, idx], what="decoded position")
+    close(got_A[3:, idx] - prev[3:, idx], A_ref[3:, idx] - prev[3:, idx].astype(np.float64), rtol=2e-3,
+          what="decoded residual")
+    proj = oracle.project(A_ref, cam, deg, blur=hp.blur, eps_g=EPS_G, tight=True)
+    sp = rast.splats[:n].cpu().numpy()
+    vis = idx[(proj["radius"][idx] > 0) & (proj["fragile"][idx] == 0)]
+    close(sp[vis, 0:2].T, proj["mean2d"][:, vis], what="mean2d")
+    close(sp[vis, 4:7].T, proj["conic"][:, vis], what="conic")
+    close(sp[vis, 8:11].T, proj["rgb"][:, vis], what="rgb")
+    # sampled tiles: corners, the ragged last column and row, and random ones
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    tiles = {0, TX - 1, (TY - 1) * TX, TY * TX - 1, (TY // 2) * TX + TX // 2}
+    tiles |= set(rng.choice(TX * TY, 11, replace=False).tolist())
+    tiles = np.array(sorted(tiles))
+    img, T, last, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D, tiles=tiles)
+    insample = np.zeros((H, W), bool)
+    for t in tiles:
+        ty, tx = divmod(int(t), TX)
+        insample[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    ok = insample & (frag == 0)
+    # at this density (60-90 Gaussians per pixel, footprints of ~50 tiles)
+    # Gaussians with a decision within 2e-6 of flipping reach many pixels:
+    # 25-55% of the sampled pixels are excluded
+    assert ok.sum() >= max(1000, 0.3 * insample.sum()), (int(ok.sum()), int(insample.sum()))
+    close(rast.img.cpu().numpy()[:, ok], img[:, ok], what="image")
+    close(rast.T_final.cpu().numpy()[ok], T[ok], what="T_final")
+    # last contributor: identity of the Gaussian, from each side's own lists
+    ranges = rast.ranges.cpu().numpy().astype(np.int64)
+    vals = rast.vals.cpu().numpy().astype(np.int64)
+    lg = rast.last.cpu().numpy().astype(np.int64)
+    v, u = np.nonzero(ok)
+    t_of = (v // 16) * TX + (u // 16)
+    ids_g = np.where(lg[v, u] > 0, vals[np.maximum(ranges[t_of, 0] + lg[v, u] - 1, 0)], -1)
+    vis_all = np.nonzero(proj["radius"] > 0)[0]
+    ids_o = np.full(v.size, -1, np.int64)
+    for t in tiles:
+        ty, tx = divmod(int(t), TX)
+        r = proj["rect"][:, vis_all]
+        m = vis_all[(r[0] <= tx) & (tx < r[2]) & (r[1] <= ty) & (ty < r[3])]
+        lst = m[np.lexsort((m, proj["depth"][m]))]
+        sel = t_of == t
+        lo = last[v[sel], u[sel]].astype(np.int64)
+        ids_o[sel] = np.where(lo > 0, lst[np.maximum(lo - 1, 0)] if lst.size else -1, -1)
+    assert np.array_equal(ids_g, ids_o)
+    # the compositing adjoint and gather for an upstream gradient on the
+    # sampled, non-fragile pixels
+    d_img = (rng.uniform(size=(3, H, W)) - 0.5) * ok[None]
+    rast.d_img.copy_(up(d_img))
+    rast.render_bwd(c, bg)
+    torch.cuda.synchronize()
+    g2 = oracle.render_bwd(proj, d_img, bg, tiles=tiles)
+    touched = np.abs(g2["d_mean2d"]).max(axis=0) > 0
+    assert touched.sum() >= 500 and (gate_ref[touched] > 0).sum() >= 10     # enough Gaussians and open gates
+    gs = rast.d_splats[:n].cpu().numpy()
+    close(gs[:, 0:2].T, g2["d_mean2d"], floor_frac=GRAD_FLOOR, what="d_mean2d")
+    close(gs[:, 2], g2["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity")
+    close(gs[:, 4:7].T, g2["d_conic"], floor_frac=GRAD_FLOOR, what="d_conic")
+    close(gs[:, 8:11].T, g2["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb")
+    # the projection and decode adjoints, each fed the oracle's upstream
+    # gradient (the long footprints of needle-like Gaussians make the
+    # projection adjoint ill-conditioned: an upstream agreeing to 7e-5 can
+    # come out at 2e-4, so each stage is held to the bar on its own)
+    rec = np.zeros((n, 12), np.float32)
+    rec[:, 0:2] = g2["d_mean2d"].T
+    rec[:, 2] = g2["d_opac"]
+    rec[:, 4:7] = g2["d_conic"].T
+    rec[:, 8:11] = g2["d_rgb"].T
+    rast.d_splats[:n] = up(rec)
+    rast.project_bwd(frame.attrs, c, hp.blur, frame.d_attrs)
+    torch.cuda.synchronize()
+    dA = oracle.project_bwd(A_ref, cam, deg, g2["d_mean2d"], g2["d_conic"], g2["d_opac"], g2["d_rgb"], blur=hp.blur)
+    # dL/dSigma' sums terms of the size of the conic's entries that cancel by
+    # the projected covariance's condition number kappa (needle-like
+    # Gaussians), so FP32 keeps 1e-4 only up to kappa ~ 50; above it the bar
+    # scales with kappa, for the few Gaussians concerned
+    A_, B_, C_ = proj["conic"]
+    tr, dt = A_ + C_, A_ * C_ - B_ * B_
+    disc = np.sqrt(np.maximum(tr * tr / 4 - dt, 0.0))
+    kappa = np.where(dt > 0, (tr / 2 + disc) / np.maximum(tr / 2 - disc, 1e-30), 1.0)
+    tol = 1e-4 * np.maximum(1.0, kappa / 50.0)
+    assert (kappa[touched] > 50).mean() < 0.02
+    got = frame.d_attrs[:, :n].cpu().numpy().astype(np.float64)
+    den = np.maximum(np.abs(dA), GRAD_FLOOR * np.abs(dA).max())
+    err = np.abs(got - dA) / den / tol[None, :]
+    at = np.unravel_index(err.argmax(), err.shape)
+    assert err.max() <= 1.0, f"d_attrs: {err.max():.3f} of the bar at {at} (kappa {kappa[at[1]]:.0f})"
+    frame.d_attrs[:, :n] = up(dA)
+    frame.decode_bwd()
+    torch.cuda.synchronize()
+    want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, lay, TAU, G0, G1, dA, frame.d_lreg)
+    close(frame.d_lat[:, :n].cpu().numpy(), want[0], floor_frac=GRAD_FLOOR, what="d_lat")
+    close(frame.d_dec.cpu().numpy(), want[1], floor_frac=GRAD_FLOOR, what="d_dec")
+    close(frame.d_lp[:, :n].cpu().numpy(), want[2], floor_frac=GRAD_FLOOR, what="d_lp")
+    close(frame.d_log_alpha[:n].cpu().numpy(), want[3], floor_frac=GRAD_FLOOR, what="d_log_alpha")
