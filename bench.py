@@ -363,6 +363,8 @@ def run_gpu(args):
                    "launch": "one CUDA graph replay per step (iteration captured once per view)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "stage_ms": {s: round(avg[s], 4) for s in STAGES},
+        # algorithmic bytes of each stage over its warm time (HBM-side work rate)
+        "stage_gbs": {s: round(algo_bytes[s] / (avg[s] * 1e-3) / 1e9, 1) for s in STAGES},
         "staged_ms_per_step": round(staged_ms / args.steps, 4),
         "roofline": roof,
         "clocks": clocks,
@@ -372,7 +374,7 @@ def run_gpu(args):
         "pair_overflow": overflow,
         "wall_s": round(t_wall, 3),
     }
-    if not args.no_seq and name == "full":
+    if not args.no_seq and (name == "full" or args.seq_config == "large"):
         del graphs, frame, rast, targets, flush
         torch.cuda.empty_cache()
         out["sequence"] = run_sequence(args)
@@ -394,7 +396,13 @@ def run_sequence(args):
     fraction of the iterations, against the plain arm."""
     from paper_2412_04469_gb300.sequence import SequenceConfig, compare
 
-    cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
+    if args.seq_config == "large":
+        # 1M Gaussians, 15 views at 1920x1080, 5% dynamic content, 30 frames
+        n, deg, W, H, V, L = WORKLOADS["large"]
+        cfg = SequenceConfig(n=n, sh_degree=deg, width=W, height=H, views=V, frames=30, iters=args.seq_iters,
+                             frac_dynamic=0.05)
+    else:
+        cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
     t0 = time.perf_counter()
     out = compare(cfg, extra_thresholds=args.seq_extra_threshold, masked_fractions=args.seq_masked)
 
@@ -563,6 +571,9 @@ def main():
     ap.add_argument("--no-seq", action="store_true", help="skip the learned-skip sequence comparison")
     ap.add_argument("--seq-frames", type=int, default=16, help="frames of the learned-skip sequence comparison")
     ap.add_argument("--seq-iters", type=int, default=250, help="training iterations per frame in that comparison")
+    ap.add_argument("--seq-config", default="full", choices=["full", "large"],
+                    help="sequence of the learned-skip comparison: the 300k one (16 frames by default) or the "
+                         "1M-Gaussian 1920x1080 one (30 frames, 5%% dynamic)")
     ap.add_argument("--seq-masked", type=float, nargs="*", default=[0.3],
                     help="fractions of iterations trained on Sec. 3.3's adaptive masks (plain gating otherwise)")
     ap.add_argument("--seq-extra-threshold", type=float, nargs="*", default=[0.97],

@@ -287,7 +287,11 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
 }
 
 // In place: counts[c][t] <- sum_{c' < c} counts[c'][t]; tile_total[t] = sum_c.
-// Block = 32 tiles (lanes) x 32 chunk segments (warps).
+// Block = 32 tiles (lanes) x 32 chunk segments (warps).  Each warp walks its
+// segment PREFIX_BATCH chunks at a time with the loads issued together (the
+// walk is otherwise one dependent memory round trip per chunk).
+constexpr int PREFIX_BATCH = 8;
+
 __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles, uint32_t *__restrict__ counts,
                                                        uint32_t *__restrict__ tile_total) {
     __shared__ uint32_t seg[32][33];
@@ -296,8 +300,17 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
     const int per = div_up_dev(n_chunks, 32);
     const int c0 = warp * per, c1 = min(n_chunks, c0 + per);
     uint32_t s = 0;
-    if (t < n_tiles)
-        for (int c = c0; c < c1; ++c) s += counts[(size_t)c * n_tiles + t];
+    if (t < n_tiles) {
+        int c = c0;
+        for (; c + PREFIX_BATCH <= c1; c += PREFIX_BATCH) {
+            uint32_t v[PREFIX_BATCH];
+#pragma unroll
+            for (int k = 0; k < PREFIX_BATCH; ++k) v[k] = counts[(size_t)(c + k) * n_tiles + t];
+#pragma unroll
+            for (int k = 0; k < PREFIX_BATCH; ++k) s += v[k];
+        }
+        for (; c < c1; ++c) s += counts[(size_t)c * n_tiles + t];
+    }
     seg[warp][lane] = s;
     __syncthreads();
     if (warp == 0) {
@@ -312,7 +325,18 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
     __syncthreads();
     if (t < n_tiles) {
         uint32_t run = seg[warp][lane];
-        for (int c = c0; c < c1; ++c) {
+        int c = c0;
+        for (; c + PREFIX_BATCH <= c1; c += PREFIX_BATCH) {
+            uint32_t v[PREFIX_BATCH];
+#pragma unroll
+            for (int k = 0; k < PREFIX_BATCH; ++k) v[k] = counts[(size_t)(c + k) * n_tiles + t];
+#pragma unroll
+            for (int k = 0; k < PREFIX_BATCH; ++k) {
+                counts[(size_t)(c + k) * n_tiles + t] = run;
+                run += v[k];
+            }
+        }
+        for (; c < c1; ++c) {
             const size_t o = (size_t)c * n_tiles + t;
             const uint32_t v = counts[o];
             counts[o] = run;
