@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
                                                          const uint32_t *__restrict__ tile_off,
                                                          const uint32_t *__restrict__ masks,
                                                          uint32_t *__restrict__ vals,
-                                                         unsigned long long *__restrict__ keys) {
+                                                         unsigned long long *__restrict__ keys, int vec) {
     __shared__ ChunkSmem s;
     __shared__ uint32_t dbits[CHUNK];                   // depth bits of the members (for keys)
     const int c = blockIdx.x;
@@ -416,17 +416,50 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
         if (!any) continue;
         const int t = ty * TX + tx;
         uint32_t pos = tile_off[t] + grow[t];
+        if (keys || !vec) {
+#pragma unroll
+            for (int w = 0; w < CHUNK_WARPS; ++w) {
+                uint32_t b = m[w];
+                while (b) {
+                    const int jj = w * 32 + __ffs(b) - 1;
+                    b &= b - 1;
+                    vals[pos] = s.id[jj];
+                    if (keys) keys[pos] = ((unsigned long long)(uint32_t)t << 32) | (unsigned long long)dbits[jj];
+                    ++pos;
+                }
+            }
+            continue;
+        }
+        // the run's slots are consecutive: single stores up to a 16-byte
+        // boundary, then four members per 16-byte store (one memory
+        // transaction instead of four), then the tail
+        uint32_t q0 = 0, q1 = 0, q2 = 0;
+        int nq = 0;
 #pragma unroll
         for (int w = 0; w < CHUNK_WARPS; ++w) {
             uint32_t b = m[w];
             while (b) {
                 const int jj = w * 32 + __ffs(b) - 1;
                 b &= b - 1;
-                vals[pos] = s.id[jj];
-                if (keys) keys[pos] = ((unsigned long long)(uint32_t)t << 32) | (unsigned long long)dbits[jj];
-                ++pos;
+                const uint32_t id = s.id[jj];
+                if (nq == 0 && (pos & 3u)) {
+                    vals[pos++] = id;
+                } else if (nq == 0) {
+                    q0 = id; nq = 1;
+                } else if (nq == 1) {
+                    q1 = id; nq = 2;
+                } else if (nq == 2) {
+                    q2 = id; nq = 3;
+                } else {
+                    *reinterpret_cast<uint4 *>(vals + pos) = make_uint4(q0, q1, q2, id);
+                    pos += 4;
+                    nq = 0;
+                }
             }
         }
+        if (nq > 0) vals[pos] = q0;
+        if (nq > 1) vals[pos + 1] = q1;
+        if (nq > 2) vals[pos + 2] = q2;
     }
 }
 
@@ -601,8 +634,10 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total);
     k_tile_offsets<<<1, 1024, 0, s>>>(n_tiles, tile_total, tile_off, ranges, hdr,
                                       (unsigned long long)pair_capacity, reinterpret_cast<long long *>(n_pairs));
+    const int vec = ((uintptr_t)vals & 15) == 0;       // 16-byte stores need a 16-byte aligned vals
     k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
-                                               tile_off, masks, vals, reinterpret_cast<unsigned long long *>(keys));
+                                               tile_off, masks, vals, reinterpret_cast<unsigned long long *>(keys),
+                                               vec);
     int st = check_launch("qn_bin_sort");
     if (st) return st;
     if (n_pairs_host) {

@@ -183,7 +183,7 @@ BIN_CASES = [  # n, tiles_x, tiles_y, seed, max_extent
 ]
 
 
-def _gpu_bin(depth, rect, tx, ty, capacity=None):
+def _gpu_bin(depth, rect, tx, ty, capacity=None, with_keys=True, vals_offset=0):
     n = depth.size
     buf = np.zeros((max(n, 1), 12), np.float32)
     buf[:n, 3] = depth
@@ -192,13 +192,13 @@ def _gpu_bin(depth, rect, tx, ty, capacity=None):
     ws = torch.zeros(max(B().qn_bin_sort_workspace_size(n, tx, ty), 256), device="cuda", dtype=torch.uint8)
     P_ref = int(np.maximum(rect[2] - rect[0], 0).dot(np.maximum(rect[3] - rect[1], 0))) if n else 0
     cap = P_ref if capacity is None else capacity
-    vals = torch.zeros(max(cap, 1), device="cuda", dtype=torch.int32)
-    keys = torch.zeros(max(cap, 1), device="cuda", dtype=torch.int64)
+    vals = torch.zeros(max(cap, 1) + vals_offset, device="cuda", dtype=torch.int32)[vals_offset:]
+    keys = torch.zeros(max(cap, 1), device="cuda", dtype=torch.int64) if with_keys else None
     ranges = torch.full((tx * ty, 2), 7, device="cuda", dtype=torch.int32)
     npairs = torch.zeros(1, device="cuda", dtype=torch.int64)
     P = B().qn_bin_sort(n, sp.data_ptr() + 12, 12, rc, tx, ty, ws, cap, vals, keys, ranges, npairs, sync=True)
-    return P, keys.cpu().numpy().view(np.uint64)[:P], vals.cpu().numpy().view(np.uint32)[:P], \
-        ranges.cpu().numpy().view(np.uint32), int(npairs.item())
+    return P, (keys.cpu().numpy().view(np.uint64)[:P] if with_keys else None), \
+        vals.cpu().numpy().view(np.uint32)[:P], ranges.cpu().numpy().view(np.uint32), int(npairs.item())
 
 
 @pytest.mark.parametrize("n,tx,ty,seed,ext", BIN_CASES)
@@ -210,6 +210,18 @@ def test_bin_sort_bit_exact(n, tx, ty, seed, ext):
     assert np.array_equal(k, k_ref)
     assert np.array_equal(v, v_ref)
     assert np.array_equal(r, r_ref)
+
+
+@pytest.mark.parametrize("n,tx,ty,seed,ext", [BIN_CASES[i] for i in (2, 4, 5, 6, 8)])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_bin_sort_without_keys(n, tx, ty, seed, ext, offset):
+    """Without keys the scatter writes four members per 16-byte store where
+    the slots allow (a 16-byte aligned vals, offset 0) and single stores
+    otherwise (offset 1): the same values either way."""
+    depth, rect = S.make_bin_inputs(n, tx, ty, seed, max_extent=ext)
+    _, v_ref, r_ref = oracle.bin_sort(depth, rect, tx, ty)
+    P, _, v, r, _ = _gpu_bin(depth, rect, tx, ty, with_keys=False, vals_offset=offset)
+    assert np.array_equal(v, v_ref) and np.array_equal(r, r_ref)
 
 
 def test_bin_sort_capacity_overflow():
