@@ -509,6 +509,24 @@ def oracle_iteration(name, n_tiles_sample, seed=0, view=0):
     return t4 - t0, full, len(tiles)
 
 
+def cpu_single_thread(name, tiles=48):
+    """The same oracle iteration on one core (OMP_NUM_THREADS=1, in a child
+    process so the parent's thread pool is untouched), on a smaller tile
+    sample; None if the child fails."""
+    import subprocess
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, oracle; oracle.build(); "
+            "s, f, k = bench.oracle_iteration(%r, %d); print(json.dumps([s, f, k, oracle.num_threads()]))"
+            % (ROOT, name, tiles))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, env=env)
+        s, f, k, cores = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": round(1.0 / f, 6), "unit": "it/s", "cores": cores,
+            "sample": f"as above on {k} random tiles; sampled run {s:.1f} s"}
+
+
 def cpu_baseline(name, budget_s=20.0):
     import oracle
     oracle.build()
@@ -517,7 +535,9 @@ def cpu_baseline(name, budget_s=20.0):
     per_tile = max(full1 / (4 * 5440), 1e-4)
     k = int(min(5440, max(32, budget_s / per_tile / 2)))
     sampled, full, k = oracle_iteration(name, k)
+    single = cpu_single_thread(name)
     return {"value": round(1.0 / full, 6), "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "single_thread": single,
             "sample": f"one iteration of the workload with compositing, its adjoint and the D-SSIM gradient (tile "
                       f"plus a 10-pixel margin) on {k} random tiles of "
                       f"{(WORKLOADS[name][2] + 15) // 16 * ((WORKLOADS[name][3] + 15) // 16)}; per-tile and "
