@@ -290,8 +290,9 @@ int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
  *     of non-skipped Gaussians)
  *   tile_visited [n_tiles] u32: length of each tile's visited prefix (written)
  *   gauss_hit [n] u8 (nullable): set to 1 for every Gaussian that some pixel
- *     composited (a record with a contribution); never cleared -- zero it
- *     before the call.  qn_bin_gather uses it to skip the others.
+ *     composited (a record with a contribution; skipped Gaussians included,
+ *     though they get no record); never cleared -- zero it before the call.
+ *     qn_bin_gather uses it to skip the others.
  * qn_bin_gather then sums the records per Gaussian.  skip (nullable, [n] u8):
  * no record is written for Gaussians with skip != 0.
  */
@@ -441,10 +442,21 @@ int qn_skip_mlp_fwd(int32_t n, int32_t n_stride, const float *X, const uint16_t 
 /*
  * Training labels: labels[i] = 1 (static) when Gaussian i's residual of the
  * finished frame is exactly zero -- gate[i] == 0 and every latent of
- * lat [n_latent][n_stride] rounds to 0 -- else 0.
+ * lat [n_latent][n_stride] rounds to 0 -- and, with hit [n] u8 (nullable),
+ * hit[i] == 0: no pixel composited it during the frame (qn_or_marks over the
+ * iterations' gauss_hit), so it received no image gradient; else 0.
  */
 int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *gate, const float *lat,
-                   uint8_t *labels, qn_stream_t stream);
+                   const uint8_t *hit, uint8_t *labels, qn_stream_t stream);
+
+/* dst[i] |= (src[i] != 0) for i < n (u8 marks): accumulates qn_render_bwd's
+ * per-iteration gauss_hit over a frame. */
+int qn_or_marks(int32_t n, const uint8_t *src, uint8_t *dst, qn_stream_t stream);
+
+/* flags[i] = 0 where marks[i] != 0, for i < n (u8): clears the skip flag of
+ * every skipped Gaussian that qn_render_bwd found composited, so that it
+ * trains from the next iteration on. */
+int qn_clear_marked(int32_t n, const uint8_t *marks, uint8_t *flags, qn_stream_t stream);
 
 /*
  * Gradient of the mean binary cross-entropy between sigmoid(logit) and

@@ -74,7 +74,9 @@ _SIGS = {
     "qn_skip_features": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_skip_mlp_fwd": ([_I32, _I32, _P, _P, _F32, _P, _P, _P], C.c_int),
     "qn_skip_mlp_bwd": ([_I32, _I32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_skip_labels": ([_I32, _I32, _I32, _P, _P, _P, _P], C.c_int),
+    "qn_skip_labels": ([_I32, _I32, _I32, _P, _P, _P, _P, _P], C.c_int),
+    "qn_or_marks": ([_I32, _P, _P, _P], C.c_int),
+    "qn_clear_marked": ([_I32, _P, _P, _P], C.c_int),
     "qn_adam": ([_I32, _I32, _I32, _P, _P, _P, _P, _I32, _F32, _F32, _F32, _F32, _P, _P, _P], C.c_int),
     "qn_adam_groups": ([_I32, _P, _P, _F32, _F32, _F32, _P, _P], C.c_int),
     "qn_partition_workspace_size": ([_I32], C.c_size_t),
@@ -317,8 +319,13 @@ def qn_skip_mlp_bwd(n, n_stride, X, labels, params_bf16, d_params, loss, partial
                                  _ptr(loss), _ptr(partials), _stream(stream)))
 
 
-def qn_skip_labels(n, n_stride, n_latent, gate, lat, labels, stream=None):
-    _check(lib().qn_skip_labels(n, n_stride, n_latent, _ptr(gate), _ptr(lat), _ptr(labels), _stream(stream)))
+def qn_skip_labels(n, n_stride, n_latent, gate, lat, labels, stream=None, hit=None):
+    _check(lib().qn_skip_labels(n, n_stride, n_latent, _ptr(gate), _ptr(lat), _ptr(hit), _ptr(labels),
+                                _stream(stream)))
+
+
+def qn_or_marks(n, src, dst, stream=None):
+    _check(lib().qn_or_marks(n, _ptr(src), _ptr(dst), _stream(stream)))
 
 
 def qn_partition_workspace_size(n):
@@ -402,3 +409,7 @@ def qn_unpack_frame(packet: bytes, n, n_stride, n_attr, layout, prev, out, works
 def qn_gate_uniform(n, seed, step, u, stream=None):
     """u[i] = Philox4x32-10 uniform of counter (i, *step) under seed."""
     _check(lib().qn_gate_uniform(n, int(seed) & ((1 << 64) - 1), _ptr(step), _ptr(u), _stream(stream)))
+
+
+def qn_clear_marked(n, marks, flags, stream=None):
+    _check(lib().qn_clear_marked(n, _ptr(marks), _ptr(flags), _stream(stream)))

@@ -240,10 +240,11 @@ __global__ void __launch_bounds__(BT) k_skip_mlp_bwd(int n, int S, const float *
 // label = 1 when the frame's residual of the Gaussian is exactly zero: gate
 // closed and every latent rounds to 0
 __global__ void k_skip_labels(int n, int S, int n_lat, const float *__restrict__ gate,
-                              const float *__restrict__ lat, uint8_t *__restrict__ labels) {
+                              const float *__restrict__ lat, const uint8_t *__restrict__ hit,
+                              uint8_t *__restrict__ labels) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool zero = gate[i] == 0.f;
+    bool zero = gate[i] == 0.f && !(hit && hit[i]);
     for (int k = 0; k < n_lat && zero; ++k) zero = rintf(lat[(size_t)k * S + i]) == 0.f;
     labels[i] = zero ? 1 : 0;
 }
@@ -307,11 +308,41 @@ extern "C" int qn_skip_mlp_bwd(int32_t n, int32_t n_stride, const float *X, cons
 }
 
 extern "C" int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *gate, const float *lat,
-                              uint8_t *labels, qn_stream_t stream) {
+                              const uint8_t *hit, uint8_t *labels, qn_stream_t stream) {
     QN_REQUIRE(n >= 0 && n_stride >= n && n_latent >= 0, "bad n / n_stride / n_latent");
     QN_REQUIRE(n == 0 || (gate && labels && (n_latent == 0 || lat)), "null pointer argument");
     if (n == 0) return QN_OK;
-    qn::k_skip_labels<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(n, n_stride, n_latent, gate, lat,
+    qn::k_skip_labels<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(n, n_stride, n_latent, gate, lat, hit,
                                                                             labels);
     return qn::check_launch("qn_skip_labels");
+}
+
+namespace qn {
+namespace {
+__global__ void k_or_marks(int n, const uint8_t *__restrict__ src, uint8_t *__restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && src[i]) dst[i] = 1;
+}
+
+__global__ void k_clear_marked(int n, const uint8_t *__restrict__ marks, uint8_t *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && marks[i]) flags[i] = 0;
+}
+}  // namespace
+}  // namespace qn
+
+extern "C" int qn_or_marks(int32_t n, const uint8_t *src, uint8_t *dst, qn_stream_t stream) {
+    QN_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return QN_OK;
+    QN_REQUIRE(src && dst, "null pointer argument");
+    qn::k_or_marks<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(n, src, dst);
+    return qn::check_launch("qn_or_marks");
+}
+
+extern "C" int qn_clear_marked(int32_t n, const uint8_t *marks, uint8_t *flags, qn_stream_t stream) {
+    QN_REQUIRE(n >= 0, "n must be >= 0");
+    if (n == 0) return QN_OK;
+    QN_REQUIRE(marks && flags, "null pointer argument");
+    qn::k_clear_marked<<<qn::div_up(n, 256), 256, 0, qn::as_stream(stream)>>>(n, marks, flags);
+    return qn::check_launch("qn_clear_marked");
 }

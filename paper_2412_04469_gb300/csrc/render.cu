@@ -311,9 +311,9 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
                 S1 += tt;
                 S2 = fmaf(tt, p.dy, S2);
             }
-            const bool hit_j = __any_sync(FULL, any) && !sskip[j];
-            if (lane == 0) hit[warp][j] = hit_j;
-            if (!hit_j) continue;
+            const bool any_j = __any_sync(FULL, any);   // the band composites j (skipped or not)
+            if (lane == 0) hit[warp][j] = any_j;
+            if (!any_j || sskip[j]) continue;
             const float Sx = r.dx * S0;
             float v[8] = {Sx, S1, r.dx * Sx, r.dx * S1, S2, So, gc0, gc1};
             const float red = reduce_scatter8(v, lane);
@@ -323,6 +323,12 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
         }
         __syncthreads();
         // one record per visited list position: the tile's sum for that Gaussian
+        if (t < cnt && my_skip && ghit) {
+            bool composited = false;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) composited |= hit[w][t] != 0;
+            if (composited) ghit[id] = 1;             // a skipped Gaussian some pixel composited
+        }
         if (t < cnt && !my_skip) {
             float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contributed = false;

@@ -75,6 +75,14 @@ class SequenceConfig:
     # storage: entropy-coded latents, COO positions with the gate binarised),
     # so the trainer holds exactly what a receiver of the packets decodes
     packet: bool = True
+    # learned skip: a Gaussian is labelled static only if, besides ending the
+    # frame with a zero residual, no pixel composited it during the frame (it
+    # received no image gradient), so that skipping it leaves training as is
+    label_visibility: bool = True
+    # learned skip: a skipped Gaussian that a pixel composites is un-skipped
+    # after that iteration (it trains from then on), so a wrong static
+    # prediction costs at most the iterations before its first use
+    unskip_composited: bool = True
 
 
 class SkipMLP:
@@ -191,6 +199,8 @@ class StreamingTrainer:
         self.X = torch.zeros((16, f.S), device="cuda")
         self.skip = torch.zeros(f.S, device="cuda", dtype=torch.uint8)
         self.labels = torch.zeros(f.S, device="cuda", dtype=torch.uint8)
+        self.frame_hit = torch.zeros(f.S, device="cuda", dtype=torch.uint8)     # composited during the frame
+        self._track_hits = False
         self.prev_gate = torch.zeros(f.S, device="cuda")
         self.prev_la = torch.zeros(f.S, device="cuda")
         self.prev_lp = torch.zeros((3, f.S), device="cuda")
@@ -292,6 +302,8 @@ class StreamingTrainer:
     def _train(self, skip):
         f, r = self.frame, self.rast
         n_masked = int(round(self.cfg.masked_fraction * self.cfg.iters))
+        if self._track_hits:
+            self.frame_hit.zero_()                    # the marks of the run that gives the frame's result
         for it in range(self.cfg.iters):
             v = it % self.V
             mask = self.masks[v] if it < n_masked else None
@@ -299,6 +311,10 @@ class StreamingTrainer:
                 self.graphs.run((v, skip is not None, mask is not None), self.cams[v], self.tgt_cur[v], skip, mask)
             else:
                 training_iteration(f, r, self.cams[v], self.tgt_cur[v], skip, mask=mask)
+            if self._track_hits:
+                B.qn_or_marks(self.cfg.n, r.gauss_hit, self.frame_hit)
+            if skip is not None and self.cfg.unskip_composited:
+                B.qn_clear_marked(self.cfg.n, r.gauss_hit, skip)
 
     def _partition(self):
         """Reorders the Gaussians so that the skipped ones form one contiguous
@@ -341,6 +357,7 @@ class StreamingTrainer:
         c, f, n = self.cfg, self.frame, self.cfg.n
         clock = _Clock()
         rec = FrameRecord(t, 0.0, 0.0, self._psnr(f.prev))
+        self._track_hits = mlp is not None and c.label_visibility
         clock.start()
         self._score_and_init()
         if c.masked_fraction > 0:
@@ -384,7 +401,8 @@ class StreamingTrainer:
         self._check_capacity()
         if mlp is not None:
             clock.start()                                  # labels and the MLP's online training count
-            B.qn_skip_labels(n, f.S, self.layout.n_latent, f.gate, f.lat, self.labels)
+            B.qn_skip_labels(n, f.S, self.layout.n_latent, f.gate, f.lat, self.labels,
+                             hit=self.frame_hit if c.label_visibility else None)
             if t <= c.train_frames:
                 mlp.train(self.X, f.S, self.labels, n, c.mlp_epochs, c.mlp_batch)
             self.prev_static.copy_(self.labels)

@@ -138,6 +138,14 @@ def test_skip_labels_zero_residual():
     B().qn_skip_labels(n, S_, 3, up(gate), planes(lat, S_), labels)
     torch.cuda.synchronize()
     assert list(labels.cpu().numpy()) == [1, 1, 0, 0, 1, 0, 0]
+    # with composited marks: a Gaussian that received an image gradient is not static
+    hit = torch.zeros(n, device="cuda", dtype=torch.uint8)
+    B().qn_or_marks(n, up(np.array([0, 1, 0, 0, 0, 0, 0], np.uint8), torch.uint8), hit)
+    B().qn_or_marks(n, up(np.array([0, 0, 0, 1, 2, 0, 0], np.uint8), torch.uint8), hit)
+    assert list(hit.cpu().numpy()) == [0, 1, 0, 1, 1, 0, 0]
+    B().qn_skip_labels(n, S_, 3, up(gate), planes(lat, S_), labels, hit=hit)
+    torch.cuda.synchronize()
+    assert list(labels.cpu().numpy()) == [1, 0, 0, 0, 0, 0, 0]
 
 
 def _mlp_params(seed):

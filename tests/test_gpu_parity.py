@@ -308,11 +308,17 @@ def test_render_skip_mask_zeroes_skipped():
     r.d_img.copy_(up(S.make_image(64, 64, 4) - 0.5))
     r.render_bwd(c, (0, 0, 0))
     full = r.d_splats.cpu().numpy().copy()
+    hit_full = r.gauss_hit.cpu().numpy().copy()
     skip = (np.arange(800) % 3 == 0).astype(np.uint8)
     r.render_bwd(c, (0, 0, 0), skip=up(skip, torch.uint8))
     part = r.d_splats.cpu().numpy()
     assert np.all(part[skip == 1] == 0)
     close(part[skip == 0], full[skip == 0], rtol=1e-5, what="unskipped")
+    # composited Gaussians are marked whether skipped or not
+    assert hit_full.any() and np.array_equal(r.gauss_hit.cpu().numpy(), hit_full)
+    flags = up(skip, torch.uint8)
+    B().qn_clear_marked(800, r.gauss_hit, flags)
+    assert np.array_equal(flags.cpu().numpy(), skip * (hit_full == 0))
 
 
 def test_empty_and_culled_scenes_render_background():
