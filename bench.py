@@ -268,21 +268,41 @@ def run_gpu(args):
                               "stage_ms": {s: float(np.mean(stage_ms[s])) for s in STAGES}}), flush=True)
         return
 
-    # ---- end to end through the public API with host buffers: H2D of the
-    # view's target from pinned memory into the graphs' target buffer and D2H
-    # of the loss every step
+    # ---- end to end through the public API with host buffers: every step
+    # copies its view's target from pinned host memory to the device and reads
+    # the loss back.  The copies run on their own stream into two target
+    # buffers, so step k + 1's copy overlaps step k's compute; each step waits
+    # for its copy, and a buffer is refilled only after the step that read it.
     loss_host = torch.zeros(1).pin_memory()
-    tgt_dev = torch.empty_like(targets[0])
-    for v in range(V):
-        tgt_dev.copy_(targets_host[v], non_blocking=True)
-        graphs.run(("e2e", v), cams[v], tgt_dev)
+    tgt_bufs = [torch.empty_like(targets[0]) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    for b in range(2):
+        for v in range(V):
+            tgt_bufs[b].copy_(targets_host[v], non_blocking=True)
+            graphs.run(("e2e", v, b), cams[v], tgt_bufs[b])
     barrier()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def upload(k):
+        b, v = k % 2, (args.warmup + k) % V
+        with torch.cuda.stream(copy_stream):
+            tgt_bufs[b].copy_(targets_host[v], non_blocking=True)
+            ready[b].record(copy_stream)
+
     e0.record(stream)
+    copy_stream.wait_event(e0)                 # no copy before the timed region starts
+    upload(0)
     for k in range(args.steps):
-        v = (args.warmup + k) % V
-        tgt_dev.copy_(targets_host[v], non_blocking=True)
-        graphs.run(("e2e", v), cams[v], tgt_dev)
+        b, v = k % 2, (args.warmup + k) % V
+        if k + 1 < args.steps:
+            if k >= 1:
+                copy_stream.wait_event(done[1 - b])   # step k - 1 has read that buffer
+            upload(k + 1)
+        stream.wait_event(ready[b])
+        graphs.run(("e2e", v, b), cams[v], tgt_bufs[b])
+        done[b].record(stream)
         loss_host.copy_(rast.loss, non_blocking=True)
     e1.record(stream)
     barrier()
