@@ -26,30 +26,38 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per block per pas
 constexpr int RADIX = 256;
 constexpr int CHUNK = 256;                             // Gaussians per binning chunk
 constexpr int CHUNK_WARPS = CHUNK / 32;
+// Rects above this many tiles are listed by the binning and summed by a whole
+// block in the gather (0.2% of the visible Gaussians of a 300k-Gaussian
+// 1352x1014 view, 2% at 1M and 1920x1080, where the largest covers ~4300
+// tiles): walked by one warp, 32 tiles a pass, they would take up to ~140
+// passes in a row and set the gather's time on their own.  Measured against
+// 512 and 1024, 384 gives the shortest gather at both sizes.
+constexpr int GATHER_BIG_AREA = 384;
 constexpr uint32_t KEY_CULLED = 0xffffffffu;
 
 struct Header {
     uint32_t n_vis;
     uint32_t overflow;
     unsigned long long pairs;
+    uint32_t n_big;                                     // entries of the large-rect list
 };
 
 struct Layout {
-    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, total;
+    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, total;
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-// masks: per chunk, the column words mx[CHUNK_WARPS][TX] then the row words
-// my[CHUNK_WARPS][TY] (built once by k_chunk_counts, read by the scatter and
-// the gather).
+// masks: per chunk, the column words mx[TX][CHUNK_WARPS] then the row words
+// my[TY][CHUNK_WARPS], tile-major so that a tile's words are contiguous
+// (built once by k_chunk_counts, read by the scatter and the gather).
 Layout layout_of(int n, int TX, int TY) {
     const int n_tiles = TX * TY;
     Layout L;
     const size_t nb = (size_t)div_up(n > 0 ? n : 1, SORT_TILE);
     const size_t chunks = (size_t)div_up(n > 0 ? n : 1, CHUNK);
     size_t o = 0;
-    L.hdr = o; o = o + sizeof(Header);
+    L.hdr = o; o = align_up(o + sizeof(Header));
     L.dtot = o; o = align_up(o + 4 * 4 * (size_t)RADIX);      // digit totals of the 4 passes
     L.keys0 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
     L.vals0 = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));
@@ -60,6 +68,7 @@ Layout layout_of(int n, int TX, int TY) {
     L.tile_total = o; o = align_up(o + 4 * (size_t)n_tiles);
     L.tile_off = o; o = align_up(o + 4 * (size_t)(n_tiles + 1));
     L.masks = o; o = align_up(o + 4 * chunks * CHUNK_WARPS * (size_t)(TX + TY));
+    L.big = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));  // depth-sorted indices of large rects
     L.total = o;
     return L;
 }
@@ -235,20 +244,19 @@ __device__ void build_masks(int TX, int TY, ChunkSmem &s) {
     __syncthreads();
 }
 
-// Copies the chunk's masks between shared memory and their workspace slot;
-// warp w moves its own rows mx[w][..] and my[w][..].
+// Copies the chunk's masks between shared memory (warp-major, as the ballots
+// build them) and their tile-major workspace slot (word i = tile i / 8, warp
+// i % 8), coalesced on the global side.
 __device__ void store_masks(int TX, int TY, const ChunkSmem &s, uint32_t *__restrict__ gm) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int tx = lane; tx < TX; tx += 32) gm[w * TX + tx] = s.mx[w][tx];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TX; i += blockDim.x) gm[i] = s.mx[i % CHUNK_WARPS][i / CHUNK_WARPS];
     uint32_t *gy = gm + CHUNK_WARPS * TX;
-    for (int ty = lane; ty < TY; ty += 32) gy[w * TY + ty] = s.my[w][ty];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TY; i += blockDim.x) gy[i] = s.my[i % CHUNK_WARPS][i / CHUNK_WARPS];
 }
 
 __device__ void fetch_masks(int TX, int TY, const uint32_t *__restrict__ gm, ChunkSmem &s) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int tx = lane; tx < TX; tx += 32) s.mx[w][tx] = gm[w * TX + tx];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TX; i += blockDim.x) s.mx[i % CHUNK_WARPS][i / CHUNK_WARPS] = gm[i];
     const uint32_t *gy = gm + CHUNK_WARPS * TX;
-    for (int ty = lane; ty < TY; ty += 32) s.my[w][ty] = gy[w * TY + ty];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TY; i += blockDim.x) s.my[i % CHUNK_WARPS][i / CHUNK_WARPS] = gy[i];
     __syncthreads();
 }
 
@@ -266,9 +274,10 @@ __device__ __forceinline__ uint32_t chunk_count(const ChunkSmem &s, int tx, int 
 }
 
 __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const uint32_t *__restrict__ sorted,
-                                                        const int4 *__restrict__ rects, const Header *hdr,
+                                                        const int4 *__restrict__ rects, Header *hdr,
                                                         uint32_t *__restrict__ counts,
-                                                        uint32_t *__restrict__ masks) {
+                                                        uint32_t *__restrict__ masks,
+                                                        uint32_t *__restrict__ big_list) {
     __shared__ ChunkSmem s;
     const int c = blockIdx.x;
     const uint32_t n_vis = hdr->n_vis;
@@ -280,6 +289,18 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
     }
     load_chunk(c, TX, TY, sorted, rects, n_vis, s);
     store_masks(TX, TY, s, masks + (size_t)c * CHUNK_WARPS * (TX + TY));
+    {
+        // list the chunk's rects above GATHER_BIG_AREA tiles (in any order:
+        // the gather sums each on its own); slots past n_vis hold empty rects
+        const int j = threadIdx.x, lane = j & 31;
+        const int4 r = s.rect[j];
+        const bool big = (r.z - r.x) * (r.w - r.y) > GATHER_BIG_AREA;
+        const unsigned b = __ballot_sync(FULL, big);
+        uint32_t at = 0;
+        if (lane == 0 && b) at = atomicAdd(&hdr->n_big, (uint32_t)__popc(b));
+        at = __shfl_sync(FULL, at, 0);
+        if (big) big_list[at + __popc(b & ((1u << lane) - 1u))] = (uint32_t)c * CHUNK + j;
+    }
     for (int t = threadIdx.x; t < n_tiles; t += CHUNK) {
         const int tx = t % TX, ty = t / TX;
         row[t] = (tx >= s.ux0 && tx < s.ux1 && ty >= s.uy0 && ty < s.uy1) ? chunk_count(s, tx, ty) : 0u;
@@ -465,86 +486,202 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
 
 // Adjoint of the pair scatter: each visible Gaussian sums the per-pair
 // gradient records of the visited positions of its tiles, walking its rect in
-// row-major order (one warp per Gaussian, a fixed lane assignment and a fixed
-// shuffle pattern) -- so the sums are reproducible.  The warps run over the
-// depth-sorted Gaussians across the whole grid: the Gaussians with visited
-// pairs are the front-most, i.e. they crowd the first chunks, and a warp per
-// Gaussian spreads them over every SM.  A Gaussian's rank in a tile's list
-// comes from its chunk's row/column bitmasks (stored by k_chunk_counts); a
-// tile is skipped when the chunk starts beyond the tile's visited prefix.
-// One Gaussian: sum its visited records (a whole warp; g is its depth-sorted
-// index, id its index in the scene).
-__device__ __forceinline__ void gather_one(int TX, int TY, uint32_t g, uint32_t id, int lane,
-                                           const int4 *__restrict__ rects, const uint32_t *__restrict__ gbase,
-                                           const uint32_t *__restrict__ tile_off,
-                                           const uint32_t *__restrict__ visited,
-                                           const float4 *__restrict__ pair_grads,
-                                           const uint32_t *__restrict__ masks, float4 *__restrict__ out) {
-    const int4 r = rects[id];
-    const int n_tiles = TX * TY;
-    const int c = (int)(g / CHUNK), j = (int)(g % CHUNK), wj = j >> 5;
-    const unsigned below = (1u << (j & 31)) - 1u;
-    const uint32_t *mx = masks + (size_t)c * CHUNK_WARPS * (TX + TY);
-    const uint32_t *my = mx + CHUNK_WARPS * TX;
-    const uint32_t *grow = gbase + (size_t)c * n_tiles;
+// row-major order with a fixed thread assignment and a fixed reduction order
+// -- so the sums are reproducible.  A Gaussian's rank in a tile's list comes
+// from its chunk's row/column bitmasks (stored by k_chunk_counts); a tile is
+// skipped when the Gaussian lies beyond the tile's visited prefix.  Every load
+// of a tile (the chunk's count-row entry, the visited length, the tile's
+// offset and its 16 mask words, four 16-byte loads) depends on the tile alone
+// and is issued before the first is used, so a tile costs two dependent memory
+// round trips: those loads, then the record.
+constexpr int GATHER_THREADS = 256;
+constexpr int GATHER_WARPS = GATHER_THREADS / 32;
+
+// Where depth-sorted Gaussian g's chunk keeps its masks and count row.
+struct GatherChunk {
+    const uint4 *mx, *my;                               // a tile column's / row's CHUNK_WARPS words
+    const uint32_t *grow;                               // the chunk's first slot in each tile
+    int wj;                                             // g's warp in the chunk
+    unsigned below;                                     // g's lower lanes in that warp
+};
+
+__device__ __forceinline__ GatherChunk gather_chunk(int TX, int TY, uint32_t g, const uint32_t *__restrict__ gbase,
+                                                    const uint32_t *__restrict__ masks) {
+    // 16-byte aligned: the workspace slot is, a chunk's masks take 32 (TX + TY)
+    // bytes and a tile's words 32
+    static_assert(CHUNK_WARPS == 8, "a tile's mask words are two uint4");
+    const int c = (int)(g / CHUNK), j = (int)(g % CHUNK);
+    GatherChunk k;
+    k.mx = reinterpret_cast<const uint4 *>(masks + (size_t)c * CHUNK_WARPS * (TX + TY));
+    k.my = k.mx + 2 * TX;
+    k.grow = gbase + (size_t)c * TX * TY;
+    k.wj = j >> 5;
+    k.below = (1u << (j & 31)) - 1u;
+    return k;
+}
+
+// Adds the record of the Gaussian in tile (tx, ty) to acc[0..8] if its slot
+// lies in the tile's visited prefix; returns whether it did.
+__device__ __forceinline__ bool gather_tile(int TX, int tx, int ty, const GatherChunk &k,
+                                            const uint32_t *__restrict__ tile_off,
+                                            const uint32_t *__restrict__ visited,
+                                            const float4 *__restrict__ pair_grads, float acc[9]) {
+    const int t = ty * TX + tx;
+    const uint32_t base = k.grow[t], vis = visited[t], off = tile_off[t];
+    const uint4 x0 = k.mx[2 * tx], x1 = k.mx[2 * tx + 1], y0 = k.my[2 * ty], y1 = k.my[2 * ty + 1];
+    const uint32_t m[CHUNK_WARPS] = {x0.x & y0.x, x0.y & y0.y, x0.z & y0.z, x0.w & y0.w,
+                                     x1.x & y1.x, x1.y & y1.y, x1.z & y1.z, x1.w & y1.w};
+    // members of the earlier warps, then those below g in its own warp
+    uint32_t rank = 0;
+#pragma unroll
+    for (int w = 0; w < CHUNK_WARPS; ++w) rank += __popc(m[w] & (w < k.wj ? ~0u : w == k.wj ? k.below : 0u));
+    if (base + rank >= vis) return false;               // past the tile's visited prefix
+    const float4 *p = pair_grads + 3 * (size_t)(off + base + rank);
+    const float4 b0 = p[0], b1 = p[1], b2 = p[2];
+    acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
+    acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
+    acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
+    return true;
+}
+
+// Thread i of `threads` walks tiles i, i + threads, ... of rect r in row-major
+// order, stepping its (column, row) without a division per tile.
+__device__ __forceinline__ bool gather_walk(int TX, int4 r, int i, int threads, const GatherChunk &k,
+                                            const uint32_t *__restrict__ tile_off,
+                                            const uint32_t *__restrict__ visited,
+                                            const float4 *__restrict__ pair_grads, float acc[9]) {
     const int rw = r.z - r.x, area = rw * (r.w - r.y);
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     bool found = false;
-    // lane l walks tiles l, l + 32, ... of the rect in row-major order,
-    // stepping its (column, row) without a division per tile
-    int cx = rw > 0 ? lane % rw : 0, cy = rw > 0 ? lane / rw : 0;
-    const int dq = rw > 0 ? 32 / rw : 0, dr = rw > 0 ? 32 % rw : 0;
-    for (int k = lane; k < area; k += 32) {
-        const int tx = r.x + cx, ty = r.y + cy;
+    int cx = rw > 0 ? i % rw : 0, cy = rw > 0 ? i / rw : 0;
+    const int dq = rw > 0 ? threads / rw : 0, dr = rw > 0 ? threads % rw : 0;
+    for (int q = i; q < area; q += threads) {
+        found |= gather_tile(TX, r.x + cx, r.y + cy, k, tile_off, visited, pair_grads, acc);
         cx += dr;
         cy += dq;
         if (cx >= rw) {
             cx -= rw;
             ++cy;
         }
-        const int t = ty * TX + tx;
-        const uint32_t base = grow[t], vis = visited[t];
-        if (base >= vis) continue;                       // the chunk starts past the visited prefix
-        uint32_t rank = __popc(mx[wj * TX + tx] & my[wj * TY + ty] & below);
-        for (int w = 0; w < wj; ++w) rank += __popc(mx[w * TX + tx] & my[w * TY + ty]);
-        if (base + rank >= vis) continue;
-        const float4 *p = pair_grads + 3 * (size_t)(tile_off[t] + base + rank);
-        const float4 b0 = p[0], b1 = p[1], b2 = p[2];
-        acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
-        acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
-        acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
-        found = true;
     }
+    return found;
+}
+
+// The nine sums of a Gaussian's record (d mean2d x, y, d opacity, d conic
+// a, b, c, d rgb) to their places in its 48-byte gradient record.
+__device__ __forceinline__ void put_record(float *o, int q, float v) { o[(q / 3) * 4 + q % 3] = v; }
+
+struct GatherSmem {
+    uint32_t g[GATHER_THREADS], id[GATHER_THREADS];
+    int4 rect[GATHER_THREADS];
+    int wcount[GATHER_WARPS];
+    float part[GATHER_WARPS][9];
+};
+
+// The large rects: block b of G takes the listed entries b, b + G, ...
+// (GATHER_THREADS at a time, loaded together), keeps the wanted ones, and
+// sums each with all its threads: per-warp sums, then the warps' sums in warp
+// order.
+__device__ void gather_big(int TX, int TY, uint32_t n_big, const uint32_t *__restrict__ big_list,
+                           const uint32_t *__restrict__ sorted, const int4 *__restrict__ rects,
+                           const uint32_t *__restrict__ gbase, const uint32_t *__restrict__ tile_off,
+                           const uint32_t *__restrict__ visited, const float4 *__restrict__ pair_grads,
+                           const uint8_t *__restrict__ skip, const uint8_t *__restrict__ ghit,
+                           const uint32_t *__restrict__ masks, float4 *__restrict__ out, GatherSmem &sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t G = gridDim.x;
+    for (size_t e0 = blockIdx.x; e0 < n_big; e0 += G * GATHER_THREADS) {
+        const size_t e = e0 + (size_t)tid * G;
+        uint32_t g = 0, id = 0;
+        int4 r = make_int4(0, 0, 0, 0);
+        bool wanted = false;
+        if (e < n_big) {
+            g = big_list[e];
+            id = sorted[g];
+            wanted = !(skip && skip[id]) && !(ghit && !ghit[id]);
+            if (wanted) r = rects[id];
+        }
+        const unsigned m = __ballot_sync(FULL, wanted);
+        if (lane == 0) sm.wcount[warp] = __popc(m);
+        __syncthreads();
+        int at = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < GATHER_WARPS; ++w) {
+            at += w < warp ? sm.wcount[w] : 0;
+            total += sm.wcount[w];
+        }
+        if (wanted) {
+            const int q = at + __popc(m & ((1u << lane) - 1u));
+            sm.g[q] = g;
+            sm.id[q] = id;
+            sm.rect[q] = r;
+        }
+        __syncthreads();
+        for (int i = 0; i < total; ++i) {
+            const GatherChunk k = gather_chunk(TX, TY, sm.g[i], gbase, masks);
+            float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            gather_walk(TX, sm.rect[i], tid, GATHER_THREADS, k, tile_off, visited, pair_grads, acc);
+            const float red = reduce_scatter8(acc, lane);  // lane 4q holds the sum of value q
+            const float red8 = warp_sum(acc[8]);
+            if ((lane & 3) == 0) sm.part[warp][lane >> 2] = red;
+            if (lane == 0) sm.part[warp][8] = red8;
+            __syncthreads();
+            if (tid < 9) {
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < GATHER_WARPS; ++w) v += sm.part[w][tid];
+                put_record(reinterpret_cast<float *>(out + 3 * (size_t)sm.id[i]), tid, v);
+            }
+            __syncthreads();                            // part and the list are reused
+        }
+    }
+}
+
+// One Gaussian by one warp (g its depth-sorted index, id its index in the
+// scene).
+__device__ __forceinline__ void gather_warp(int TX, int TY, uint32_t g, uint32_t id, int4 r, int lane,
+                                            const uint32_t *__restrict__ gbase,
+                                            const uint32_t *__restrict__ tile_off,
+                                            const uint32_t *__restrict__ visited,
+                                            const float4 *__restrict__ pair_grads,
+                                            const uint32_t *__restrict__ masks, float4 *__restrict__ out) {
+    const GatherChunk k = gather_chunk(TX, TY, g, gbase, masks);
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool found = gather_walk(TX, r, lane, 32, k, tile_off, visited, pair_grads, acc);
     if (!__any_sync(FULL, found)) return;               // no visited pair: stays 0
     float *o = reinterpret_cast<float *>(out + 3 * (size_t)id);
     const float red = reduce_scatter8(acc, lane);       // lane 4q holds the sum of value q
     const float red8 = warp_sum(acc[8]);
-    if ((lane & 3) == 0) {
-        const int q = lane >> 2;
-        o[(q / 3) * 4 + q % 3] = red;
-    }
+    if ((lane & 3) == 0) put_record(o, lane >> 2, red);
     if (lane == 0) {
-        o[10] = red8;
+        put_record(o, 8, red8);
         o[3] = o[7] = o[11] = 0.f;
     }
 }
 
-// Warp w of W takes the depth-sorted Gaussians w, w + W, w + 2W, ...: its
-// lanes test 32 of them at once (skipped, or without a composited record ->
-// nothing to do), then the warp sums the wanted ones one after another.  The
-// stride spreads the front-most Gaussians, which own nearly all visited pairs,
-// over every warp.
-__global__ void __launch_bounds__(256, 6) k_bin_gather(int TX, int TY, const uint32_t *__restrict__ sorted,
-                                                    const int4 *__restrict__ rects, const Header *hdr,
-                                                    const uint32_t *__restrict__ gbase,
-                                                    const uint32_t *__restrict__ tile_off,
-                                                    const uint32_t *__restrict__ visited,
-                                                    const float4 *__restrict__ pair_grads,
-                                                    const uint8_t *__restrict__ skip,
-                                                    const uint8_t *__restrict__ ghit,
-                                                    const uint32_t *__restrict__ masks, float4 *__restrict__ out) {
+// Every block first takes its share of the large rects (gather_big); then
+// warp w of W takes the depth-sorted Gaussians w, w + W, w + 2W, ...: its
+// lanes test 32 of them at once (skipped, without a composited record, or a
+// large rect -> not its work) and load the rects of the wanted ones, then the
+// warp sums the wanted ones one after another.  The stride spreads the
+// front-most Gaussians, which own nearly all visited pairs, over every warp.
+// The grid is one wave of resident blocks.
+__global__ void __launch_bounds__(GATHER_THREADS, 4) k_bin_gather(int TX, int TY,
+                                                               const uint32_t *__restrict__ sorted,
+                                                               const int4 *__restrict__ rects, const Header *hdr,
+                                                               const uint32_t *__restrict__ big_list,
+                                                               const uint32_t *__restrict__ gbase,
+                                                               const uint32_t *__restrict__ tile_off,
+                                                               const uint32_t *__restrict__ visited,
+                                                               const float4 *__restrict__ pair_grads,
+                                                               const uint8_t *__restrict__ skip,
+                                                               const uint8_t *__restrict__ ghit,
+                                                               const uint32_t *__restrict__ masks,
+                                                               float4 *__restrict__ out) {
+    __shared__ GatherSmem sm;
     if (hdr->overflow) return;
     const uint32_t n_vis = hdr->n_vis;
+    gather_big(TX, TY, hdr->n_big, big_list, sorted, rects, gbase, tile_off, visited, pair_grads, skip, ghit,
+               masks, out, sm);
     const uint32_t W = (uint32_t)((gridDim.x * (size_t)blockDim.x) >> 5);
     const uint32_t w = (uint32_t)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -556,13 +693,17 @@ __global__ void __launch_bounds__(256, 6) k_bin_gather(int TX, int TY, const uin
             id = sorted[gl];
             wanted = !(skip && skip[id]) && !(ghit && !ghit[id]);
         }
+        const int4 rr = wanted ? rects[id] : make_int4(0, 0, 0, 0);
+        wanted = wanted && (rr.z - rr.x) * (rr.w - rr.y) <= GATHER_BIG_AREA;
         unsigned m = __ballot_sync(FULL, wanted);
         while (m) {
             const int l = __ffs(m) - 1;
             m &= m - 1;
             const uint32_t gid = __shfl_sync(FULL, id, l);
-            gather_one(TX, TY, (uint32_t)(w + (size_t)(k0 + l) * W), gid, lane, rects, gbase, tile_off, visited,
-                       pair_grads, masks, out);
+            const int4 r = make_int4(__shfl_sync(FULL, rr.x, l), __shfl_sync(FULL, rr.y, l),
+                                     __shfl_sync(FULL, rr.z, l), __shfl_sync(FULL, rr.w, l));
+            gather_warp(TX, TY, (uint32_t)(w + (size_t)(k0 + l) * W), gid, r, lane, gbase, tile_off, visited,
+                        pair_grads, masks, out);
         }
     }
 }
@@ -630,7 +771,8 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     // after 4 passes the sorted (depth, index) order is back in k0 / v0
     const int n_chunks = div_up(n, CHUNK);
     uint32_t *masks = reinterpret_cast<uint32_t *>(ws + L.masks);
-    k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts, masks);
+    k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts, masks,
+                                              reinterpret_cast<uint32_t *>(ws + L.big));
     k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total);
     k_tile_offsets<<<1, 1024, 0, s>>>(n_tiles, tile_total, tile_off, ranges, hdr,
                                       (unsigned long long)pair_capacity, reinterpret_cast<long long *>(n_pairs));
@@ -671,15 +813,20 @@ extern "C" int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, i
     if (cudaMemsetAsync(d_splats, 0, sizeof(qn_splat) * (size_t)n, s) != cudaSuccess)
         return check_launch("qn_bin_gather memset");
     const char *ws = static_cast<const char *>(workspace);
-    int dev = 0, sms = 148;
+    int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = std::min(div_up((int64_t)n * 32, 256), sms * 8);   // 8 warps per block
-    k_bin_gather<<<blocks, 256, 0, s>>>(
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_gather, GATHER_THREADS, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    // one resident wave: a second one would start only as the first's blocks
+    // end, doubling the time of equal strided shares
+    const int blocks = (int)std::min<int64_t>(div_up((int64_t)n * 32, GATHER_THREADS), (int64_t)sms * per_sm);
+    k_bin_gather<<<blocks, GATHER_THREADS, 0, s>>>(
         tiles_x, tiles_y, reinterpret_cast<const uint32_t *>(ws + L.vals0), reinterpret_cast<const int4 *>(rects),
-        reinterpret_cast<const Header *>(ws + L.hdr), reinterpret_cast<const uint32_t *>(ws + L.counts),
-        reinterpret_cast<const uint32_t *>(ws + L.tile_off), tile_visited,
-        reinterpret_cast<const float4 *>(pair_grads), skip, gauss_hit,
+        reinterpret_cast<const Header *>(ws + L.hdr), reinterpret_cast<const uint32_t *>(ws + L.big),
+        reinterpret_cast<const uint32_t *>(ws + L.counts), reinterpret_cast<const uint32_t *>(ws + L.tile_off),
+        tile_visited, reinterpret_cast<const float4 *>(pair_grads), skip, gauss_hit,
         reinterpret_cast<const uint32_t *>(ws + L.masks), reinterpret_cast<float4 *>(d_splats));
     return check_launch("qn_bin_gather");
 }

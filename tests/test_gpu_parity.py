@@ -281,6 +281,36 @@ def test_render_backward_matches_oracle(n, W, H, deg, blur, seed):
     close(g[:, 8:11].T, ref["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb")
 
 
+def test_render_backward_large_footprints():
+    """A fifth of the Gaussians scaled up (log-scale + 2) on a ragged 33 x 26
+    tile grid: rects above 384 tiles, up to the whole grid, are listed by the
+    binning and summed by a whole block each, the rest by one warp each, in
+    the same launch."""
+    n, W, H, deg, blur = 400, 520, 410, 1, 0.3
+    A, cam = _scene(n, W, H, deg, 4)
+    big = np.random.default_rng(4).choice(n, n // 5, replace=False)
+    A[7:10, big] += 2.0
+    bg = (0.2, 0.1, 0.05)
+    r, c, _ = gpu_raster(A, cam, deg, blur, bg)
+    proj = oracle.project(A.astype(np.float64), cam, deg, blur=blur, eps_g=EPS_G, tight=True)
+    _, _, _, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D)
+    assert (frag != 0).mean() < MAX_FRAGILE
+    d_img = (S.make_image(W, H, 4) - 0.5) * (frag == 0)[None]
+    r.d_img.copy_(up(d_img))
+    r.render_bwd(c, bg)
+    torch.cuda.synchronize()
+    g = r.d_splats.cpu().numpy()[:n]
+    ref = oracle.render_bwd(proj, d_img, bg)
+    rect = proj["rect"]
+    area = (rect[2] - rect[0]) * (rect[3] - rect[1])
+    touched = np.abs(ref["d_rgb"]).max(axis=0) > 0
+    assert (touched & (area > 384)).sum() >= 5 and (touched & (area <= 384)).sum() >= 100
+    close(g[:, 0:2].T, ref["d_mean2d"], floor_frac=GRAD_FLOOR, what="d_mean2d")
+    close(g[:, 2], ref["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity")
+    close(g[:, 4:7].T, ref["d_conic"], floor_frac=GRAD_FLOOR, what="d_conic")
+    close(g[:, 8:11].T, ref["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb")
+
+
 @pytest.mark.parametrize("n,W,H,deg,blur,seed", SCENES[:2])
 def test_tight_rects_leave_rendering_unchanged(n, W, H, deg, blur, seed):
     """The tile lists built from tight rects are a subset of the 3-sigma ones
