@@ -389,7 +389,8 @@ def run_gpu(args):
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": round(job_rate(world, args.steps, e2e_ms), 3), "unit": "it/s",
-                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4},
+                "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4,
+                "l2": "not flushed: steps back to back, as a training loop runs them"},
         "gpu_launches": launches,
         "pair_overflow": overflow,
         "wall_s": round(t_wall, 3),
