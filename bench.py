@@ -152,14 +152,8 @@ def setup(name, seed=0, quick=False):
     targets_host = [torch.from_numpy(S.make_image(W, H, 100 + v)).pin_memory() for v in range(V)]
     targets = [t.cuda() for t in targets_host]
     # size the pair buffer from every view (synchronising, outside any timing)
-    Pmax = 0
     frame.decode()
-    for c in ccams:
-        rast.project(frame.attrs, c, frame.hp.blur)
-        rast.bin_sort(sync=False)
-        torch.cuda.synchronize()
-        Pmax = max(Pmax, int(rast.n_pairs.item()))
-    rast.set_capacity(int(Pmax * 1.25) + 4096)
+    rast.size_for_views(frame.attrs, ccams, frame.hp.blur, margin=1.25)
     return frame, rast, ccams, targets, targets_host, lay, prev, res, cams
 
 

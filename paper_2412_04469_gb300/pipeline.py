@@ -324,6 +324,29 @@ class Rasterizer:
             self.bin_sort(sync=True)
         return P
 
+    def size_for_views(self, attrs, cams, blur, margin: float = 1.25, stream=None) -> int:
+        """Synchronising: bins attrs for every camera and sets the pair buffer
+        to margin x the largest pair count (+ 4096); returns that count.  The
+        training iteration never synchronises, so the buffer is sized before
+        training; a binning that overflows it writes empty ranges (nothing is
+        composited in that iteration), which check_capacity() reports."""
+        P = 0
+        for c in cams:
+            self.project(attrs, c, blur, stream)
+            self.bin_sort(False, stream)
+            torch.cuda.synchronize()
+            P = max(P, int(self.n_pairs.item()))
+        self.set_capacity(int(P * margin) + 4096)
+        return P
+
+    def check_capacity(self) -> int:
+        """Synchronising: the last binning's pair count; raises if it
+        overflowed the pair buffer."""
+        P = int(self.n_pairs.item())
+        if P > self.capacity:
+            raise RuntimeError(f"pair buffer overflow ({P} > {self.capacity})")
+        return P
+
 
 @dataclass
 class ViewMask:

@@ -219,14 +219,7 @@ class StreamingTrainer:
 
     # ---------------------------------------------------------------- helpers
     def _size_pairs(self):
-        r, f = self.rast, self.frame
-        P = 0
-        for c in self.cams:
-            r.project(f.prev, c, self.hp.blur)
-            r.bin_sort(sync=False)
-            torch.cuda.synchronize()
-            P = max(P, int(r.n_pairs.item()))
-        r.set_capacity(int(P * 1.5) + 4096)
+        self.rast.size_for_views(self.frame.prev, self.cams, self.hp.blur, margin=1.5)
 
     def _render(self, attrs, cam):
         r = self.rast
@@ -242,9 +235,7 @@ class StreamingTrainer:
             out[v].copy_(self.rast.img)
 
     def _check_capacity(self):
-        P = int(self.rast.n_pairs.item())
-        if P > self.rast.capacity:
-            raise RuntimeError(f"pair buffer overflow ({P} > {self.rast.capacity})")
+        self.rast.check_capacity()
 
     def _psnr(self, attrs, views=None):
         """Held-out PSNR (views None), or the mean PSNR over the given views."""

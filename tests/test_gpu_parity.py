@@ -233,6 +233,39 @@ def test_bin_sort_capacity_overflow():
     assert e.value.code == QN_ERR_CAPACITY
 
 
+def test_pair_buffer_sizing_and_overflow_report():
+    """Rasterizer.size_for_views sizes the pair buffer from every view's
+    pair count; check_capacity reports the count, and raises after a binning
+    that overflowed a buffer made too small (which wrote empty ranges)."""
+    from paper_2412_04469_gb300.pipeline import QueenFrame, Rasterizer, training_iteration
+    n, deg, W, H = 3000, 1, 200, 150
+    lay = DecoderLayout.default(sh_degree=deg, latent=8)
+    prev = S.make_scene(n, deg, 9)
+    res = S.make_residuals(n, lay, 9)
+    frame = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+    rast = Rasterizer(n, frame.S, deg, W, H, 1)
+    cams = [B().make_camera(c) for c in S.make_arc_cameras(3, W, H)]
+    frame.decode()
+    counts = []
+    for c in cams:
+        rast.project(frame.attrs, c, frame.hp.blur)
+        rast.bin_sort(sync=False)
+        torch.cuda.synchronize()
+        counts.append(int(rast.n_pairs.item()))
+    P = rast.size_for_views(frame.attrs, cams, frame.hp.blur, margin=1.25)
+    assert P == max(counts) > 0 and rast.capacity == int(P * 1.25) + 4096
+    targets = [up(S.make_image(W, H, v)) for v in range(3)]
+    for it in range(3):
+        training_iteration(frame, rast, cams[it], targets[it])
+    assert 0 < rast.check_capacity() <= rast.capacity
+    rast.set_capacity(min(counts) // 2)
+    rast.project(frame.attrs, cams[0], frame.hp.blur)
+    rast.bin_sort(sync=False)
+    with pytest.raises(RuntimeError, match="overflow"):
+        rast.check_capacity()
+    assert not rast.ranges.cpu().numpy().any()          # every range (0, 0): nothing to composite
+
+
 def test_bin_sort_all_culled_and_tie_heavy():
     depth, rect = S.make_bin_inputs(1000, 8, 8, 12, max_extent=8, tie_frac=0.9, empty_frac=0.0)
     depth[:] = depth[0]                                  # every key's depth bits equal
