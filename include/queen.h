@@ -222,7 +222,8 @@ size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y);
  *   n_pairs [1] i64 device: the pair count P (written)
  *   n_pairs_host (nullable): if given, the call synchronises `stream`, stores
  *     P there and returns QN_ERR_CAPACITY when P > pair_capacity.
- * When P > pair_capacity no pair is written and every range is (0, 0).
+ * When P > pair_capacity no pair is written and every range is (0, 0).  Pair
+ * positions are 32-bit, so a capacity above 2^32 - 1 counts as 2^32 - 1.
  */
 int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
                 int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,

@@ -734,6 +734,7 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     const int n_tiles = tiles_x * tiles_y;
     const Layout L = layout_of(n, tiles_x, tiles_y);
     QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
+    const int64_t capacity = std::min<int64_t>(pair_capacity, 0xffffffffll);   // pair positions are 32-bit
     cudaStream_t s = as_stream(stream);
     if (n == 0) {
         if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * n_tiles, s) != cudaSuccess ||
@@ -775,7 +776,7 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
                                               reinterpret_cast<uint32_t *>(ws + L.big));
     k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total);
     k_tile_offsets<<<1, 1024, 0, s>>>(n_tiles, tile_total, tile_off, ranges, hdr,
-                                      (unsigned long long)pair_capacity, reinterpret_cast<long long *>(n_pairs));
+                                      (unsigned long long)capacity, reinterpret_cast<long long *>(n_pairs));
     const int vec = ((uintptr_t)vals & 15) == 0;       // 16-byte stores need a 16-byte aligned vals
     k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
                                                tile_off, masks, vals, reinterpret_cast<unsigned long long *>(keys),
@@ -786,8 +787,8 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
         if (cudaMemcpyAsync(n_pairs_host, n_pairs, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return check_launch("qn_bin_sort readback");
-        if (*n_pairs_host > pair_capacity) {
-            set_error("pair count %lld exceeds capacity %lld", (long long)*n_pairs_host, (long long)pair_capacity);
+        if (*n_pairs_host > capacity) {
+            set_error("pair count %lld exceeds capacity %lld", (long long)*n_pairs_host, (long long)capacity);
             return QN_ERR_CAPACITY;
         }
     }
