@@ -45,7 +45,7 @@ STAGES = list(KERNELS_PER_STAGE)
 NCU_TRAFFIC = {
     "render_bwd": {"bytes": 38.057472e6 + 9.846272e6,
                    "sources": ("paper_2412_04469_gb300/csrc/render.cu", "paper_2412_04469_gb300/csrc/common.cuh"),
-                   "sha256": "f9c1a9598997503d61c25a1ef9eb132e9fda96237180739e9f8f316eb6e66157"},
+                   "sha256": "d2ac1a5f5d89d447af41b6700c603f501359e1fc84f20897efdabde6b6defd97"},
 }
 
 

@@ -349,12 +349,12 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
     }
 }
 
-int check_render_args(const qn_camera *cam, const uint32_t *ranges, const qn_splat *sp) {
+int check_render_args(const qn_camera *cam, const uint32_t *ranges, const uint32_t *vals, const qn_splat *sp) {
     QN_REQUIRE(cam, "camera is required");
     QN_REQUIRE(cam->width > 0 && cam->height > 0 && cam->width <= QN_TILE * QN_MAX_TILES_X &&
                    cam->height <= QN_TILE * QN_MAX_TILES_Y,
                "image size %dx%d out of range", cam->width, cam->height);
-    QN_REQUIRE(ranges, "ranges is required");
+    QN_REQUIRE(ranges && vals && sp, "ranges, vals and splats are required");
     QN_REQUIRE(((uintptr_t)sp & 15) == 0, "splats must be 16-byte aligned");
     return QN_OK;
 }
@@ -365,7 +365,7 @@ int check_render_args(const qn_camera *cam, const uint32_t *ranges, const qn_spl
 extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
                              const qn_splat *splats, const float *bg_host, float *img, float *T_final,
                              uint32_t *last, uint32_t *n_contrib, qn_stream_t stream) {
-    int st = qn::check_render_args(cam_host, ranges, splats);
+    int st = qn::check_render_args(cam_host, ranges, vals, splats);
     if (st) return st;
     QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
     const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
@@ -381,7 +381,7 @@ extern "C" int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, 
                              const uint32_t *last, const float *d_img, const uint8_t *skip,
                              qn_splat *pair_grads, uint32_t *tile_visited, uint8_t *gauss_hit,
                              qn_stream_t stream) {
-    int st = qn::check_render_args(cam_host, ranges, splats);
+    int st = qn::check_render_args(cam_host, ranges, vals, splats);
     if (st) return st;
     QN_REQUIRE(T_final && last && d_img && bg_host && pair_grads && tile_visited, "null pointer argument");
     QN_REQUIRE(((uintptr_t)pair_grads & 15) == 0, "pair_grads must be 16-byte aligned");

@@ -64,6 +64,14 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert b"category" in B.lib().qn_last_error()
     assert B.lib().qn_render_bwd(None, None, None, None, None, None, None, None, None, None, None, None, None) == \
         B.QN_ERR_INVALID_ARG
+    bg = (C.c_float * 3)()
+    assert B.lib().qn_render_fwd(C.byref(cam), 16, None, 32, bg, 64, 128, 256, None, None) == B.QN_ERR_INVALID_ARG
+    assert b"vals" in B.lib().qn_last_error()                                        # sorted pair values missing
+    assert B.lib().qn_render_fwd(C.byref(cam), 16, 16, 40, bg, 64, 128, 256, None, None) == B.QN_ERR_INVALID_ARG
+    assert b"aligned" in B.lib().qn_last_error()                                     # splats misaligned
+    assert B.lib().qn_bin_sort(4, 16, 1, 32, 4, 4, 256, 16, 1 << 40, 64, None, 128, 256, None, None) == \
+        B.QN_ERR_INVALID_ARG                                                          # workspace too small
+    assert b"workspace too small" in B.lib().qn_last_error()
     gp_bad = B.make_gate(0.3, 0.5, 1.01)
     lay.attr_begin[0] = 3
     assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp_bad),
