@@ -129,6 +129,93 @@ def test_brute_force_tiny_scenes(n, W, H, seed):
     assert np.abs(img - bimg).max() < 1e-13 and np.abs(T - bT).max() < 1e-13
 
 
+def brute_all_gaussians(pr, W, H, bg):
+    """Per pixel, every visible Gaussian -- no tile-rect membership test --
+    sorted by (depth, index) and composited with Eq. 2; also returns, per
+    pixel, the Gaussians it composited whose rect misses the pixel's tile."""
+    vis = [i for i in range(pr["opac"].size) if pr["radius"][i] > 0]
+    order = sorted(vis, key=lambda i: (pr["depth"][i], i))
+    img = np.zeros((3, H, W))
+    T_all = np.zeros((H, W))
+    outside = {}
+    for v in range(H):
+        for u in range(W):
+            tx, ty = u // 16, v // 16
+            T, C = 1.0, np.zeros(3)
+            for i in order:
+                dx, dy = u + 0.5 - pr["mean2d"][0, i], v + 0.5 - pr["mean2d"][1, i]
+                a, b, c = pr["conic"][:, i]
+                pw = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+                if pw > 0:
+                    continue
+                al = min(0.99, pr["opac"][i] * math.exp(pw))
+                if al < 1 / 255:
+                    continue
+                if T * (1 - al) < 1e-4:
+                    break
+                r = pr["rect"][:, i]
+                if not (r[0] <= tx < r[2] and r[1] <= ty < r[3]):
+                    outside.setdefault((v, u), []).append(i)
+                C += pr["rgb"][:, i] * al * T
+                T *= 1 - al
+            img[:, v, u] = C + T * np.asarray(bg)
+            T_all[v, u] = T
+    return img, T_all, outside
+
+
+# A pixel outside a Gaussian's rect lies more than r = ceil(3 sqrt(lambda_max))
+# from its centre along x or y, so its Mahalanobis distance exceeds 3 and
+# alpha < o e^(-4.5): only an opacity above e^4.5 / 255 reaches 1/255 there.
+OPAC_BEYOND_RECT = math.exp(4.5) / 255
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_rect_only_drops_alpha_beyond_three_sigma(seed):
+    W, H, bg = 48, 40, (0.1, 0.2, 0.3)
+    A, oc = _scene(60, W, H, seed, grow=1.0)
+    pr = oracle.project(A, oc, 0)                         # rects from the 3-sigma radius
+    vis = np.nonzero(pr["radius"] > 0)[0]
+    v, u = np.mgrid[0:H, 0:W]
+    for i in vis:                                         # every pixel outside the rect: power < -4.5
+        r = pr["rect"][:, i]
+        out = ~((r[0] <= u // 16) & (u // 16 < r[2]) & (r[1] <= v // 16) & (v // 16 < r[3]))
+        dx, dy = u + 0.5 - pr["mean2d"][0, i], v + 0.5 - pr["mean2d"][1, i]
+        a, b, c = pr["conic"][:, i]
+        pw = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+        assert not out.any() or pw[out].max() < -4.5
+    img, T, _, _ = oracle.render_fwd(pr, bg=bg)
+    bimg, bT, outside = brute_all_gaussians(pr, W, H, bg)
+    differ = (np.abs(img - bimg).max(axis=0) > 1e-13) | (np.abs(T - bT) > 1e-13)
+    for pix in zip(*np.nonzero(differ)):                  # explained by a Gaussian composited from outside its rect
+        assert pix in outside
+    for ids in outside.values():
+        assert all(pr["opac"][i] > OPAC_BEYOND_RECT for i in ids)
+    assert (pr["opac"][vis] > OPAC_BEYOND_RECT).any()
+
+
+@pytest.mark.parametrize("o,differs", [(0.99, True), (0.34, False)])
+def test_rect_cut_off_hand_case(o, differs):
+    """sigma = 4 at x = 28: r = 12 and the rect's first tile column is 1
+    (pixels 16..47).  Column 15's pixel centres are at least 12.5 = 3.125
+    sigma away, where alpha <= o e^(-4.88): 0.0075 for o = 0.99 (composited
+    without the rect), 0.0026 < 1/255 for o = 0.34 (no difference anywhere)."""
+    W, H = 64, 32
+    pr = splats(W, H, [(28.0, 16.0)], 4.0, [o], [(1.0, 0.5, 0.25)], [1.0])
+    r = 12
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    pr["rect"] = np.array([[max(0, (28 - r) // 16)], [max(0, (16 - r) // 16)],
+                           [min(TX, (28 + r + 15) // 16)], [min(TY, (16 + r + 15) // 16)]], np.int32)
+    assert list(pr["rect"][:, 0]) == [1, 0, 3, 2]
+    img, T, _, _ = oracle.render_fwd(pr)
+    bimg, bT, outside = brute_all_gaussians(pr, W, H, (0.0, 0.0, 0.0))
+    assert np.all(img[:, :, 16:48] == bimg[:, :, 16:48])  # inside the rect's columns: identical
+    assert (np.abs(img - bimg).max() > 0) == differs
+    if differs:
+        r2 = 12.5 ** 2 + 0.5 ** 2                         # pixel (15, 16)'s centre from the mean
+        assert img[0, 16, 15] == 0.0 and bimg[0, 16, 15] == pytest.approx(o * math.exp(-r2 / 32), rel=1e-12)
+        assert o > OPAC_BEYOND_RECT
+
+
 def _fd_scene(seed):
     A, oc = _scene(24, 32, 32, seed, degree=0, grow=1.0)
     pr = oracle.project(A, oc, 0, eps_g=1e-5)
