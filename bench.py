@@ -431,6 +431,11 @@ def run_sequence(args):
                                  / summary["s_per_frame_learned_skip_frames"], 4),
                 "skip_frames": len(skip), "fallbacks": summary["fallbacks"],
                 "mean_skipped_fraction": round(summary["mean_skipped"], 4),
+                # against the Gaussians static by construction (the 90% that do not move)
+                "static_recall": round(summary["static_recall"], 4),
+                "static_precision": round(summary["static_precision"], 4),
+                "plain_gate0_static_recall": round(summary["plain_gate0_recall"], 4),
+                "plain_gate0_static_precision": round(summary["plain_gate0_precision"], 4),
                 "dpsnr_train_views_min": round(summary["min_dpsnr_train_skip_frames"], 4),
                 "dpsnr_train_views_mean": round(summary["mean_dpsnr_train_skip_frames"], 4),
                 "dpsnr_heldout_min": round(summary["min_dpsnr_skip_frames"], 4),

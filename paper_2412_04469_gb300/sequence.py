@@ -453,7 +453,9 @@ class StreamingTrainer:
 
 def summarize(cfg: SequenceConfig, plain: list, learned: list) -> dict:
     """s/frame of both arms on the skip frames and the skip's PSNR cost
-    against same-state plain training (held-out view and training views)."""
+    against same-state plain training (held-out view and training views);
+    the skipped set's recall and precision against the Gaussians that are
+    static by construction, beside those of the plain arm's zero gates."""
     skip_frames = [i for i, r in enumerate(learned) if r.t > cfg.train_frames]
     sp = [plain[i].seconds for i in skip_frames]
     sl = [learned[i].seconds for i in skip_frames]
@@ -470,7 +472,15 @@ def summarize(cfg: SequenceConfig, plain: list, learned: list) -> dict:
         "mean_dpsnr_train_skip_frames": float(np.mean(dpt)) if dpt else float("nan"),
         "fallbacks": int(sum(r.fallback for r in learned)),
         "mean_skipped": float(np.mean([learned[i].skipped for i in skip_frames])) if skip_frames else 0.0,
+        "static_recall": _mean([learned[i].static_recall for i in skip_frames]),
+        "static_precision": _mean([learned[i].static_precision for i in skip_frames]),
+        "plain_gate0_recall": _mean([plain[i].gate0_recall for i in skip_frames]),
+        "plain_gate0_precision": _mean([plain[i].gate0_precision for i in skip_frames]),
     }
+
+
+def _mean(v: list) -> float:
+    return float(np.mean(v)) if v else float("nan")
 
 
 def compare(cfg: SequenceConfig, frames: int | None = None, extra_thresholds=(), masked_fractions=()) -> dict:

@@ -1,10 +1,12 @@
-"""bench.py's host side on the CPU: the module parses and imports, and the
+"""bench.py's host side on the CPU: the module parses and imports, the
 reference arm (the oracle) prints one JSON line with the contract's keys on
-the small workload."""
+the small workload, and the learned-skip sequence summary of hand records."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -30,3 +32,25 @@ def test_reference_arm_prints_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_sequence_summary_of_hand_records():
+    """The skip-frame summary: frames after the MLP's training frames only,
+    s/frame of both arms, the PSNR differences against same-state plain
+    training, fallbacks, and the static-set recall and precision of the
+    skipped set and of the plain arm's zero gates."""
+    from paper_2412_04469_gb300.sequence import FrameRecord, SequenceConfig, summarize
+    cfg = SequenceConfig(frames=14, train_frames=10)
+    plain = [FrameRecord(t=t, seconds=1.0 + 0.01 * t, psnr=30.0, gate0_recall=0.9 + 0.01 * (t > 10),
+                         gate0_precision=0.8) for t in range(1, 14)]
+    learned = [FrameRecord(t=t, seconds=1.0 if t <= 10 else 0.5, psnr=30.0 - 0.1 * (t == 12), psnr_plain=30.0,
+                           psnr_train=31.0, psnr_plain_train=31.0 + 0.02 * (t == 13), fallback=t == 13,
+                           skipped=0.25 * (t > 10), static_recall=0.6 if t > 10 else float("nan"),
+                           static_precision=0.99 if t > 10 else float("nan")) for t in range(1, 14)]
+    s = summarize(cfg, plain, learned)
+    assert s["s_per_frame_plain_skip_frames"] == pytest.approx(1.12)           # frames 11, 12, 13
+    assert s["s_per_frame_learned_skip_frames"] == pytest.approx(0.5)
+    assert s["min_dpsnr_skip_frames"] == pytest.approx(-0.1) and s["min_dpsnr_train_skip_frames"] == pytest.approx(-0.02)
+    assert s["fallbacks"] == 1 and s["mean_skipped"] == pytest.approx(0.25)
+    assert s["static_recall"] == pytest.approx(0.6) and s["static_precision"] == pytest.approx(0.99)
+    assert s["plain_gate0_recall"] == pytest.approx(0.91) and s["plain_gate0_precision"] == pytest.approx(0.8)
