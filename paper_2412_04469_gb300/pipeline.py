@@ -365,15 +365,20 @@ class ViewMask:
 
 
 def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None,
-                       mask: ViewMask | None = None):
+                       mask: ViewMask | None = None, unskip: bool = False):
     """One view of Eq. 11's optimisation: forward, Eq. 3's loss ((1 - lambda)
     L1 + lambda D-SSIM) + lambda_reg L_reg (the L_reg gradient is folded into
     the gate adjoint), full
     adjoint and the Adam step.  No host synchronisation.  Gaussians with skip
     set are frozen: no gradient, no update, and their decoded columns are
     reused (frame.attrs must hold their A_t, e.g. from a decode without
-    skip).  With a mask (Sec. 3.3's masked training) only the masked tiles
-    are composited and the loss is the mean over the masked pixels."""
+    skip).  With unskip, a skipped Gaussian that some pixel composites in
+    this iteration is un-skipped before its gradient is gathered (the
+    compositing adjoint runs without the skip mask, which costs nothing for
+    the Gaussians no pixel composites), so it takes this iteration's update
+    as plain training does and trains like the others from then on.  With a
+    mask (Sec. 3.3's masked training) only the masked tiles are composited
+    and the loss is the mean over the masked pixels."""
     hp = frame.hp
     frame.decode(stream, skip, train=True)
     rast.project(frame.attrs, cam, hp.blur, stream)
@@ -384,7 +389,12 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
         ranges = rast.ranges_masked
     rast.render_fwd(cam, hp.bg, stream=stream, ranges=ranges)
     rast.photometric_loss(target, hp.lambda_dssim, mask, stream)
-    rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges)
+    if skip is not None and unskip:
+        rast.render_bwd_pairs(cam, hp.bg, None, stream, ranges=ranges)
+        B.qn_clear_marked(rast.n, rast.gauss_hit, skip, stream)
+        rast.gather(skip, stream)
+    else:
+        rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges)
     rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
     frame.decode_bwd(skip, stream)
     frame.adam(skip, stream)
@@ -406,19 +416,20 @@ class IterationGraph:
         self.pool = None
         self.warm = False
 
-    def _signature(self, target, skip, mask):
+    def _signature(self, target, skip, mask, unskip):
         r = self.rast
         return (target.data_ptr(), None if skip is None else skip.data_ptr(), r.vals.data_ptr(),
-                r.pair_grads.data_ptr(), r.workspace.data_ptr(), None if mask is None else mask.pixel.data_ptr())
+                r.pair_grads.data_ptr(), r.workspace.data_ptr(), None if mask is None else mask.pixel.data_ptr(),
+                bool(unskip))
 
-    def run(self, key, cam, target, skip=None, mask=None):
-        sig = self._signature(target, skip, mask)
+    def run(self, key, cam, target, skip=None, mask=None, unskip=False):
+        sig = self._signature(target, skip, mask, unskip)
         ent = self.graphs.get(key)
         if ent is None or ent[1] != sig:
             if not self.warm:
                 # one eager iteration first: lazily allocated scratch must
                 # exist before capture; it is a real training step
-                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask)
+                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip)
                 self.warm = True
                 return
             if self.pool is None:
@@ -426,7 +437,7 @@ class IterationGraph:
             g = torch.cuda.CUDAGraph()
             torch.cuda.synchronize()
             with torch.cuda.graph(g, pool=self.pool):
-                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask)
+                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip)
             ent = (g, sig, cam, target, skip, mask)     # keep what the graph points at alive
             self.graphs[key] = ent
         ent[0].replay()

@@ -80,8 +80,8 @@ class SequenceConfig:
     # received no image gradient), so that skipping it leaves training as is
     label_visibility: bool = True
     # learned skip: a skipped Gaussian that a pixel composites is un-skipped
-    # after that iteration (it trains from then on), so a wrong static
-    # prediction costs at most the iterations before its first use
+    # within that iteration, before its gradient is gathered, so it takes that
+    # update and trains from then on (training_iteration's unskip)
     unskip_composited: bool = True
 
 
@@ -298,14 +298,14 @@ class StreamingTrainer:
         for it in range(self.cfg.iters):
             v = it % self.V
             mask = self.masks[v] if it < n_masked else None
+            unskip = skip is not None and self.cfg.unskip_composited
             if self.cfg.graphs:
-                self.graphs.run((v, skip is not None, mask is not None), self.cams[v], self.tgt_cur[v], skip, mask)
+                self.graphs.run((v, skip is not None, mask is not None), self.cams[v], self.tgt_cur[v], skip, mask,
+                                unskip=unskip)
             else:
-                training_iteration(f, r, self.cams[v], self.tgt_cur[v], skip, mask=mask)
+                training_iteration(f, r, self.cams[v], self.tgt_cur[v], skip, mask=mask, unskip=unskip)
             if self._track_hits:
                 B.qn_or_marks(self.cfg.n, r.gauss_hit, self.frame_hit)
-            if skip is not None and self.cfg.unskip_composited:
-                B.qn_clear_marked(self.cfg.n, r.gauss_hit, skip)
 
     def _partition(self):
         """Reorders the Gaussians so that the skipped ones form one contiguous
