@@ -1,6 +1,7 @@
 """GPU parity of the viewspace gradient difference (Eq. 9), gate
 initialisation (Eq. 10) and the static-skip MLP kernels against the oracle,
-through the C ABI, on seeded inputs."""
+through the C ABI, on seeded inputs; and the skip's in-iteration un-skipping
+of composited Gaussians against plain training."""
 import math
 
 import numpy as np
@@ -190,3 +191,48 @@ def test_skip_mlp_forward_and_backward_match_oracle(n):
     assert float(loss.item()) == pytest.approx(l_ref, rel=1e-4)
     g_ref = _flat(oracle.mlp_backward(dz, P, cache))
     close(dP.cpu().numpy(), g_ref, what="MLP parameter gradient")
+
+
+def test_unskip_within_iteration_matches_plain_for_composited():
+    """Every Gaussian marked skipped, one iteration with unskip: exactly the
+    Gaussians some pixel composites are un-skipped, and they -- with the
+    shared decoders -- take the update plain training gives them (the
+    compositing adjoint ran without the mask, the gather and every later
+    stage with it); the others stay frozen at their initial values."""
+    from paper_2412_04469_gb300.pipeline import QueenFrame, Rasterizer, training_iteration
+    from paper_2412_04469_gb300.synthetic import DecoderLayout
+    n, deg, W, H = 3000, 1, 160, 120
+    lay = DecoderLayout.default(sh_degree=deg, latent=8)
+    prev = S.make_scene(n, deg, 12)
+    res = S.make_residuals(n, lay, 12)
+    cam = B().make_camera(S.make_camera(W, H, 60.0, eye=(0.4, 0.3, 4.0)))
+    tgt = up(S.make_image(W, H, 12))
+    arms = {}
+    for mode in ("plain", "unskip"):
+        f = QueenFrame(prev, deg, lay, res.lat, res.dec, res.lp, res.log_alpha)
+        r = Rasterizer(n, f.S, deg, W, H, 1)
+        f.decode()                                    # A_t of every column, reused for the skipped ones
+        r.size_for_views(f.attrs, [cam], f.hp.blur)
+        skip = torch.ones(f.S, device="cuda", dtype=torch.uint8) if mode == "unskip" else None
+        la0 = f.log_alpha.clone()
+        training_iteration(f, r, cam, tgt, skip, unskip=mode == "unskip")
+        torch.cuda.synchronize()
+        arms[mode] = (f, r, skip, la0)
+    fp, rp, _, _ = arms["plain"]
+    fu, ru, sk, la0 = arms["unskip"]
+    hit = ru.gauss_hit[:n].bool()
+    assert torch.equal(rp.gauss_hit[:n], ru.gauss_hit[:n])
+    assert 100 < int(hit.sum()) < n                   # some composited, some not
+    assert torch.equal(sk[:n].bool(), ~hit)           # exactly the composited ones un-skipped
+    h = hit.cpu().numpy()
+    for name, a, b in (("latents", fp.lat, fu.lat), ("position residuals", fp.lp, fu.lp)):
+        close(b[:, :n].cpu().numpy()[:, h], a[:, :n].cpu().numpy()[:, h], rtol=1e-6, floor_frac=1e-3, what=name)
+        moved = (b[:, :n][:, hit] != planes(res.lat if name == "latents" else res.lp, fu.S)[:, :n][:, hit])
+        assert moved.any(), name
+    close(fu.log_alpha[:n].cpu().numpy()[h], fp.log_alpha[:n].cpu().numpy()[h], rtol=1e-6, floor_frac=1e-3,
+          what="log alpha")
+    close(fu.dec.cpu().numpy(), fp.dec.cpu().numpy(), rtol=1e-6, floor_frac=1e-3, what="decoders")
+    frozen = ~hit
+    assert torch.equal(fu.lat[:, :n][:, frozen], planes(res.lat, fu.S)[:, :n][:, frozen])
+    assert torch.equal(fu.lp[:, :n][:, frozen], planes(res.lp, fu.S)[:, :n][:, frozen])
+    assert torch.equal(fu.log_alpha[:n][frozen], la0[:n][frozen])
