@@ -587,7 +587,7 @@ def oracle_iteration(name, n_tiles_sample, seed=0, view=0):
     return r["sampled"], r["full"], r["tiles"]
 
 
-ORACLE_SAMPLE = ("one iteration: decode, projection and their adjoints on {m} of {n} Gaussians (scaled by n/m), "
+ORACLE_SAMPLE = ("one iteration: decode, projection and their adjoints on {m} of {n} Gaussians{gauss_note}, "
                  "compositing and its adjoint on {k} of {nt} tiles{tiles_note}, the L1 term on the whole image, "
                  "D-SSIM timed once on the whole image ({dssim:.1f} s)")
 
@@ -621,7 +621,7 @@ def cpu_baseline(name):
     return {"value": round(1.0 / r["full"], 6), "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
             "single_thread": single,
             "sample": ORACLE_SAMPLE.format(m=r["m"], n=r["n"], k=r["tiles"], nt=r["n_tiles"], dssim=r["dssim"],
-                                           tiles_note="")
+                                           tiles_note="", gauss_note="")
             + f"; sampled run {r['sampled']:.1f} s"}
 
 
@@ -665,6 +665,7 @@ def run_reference(args):
                             "kind": "oracle",
                             "sample": "per step " + ORACLE_SAMPLE.format(
                                 m=r["m"], n=n, k=k, nt=ntiles, dssim=r["dssim"],
+                                gauss_note=" (scaled by n/m)" if r["m"] < n else "",
                                 tiles_note=(f" (per-call set-up timed apart; the per-tile time scaled to every "
                                             f"tile with a calibration of {calib:.2f} against a composite of all "
                                             f"tiles of view 0)" if k < ntiles else ""))
