@@ -92,8 +92,9 @@ def adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, mas
 def skip_features(score, prev, prev_gate, prev_log_alpha, prev_lp, tau, gamma0, gamma1, nonzero_median=True,
                   prev_static=None):
     """Returns X[16][n] (float64).  score [2][n], prev [n_attr][n] (A_{t-1}),
-    prev_gate [n], prev_log_alpha [n], prev_lp [3][n].  Parity unpinned by the
-    paper (the MLP is not part of it); pinned here by a hand example."""
+    prev_gate [n], prev_log_alpha [n], prev_lp [3][n].  The paper does not
+    define these features (the MLP is not part of it); a hand example with
+    every feature worked out pins them."""
     d = np.asarray(score, np.float64)
     A = np.asarray(prev, np.float64)
     n = d.shape[1]
