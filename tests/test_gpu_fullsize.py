@@ -7,7 +7,14 @@ and last contributors of sampled tiles (corner and ragged-edge tiles
 included), the compositing adjoint and gather for an upstream image gradient
 that lives on those tiles only (every per-Gaussian gradient is then the
 oracle's sum over the sampled tiles), and the projection and decode adjoints
-of all Gaussians fed the oracle's upstream gradients."""
+of all Gaussians fed the oracle's upstream gradients.
+
+The compositing is compared twice.  First against the oracle fed the GPU's
+own FP32 records and rects (the same tile lists, so only the alpha and
+termination decisions can flip: at most 0.1% of the sampled pixels
+excluded), then against the oracle's own FP64 projection, where every
+projection decision within 2e-6 of flipping must also be excluded (at 60-90
+Gaussians per pixel, a large share of the pixels)."""
 import os
 import sys
 
@@ -16,13 +23,15 @@ import pytest
 import torch
 
 import oracle
+from tests._oracle_fed import proj_from_gpu
 
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 EPS_A, EPS_D, EPS_G = 2e-5, 1e-6, 2e-6
 TAU, G0, G1 = 0.3, -0.5, 1.01
-GRAD_FLOOR = 0.05
+GRAD_FLOOR = 0.01
+MAX_FRAGILE_FED = 0.001
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -88,18 +97,42 @@ def test_full_size_path_on_sampled_outputs(name):
     tiles = {0, TX - 1, (TY - 1) * TX, TY * TX - 1, (TY // 2) * TX + TX // 2}
     tiles |= set(rng.choice(TX * TY, 11, replace=False).tolist())
     tiles = np.array(sorted(tiles))
-    img, T, last, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D, tiles=tiles)
     insample = np.zeros((H, W), bool)
     for t in tiles:
         ty, tx = divmod(int(t), TX)
         insample[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    gimg, gT, glast = rast.img.cpu().numpy(), rast.T_final.cpu().numpy(), rast.last.cpu().numpy()
+    # leg 1: the oracle composites the GPU's own FP32 projection
+    pf = proj_from_gpu(rast.splats.cpu().numpy(), rast.rects.cpu().numpy(), n, W, H)
+    img_f, T_f, last_f, frag_f = oracle.render_fwd(pf, bg, eps=EPS_A, eps_d=0.0, tiles=tiles)
+    ok_f = insample & (frag_f == 0)
+    excluded = 1.0 - ok_f.sum() / insample.sum()
+    print(f"[{name}] fed the GPU projection: {excluded:.5f} of {int(insample.sum())} sampled pixels excluded")
+    assert excluded <= MAX_FRAGILE_FED, excluded
+    close(gimg[:, ok_f], img_f[:, ok_f], what="image (fed)")
+    close(gT[ok_f], T_f[ok_f], what="T_final (fed)")
+    assert np.array_equal(glast[ok_f], last_f[ok_f])
+    d_img_f = (rng.uniform(size=(3, H, W)) - 0.5) * ok_f[None]
+    rast.d_img.copy_(up(d_img_f))
+    rast.render_bwd(c, bg)
+    torch.cuda.synchronize()
+    gf = oracle.render_bwd(pf, d_img_f, bg, tiles=tiles)
+    assert (np.abs(gf["d_rgb"]).max(axis=0) > 0).sum() >= 500
+    gs = rast.d_splats[:n].cpu().numpy()
+    close(gs[:, 0:2].T, gf["d_mean2d"], floor_frac=GRAD_FLOOR, what="d_mean2d (fed)")
+    close(gs[:, 2], gf["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity (fed)")
+    close(gs[:, 4:7].T, gf["d_conic"], floor_frac=GRAD_FLOOR, what="d_conic (fed)")
+    close(gs[:, 8:11].T, gf["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb (fed)")
+    # leg 2: the oracle's own FP64 projection
+    img, T, last, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D, tiles=tiles)
     ok = insample & (frag == 0)
     # at this density (60-90 Gaussians per pixel, footprints of ~50 tiles)
-    # Gaussians with a decision within 2e-6 of flipping reach many pixels:
-    # 25-55% of the sampled pixels are excluded
+    # Gaussians with a projection decision within 2e-6 of flipping reach many
+    # pixels, so this leg compares fewer of them (leg 1 covers the rest)
+    print(f"[{name}] FP64 projection: {1 - ok.sum() / insample.sum():.4f} of the sampled pixels excluded")
     assert ok.sum() >= max(1000, 0.3 * insample.sum()), (int(ok.sum()), int(insample.sum()))
-    close(rast.img.cpu().numpy()[:, ok], img[:, ok], what="image")
-    close(rast.T_final.cpu().numpy()[ok], T[ok], what="T_final")
+    close(gimg[:, ok], img[:, ok], what="image")
+    close(gT[ok], T[ok], what="T_final")
     # last contributor: identity of the Gaussian, from each side's own lists
     ranges = rast.ranges.cpu().numpy().astype(np.int64)
     vals = rast.vals.cpu().numpy().astype(np.int64)
