@@ -248,10 +248,16 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
  * QN_ERR_INVALID_ARG before any launch (40 MiB covers 300,000 Gaussians on a
  * 1352 x 1014 image).
  * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture.  The kept address assumes the
+ * device's primary context lives as long: after cudaDeviceReset it is stale.
  * No call allocates or frees memory.  All calls share the one array, and each
  * call re-initialises what it reads: calls that overlap on the GPU (another
  * stream, another host thread) race on it and must be serialised by the caller.
+ * The binning state (sorted values, per-chunk counts, tile offsets, masks)
+ * stays in that private array, so this call feeds the forward compositing
+ * only: the compositing adjoint's per-Gaussian sum (qn_render_bwd) needs the
+ * workspace of a qn_bin_sort call.
  */
 int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
                         int32_t tiles_x, int32_t tiles_y, int64_t pair_capacity, uint32_t *vals,
@@ -270,52 +276,82 @@ int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_stride, con
  *   img [3][H][W] f32, T_final [H][W] f32, last [H][W] u32 = 1 + list position
  *   (within the tile) of the last contributor, 0 if none (all written).
  *   n_contrib [H][W] u32 (nullable): number of contributors of each pixel.
+ *   composited [n] u8 (nullable): set to 1 for every Gaussian that some pixel
+ *     composites (never cleared -- zero it before the call).
+ *   tile_order [n_tiles] u32 (nullable): a permutation of the tiles, the
+ *     order in which the tiles are started (e.g. qn_tile_order's, heaviest
+ *     first); it changes no result.
+ *   tile_cost [n_tiles] u32 (nullable): written with each tile's largest
+ *     `last`, the length of the list prefix its pixels visit.
  *   bg_host: 3 floats in host memory.
  */
 int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
                   const qn_splat *splats, const float *bg_host, float *img, float *T_final,
-                  uint32_t *last, uint32_t *n_contrib, qn_stream_t stream);
+                  uint32_t *last, uint32_t *n_contrib, uint8_t *composited, const uint32_t *tile_order,
+                  uint32_t *tile_cost, qn_stream_t stream);
 
 /*
- * Adjoint of qn_render_fwd for d_img [3][H][W], first half: walks each
- * pixel's list from its last contributor back to the front, rebuilding T by
- * division by (1 - alpha) and carrying the colour behind each Gaussian:
+ * tile_order = the tiles by descending tile_cost (costs above 1023 count as
+ * 1023; the order among equal costs is unspecified).  The compositing
+ * kernels start their tiles in index order, so a deep tile that starts late
+ * sets the end of the launch; started first, it overlaps the rest.  Not part
+ * of the paper: a scheduling aid.  tile_cost, tile_order [n_tiles] u32.
+ */
+int qn_tile_order(int32_t n_tiles, const uint32_t *tile_cost, uint32_t *tile_order, qn_stream_t stream);
+
+/*
+ * Adjoint of qn_render_fwd for d_img [3][H][W]: the per-Gaussian gradient
+ * records d_splats [n] (qn_splat layout: d mean2d, d opacity, d conic,
+ * d rgb; overwritten; zero for culled and skipped Gaussians).  Each pixel's
+ * list is walked from its last contributor back to the front, T rebuilt by
+ * division by (1 - alpha) and the colour behind each Gaussian carried along:
  *   dC/dc_k = alpha_k T_k, dC/dalpha_k = T_k (c_k - B_k), B_last = bg,
  *   B_{k-1} = alpha_k c_k + (1 - alpha_k) B_k; the 0.99 cap passes zero
- *   gradient to opacity, conic and mean.
- * Per tile, the gradients of each Gaussian are summed over the tile's pixels
- * (warp reduce-scatter, then a fixed-order sum over warps; no atomics) and
- * written as one record per visited list position:
- *   pair_grads [pair_capacity] qn_splat: record of sorted pair p (written only
- *     for the visited positions ranges[t][0] .. ranges[t][0] + tile_visited[t] - 1
- *     of non-skipped Gaussians)
- *   tile_visited [n_tiles] u32: length of each tile's visited prefix (written)
- *   gauss_hit [n] u8 (nullable): set to 1 for every Gaussian that some pixel
- *     composited (a record with a contribution; skipped Gaussians included,
- *     though they get no record); never cleared -- zero it before the call.
- *     qn_bin_gather uses it to skip the others.
- * qn_bin_gather then sums the records per Gaussian.  skip (nullable, [n] u8):
- * no record is written for Gaussians with skip != 0.
+ *   gradient to opacity, conic and mean; alpha = o G gives dalpha/do = G.
+ * Two passes, both without float atomics (every sum has a fixed order, so the
+ * result is reproducible bit for bit): per tile, each Gaussian's gradients are
+ * summed over the tile's pixels into one record per visited list position of
+ * pair_scratch; then each Gaussian's records are summed over the tiles of its
+ * rect in row-major order.
+ *   n, rects: the Gaussians and int4 rects given to qn_bin_sort; ranges, vals:
+ *     its output (ranges may have tiles emptied, e.g. a training mask's).
+ *   workspace: the qn_bin_sort workspace that produced the pairs (same n,
+ *     rects and tile grid); the call also keeps its own state there.
+ *   pair_scratch [pair_capacity] qn_splat: scratch, pair_capacity as given to
+ *     that qn_bin_sort call.
+ *   skip (nullable, [n] u8): Gaussians with skip != 0 get zero gradient.  A
+ *     skipped Gaussian that some pixel composites still enters the others'
+ *     gradients (through T and the colour behind).
+ *   composited (nullable, [n] u8): qn_render_fwd's marks of the same
+ *     forward pass.  A Gaussian without one changes no pixel, so the walk
+ *     drops it before any arithmetic; the result is the same.  (Learned skip:
+ *     clearing the skip of the composited Gaussians first -- qn_clear_marked
+ *     -- drops every still-skipped Gaussian from the walk.)
+ *   tile_order (nullable): as for qn_render_fwd (e.g. qn_tile_order of the
+ *     forward's tile_cost).
+ * Errors: QN_ERR_INVALID_ARG for a null required pointer, a misaligned
+ * pointer or a workspace smaller than qn_bin_sort_workspace_size.
  */
-int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
-                  const qn_splat *splats, const float *bg_host, const float *T_final,
-                  const uint32_t *last, const float *d_img, const uint8_t *skip,
-                  qn_splat *pair_grads, uint32_t *tile_visited, uint8_t *gauss_hit, qn_stream_t stream);
+int qn_render_bwd(const qn_camera *cam_host, int32_t n, const int32_t *rects, const uint32_t *ranges,
+                  const uint32_t *vals, const qn_splat *splats, const float *bg_host, const float *T_final,
+                  const uint32_t *last, const float *d_img, const uint8_t *skip, const uint8_t *composited,
+                  const uint32_t *tile_order, void *workspace, size_t workspace_bytes, qn_splat *pair_scratch,
+                  qn_splat *d_splats, qn_stream_t stream);
 
 /*
- * Second half of the compositing adjoint, the adjoint of the binning scatter:
- * d_splats[i] = sum over the tiles of Gaussian i's rect (row-major order) of
- * the record of its pair when that pair lies in the tile's visited prefix;
- * zero for culled and skipped Gaussians.  The fixed summation order makes the
- * result reproducible bit for bit.  workspace must still hold the state of the
- * qn_bin_sort call that produced the pairs (same n, rects, tile grid);
- * d_splats [n] qn_splat is overwritten.  gauss_hit (nullable): qn_render_bwd's
- * marks; an unmarked Gaussian has only zero records, so its sum is 0 without
- * walking its tiles (the result is the same).
+ * The two passes of qn_render_bwd as separate calls (for stage timing);
+ * qn_render_bwd_pairs followed by qn_render_bwd_gather with the same
+ * arguments is qn_render_bwd.  The first writes pair_scratch and the
+ * visited prefix of every tile into the workspace; the second reads them.
  */
-int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, int32_t tiles_y, const void *workspace,
-                  size_t workspace_bytes, const uint32_t *tile_visited, const qn_splat *pair_grads,
-                  const uint8_t *skip, const uint8_t *gauss_hit, qn_splat *d_splats, qn_stream_t stream);
+int qn_render_bwd_pairs(const qn_camera *cam_host, int32_t n, const uint32_t *ranges, const uint32_t *vals,
+                        const qn_splat *splats, const float *bg_host, const float *T_final, const uint32_t *last,
+                        const float *d_img, const uint8_t *skip, const uint8_t *composited,
+                        const uint32_t *tile_order, void *workspace, size_t workspace_bytes, qn_splat *pair_scratch,
+                        qn_stream_t stream);
+int qn_render_bwd_gather(const qn_camera *cam_host, int32_t n, const int32_t *rects, const uint8_t *skip,
+                         const void *workspace, size_t workspace_bytes, const qn_splat *pair_scratch,
+                         qn_splat *d_splats, qn_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Loss and optimiser steps of the training iteration (Eq. 3, Eq. 11).       */
@@ -445,18 +481,20 @@ int qn_skip_mlp_fwd(int32_t n, int32_t n_stride, const float *X, const uint16_t 
  * finished frame is exactly zero -- gate[i] == 0 and every latent of
  * lat [n_latent][n_stride] rounds to 0 -- and, with hit [n] u8 (nullable),
  * hit[i] == 0: no pixel composited it during the frame (qn_or_marks over the
- * iterations' gauss_hit), so it received no image gradient; else 0.
+ * iterations' qn_render_fwd composited marks), so it received no image
+ * gradient; else 0.
  */
 int qn_skip_labels(int32_t n, int32_t n_stride, int32_t n_latent, const float *gate, const float *lat,
                    const uint8_t *hit, uint8_t *labels, qn_stream_t stream);
 
-/* dst[i] |= (src[i] != 0) for i < n (u8 marks): accumulates qn_render_bwd's
- * per-iteration gauss_hit over a frame. */
+/* dst[i] |= (src[i] != 0) for i < n (u8 marks): accumulates qn_render_fwd's
+ * per-iteration composited marks over a frame. */
 int qn_or_marks(int32_t n, const uint8_t *src, uint8_t *dst, qn_stream_t stream);
 
 /* flags[i] = 0 where marks[i] != 0, for i < n (u8): clears the skip flag of
- * every skipped Gaussian that qn_render_bwd found composited, so that it
- * trains from the next iteration on. */
+ * every skipped Gaussian that qn_render_fwd found composited, so that the
+ * adjoint of the same iteration gives it its gradient and it trains from then
+ * on. */
 int qn_clear_marked(int32_t n, const uint8_t *marks, uint8_t *flags, qn_stream_t stream);
 
 /*
@@ -512,8 +550,8 @@ int qn_dilate_mask(int32_t width, int32_t height, const uint32_t *last, int32_t 
 
 /*
  * ranges_out[t] = ranges[t] for tiles with tile_mask[t] != 0, else the empty
- * range [ranges[t][0], ranges[t][0]): qn_render_fwd, qn_render_bwd and
- * qn_bin_gather given ranges_out skip the unmasked tiles.
+ * range [ranges[t][0], ranges[t][0]): qn_render_fwd and qn_render_bwd given
+ * ranges_out skip the unmasked tiles.
  */
 int qn_mask_ranges(int32_t n_tiles, const uint32_t *ranges, const uint8_t *tile_mask, uint32_t *ranges_out,
                    qn_stream_t stream);

@@ -689,13 +689,14 @@ typedef struct {
 /*
  * Composites one pixel.  Returns the number of list entries up to and
  * including the last contributor (0 if none); writes color, final T and the
- * fragility bits (1 alpha near 1/255 or 0.99 and 2 T near 1e-4, both within
- * eps relative; 4 consecutive contributors whose depths lie within eps_d
- * relative, an order FP32 depths could swap).  If rec != NULL the contributors are stored.
+ * fragility bits (1 alpha near 1/255 or 0.99 within eps relative, 2 T near
+ * 1e-4 within eps_t relative; 4 consecutive contributors whose depths lie
+ * within eps_d relative, an order FP32 depths could swap).  If rec != NULL
+ * the contributors are stored.
  */
 static int or_pixel(const or_dk *list, int m, int n, double px, double py, const double *mean2d,
                     const double *conic, const double *opac, const double *rgb, const double *bg,
-                    double eps, double eps_d, double col[3], double *Tout, int *frag, or_contrib *rec,
+                    double eps, double eps_t, double eps_d, double col[3], double *Tout, int *frag, or_contrib *rec,
                     int *nrec) {
     double T = 1.0, C[3] = {0, 0, 0};
     int last = 0, fr = 0, nr = 0;
@@ -714,7 +715,7 @@ static int or_pixel(const or_dk *list, int m, int n, double px, double py, const
         double alpha = capped ? OR_C.alpha_max : v;
         if (alpha < OR_C.alpha_min) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - OR_C.t_min) <= eps * OR_C.t_min) fr |= 2;
+        if (fabs(Tn - OR_C.t_min) <= eps_t * OR_C.t_min) fr |= 2;
         if (Tn < OR_C.t_min) break;
         if (prev_depth >= 0.0 && fabs(list[k].depth - prev_depth) <= eps_d * list[k].depth) fr |= 4;
         prev_depth = list[k].depth;
@@ -762,7 +763,7 @@ static int or_max_list(int n, const int *rect, int TX, int TY) {
  */
 void or_render_fwd(int n, const double *mean2d, const double *conic, const double *opac,
                    const double *rgb, const double *depth, const int *rect, const int *frag_g,
-                   const int *frag_rect, int W, int H, const double *bg, double eps, double eps_d,
+                   const int *frag_rect, int W, int H, const double *bg, double eps, double eps_t, double eps_d,
                    const int *tiles, int n_tiles_sel, double *img, double *T_final, int *last,
                    int *fragile) {
     int TX = (W + OR_TILE - 1) / OR_TILE, TY = (H + OR_TILE - 1) / OR_TILE;
@@ -788,7 +789,7 @@ void or_render_fwd(int n, const double *mean2d, const double *conic, const doubl
                 for (int u = tx * OR_TILE; u < (tx + 1) * OR_TILE && u < W; ++u) {
                     double col[3], T;
                     int fr;
-                    int l = or_pixel(buf, m, n, u + 0.5, v + 0.5, mean2d, conic, opac, rgb, bg, eps, eps_d, col,
+                    int l = or_pixel(buf, m, n, u + 0.5, v + 0.5, mean2d, conic, opac, rgb, bg, eps, eps_t, eps_d, col,
                                      &T, &fr, NULL, NULL);
                     for (int f = 0; f < nfrag; ++f) {
                         int i = fidx[f];
@@ -865,7 +866,7 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
                 for (int u = tx * OR_TILE; u < (tx + 1) * OR_TILE && u < W; ++u) {
                     double col[3], T;
                     int fr, nr;
-                    or_pixel(buf, m, n, u + 0.5, v + 0.5, mean2d, conic, opac, rgb, bg, 0.0, 0.0, col, &T, &fr, rec,
+                    or_pixel(buf, m, n, u + 0.5, v + 0.5, mean2d, conic, opac, rgb, bg, 0.0, 0.0, 0.0, col, &T, &fr, rec,
                              &nr);
                     size_t px = (size_t)v * W + u;
                     double dC[3];

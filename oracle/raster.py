@@ -59,7 +59,7 @@ def _load():
     lib.or_bin_sort.argtypes = [C.c_int, _F, _I, C.c_int, C.c_int, _U64, _U32, _U32]
     lib.or_bin_sort.restype = C.c_int64
     lib.or_render_fwd.argtypes = [C.c_int, _D, _D, _D, _D, _D, _I, _I, _I, C.c_int, C.c_int, _D,
-                                  C.c_double, C.c_double, C.c_void_p, C.c_int, _D, _D, _I, _I]
+                                  C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_int, _D, _D, _I, _I]
     lib.or_render_bwd.argtypes = [C.c_int, _D, _D, _D, _D, _D, _I, C.c_int, C.c_int, _D, _D,
                                   C.c_void_p, C.c_int, _D, _D, _D, _D]
     lib.or_num_threads.restype = C.c_int
@@ -241,11 +241,16 @@ def _tiles(tiles):
     return t.ctypes.data, int(t.size), t
 
 
-def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0, tiles=None):
+def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0, tiles=None, eps_t=None):
     """Eq. 2 per pixel.  Returns (img[3][H][W], T_final, last, fragile).
     Pinned: single-Gaussian footprint closed form, two-Gaussian hand blend,
     transmittance invariants, pure-Python brute force.  `tiles` (optional)
-    restricts the work to those tile indices."""
+    restricts the work to those tile indices.  Fragility flags (pinned by
+    tests/test_oracle_fragility.py): eps is the relative margin of the alpha
+    decisions (threshold and cap), eps_t that of the termination product
+    (default eps); consecutive contributors whose depths lie within eps_d
+    relative are flagged (eps_d < 0 flags none, for depths that are the GPU's
+    own FP32 values, which both sides order alike)."""
     lib = _load()
     tp, tn, _keep = _tiles(tiles)
     W, H = proj["width"], proj["height"]
@@ -256,7 +261,7 @@ def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0, tiles=None):
     frag = np.zeros((H, W), np.int32)
     lib.or_render_fwd(n, _d(proj["mean2d"]), _d(proj["conic"]), _d(proj["opac"]), _d(proj["rgb"]),
                       _d(proj["depth"]), _i(proj["rect"]), _i(proj["fragile"]), _i(proj["frag_rect"]),
-                      W, H, _d(bg), eps, eps_d, tp, tn, img, T, last, frag)
+                      W, H, _d(bg), eps, eps if eps_t is None else eps_t, eps_d, tp, tn, img, T, last, frag)
     return img, T, last, frag
 
 

@@ -65,9 +65,11 @@ _SIGS = {
     "qn_bin_sort_workspace_size": ([_I32, _I32, _I32], _SZ),
     "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_noalloc": ([_I32, _P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_render_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
-    "qn_bin_gather": ([_I32, _P, _I32, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_tile_order": ([_I32, _P, _P, _P], C.c_int),
+    "qn_render_bwd": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P, _P], C.c_int),
+    "qn_render_bwd_pairs": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P], C.c_int),
+    "qn_render_bwd_gather": ([_P, _I32, _P, _P, _P, _SZ, _P, _P, _P], C.c_int),
     "qn_image_loss": ([_I64, _P, _P, _F32, _I32, _P, _P, _P, _P], C.c_int),
     "qn_viewspace_accum": ([_I32, _I32, _P, _F32, _P, _P], C.c_int),
     "qn_gate_init": ([_I32, _I32, _P, _P, _I32, _P, _P, _P, _P], C.c_int),
@@ -229,23 +231,40 @@ def _bg(bg):
     return (C.c_float * 3)(*[float(v) for v in bg])
 
 
-def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=None, stream=None):
+def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=None, stream=None, composited=None,
+                  tile_order=None, tile_cost=None):
     _check(lib().qn_render_fwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg), _ptr(img),
-                               _ptr(T_final), _ptr(last), _ptr(n_contrib), _stream(stream)))
+                               _ptr(T_final), _ptr(last), _ptr(n_contrib), _ptr(composited), _ptr(tile_order),
+                               _ptr(tile_cost), _stream(stream)))
 
 
-def qn_render_bwd(cam, ranges, vals, splats, bg, T_final, last, d_img, skip, pair_grads, tile_visited,
-                  stream=None, gauss_hit=None):
-    _check(lib().qn_render_bwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg), _ptr(T_final),
-                               _ptr(last), _ptr(d_img), _ptr(skip), _ptr(pair_grads), _ptr(tile_visited),
-                               _ptr(gauss_hit), _stream(stream)))
+def qn_tile_order(n_tiles, tile_cost, tile_order, stream=None):
+    _check(lib().qn_tile_order(n_tiles, _ptr(tile_cost), _ptr(tile_order), _stream(stream)))
 
 
-def qn_bin_gather(n, rects, tiles_x, tiles_y, workspace, tile_visited, pair_grads, skip, d_splats, stream=None,
-                  gauss_hit=None):
-    ws_bytes = workspace.numel() * workspace.element_size()
-    _check(lib().qn_bin_gather(n, _ptr(rects), tiles_x, tiles_y, _ptr(workspace), ws_bytes, _ptr(tile_visited),
-                               _ptr(pair_grads), _ptr(skip), _ptr(gauss_hit), _ptr(d_splats), _stream(stream)))
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def qn_render_bwd(cam, n, rects, ranges, vals, splats, bg, T_final, last, d_img, skip, composited, workspace,
+                  pair_scratch, d_splats, stream=None, tile_order=None):
+    _check(lib().qn_render_bwd(C.byref(cam), n, _ptr(rects), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg),
+                               _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(skip), _ptr(composited),
+                               _ptr(tile_order), _ptr(workspace), _nbytes(workspace), _ptr(pair_scratch),
+                               _ptr(d_splats), _stream(stream)))
+
+
+def qn_render_bwd_pairs(cam, n, ranges, vals, splats, bg, T_final, last, d_img, skip, composited, workspace,
+                        pair_scratch, stream=None, tile_order=None):
+    _check(lib().qn_render_bwd_pairs(C.byref(cam), n, _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg),
+                                     _ptr(T_final), _ptr(last), _ptr(d_img), _ptr(skip), _ptr(composited),
+                                     _ptr(tile_order), _ptr(workspace), _nbytes(workspace), _ptr(pair_scratch),
+                                     _stream(stream)))
+
+
+def qn_render_bwd_gather(cam, n, rects, skip, workspace, pair_scratch, d_splats, stream=None):
+    _check(lib().qn_render_bwd_gather(C.byref(cam), n, _ptr(rects), _ptr(skip), _ptr(workspace),
+                                      _nbytes(workspace), _ptr(pair_scratch), _ptr(d_splats), _stream(stream)))
 
 
 QN_LOSS_BLOCKS = 2048

@@ -43,7 +43,7 @@ struct Header {
 };
 
 struct Layout {
-    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, total;
+    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, visited, hit, total;
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
@@ -69,6 +69,9 @@ Layout layout_of(int n, int TX, int TY) {
     L.tile_off = o; o = align_up(o + 4 * (size_t)(n_tiles + 1));
     L.masks = o; o = align_up(o + 4 * chunks * CHUNK_WARPS * (size_t)(TX + TY));
     L.big = o; o = align_up(o + 4 * (size_t)(n > 0 ? n : 1));  // depth-sorted indices of large rects
+    // written by the compositing adjoint's first pass, read by its gather
+    L.visited = o; o = align_up(o + 4 * (size_t)n_tiles);       // visited prefix of each tile's list
+    L.hit = o; o = align_up(o + (size_t)(n > 0 ? n : 1));        // Gaussians with a contributing record
     L.total = o;
     return L;
 }
@@ -795,24 +798,63 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     return QN_OK;
 }
 
-extern "C" int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, int32_t tiles_y,
-                             const void *workspace, size_t workspace_bytes, const uint32_t *tile_visited,
-                             const qn_splat *pair_grads, const uint8_t *skip, const uint8_t *gauss_hit,
-                             qn_splat *d_splats, qn_stream_t stream) {
+namespace {
+
+// The camera's tile grid and the workspace checks shared by both passes of
+// the compositing adjoint.
+int adjoint_setup(const qn_camera *cam, int32_t n, const void *workspace, size_t workspace_bytes, int &TX, int &TY,
+                  qn::Layout &L) {
     using namespace qn;
+    QN_REQUIRE(cam, "camera is required");
+    QN_REQUIRE(cam->width > 0 && cam->height > 0 && cam->width <= QN_TILE * QN_MAX_TILES_X &&
+                   cam->height <= QN_TILE * QN_MAX_TILES_Y,
+               "image size %dx%d out of range", cam->width, cam->height);
     QN_REQUIRE(n >= 0, "n must be >= 0");
-    QN_REQUIRE(tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
-               "tile grid %dx%d out of range", tiles_x, tiles_y);
-    QN_REQUIRE(n == 0 || (rects && workspace && tile_visited && pair_grads && d_splats), "null pointer argument");
-    QN_REQUIRE(((uintptr_t)d_splats & 15) == 0 && ((uintptr_t)pair_grads & 15) == 0 &&
-                   ((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
+    QN_REQUIRE(workspace && ((uintptr_t)workspace & 255) == 0, "workspace is required, 256-byte aligned");
+    TX = (cam->width + QN_TILE - 1) / QN_TILE;
+    TY = (cam->height + QN_TILE - 1) / QN_TILE;
+    L = layout_of(n, TX, TY);
+    QN_REQUIRE(workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
+    return QN_OK;
+}
+
+}  // namespace
+
+extern "C" int qn_render_bwd_pairs(const qn_camera *cam_host, int32_t n, const uint32_t *ranges,
+                                   const uint32_t *vals, const qn_splat *splats, const float *bg_host,
+                                   const float *T_final, const uint32_t *last, const float *d_img,
+                                   const uint8_t *skip, const uint8_t *composited, const uint32_t *tile_order,
+                                   void *workspace, size_t workspace_bytes, qn_splat *pair_scratch,
+                                   qn_stream_t stream) {
+    using namespace qn;
+    int TX, TY;
+    Layout L;
+    int st = adjoint_setup(cam_host, n, workspace, workspace_bytes, TX, TY, L);
+    if (st) return st;
+    char *ws = static_cast<char *>(workspace);
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(ws + L.hit, 0, (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
+        return check_launch("qn_render_bwd memset");
+    return launch_render_bwd(cam_host, ranges, vals, splats, bg_host, T_final, last, d_img, skip, composited,
+                             tile_order, pair_scratch, reinterpret_cast<uint32_t *>(ws + L.visited),
+                             reinterpret_cast<uint8_t *>(ws + L.hit), s);
+}
+
+extern "C" int qn_render_bwd_gather(const qn_camera *cam_host, int32_t n, const int32_t *rects, const uint8_t *skip,
+                                    const void *workspace, size_t workspace_bytes, const qn_splat *pair_scratch,
+                                    qn_splat *d_splats, qn_stream_t stream) {
+    using namespace qn;
+    int TX, TY;
+    Layout L;
+    int st = adjoint_setup(cam_host, n, workspace, workspace_bytes, TX, TY, L);
+    if (st) return st;
+    QN_REQUIRE(n == 0 || (rects && pair_scratch && d_splats), "null pointer argument");
+    QN_REQUIRE(((uintptr_t)d_splats & 15) == 0 && ((uintptr_t)pair_scratch & 15) == 0 && ((uintptr_t)rects & 15) == 0,
                "misaligned pointer argument");
-    const Layout L = layout_of(n, tiles_x, tiles_y);
-    QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
     cudaStream_t s = as_stream(stream);
     if (n == 0) return QN_OK;
     if (cudaMemsetAsync(d_splats, 0, sizeof(qn_splat) * (size_t)n, s) != cudaSuccess)
-        return check_launch("qn_bin_gather memset");
+        return check_launch("qn_render_bwd memset");
     const char *ws = static_cast<const char *>(workspace);
     int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
@@ -824,12 +866,26 @@ extern "C" int qn_bin_gather(int32_t n, const int32_t *rects, int32_t tiles_x, i
     // end, doubling the time of equal strided shares
     const int blocks = (int)std::min<int64_t>(div_up((int64_t)n * 32, GATHER_THREADS), (int64_t)sms * per_sm);
     k_bin_gather<<<blocks, GATHER_THREADS, 0, s>>>(
-        tiles_x, tiles_y, reinterpret_cast<const uint32_t *>(ws + L.vals0), reinterpret_cast<const int4 *>(rects),
+        TX, TY, reinterpret_cast<const uint32_t *>(ws + L.vals0), reinterpret_cast<const int4 *>(rects),
         reinterpret_cast<const Header *>(ws + L.hdr), reinterpret_cast<const uint32_t *>(ws + L.big),
         reinterpret_cast<const uint32_t *>(ws + L.counts), reinterpret_cast<const uint32_t *>(ws + L.tile_off),
-        tile_visited, reinterpret_cast<const float4 *>(pair_grads), skip, gauss_hit,
-        reinterpret_cast<const uint32_t *>(ws + L.masks), reinterpret_cast<float4 *>(d_splats));
-    return check_launch("qn_bin_gather");
+        reinterpret_cast<const uint32_t *>(ws + L.visited), reinterpret_cast<const float4 *>(pair_scratch), skip,
+        reinterpret_cast<const uint8_t *>(ws + L.hit), reinterpret_cast<const uint32_t *>(ws + L.masks),
+        reinterpret_cast<float4 *>(d_splats));
+    return check_launch("qn_render_bwd gather");
+}
+
+extern "C" int qn_render_bwd(const qn_camera *cam_host, int32_t n, const int32_t *rects, const uint32_t *ranges,
+                             const uint32_t *vals, const qn_splat *splats, const float *bg_host, const float *T_final,
+                             const uint32_t *last, const float *d_img, const uint8_t *skip,
+                             const uint8_t *composited, const uint32_t *tile_order, void *workspace,
+                             size_t workspace_bytes, qn_splat *pair_scratch, qn_splat *d_splats, qn_stream_t stream) {
+    QN_REQUIRE(n == 0 || (rects && d_splats), "null pointer argument");
+    int st = qn_render_bwd_pairs(cam_host, n, ranges, vals, splats, bg_host, T_final, last, d_img, skip, composited,
+                                 tile_order, workspace, workspace_bytes, pair_scratch, stream);
+    if (st) return st;
+    return qn_render_bwd_gather(cam_host, n, rects, skip, workspace, workspace_bytes, pair_scratch, d_splats,
+                                stream);
 }
 
 // ---------------------------------------------------------------- no-allocation variant

@@ -68,6 +68,15 @@ inline int sum_partials_grid(int count) { return (int)(((int64_t)count * 32 + 25
 
 __device__ __forceinline__ int div_up_dev(int a, int b) { return (a + b - 1) / b; }
 
+// Compositing (render.cu), used by the workspace-aware entry points of the
+// compositing adjoint (binning.cu): argument checks shared by both passes, and
+// the first pass of the adjoint (per-pair records, visited prefixes, marks).
+int check_render_args(const qn_camera *cam, const uint32_t *ranges, const uint32_t *vals, const qn_splat *sp);
+int launch_render_bwd(const qn_camera *cam, const uint32_t *ranges, const uint32_t *vals, const qn_splat *splats,
+                      const float *bg, const float *T_final, const uint32_t *last, const float *d_img,
+                      const uint8_t *skip, const uint8_t *composited, const uint32_t *order,
+                      qn_splat *pair_grads, uint32_t *visited, uint8_t *hit, cudaStream_t stream);
+
 }  // namespace qn
 
 #define QN_REQUIRE(cond, ...)                 \

@@ -1,6 +1,10 @@
 // Front-to-back alpha compositing per 16 x 16 tile (Sec. 3.1, Eq. 2) and its
-// adjoint.  One warp per tile, eight pixels per lane; Gaussian records are
-// staged in shared memory in batches of 32 and read back as broadcasts.
+// adjoint.  A tile is split into horizontal bands of 2 PPT rows, one warp per
+// band; a lane owns PPT pixels of one column and works on them in pairs with
+// Blackwell's packed FP32 instructions (add/sub/mul/fma .f32x2: two lanes of
+// arithmetic per issued instruction).  Gaussian records are staged in shared
+// memory with every per-Gaussian scalar duplicated into a pair, so a 128-bit
+// broadcast load yields ready operand pairs.
 #include "common.cuh"
 
 namespace qn {
@@ -10,35 +14,58 @@ constexpr float ALPHA_MIN = 1.f / 255.f;
 constexpr float ALPHA_MAX = 0.99f;
 constexpr float T_MIN = 1e-4f;
 constexpr float LOG2E = 1.4426950408889634f;
+// A band whose pixels all have log2(e) power below -log2(255 o) minus this
+// margin (far wider than the rounding of ex2 and log2) cannot pass the
+// alpha >= 1/255 test anywhere and skips the Gaussian: the cull never changes
+// a result.
+constexpr float CULL_MARGIN = 1e-3f;
 
-// A 16 x 16 tile is split into 16 / (2 PPT) horizontal bands of 2 PPT rows,
-// one warp per band.  Lane l owns the PPT pixels of column l % 16 in rows
-// PPT (l / 16) .. PPT (l / 16) + PPT - 1 of its band, so the horizontal
-// offset dx and the dx^2 term of the exponent are shared by all of them, and
-// every record read from shared memory and every per-Gaussian reduction
-// serves PPT pixels.
+// pixels per lane (even): 16 x 16 / (32 PPT) warps per tile
+#ifndef QN_FWD_PPT
+#define QN_FWD_PPT 4
+#endif
+#ifndef QN_BWD_PPT
+#define QN_BWD_PPT 4
+#endif
+
 template <int PPT>
 struct Band {
+    static_assert(PPT % 2 == 0 && QN_TILE % (2 * PPT) == 0, "pixels per lane");
+    static constexpr int NP = PPT / 2;                  // packed pairs per lane
     static constexpr int WARPS = QN_TILE / (2 * PPT);   // warps per tile
     static constexpr int THREADS = 32 * WARPS;
 };
-constexpr int FWD_PPT = 2;                      // forward: little work per (lane, Gaussian) besides the pixels
-constexpr int BWD_PPT = 2;                      // adjoint: a warp reduction per (warp, Gaussian)
-constexpr int BATCH = 32;                       // records staged per round by each forward warp
 
-// Staged record: (mean x, mean y, opacity, -) and the conic scaled for a
-// base-2 exponential, log2(e) * power = A dx^2 + B dx dy + C dy^2 with
-// A = -a log2(e) / 2, B = -b log2(e), C = -c log2(e) / 2, plus a cull bound:
-// alpha >= 1/255 needs o 2^e >= 1/255, i.e. e >= -log2(255 o); a band whose
-// pixels all have e below that bound minus a margin (far wider than the
-// rounding of ex2 and log2) cannot pass the alpha test anywhere and skips the
-// Gaussian, so the cull never changes a result.
-constexpr float CULL_MARGIN = 1e-3f;
+// ---------------------------------------------------------------- packed pairs
+// Two floats in one 64-bit register pair; the .rn forms round each half
+// exactly as the scalar __fadd_rn / __fmul_rn / __fmaf_rn do.
+typedef unsigned long long f2;
 
-__device__ __forceinline__ float4 scaled_conic(float4 g1, float opacity) {
-    const float bound = opacity > 0.f ? -log2f(255.f * opacity) - CULL_MARGIN : INFINITY;
-    return make_float4(__fmul_rn(-0.5f * LOG2E, g1.x), __fmul_rn(-LOG2E, g1.y), __fmul_rn(-0.5f * LOG2E, g1.z),
-                       bound);
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {   // a b + c
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -46,50 +73,63 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-
-// Per (lane, Gaussian): the dx-only part of the exponent.
-struct RowTerms {
-    float dx, p0, bdx;
-};
-
-__device__ __forceinline__ RowTerms row_terms(const float4 &g0, const float4 &k, float fx) {
-    RowTerms r;
-    r.dx = __fsub_rn(fx, g0.x);
-    r.p0 = __fmul_rn(__fmul_rn(k.x, r.dx), r.dx);
-    r.bdx = __fmul_rn(k.y, r.dx);
-    return r;
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-struct PixelAlpha {
-    float alpha, G, dy;
-    bool capped, ok;
+// ---------------------------------------------------------------- staged record
+// log2(e) power = A dx^2 + B dx dy + C dy^2 with A = -a log2(e) / 2,
+// B = -b log2(e), C = -c log2(e) / 2 (conic (a, b, c)), dx = x - mean_x.
+struct __align__(16) Rec {
+    f2 mx, my;      // mean
+    f2 A, B;        // scaled conic
+    f2 C, o;        // scaled conic, opacity
+    f2 cr, cg;      // colour
+    f2 cb;
+    float kw;       // cull bound -log2(255 o) - margin
+    uint32_t id;    // Gaussian index
 };
 
-// log2(e) * power at one pixel of the lane's column; dy = y - mean_y.
-__device__ __forceinline__ float pixel_e2(const float4 &g0, const float4 &k, const RowTerms &r, float fy, float &dy) {
-    dy = __fsub_rn(fy, g0.y);
-    return __fmaf_rn(dy, __fmaf_rn(k.z, dy, r.bdx), r.p0);
+__device__ __forceinline__ void stage_rec(Rec &r, float4 g0, float4 g1, float4 g2, uint32_t id) {
+    const float A = __fmul_rn(-0.5f * LOG2E, g1.x), B = __fmul_rn(-LOG2E, g1.y), C = __fmul_rn(-0.5f * LOG2E, g1.z);
+    r.mx = pk(g0.x, g0.x);
+    r.my = pk(g0.y, g0.y);
+    r.A = pk(A, A);
+    r.B = pk(B, B);
+    r.C = pk(C, C);
+    r.o = pk(g0.z, g0.z);
+    r.cr = pk(g2.x, g2.x);
+    r.cg = pk(g2.y, g2.y);
+    r.cb = pk(g2.z, g2.z);
+    r.kw = g0.z > 0.f ? -log2f(255.f * g0.z) - CULL_MARGIN : INFINITY;
+    r.id = id;
 }
 
-// alpha = min(0.99, o 2^(log2(e) power)) from the exponent, with explicit
-// round-to-nearest operations so that the forward pass and the adjoint
-// evaluate bit-identical alphas and take identical skip decisions.
-// ok: power <= 0 and alpha >= 1/255.
-__device__ __forceinline__ PixelAlpha pixel_alpha(const float4 &g0, float e2, float dy) {
-    PixelAlpha p;
-    p.dy = dy;
-    p.G = ex2_approx(e2);
-    const float v = __fmul_rn(g0.z, p.G);
-    p.capped = v > ALPHA_MAX;
-    p.alpha = fminf(v, ALPHA_MAX);
-    p.ok = e2 <= 0.f && p.alpha >= ALPHA_MIN;
-    return p;
-}
-
-template <int NB>
-struct StageBuf {
-    float4 g0[NB], k[NB], c[NB];
+// The exponent at the lane's pixel pairs, with explicit round-to-nearest
+// operations so that the forward pass and the adjoint evaluate bit-identical
+// alphas and take identical decisions:
+//   dx = x - mx, dy = y - my, e = fma(dy, fma(C, dy, B dx), (A dx) dx).
+template <int NP>
+struct Expo {
+    f2 dx;          // (dx, dx)
+    f2 dy[NP], e[NP];
 };
+
+template <int NP>
+__device__ __forceinline__ Expo<NP> exponent(const Rec &r, f2 FX, const f2 (&FY)[NP]) {
+    Expo<NP> x;
+    x.dx = sub2(FX, r.mx);
+    const f2 p0 = mul2(mul2(r.A, x.dx), x.dx);
+    const f2 bdx = mul2(r.B, x.dx);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        x.dy[p] = sub2(FY[p], r.my);
+        x.e[p] = fma2(x.dy[p], fma2(r.C, x.dy[p], bdx), p0);
+    }
+    return x;
+}
 
 template <int PPT>
 __device__ __forceinline__ void pixel_coords(int tile, int TX, int &px, int &py0) {
@@ -98,20 +138,66 @@ __device__ __forceinline__ void pixel_coords(int tile, int TX, int &px, int &py0
     py0 = (tile / TX) * QN_TILE + warp * (2 * PPT) + (lane >> 4) * PPT;
 }
 
+// ---------------------------------------------------------------- forward
 // Every warp composites its band independently: it stages its own copy of
-// each batch of records and stops when its pixels have all terminated.  The
-// per-pixel update is branch-free (selects and zero weights), so the PPT
-// pixel chains of a lane interleave.
-template <bool COUNT, int PPT = FWD_PPT, int WARPS = Band<PPT>::WARPS>
-__global__ void __launch_bounds__(32 * WARPS) k_render_fwd(int W, int H, int TX, const uint32_t *__restrict__ ranges,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const float4 *__restrict__ sp, float bg0, float bg1,
-                                                        float bg2, float *__restrict__ img,
-                                                        float *__restrict__ Tf, uint32_t *__restrict__ last,
-                                                        uint32_t *__restrict__ ncon) {
-    __shared__ StageBuf<BATCH> sbuf[WARPS];
-    StageBuf<BATCH> &s = sbuf[threadIdx.x >> 5];
-    const int tile = blockIdx.x;
+// each batch of records (48 bytes: mean, opacity, scaled conic and cull bound,
+// colour) and stops when its pixels have all terminated.  A lane owns
+// FWD_PPT pixels of one column as independent scalar chains (packing them
+// buys no FP32 throughput here, and the forward's alpha test and update are
+// mostly compares and selects).  The per-pixel update is branch-free
+// (selects and zero weights).  Per pixel:
+//   alpha = min(0.99, o 2^e); skipped unless e <= 0 and alpha >= 1/255;
+//   T' = T (1 - alpha); stop before the Gaussian if T' < 1e-4;
+//   C += c alpha T; T = T'.
+// comp (nullable): set to 1 for every Gaussian some pixel composites (one
+// store per composited record and warp, after each batch).  order
+// (nullable): block b composites tile order[b] (heaviest first: the blocks
+// start in index order, and a deep tile that starts late sets the kernel's
+// end).  cost (nullable): each tile's visited prefix, the largest `last` of
+// its pixels, the work measure that orders the next launches.
+constexpr int FWD_BATCH = 32;
+
+struct SRec {
+    float4 g;   // (mean x, mean y, opacity, cull bound -log2(255 o) - margin)
+    float4 k;   // scaled conic (A, B, C, -)
+    float4 c;   // colour (r, g, b, -)
+};
+
+__device__ __forceinline__ void stage_srec(SRec &r, float4 g0, float4 g1, float4 g2) {
+    r.g = make_float4(g0.x, g0.y, g0.z, g0.z > 0.f ? -log2f(255.f * g0.z) - CULL_MARGIN : INFINITY);
+    r.k = make_float4(__fmul_rn(-0.5f * LOG2E, g1.x), __fmul_rn(-LOG2E, g1.y), __fmul_rn(-0.5f * LOG2E, g1.z), 0.f);
+    r.c = g2;
+}
+
+// log2(e) power at the lane's PPT pixels, the same round-to-nearest sequence
+// as exponent(): dx = x - mx, dy = y - my, e = fma(dy, fma(C, dy, B dx), (A dx) dx).
+template <int PPT>
+__device__ __forceinline__ void scalar_exponent(const SRec &r, float fx, float fy0, float (&e)[PPT]) {
+    const float dx = __fsub_rn(fx, r.g.x);
+    const float p0 = __fmul_rn(__fmul_rn(r.k.x, dx), dx), bdx = __fmul_rn(r.k.y, dx);
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const float dy = __fsub_rn(fy0 + (float)q, r.g.y);
+        e[q] = __fmaf_rn(dy, __fmaf_rn(r.k.z, dy, bdx), p0);
+    }
+}
+
+template <bool COUNT, int PPT>
+__global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H, int TX,
+                                                                  const uint32_t *__restrict__ ranges,
+                                                                  const uint32_t *__restrict__ vals,
+                                                                  const float4 *__restrict__ sp, float bg0, float bg1,
+                                                                  float bg2, float *__restrict__ img,
+                                                                  float *__restrict__ Tf, uint32_t *__restrict__ last,
+                                                                  uint32_t *__restrict__ ncon,
+                                                                  uint8_t *__restrict__ comp,
+                                                                  const uint32_t *__restrict__ order,
+                                                                  uint32_t *__restrict__ cost) {
+    constexpr int WARPS = Band<PPT>::WARPS;
+    __shared__ SRec sbuf[WARPS][FWD_BATCH];
+    __shared__ uint32_t wmax[WARPS];
+    SRec *s = sbuf[threadIdx.x >> 5];
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int lane = threadIdx.x & 31;
     int px, py0;
     pixel_coords<PPT>(tile, TX, px, py0);
@@ -123,50 +209,54 @@ __global__ void __launch_bounds__(32 * WARPS) k_render_fwd(int W, int H, int TX,
     uint32_t live = 0;                                  // bit q: pixel q still compositing
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        T[q] = 1.f; c0[q] = c1[q] = c2[q] = 0.f; lastc[q] = nc[q] = 0;
+        T[q] = 1.f;
+        c0[q] = c1[q] = c2[q] = 0.f;
+        lastc[q] = nc[q] = 0;
         if (px < W && py0 + q < H) live |= 1u << q;
     }
-    for (int b0 = 0; b0 < n; b0 += BATCH) {
+    for (int b0 = 0; b0 < n; b0 += FWD_BATCH) {
         if (!__any_sync(FULL, live)) break;
+        uint32_t my_id = 0;
         if (b0 + lane < n) {
-            const size_t id = vals[beg + b0 + lane];
-            const float4 g0 = sp[3 * id];
-            s.g0[lane] = g0;
-            s.k[lane] = scaled_conic(sp[3 * id + 1], g0.z);
-            s.c[lane] = sp[3 * id + 2];
+            my_id = vals[beg + b0 + lane];
+            stage_srec(s[lane], sp[3 * (size_t)my_id], sp[3 * (size_t)my_id + 1], sp[3 * (size_t)my_id + 2]);
         }
         __syncwarp();
-        const int cnt = min(BATCH, n - b0);
+        const int cnt = min(FWD_BATCH, n - b0);
+        uint32_t batch_added = 0;                       // bit j: record j composited by this warp
         for (int j = 0; j < cnt; ++j) {
             if (!__any_sync(FULL, live)) break;
-            const float4 g0 = s.g0[j], k = s.k[j], c = s.c[j];
-            const RowTerms r = row_terms(g0, k, fx);
-            float e2[PPT], dy[PPT];
+            const SRec &r = s[j];
+            float e[PPT];
+            scalar_exponent<PPT>(r, fx, fy0, e);
             bool near = false;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                e2[q] = pixel_e2(g0, k, r, fy0 + (float)q, dy[q]);
-                near |= e2[q] >= k.w;
-            }
+            for (int q = 0; q < PPT; ++q) near |= e[q] >= r.g.w;
             if (!__any_sync(FULL, near)) continue;      // alpha < 1/255 on every pixel of the band
+            const float4 c = r.c;
             const uint32_t pos1 = (uint32_t)(b0 + j + 1);
+            bool added = false;
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
-                const PixelAlpha p = pixel_alpha(g0, e2[q], dy[q]);
-                const bool ok = ((live >> q) & 1u) && p.ok;
-                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, p.alpha));
+                const float v = __fmul_rn(r.g.z, ex2_approx(e[q]));
+                const float al = fminf(v, ALPHA_MAX);
+                const bool ok = ((live >> q) & 1u) && e[q] <= 0.f && al >= ALPHA_MIN;
+                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, al));
                 const bool stop = Tn < T_MIN;
                 const bool add = ok && !stop;
                 if (ok && stop) live &= ~(1u << q);
-                const float w = add ? p.alpha * T[q] : 0.f;
+                const float w = add ? al * T[q] : 0.f;
                 c0[q] = fmaf(c.x, w, c0[q]);
                 c1[q] = fmaf(c.y, w, c1[q]);
                 c2[q] = fmaf(c.z, w, c2[q]);
                 T[q] = add ? Tn : T[q];
                 lastc[q] = add ? pos1 : lastc[q];
                 if (COUNT) nc[q] += add ? 1u : 0u;
+                added |= add;
             }
+            if (comp && __any_sync(FULL, added)) batch_added |= 1u << j;
         }
+        if (comp && ((batch_added >> lane) & 1u)) comp[my_id] = 1;
         __syncwarp();
     }
     const size_t plane = (size_t)W * H;
@@ -182,62 +272,99 @@ __global__ void __launch_bounds__(32 * WARPS) k_render_fwd(int W, int H, int TX,
         last[o] = lastc[q];
         if (COUNT) ncon[o] = nc[q];
     }
+    if (cost) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) m = max(m, lastc[q]);
+        m = __reduce_max_sync(FULL, m);
+        if (lane == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int w = 1; w < WARPS; ++w) m = max(m, wmax[w]);
+            cost[tile] = m;
+        }
+    }
 }
 
+// ---------------------------------------------------------------- adjoint
 // Adjoint of k_render_fwd for one tile, walking its list back to front from
-// the last contributor of any of its pixels.  Per (lane, Gaussian) the lane
-// accumulates, over its pixels, s = dL/dpower and the moments
-// sum s dx, sum s dy, sum s dx^2, sum s dx dy, sum s dy^2 (dx shared by the
-// column); each warp sums them with a fixed shuffle pattern, the warps'
-// sums are added in warp order, and the record of the pair is formed once
-// from the conic:
+// the last contributor of any of its pixels.  Per pixel the walk rebuilds T in
+// front of each Gaussian by division by (1 - alpha) and carries the scalar
+// b = B . dL/dC, B the colour behind the Gaussian (B = bg behind the last
+// contributor, B <- alpha c + (1 - alpha) B past each one), so that
+//   dL/dalpha = T (c . dL/dC - b),   b <- b + alpha (c . dL/dC - b),
+//   dL/dc = alpha T dL/dC,           dL/dpower = dL/dalpha alpha (0 if capped).
+// Per (lane, Gaussian) the lane accumulates over its pixels s = dL/dpower
+// and the moments sum s, sum s dy, sum s dy^2 (dx is shared by the column)
+// and the colour sums; each warp sums them with a fixed shuffle pattern, the
+// warps' sums are added in warp order, and the record of the pair is formed
+// once from the conic (a, b, c):
 //   dL/dmean = (a Sx + b Sy, b Sx + c Sy),
 //   dL/d(a, b, c) = (-Sxx / 2, -Sxy, -Syy / 2),
+//   dL/do = sum s / o   (alpha = o G: dalpha/do = G = alpha / o),
 // since power = -(a dx^2 + c dy^2) / 2 - b dx dy and dx = x - mean_x.
-constexpr int PPT = BWD_PPT;
-constexpr int WARPS = Band<BWD_PPT>::WARPS;
-constexpr int BWD_THREADS = Band<BWD_PPT>::THREADS;
-constexpr int BWD_BATCH = BWD_THREADS;          // records staged per round, one per thread
-
-__global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX, const uint32_t *__restrict__ ranges,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const float4 *__restrict__ sp, float bg0, float bg1,
-                                                        float bg2, const float *__restrict__ Tf,
-                                                        const uint32_t *__restrict__ last,
-                                                        const float *__restrict__ dimg,
-                                                        const uint8_t *__restrict__ skip,
-                                                        float4 *__restrict__ pair_grads,
-                                                        uint32_t *__restrict__ visited,
-                                                        uint8_t *__restrict__ ghit) {
-    __shared__ StageBuf<BWD_BATCH> s;
-    __shared__ float rec[WARPS][BWD_BATCH][9];
-    __shared__ int hit[WARPS][BWD_BATCH];
-    __shared__ int sskip[BWD_BATCH];
+// skip (nullable): no record for those Gaussians.  comp (nullable): the
+// forward's composited marks; a Gaussian without one changes no pixel, so it
+// is dropped from the walk before any arithmetic (skipped or not).  A skipped
+// Gaussian that is composited still enters T and b.  hit: set to 1 for every
+// Gaussian that gets a record with a contribution.  order (nullable): block b
+// walks tile order[b].
+template <int PPT>
+__global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H, int TX,
+                                                                  const uint32_t *__restrict__ ranges,
+                                                                  const uint32_t *__restrict__ vals,
+                                                                  const float4 *__restrict__ sp, float bg0, float bg1,
+                                                                  float bg2, const float *__restrict__ Tf,
+                                                                  const uint32_t *__restrict__ last,
+                                                                  const float *__restrict__ dimg,
+                                                                  const uint8_t *__restrict__ skip,
+                                                                  const uint8_t *__restrict__ comp,
+                                                                  float4 *__restrict__ pair_grads,
+                                                                  uint32_t *__restrict__ visited,
+                                                                  uint8_t *__restrict__ hitg,
+                                                                  const uint32_t *__restrict__ order) {
+    constexpr int NP = Band<PPT>::NP, WARPS = Band<PPT>::WARPS, BATCH = Band<PPT>::THREADS;
+    __shared__ Rec s[BATCH];
+    __shared__ float rec[WARPS][BATCH][9];
+    __shared__ uint8_t hit[WARPS][BATCH];
+    __shared__ uint8_t sflag[BATCH];                    // bit 0: skipped, bit 1: composited nowhere
     __shared__ uint32_t wmax[WARPS];
-    const int tile = blockIdx.x;
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int px, py0;
     pixel_coords<PPT>(tile, TX, px, py0);
     const uint32_t beg = ranges[2 * tile];
     const float fx = px + 0.5f, fy0 = py0 + 0.5f;
-    float T[PPT], dc0[PPT], dc1[PPT], dc2[PPT], B0[PPT], B1[PPT], B2[PPT];
+    const f2 FX = pk(fx, fx), ONE = pk(1.f, 1.f);
+    f2 FY[NP], T[NP], Bd[NP], D0[NP], D1[NP], D2[NP];
     uint32_t lastp[PPT];
     uint32_t mymax = 0;
     const size_t plane = (size_t)W * H;
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        const int py = py0 + q;
-        T[q] = 1.f; dc0[q] = dc1[q] = dc2[q] = 0.f; lastp[q] = 0;
-        B0[q] = bg0; B1[q] = bg1; B2[q] = bg2;          // colour behind the current Gaussian
-        if (px < W && py < H) {
-            const size_t o = (size_t)py * W + px;
-            T[q] = Tf[o];
-            lastp[q] = last[o];
-            dc0[q] = dimg[o];
-            dc1[q] = dimg[plane + o];
-            dc2[q] = dimg[2 * plane + o];
+    for (int p = 0; p < NP; ++p) {
+        float t[2] = {1.f, 1.f}, d0[2] = {0.f, 0.f}, d1[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f}, b[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = 2 * p + h, py = py0 + q;
+            lastp[q] = 0;
+            if (px < W && py < H) {
+                const size_t o = (size_t)py * W + px;
+                t[h] = Tf[o];
+                lastp[q] = last[o];
+                d0[h] = dimg[o];
+                d1[h] = dimg[plane + o];
+                d2[h] = dimg[2 * plane + o];
+            }
+            b[h] = fmaf(bg2, d2[h], fmaf(bg1, d1[h], bg0 * d0[h]));      // colour behind = background
+            mymax = max(mymax, lastp[q]);
         }
-        mymax = max(mymax, lastp[q]);
+        FY[p] = pk(fy0 + (float)(2 * p), fy0 + (float)(2 * p + 1));
+        T[p] = pk(t[0], t[1]);
+        Bd[p] = pk(b[0], b[1]);
+        D0[p] = pk(d0[0], d0[1]);
+        D1[p] = pk(d1[0], d1[1]);
+        D2[p] = pk(d2[0], d2[1]);
     }
     const uint32_t wm = __reduce_max_sync(FULL, mymax);
     if (lane == 0) wmax[warp] = wm;
@@ -247,89 +374,104 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
     for (int w = 0; w < WARPS; ++w) tmax = max(tmax, wmax[w]);
     const int n = (int)tmax;
     if (threadIdx.x == 0) visited[tile] = tmax;
-    for (int hi = n; hi > 0; hi -= BWD_BATCH) {
-        const int lo = max(0, hi - BWD_BATCH);
+    for (int hi = n; hi > 0; hi -= BATCH) {
+        const int lo = max(0, hi - BATCH);
         const int cnt = hi - lo;
         const int t = threadIdx.x;
-        float4 conic = make_float4(0.f, 0.f, 0.f, 0.f);   // thread t: raw conic of record lo + t
+        float4 conic = make_float4(0.f, 0.f, 0.f, 0.f);   // thread t: raw conic and opacity of record lo + t
+        float opac = 0.f;
         bool my_skip = true;
         uint32_t id = 0;
         if (t < cnt) {
             id = vals[beg + lo + t];
             my_skip = skip ? skip[id] != 0 : false;
-            const float4 g0 = sp[3 * (size_t)id];
-            s.g0[t] = g0;
-            conic = sp[3 * (size_t)id + 1];
-            s.k[t] = scaled_conic(conic, g0.z);
-            s.c[t] = sp[3 * (size_t)id + 2];
-            sskip[t] = my_skip;
+            const bool inert = comp ? comp[id] == 0 : false;
+            sflag[t] = (my_skip ? 1 : 0) | (inert ? 2 : 0);
+            if (!inert) {
+                const float4 g0 = sp[3 * (size_t)id];
+                conic = sp[3 * (size_t)id + 1];
+                opac = g0.z;
+                stage_rec(s[t], g0, conic, sp[3 * (size_t)id + 2], id);
+            }
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const uint32_t pos = (uint32_t)(lo + j);
-            if (!__any_sync(FULL, pos < mymax)) {
+            if ((sflag[j] & 2) || !__any_sync(FULL, pos < mymax)) {
                 if (lane == 0) hit[warp][j] = 0;
                 continue;
             }
-            const float4 g0 = s.g0[j], k = s.k[j], c = s.c[j];
-            const RowTerms r = row_terms(g0, k, fx);
-            float e2[PPT], dy[PPT];
+            const Rec r = s[j];
+            const Expo<NP> x = exponent<NP>(r, FX, FY);
             bool near = false;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                e2[q] = pixel_e2(g0, k, r, fy0 + (float)q, dy[q]);
-                near |= e2[q] >= k.w && pos < lastp[q];
+            for (int p = 0; p < NP; ++p) {
+                float e0, e1;
+                upk(x.e[p], e0, e1);
+                near |= (e0 >= r.kw && pos < lastp[2 * p]) || (e1 >= r.kw && pos < lastp[2 * p + 1]);
             }
             if (!__any_sync(FULL, near)) {              // no pixel of the band can take j
                 if (lane == 0) hit[warp][j] = 0;
                 continue;
             }
-            float S0 = 0.f, S1 = 0.f, S2 = 0.f, So = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+            const f2 Z = pk(0.f, 0.f);
+            f2 S0 = Z, S1 = Z, S2 = Z, G0 = Z, G1 = Z, G2 = Z;
             bool any = false;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                const PixelAlpha p = pixel_alpha(g0, e2[q], dy[q]);
-                const bool valid = pos < lastp[q] && p.ok;
-                any |= valid;
-                const float Tq = valid ? __fdividef(T[q], 1.f - p.alpha) : T[q];   // in front of j
-                T[q] = Tq;
-                const float av = valid ? p.alpha : 0.f;
-                const float w = av * Tq;
-                const float e0 = c.x - B0[q], e1 = c.y - B1[q], e2 = c.z - B2[q];
-                const float da = valid ? Tq * (dc0[q] * e0 + dc1[q] * e1 + dc2[q] * e2) : 0.f;
-                B0[q] = fmaf(av, e0, B0[q]);
-                B1[q] = fmaf(av, e1, B1[q]);
-                B2[q] = fmaf(av, e2, B2[q]);
-                gc0 = fmaf(w, dc0[q], gc0);
-                gc1 = fmaf(w, dc1[q], gc1);
-                gc2 = fmaf(w, dc2[q], gc2);
-                const float dav = p.capped ? 0.f : da;         // the 0.99 cap passes no gradient
-                So = fmaf(dav, p.G, So);                       // d opacity
-                const float sdp = dav * p.alpha;               // dL/dpower
-                const float tt = sdp * p.dy;
-                S0 += sdp;
-                S1 += tt;
-                S2 = fmaf(tt, p.dy, S2);
+            for (int p = 0; p < NP; ++p) {
+                float e0, e1, v0, v1, m0, m1;
+                upk(x.e[p], e0, e1);
+                upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
+                const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
+                const bool ok0 = pos < lastp[2 * p] && e0 <= 0.f && a0 >= ALPHA_MIN;
+                const bool ok1 = pos < lastp[2 * p + 1] && e1 <= 0.f && a1 >= ALPHA_MIN;
+                any |= ok0 | ok1;
+                const float ae0 = ok0 ? a0 : 0.f, ae1 = ok1 ? a1 : 0.f;
+                const f2 AE = pk(ae0, ae1);
+                const f2 AG = pk(v0 > ALPHA_MAX ? 0.f : ae0, v1 > ALPHA_MAX ? 0.f : ae1);   // the cap passes no gradient
+                upk(sub2(ONE, AE), m0, m1);
+                const f2 TQ = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));  // in front of j
+                T[p] = TQ;
+                const f2 cd = fma2(r.cr, D0[p], fma2(r.cg, D1[p], mul2(r.cb, D2[p])));
+                const f2 dot = sub2(cd, Bd[p]);
+                Bd[p] = fma2(AE, dot, Bd[p]);
+                const f2 w = mul2(AE, TQ);
+                G0 = fma2(w, D0[p], G0);
+                G1 = fma2(w, D1[p], G1);
+                G2 = fma2(w, D2[p], G2);
+                const f2 sdp = mul2(mul2(TQ, dot), AG);           // dL/dpower
+                const f2 tt = mul2(sdp, x.dy[p]);
+                S0 = add2(S0, sdp);
+                S1 = add2(S1, tt);
+                S2 = fma2(tt, x.dy[p], S2);
             }
             const bool any_j = __any_sync(FULL, any);   // the band composites j (skipped or not)
             if (lane == 0) hit[warp][j] = any_j;
-            if (!any_j || sskip[j]) continue;
-            const float Sx = r.dx * S0;
-            float v[8] = {Sx, S1, r.dx * Sx, r.dx * S1, S2, So, gc0, gc1};
+            if (!any_j || (sflag[j] & 1)) continue;
+            float h0, h1, dx, dxx;
+            upk(x.dx, dx, dxx);
+            upk(S0, h0, h1);
+            const float s0 = h0 + h1;
+            upk(S1, h0, h1);
+            const float s1 = h0 + h1;
+            upk(S2, h0, h1);
+            const float s2 = h0 + h1;
+            upk(G0, h0, h1);
+            const float g0 = h0 + h1;
+            upk(G1, h0, h1);
+            const float g1 = h0 + h1;
+            upk(G2, h0, h1);
+            const float g2 = h0 + h1;
+            const float sx = dx * s0;
+            float v[8] = {s0, sx, s1, dx * sx, dx * s1, s2, g0, g1};
             const float red = reduce_scatter8(v, lane);
-            const float red8 = warp_sum(gc2);
+            const float red8 = warp_sum(g2);
             if ((lane & 3) == 0) rec[warp][j][(lane >> 2) & 7] = red;
             if (lane == 0) rec[warp][j][8] = red8;
         }
         __syncthreads();
         // one record per visited list position: the tile's sum for that Gaussian
-        if (t < cnt && my_skip && ghit) {
-            bool composited = false;
-#pragma unroll
-            for (int w = 0; w < WARPS; ++w) composited |= hit[w][t] != 0;
-            if (composited) ghit[id] = 1;             // a skipped Gaussian some pixel composited
-        }
-        if (t < cnt && !my_skip) {
+        if (t < cnt && !my_skip && !(sflag[t] & 2)) {
             float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contributed = false;
 #pragma unroll
@@ -339,15 +481,60 @@ __global__ void __launch_bounds__(BWD_THREADS) k_render_bwd(int W, int H, int TX
 #pragma unroll
                 for (int q = 0; q < 9; ++q) m[q] += rec[w][t][q];
             }
-            if (ghit && contributed) ghit[id] = 1;
+            if (contributed) hitg[id] = 1;
+            // m = (S, Sx, Sy, Sxx, Sxy, Syy, dr, dg, db)
+            const float d_o = opac > 0.f ? __fdiv_rn(m[0], opac) : 0.f;
             float4 *d = pair_grads + 3 * (size_t)(beg + lo + t);
-            d[0] = make_float4(conic.x * m[0] + conic.y * m[1], conic.y * m[0] + conic.z * m[1], m[5], 0.f);
-            d[1] = make_float4(-0.5f * m[2], -m[3], -0.5f * m[4], 0.f);
+            d[0] = make_float4(conic.x * m[1] + conic.y * m[2], conic.y * m[1] + conic.z * m[2], d_o, 0.f);
+            d[1] = make_float4(-0.5f * m[3], -m[4], -0.5f * m[5], 0.f);
             d[2] = make_float4(m[6], m[7], m[8], 0.f);
         }
         __syncthreads();
     }
 }
+
+// ---------------------------------------------------------------- tile order
+// Counting sort of the tiles by descending cost in one block: bucket
+// min(cost, ORDER_BUCKETS - 1), heaviest bucket first.  The order inside a
+// bucket depends on atomic timing; no result depends on the order.
+constexpr int ORDER_BUCKETS = 1024;
+
+__global__ void __launch_bounds__(1024) k_tile_order(int n_tiles, const uint32_t *__restrict__ cost,
+                                                     uint32_t *__restrict__ order) {
+    __shared__ uint32_t cnt[ORDER_BUCKETS];
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    cnt[t] = 0;
+    __syncthreads();
+    for (int i = t; i < n_tiles; i += 1024) atomicAdd(&cnt[ORDER_BUCKETS - 1 - min(cost[i], ORDER_BUCKETS - 1u)], 1u);
+    __syncthreads();
+    // exclusive scan of the 1024 bucket counts
+    const uint32_t c = cnt[t];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    cnt[t] = x - c + (warp ? wsum[warp - 1] : 0u);
+    __syncthreads();
+    for (int i = t; i < n_tiles; i += 1024)
+        order[atomicAdd(&cnt[ORDER_BUCKETS - 1 - min(cost[i], ORDER_BUCKETS - 1u)], 1u)] = (uint32_t)i;
+}
+
+}  // namespace
 
 int check_render_args(const qn_camera *cam, const uint32_t *ranges, const uint32_t *vals, const qn_splat *sp) {
     QN_REQUIRE(cam, "camera is required");
@@ -359,36 +546,44 @@ int check_render_args(const qn_camera *cam, const uint32_t *ranges, const uint32
     return QN_OK;
 }
 
-}  // namespace
+int launch_render_bwd(const qn_camera *cam, const uint32_t *ranges, const uint32_t *vals, const qn_splat *splats,
+                      const float *bg, const float *T_final, const uint32_t *last, const float *d_img,
+                      const uint8_t *skip, const uint8_t *composited, const uint32_t *order,
+                      qn_splat *pair_grads, uint32_t *visited, uint8_t *hit, cudaStream_t stream) {
+    int st = check_render_args(cam, ranges, vals, splats);
+    if (st) return st;
+    QN_REQUIRE(T_final && last && d_img && bg && pair_grads, "null pointer argument");
+    QN_REQUIRE(((uintptr_t)pair_grads & 15) == 0, "pair records must be 16-byte aligned");
+    const int TX = (cam->width + QN_TILE - 1) / QN_TILE, TY = (cam->height + QN_TILE - 1) / QN_TILE;
+    constexpr int PPT = QN_BWD_PPT;
+    k_render_bwd<PPT><<<TX * TY, Band<PPT>::THREADS, 0, stream>>>(
+        cam->width, cam->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg[0], bg[1], bg[2],
+        T_final, last, d_img, skip, composited, reinterpret_cast<float4 *>(pair_grads), visited, hit, order);
+    return check_launch("qn_render_bwd");
+}
+
 }  // namespace qn
 
 extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
                              const qn_splat *splats, const float *bg_host, float *img, float *T_final,
-                             uint32_t *last, uint32_t *n_contrib, qn_stream_t stream) {
+                             uint32_t *last, uint32_t *n_contrib, uint8_t *composited, const uint32_t *tile_order,
+                             uint32_t *tile_cost, qn_stream_t stream) {
     int st = qn::check_render_args(cam_host, ranges, vals, splats);
     if (st) return st;
     QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
     const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
-    auto kern = n_contrib ? qn::k_render_fwd<true> : qn::k_render_fwd<false>;
-    kern<<<TX * TY, qn::Band<qn::FWD_PPT>::THREADS, 0, qn::as_stream(stream)>>>(cam_host->width, cam_host->height, TX, ranges, vals,
-                                                   reinterpret_cast<const float4 *>(splats), bg_host[0], bg_host[1],
-                                                   bg_host[2], img, T_final, last, n_contrib);
+    constexpr int PPT = QN_FWD_PPT;
+    auto kern = n_contrib ? qn::k_render_fwd<true, PPT> : qn::k_render_fwd<false, PPT>;
+    kern<<<TX * TY, qn::Band<PPT>::THREADS, 0, qn::as_stream(stream)>>>(
+        cam_host->width, cam_host->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg_host[0],
+        bg_host[1], bg_host[2], img, T_final, last, n_contrib, composited, tile_order, tile_cost);
     return qn::check_launch("qn_render_fwd");
 }
 
-extern "C" int qn_render_bwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
-                             const qn_splat *splats, const float *bg_host, const float *T_final,
-                             const uint32_t *last, const float *d_img, const uint8_t *skip,
-                             qn_splat *pair_grads, uint32_t *tile_visited, uint8_t *gauss_hit,
-                             qn_stream_t stream) {
-    int st = qn::check_render_args(cam_host, ranges, vals, splats);
-    if (st) return st;
-    QN_REQUIRE(T_final && last && d_img && bg_host && pair_grads && tile_visited, "null pointer argument");
-    QN_REQUIRE(((uintptr_t)pair_grads & 15) == 0, "pair_grads must be 16-byte aligned");
-    const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
-    qn::k_render_bwd<<<TX * TY, qn::BWD_THREADS, 0, qn::as_stream(stream)>>>(
-        cam_host->width, cam_host->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg_host[0],
-        bg_host[1], bg_host[2], T_final, last, d_img, skip, reinterpret_cast<float4 *>(pair_grads), tile_visited,
-        gauss_hit);
-    return qn::check_launch("qn_render_bwd");
+extern "C" int qn_tile_order(int32_t n_tiles, const uint32_t *tile_cost, uint32_t *tile_order, qn_stream_t stream) {
+    QN_REQUIRE(n_tiles >= 0 && n_tiles <= QN_MAX_TILES_X * QN_MAX_TILES_Y, "n_tiles out of range");
+    QN_REQUIRE(n_tiles == 0 || (tile_cost && tile_order), "null pointer argument");
+    if (n_tiles == 0) return QN_OK;
+    qn::k_tile_order<<<1, 1024, 0, qn::as_stream(stream)>>>(n_tiles, tile_cost, tile_order);
+    return qn::check_launch("qn_tile_order");
 }

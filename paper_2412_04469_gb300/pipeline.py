@@ -52,6 +52,14 @@ class HParams:
     lr_decoder: tuple = (1e-3, 1e-4, 1e-4, 1e-3)
     blur: float = 0.3
     bg: tuple = (0.0, 0.0, 0.0)
+    # the forward marks the Gaussians some pixel composites and the adjoint
+    # drops the others from its per-tile walk (the same result; the marks
+    # cost the forward about what they save the adjoint, so plain training
+    # leaves them off and the learned skip, which needs them, turns them on)
+    mark_composited: bool = False
+    # the compositing kernels start their tiles heaviest first (by the
+    # per-tile visited prefixes of the last forward; the same result)
+    order_tiles: bool = True
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
@@ -223,11 +231,15 @@ class Rasterizer:
         self.workspace = torch.zeros(max(ws, 256), device=dev, dtype=torch.uint8)
         self.ranges = torch.zeros((self.TX * self.TY, 2), device=dev, dtype=torch.int32)
         self.n_pairs = torch.zeros(1, device=dev, dtype=torch.int64)
-        self.tile_visited = torch.zeros(self.TX * self.TY, device=dev, dtype=torch.int32)
         self.ranges_masked = torch.zeros_like(self.ranges)         # masked iterations: inactive tiles emptied
         self.rects_sel = torch.zeros_like(self.rects)              # mask building: dynamic Gaussians' rects
         self.mask_tmp = torch.zeros((height, width), device=dev, dtype=torch.uint8)
-        self.gauss_hit = torch.zeros(nn, device=dev, dtype=torch.uint8)      # Gaussians some pixel composited
+        self.composited = torch.zeros(nn, device=dev, dtype=torch.uint8)     # Gaussians some pixel composited
+        # tiles by descending work: written after each forward from its
+        # per-tile visited prefix (tile_cost), read by the adjoint of the same
+        # iteration and the forward of the next (neighbouring views cost alike)
+        self.tile_cost = torch.zeros(self.TX * self.TY, device=dev, dtype=torch.int32)
+        self.tile_order = torch.arange(self.TX * self.TY, device=dev, dtype=torch.int32)
         self.keep_keys = keep_keys
         self.set_capacity(pair_capacity)
         self.img = torch.zeros((3, height, width), device=dev)
@@ -254,9 +266,18 @@ class Rasterizer:
                              self.workspace, self.capacity, self.vals, self.keys, self.ranges, self.n_pairs, sync,
                              stream)
 
-    def render_fwd(self, cam, bg, n_contrib=None, stream=None, ranges=None):
+    def render_fwd(self, cam, bg, n_contrib=None, stream=None, ranges=None, mark=False, order=False):
+        """Compositing; with mark, `composited` holds afterwards the Gaussians
+        some pixel composited; with order, the tiles start heaviest first (by
+        the previous ordered forward's costs) and tile_order is refreshed from
+        this forward's costs."""
+        if mark:
+            self.composited.zero_()
         B.qn_render_fwd(cam, self.ranges if ranges is None else ranges, self.vals, self.splats, bg, self.img,
-                        self.T_final, self.last, n_contrib, stream)
+                        self.T_final, self.last, n_contrib, stream, composited=self.composited if mark else None,
+                        tile_order=self.tile_order if order else None, tile_cost=self.tile_cost if order else None)
+        if order:
+            B.qn_tile_order(self.TX * self.TY, self.tile_cost, self.tile_order, stream)
 
     def loss_grad(self, target, w=1.0, mse=False, stream=None):
         B.qn_image_loss(self.img.numel(), self.img, target, w, mse, self.loss, self.d_img, stream)
@@ -277,20 +298,24 @@ class Rasterizer:
         if lambda_dssim > 0:
             self.dssim_grad(target, lambda_dssim, mask, stream)
 
-    def render_bwd(self, cam, bg, skip=None, stream=None, ranges=None):
-        """Compositing adjoint: per-pair records, then the per-Gaussian gather."""
-        self.render_bwd_pairs(cam, bg, skip, stream, ranges)
-        self.gather(skip, stream)
+    def render_bwd(self, cam, bg, skip=None, stream=None, ranges=None, marks=False, order=False):
+        """Compositing adjoint into d_splats; with marks, the adjoint drops the
+        Gaussians the last marked forward did not composite; with order, the
+        tiles start in tile_order."""
+        B.qn_render_bwd(cam, self.n, self.rects, self.ranges if ranges is None else ranges, self.vals, self.splats,
+                        bg, self.T_final, self.last, self.d_img, skip, self.composited if marks else None,
+                        self.workspace, self.pair_grads, self.d_splats, stream,
+                        tile_order=self.tile_order if order else None)
 
-    def render_bwd_pairs(self, cam, bg, skip=None, stream=None, ranges=None):
-        self.gauss_hit.zero_()
-        B.qn_render_bwd(cam, self.ranges if ranges is None else ranges, self.vals, self.splats, bg, self.T_final,
-                        self.last, self.d_img, skip, self.pair_grads, self.tile_visited, stream,
-                        gauss_hit=self.gauss_hit)
+    def render_bwd_pairs(self, cam, bg, skip=None, stream=None, ranges=None, marks=False, order=False):
+        """First pass of render_bwd (per-pair records)."""
+        B.qn_render_bwd_pairs(cam, self.n, self.ranges if ranges is None else ranges, self.vals, self.splats, bg,
+                              self.T_final, self.last, self.d_img, skip, self.composited if marks else None,
+                              self.workspace, self.pair_grads, stream, tile_order=self.tile_order if order else None)
 
-    def gather(self, skip=None, stream=None):
-        B.qn_bin_gather(self.n, self.rects, self.TX, self.TY, self.workspace, self.tile_visited, self.pair_grads,
-                        skip, self.d_splats, stream, gauss_hit=self.gauss_hit)
+    def gather(self, cam, skip=None, stream=None):
+        """Second pass of render_bwd (per-Gaussian sums)."""
+        B.qn_render_bwd_gather(cam, self.n, self.rects, skip, self.workspace, self.pair_grads, self.d_splats, stream)
 
     def project_bwd(self, attrs, cam, blur, d_attrs, skip=None, stream=None):
         B.qn_project_bwd(self.n, self.S, self.sh_degree, attrs, cam, blur, self.d_splats, skip, d_attrs, stream)
@@ -365,21 +390,24 @@ class ViewMask:
 
 
 def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=None, stream=None,
-                       mask: ViewMask | None = None, unskip: bool = False):
+                       mask: ViewMask | None = None, unskip: bool = False, mark: bool = False):
     """One view of Eq. 11's optimisation: forward, Eq. 3's loss ((1 - lambda)
     L1 + lambda D-SSIM) + lambda_reg L_reg (the L_reg gradient is folded into
-    the gate adjoint), full
-    adjoint and the Adam step.  No host synchronisation.  Gaussians with skip
-    set are frozen: no gradient, no update, and their decoded columns are
-    reused (frame.attrs must hold their A_t, e.g. from a decode without
-    skip).  With unskip, a skipped Gaussian that some pixel composites in
-    this iteration is un-skipped before its gradient is gathered (the
-    compositing adjoint runs without the skip mask, which costs nothing for
-    the Gaussians no pixel composites), so it takes this iteration's update
-    as plain training does and trains like the others from then on.  With a
-    mask (Sec. 3.3's masked training) only the masked tiles are composited
-    and the loss is the mean over the masked pixels."""
+    the gate adjoint), full adjoint and the Adam step.  No host
+    synchronisation.  Gaussians with skip set are frozen: no gradient, no
+    update, and their decoded columns are reused (frame.attrs must hold their
+    A_t, e.g. from a decode without skip).  With unskip, a skipped Gaussian
+    that some pixel composites in this iteration is un-skipped before the
+    adjoint (the forward marks the composited Gaussians), so it takes this
+    iteration's update as plain training does and trains like the others from
+    then on; the adjoint drops the Gaussians left skipped, which no pixel
+    composites.  With HParams.mark_composited (or mark) the forward marks the
+    composited Gaussians in rast.composited and the adjoint drops the others.
+    With a mask (Sec. 3.3's masked training) only the masked tiles are
+    composited and the loss is the mean over the masked pixels."""
     hp = frame.hp
+    unskip = unskip and skip is not None
+    mark = mark or unskip or hp.mark_composited
     frame.decode(stream, skip, train=True)
     rast.project(frame.attrs, cam, hp.blur, stream)
     rast.bin_sort(False, stream)
@@ -387,14 +415,11 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     if mask is not None:
         rast.mask_ranges(mask, stream)
         ranges = rast.ranges_masked
-    rast.render_fwd(cam, hp.bg, stream=stream, ranges=ranges)
+    rast.render_fwd(cam, hp.bg, stream=stream, ranges=ranges, mark=mark, order=hp.order_tiles)
     rast.photometric_loss(target, hp.lambda_dssim, mask, stream)
-    if skip is not None and unskip:
-        rast.render_bwd_pairs(cam, hp.bg, None, stream, ranges=ranges)
-        B.qn_clear_marked(rast.n, rast.gauss_hit, skip, stream)
-        rast.gather(skip, stream)
-    else:
-        rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges)
+    if unskip:
+        B.qn_clear_marked(rast.n, rast.composited, skip, stream)
+    rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges, marks=mark, order=hp.order_tiles)
     rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
     frame.decode_bwd(skip, stream)
     frame.adam(skip, stream)
@@ -416,20 +441,20 @@ class IterationGraph:
         self.pool = None
         self.warm = False
 
-    def _signature(self, target, skip, mask, unskip):
+    def _signature(self, target, skip, mask, unskip, mark):
         r = self.rast
         return (target.data_ptr(), None if skip is None else skip.data_ptr(), r.vals.data_ptr(),
                 r.pair_grads.data_ptr(), r.workspace.data_ptr(), None if mask is None else mask.pixel.data_ptr(),
-                bool(unskip))
+                bool(unskip), bool(mark))
 
-    def run(self, key, cam, target, skip=None, mask=None, unskip=False):
-        sig = self._signature(target, skip, mask, unskip)
+    def run(self, key, cam, target, skip=None, mask=None, unskip=False, mark=False):
+        sig = self._signature(target, skip, mask, unskip, mark)
         ent = self.graphs.get(key)
         if ent is None or ent[1] != sig:
             if not self.warm:
                 # one eager iteration first: lazily allocated scratch must
                 # exist before capture; it is a real training step
-                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip)
+                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip, mark=mark)
                 self.warm = True
                 return
             if self.pool is None:
@@ -437,7 +462,7 @@ class IterationGraph:
             g = torch.cuda.CUDAGraph()
             torch.cuda.synchronize()
             with torch.cuda.graph(g, pool=self.pool):
-                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip)
+                training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip, mark=mark)
             ent = (g, sig, cam, target, skip, mask)     # keep what the graph points at alive
             self.graphs[key] = ent
         ent[0].replay()

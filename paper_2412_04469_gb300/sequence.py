@@ -301,11 +301,12 @@ class StreamingTrainer:
             unskip = skip is not None and self.cfg.unskip_composited
             if self.cfg.graphs:
                 self.graphs.run((v, skip is not None, mask is not None), self.cams[v], self.tgt_cur[v], skip, mask,
-                                unskip=unskip)
+                                unskip=unskip, mark=self._track_hits)
             else:
-                training_iteration(f, r, self.cams[v], self.tgt_cur[v], skip, mask=mask, unskip=unskip)
+                training_iteration(f, r, self.cams[v], self.tgt_cur[v], skip, mask=mask, unskip=unskip,
+                                   mark=self._track_hits)
             if self._track_hits:
-                B.qn_or_marks(self.cfg.n, r.gauss_hit, self.frame_hit)
+                B.qn_or_marks(self.cfg.n, r.composited, self.frame_hit)
 
     def _partition(self):
         """Reorders the Gaussians so that the skipped ones form one contiguous

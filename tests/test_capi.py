@@ -62,12 +62,22 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp),
                                        None, None, None, None, None) == B.QN_ERR_INVALID_ARG
     assert b"category" in B.lib().qn_last_error()
-    assert B.lib().qn_render_bwd(None, None, None, None, None, None, None, None, None, None, None, None, None) == \
+    assert B.lib().qn_render_bwd(None, 0, None, None, None, None, None, None, None, None, None, None, None, None, 0,
+                                 None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_render_bwd(C.byref(cam), 4, 16, 16, 16, 32, None, 64, 128, 256, None, None, None, 512, 0,
+                                 1024, 2048, None) == B.QN_ERR_INVALID_ARG
+    assert b"workspace too small" in B.lib().qn_last_error()
+    assert B.lib().qn_render_bwd_gather(C.byref(cam), 4, 16, None, 256, 1 << 20, 1024, 40, None) == \
         B.QN_ERR_INVALID_ARG
+    assert b"misaligned" in B.lib().qn_last_error()
+    assert B.lib().qn_tile_order(-1, None, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_tile_order(4, None, 16, None) == B.QN_ERR_INVALID_ARG
     bg = (C.c_float * 3)()
-    assert B.lib().qn_render_fwd(C.byref(cam), 16, None, 32, bg, 64, 128, 256, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_render_fwd(C.byref(cam), 16, None, 32, bg, 64, 128, 256, None, None, None, None, None) == \
+        B.QN_ERR_INVALID_ARG
     assert b"vals" in B.lib().qn_last_error()                                        # sorted pair values missing
-    assert B.lib().qn_render_fwd(C.byref(cam), 16, 16, 40, bg, 64, 128, 256, None, None) == B.QN_ERR_INVALID_ARG
+    assert B.lib().qn_render_fwd(C.byref(cam), 16, 16, 40, bg, 64, 128, 256, None, None, None, None, None) == \
+        B.QN_ERR_INVALID_ARG
     assert b"aligned" in B.lib().qn_last_error()                                     # splats misaligned
     assert B.lib().qn_bin_sort(4, 16, 1, 32, 4, 4, 256, 16, 1 << 40, 64, None, 128, 256, None, None) == \
         B.QN_ERR_INVALID_ARG                                                          # workspace too small

@@ -197,8 +197,10 @@ def test_unskip_within_iteration_matches_plain_for_composited():
     """Every Gaussian marked skipped, one iteration with unskip: exactly the
     Gaussians some pixel composites are un-skipped, and they -- with the
     shared decoders -- take the update plain training gives them (the
-    compositing adjoint ran without the mask, the gather and every later
-    stage with it); the others stay frozen at their initial values."""
+    forward marks them, they are un-skipped before the compositing adjoint,
+    and the adjoint, which drops the Gaussians left skipped, and every later
+    stage run with the mask); the others stay frozen at their initial
+    values."""
     from paper_2412_04469_gb300.pipeline import QueenFrame, Rasterizer, training_iteration
     from paper_2412_04469_gb300.synthetic import DecoderLayout
     n, deg, W, H = 3000, 1, 160, 120
@@ -215,13 +217,13 @@ def test_unskip_within_iteration_matches_plain_for_composited():
         r.size_for_views(f.attrs, [cam], f.hp.blur)
         skip = torch.ones(f.S, device="cuda", dtype=torch.uint8) if mode == "unskip" else None
         la0 = f.log_alpha.clone()
-        training_iteration(f, r, cam, tgt, skip, unskip=mode == "unskip")
+        training_iteration(f, r, cam, tgt, skip, unskip=mode == "unskip", mark=True)
         torch.cuda.synchronize()
         arms[mode] = (f, r, skip, la0)
     fp, rp, _, _ = arms["plain"]
     fu, ru, sk, la0 = arms["unskip"]
-    hit = ru.gauss_hit[:n].bool()
-    assert torch.equal(rp.gauss_hit[:n], ru.gauss_hit[:n])
+    hit = ru.composited[:n].bool()
+    assert torch.equal(rp.composited[:n], ru.composited[:n])
     assert 100 < int(hit.sum()) < n                   # some composited, some not
     assert torch.equal(sk[:n].bool(), ~hit)           # exactly the composited ones un-skipped
     h = hit.cpu().numpy()

@@ -233,11 +233,28 @@ def test_termination_product_near_the_bound_is_flagged():
         assert fr == flag and last == n_drawn, (d, fr, last)
 
 
+def test_termination_margin_is_separate_from_the_alpha_margin():
+    # eps_t alone governs the termination flag; eps alone the alpha flags
+    d = 0.5 * EPS_A
+    a4 = 1 - 1e-4 * (1 + d) / _t3()
+    pr = splats([(100.5, 60.5)] * 4, 1e6, [0.9, 0.9, 0.9, a4], [1.0, 2.0, 3.0, 4.0])
+    assert oracle.render_fwd(pr, eps=EPS_A / 10, eps_t=EPS_A, eps_d=EPS_D)[3][60, 100] == 2
+    assert oracle.render_fwd(pr, eps=EPS_A, eps_t=EPS_A / 10, eps_d=EPS_D)[3][60, 100] == 0
+    pr = splats([(100.5, 60.5)], 1e6, [1 / 255 * (1 + 0.5 * EPS_A)], [1.0])
+    assert oracle.render_fwd(pr, eps=EPS_A, eps_t=0.0, eps_d=EPS_D)[3][60, 100] == 1
+    assert oracle.render_fwd(pr, eps=EPS_A / 10, eps_t=1.0, eps_d=EPS_D)[3][60, 100] == 0
+
+
 def test_near_equal_depths_of_consecutive_contributors_are_flagged():
     for rel, flag in ((0.5 * EPS_D, 4), (3 * EPS_D, 0)):
         pr = splats([(100.5, 60.5)] * 2, 1e6, [0.5, 0.5], [1.0, 1.0 * (1 + rel)])
         _, _, last, fr = _pixel(pr)
         assert fr == flag and last == 2, (rel, fr)
+    # depths both sides share (the GPU's own FP32 values) order alike: eps_d < 0 flags no tie
+    pr = splats([(100.5, 60.5)] * 2, 1e6, [0.5, 0.5], [1.0, 1.0])
+    img, T, last, frag = oracle.render_fwd(pr, eps=EPS_A, eps_d=-1.0)
+    assert frag[60, 100] == 0 and last[60, 100] == 2
+    assert _pixel(pr)[3] == 4
     # equal-depth non-contributors do not count: the second is below 1/255
     pr = splats([(100.5, 60.5)] * 2, 1e6, [0.5, 0.001], [1.0, 1.0])
     assert _pixel(pr)[3] == 0

@@ -2,15 +2,17 @@
 memory (allocator hooks, plugins inside another application's memory pool,
 real-time loops), using the library's fixed device workspace.
 
-Checked through the C ABI against qn_bin_sort with a caller workspace, on two
-calls in a row (a large problem, then a small one, so stale contents of the
-shared array would show), bit for bit like the rest of the integer binning
-tests.  The file is named to be collected last.
+Checked through the C ABI, bit for bit like the rest of the integer binning
+tests, against the oracle's stable sort and against qn_bin_sort with a caller
+workspace, on two calls in a row (a large problem, then a small one, so
+stale contents of the shared array would show).  The file is named to be
+collected last.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2412_04469_gb300 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +55,11 @@ def _compare(n, tx, ty, seed, ext):
     assert got1 == got2 == P
     assert torch.equal(v1[:P], v2[:P]) and torch.equal(k1[:P], k2[:P])
     assert torch.equal(r1, r2) and torch.equal(p1, p2)
+    keys, vals, ranges = oracle.bin_sort(sp[:n, 3].cpu().numpy(), rc[:n].cpu().numpy().T, tx, ty)
+    assert keys.size == P
+    assert np.array_equal(v2[:P].cpu().numpy().view(np.uint32), vals)
+    assert np.array_equal(k2[:P].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(r2.cpu().numpy().view(np.uint32), ranges)
 
 
 def test_noalloc_matches_workspace_version_twice():
