@@ -38,7 +38,9 @@ L2_FLUSH_BYTES = 256 << 20
 # the reference arm times whole oracle iterations when its K + W steps fit in this
 REF_WHOLE_BUDGET_S = 300.0
 # kernels each stage launches (memsets are not counted)
-KERNELS_PER_STAGE = {"decode": 1, "project": 1, "bin_sort": 17, "render_fwd": 1, "loss": 4, "render_bwd": 1,
+# kernels each stage launches (memsets are not counted); the step decodes and
+# projects in one kernel
+KERNELS_PER_STAGE = {"decode_project": 1, "bin_sort": 17, "render_fwd": 2, "loss": 4, "render_bwd": 1,
                      "gather": 1, "project_bwd": 1, "decode_bwd": 2, "adam": 2}
 STAGES = list(KERNELS_PER_STAGE)
 # DRAM bytes per launch of a kernel on the full workload, from one ncu capture
@@ -211,8 +213,8 @@ def run_gpu(args):
         """One iteration issued stage by stage with an event between stages."""
         c = cams[v]
         mk, od = hp.mark_composited, hp.order_tiles
-        calls = (lambda: frame.decode(train=True), lambda: rast.project(frame.attrs, c, hp.blur),
-                 lambda: rast.bin_sort(False), lambda: rast.render_fwd(c, hp.bg, mark=mk, order=od),
+        calls = (lambda: frame.decode_project(rast, c), lambda: rast.bin_sort(False),
+                 lambda: rast.render_fwd(c, hp.bg, mark=mk, order=od),
                  lambda: rast.photometric_loss(targets[v], hp.lambda_dssim),
                  lambda: rast.render_bwd_pairs(c, hp.bg, marks=mk, order=od), lambda: rast.gather(c),
                  lambda: rast.project_bwd(frame.attrs, c, hp.blur, frame.d_attrs), lambda: frame.decode_bwd(),
@@ -334,7 +336,9 @@ def run_gpu(args):
     # algorithmic bytes per launch: what each stage must read and write once
     # (a projected record or a pair's gradient record is 48 bytes)
     algo_bytes = {
-        "decode": 620.0 * n, "project": 300.0 * n, "bin_sort": 20.0 * n + 36.0 * P,
+        # read A_{t-1} 236 + latents 128 + lp 12 + log alpha 4, write the 2D record 48
+        # (and A_t 236 for the projection adjoint)
+        "decode_project": (428.0 + 236.0) * n, "bin_sort": 20.0 * n + 36.0 * P,
         "render_fwd": 20.0 * px + 4.0 * Pvis + 48.0 * n_vis,
         # L1: img, target, d_img; D-SSIM: img, target, 3 maps out, 3 maps in, img, target, d_img += (3 channels)
         "loss": 36.0 * px + (144.0 * px if hp.lambda_dssim > 0 else 0.0),
@@ -360,14 +364,24 @@ def run_gpu(args):
     alu = {"kernel": "render_bwd", "achieved": round(flops_bwd / (avg["render_bwd"] * 1e-3) / 1e12, 3),
            "peak": round(fp32_peak, 2), "unit": "TFLOP/s"}
     alu["frac"] = round(alu["achieved"] / alu["peak"], 4)
+    # special-function unit: one ex2 per alpha evaluation, one reciprocal per
+    # contributing evaluation (T rebuilt in front of the Gaussian), against 32
+    # MUFU results per SM and clock (an independent-chain ex2.approx loop
+    # measures 30.4 on this part)
+    sfu_ops = float(np.mean(last_sum) + np.mean(contrib_sum))
+    sfu = {"kernel": "render_bwd", "achieved": round(sfu_ops / (avg["render_bwd"] * 1e-3) / 1e12, 3),
+           "peak": round(n_sm * 32 * sm_mhz * 1e6 / 1e12, 3), "unit": "Tops/s",
+           "peak_source": f"{n_sm} SM x 32 MUFU results x median SM clock"}
+    sfu["frac"] = round(sfu["achieved"] / sfu["peak"], 4)
     if dom == "render_bwd" and alu["frac"] > roof["frac"]:
         roof_alu = dict(roof)
         roof = {"bound": "alu", "kernel": dom, "achieved": alu["achieved"], "peak": alu["peak"],
                 "unit": "TFLOP/s", "frac": alu["frac"], "peak_source": f"{n_sm} SM x 128 FP32 lanes x 2 x median SM clock",
                 "traffic": ncu_traffic(dom), "algorithmic_bytes": algo_bytes[dom],
-                "hbm": {k: roof_alu[k] for k in ("achieved", "peak", "unit", "frac")}}
+                "hbm": {k: roof_alu[k] for k in ("achieved", "peak", "unit", "frac")}, "sfu": sfu}
     else:
         roof["alu_render_bwd"] = alu
+        roof["sfu_render_bwd"] = sfu
 
     value = job_rate(world, args.steps, max_ms)
     launches = args.steps * (sum(KERNELS_PER_STAGE.values()) - (2 if hp.lambda_dssim == 0 else 0)
@@ -425,9 +439,10 @@ def run_sequence(args):
         cfg = SequenceConfig(n=n, sh_degree=deg, width=W, height=H, views=V, frames=30, iters=args.seq_iters,
                              frac_dynamic=0.05)
     else:
-        cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters)
+        cfg = SequenceConfig(frames=args.seq_frames, iters=args.seq_iters, frac_dynamic=args.seq_dynamic)
     t0 = time.perf_counter()
-    out = compare(cfg, extra_thresholds=args.seq_extra_threshold, masked_fractions=args.seq_masked)
+    out = compare(cfg, extra_thresholds=args.seq_extra_threshold, masked_fractions=args.seq_masked,
+                  learned=not args.seq_masked_only, no_unskip=not args.seq_masked_only)
 
     def arm(summary, learned, thr):
         skip = [r for r in learned if r.t > cfg.train_frames]
@@ -451,7 +466,10 @@ def run_sequence(args):
                 "frame_s_learned": [round(r.seconds, 4) for r in skip],
                 "s_per_frame_learned_kept": round(float(np.mean(kept)), 4) if kept else None,
                 "fallback_dpsnr_train_before": [round(r.psnr_skip_train - r.psnr_plain_train, 4)
-                                                for r in skip if r.fallback]}
+                                                for r in skip if r.fallback],
+                # the compositing adjoint of one view at each skip frame's end, with and without the skip
+                "render_bwd_ms_skip": round(summary["render_bwd_ms_skip"], 4),
+                "render_bwd_ms_plain": round(summary["render_bwd_ms_plain"], 4)}
 
     res = {"config": {"n_gaussians": cfg.n, "sh_degree": cfg.sh_degree, "width": cfg.width, "height": cfg.height,
                       "views": cfg.views, "frames": cfg.frames, "iters_per_frame": cfg.iters,
@@ -459,10 +477,18 @@ def run_sequence(args):
                       "max_dpsnr": cfg.max_dpsnr, "fallback_psnr": cfg.fallback_psnr,
                       "dpsnr_reference": "plain gated training of the same frame from the same state",
                       "timed": "training work only (PSNR evaluation and the reference run excluded)",
-                      "launch": "CUDA graph replays" if cfg.graphs else "eager"},
-           "configured": arm(out, out["learned"], cfg.threshold)}
+                      "launch": "CUDA graph replays" if cfg.graphs else "eager"}}
+    if "learned" in out:
+        res["configured"] = arm(out, out["learned"], cfg.threshold)
     for thr, v in out["by_threshold"].items():
         res[f"threshold_{thr:g}"] = arm(v, v["learned"], thr)
+    if "rule" in out:
+        # the non-learned skip: what the previous frame's label called static
+        res["rule_previous_label"] = arm(out["rule"], out["rule"]["learned"], None)
+    if "no_unskip" in out:
+        # the learned skip with composited skipped Gaussians kept skipped: the
+        # compositing adjoint drops their gradients, the frame may fall back
+        res["learned_no_unskip"] = arm(out["no_unskip"], out["no_unskip"]["learned"], cfg.threshold)
     plain = out["plain"]
     if cfg.packet:
         res["packet"] = {
@@ -738,14 +764,19 @@ def main():
     ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-seq", action="store_true", help="skip the learned-skip sequence comparison")
-    ap.add_argument("--seq-frames", type=int, default=16, help="frames of the learned-skip sequence comparison")
+    ap.add_argument("--seq-frames", type=int, default=60, help="frames of the learned-skip sequence comparison")
     ap.add_argument("--seq-iters", type=int, default=250, help="training iterations per frame in that comparison")
     ap.add_argument("--seq-config", default="full", choices=["full", "large"],
-                    help="sequence of the learned-skip comparison: the 300k one (16 frames by default) or the "
+                    help="sequence of the learned-skip comparison: the 300k one (60 frames by default) or the "
                          "1M-Gaussian 1920x1080 one (30 frames, 5%% dynamic)")
-    ap.add_argument("--seq-masked", type=float, nargs="*", default=[0.3],
+    ap.add_argument("--seq-dynamic", type=float, default=0.10,
+                    help="fraction of the Gaussians that move in the 300k sequence (the ones nearest the middle "
+                         "of the face the cameras see)")
+    ap.add_argument("--seq-masked-only", action="store_true",
+                    help="sequence: the plain and masked-training arms only (no skip arms)")
+    ap.add_argument("--seq-masked", type=float, nargs="*", default=[],
                     help="fractions of iterations trained on Sec. 3.3's adaptive masks (plain gating otherwise)")
-    ap.add_argument("--seq-extra-threshold", type=float, nargs="*", default=[0.97],
+    ap.add_argument("--seq-extra-threshold", type=float, nargs="*", default=[],
                     help="further skip thresholds to run in that comparison (same plain arm)")
     ap.add_argument("--quick", action="store_true",
                     help="one view, timed steps only (for profiler captures); prints stage times")

@@ -199,6 +199,32 @@ int qn_project_bwd(int32_t n, int32_t n_stride, int32_t sh_degree, const float *
                    const qn_camera *cam_host, float blur, const qn_splat *d_splats,
                    const uint8_t *skip, float *d_attrs, qn_stream_t stream);
 
+/*
+ * qn_decode_residuals then qn_project in one pass (Eq. 4-8, then Eq. 1): each
+ * block stages a tile of 64 Gaussians' columns of prev, lat and lp in shared
+ * memory, adds the residuals there with the same operations in the same
+ * order as qn_decode_residuals, and projects the result as qn_project does,
+ * so gate, lreg, out, splats and rects equal those of the two calls bit for
+ * bit (lreg up to the order of its float sum).  A_t is not read back: the
+ * projection reads the staged tile.
+ *   Arguments as for qn_decode_residuals and qn_project (n_attr ==
+ *   11 + 3 (sh_degree + 1)^2).  out [n_attr][n_stride] (nullable) receives
+ *   A_t for the projection adjoint; it may not alias prev.
+ *   skip (nullable): skipped Gaussians keep their gate entries and add
+ *   nothing to lreg, but unlike qn_decode_residuals they are decoded,
+ *   projected and written to out like the rest (their residual parameters
+ *   are frozen, so they reproduce the A_t of the last call that trained them).
+ * prev, lat, lp, splats and rects must be 16-byte aligned (the staging copies
+ * 16-byte chunks); n_stride is a multiple of 4 as everywhere.
+ * Errors: QN_ERR_INVALID_ARG as for the two calls, and for misaligned pointers.
+ */
+int qn_decode_project(int32_t n, int32_t n_stride, int32_t n_attr, int32_t sh_degree, const float *prev,
+                      const float *lat, const uint16_t *dec, const qn_decoder_layout *layout_host,
+                      const float *lp, const float *log_alpha, const qn_gate_params *gate_host,
+                      const uint8_t *skip, const qn_camera *cam_host, float blur, int32_t tight_rects,
+                      float *gate, float *lreg, float *out, qn_splat *splats, int32_t *rects,
+                      qn_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Tile binning -- the tile-based rasterizer the paper builds on (Sec. 4).    */
 /* ------------------------------------------------------------------------ */

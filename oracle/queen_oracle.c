@@ -835,11 +835,17 @@ void or_render_fwd(int n, const double *mean2d, const double *conic, const doubl
  * and alpha_k = o G (uncapped) carries dL/do = dL/dalpha G and
  * dL/dpower = dL/dalpha alpha into the conic and mean.
  * Outputs are [.][n] planes, zeroed first.
+ * mag (nullable, [9][n] in the order d_mean2d, d_conic, d_opac, d_rgb):
+ * the same sums with every term replaced by its magnitude, each factor that
+ * is itself a sum of signed parts by the sum of their magnitudes
+ * (dL/dalpha_k by T_k sum_ch |dC_ch| (|c_k| + |B_k|)).  An entry computed in
+ * floating point with relative precision u cannot be trusted beyond a small
+ * multiple of u mag: where it cancels, mag says by how much.
  */
 void or_render_bwd(int n, const double *mean2d, const double *conic, const double *opac,
                    const double *rgb, const double *depth, const int *rect, int W, int H,
                    const double *bg, const double *d_img, const int *tiles, int n_tiles_sel,
-                   double *d_mean2d, double *d_conic, double *d_opac, double *d_rgb) {
+                   double *d_mean2d, double *d_conic, double *d_opac, double *d_rgb, double *mag) {
     int TX = (W + OR_TILE - 1) / OR_TILE, TY = (H + OR_TILE - 1) / OR_TILE;
     int NT = tiles ? n_tiles_sel : TX * TY;
     int maxl = or_max_list(n, rect, TX, TY);
@@ -848,6 +854,7 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
     nthr = omp_get_max_threads();
 #endif
     double *acc = (double *)calloc((size_t)nthr * 9 * n, sizeof(double));
+    double *macc = mag ? (double *)calloc((size_t)nthr * 9 * n, sizeof(double)) : NULL;
 #pragma omp parallel
     {
         int tid = 0;
@@ -855,6 +862,7 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
         tid = omp_get_thread_num();
 #endif
         double *my = acc + (size_t)tid * 9 * n;
+        double *mm = macc ? macc + (size_t)tid * 9 * n : NULL;
         or_dk *buf = (or_dk *)malloc(sizeof(or_dk) * (size_t)(maxl > 0 ? maxl : 1));
         or_contrib *rec = (or_contrib *)malloc(sizeof(or_contrib) * (size_t)(maxl > 0 ? maxl : 1));
 #pragma omp for schedule(static, 1)   /* fixed tile -> thread map: reproducible sums */
@@ -872,15 +880,21 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
                     double dC[3];
                     for (int ch = 0; ch < 3; ++ch) dC[ch] = d_img[(size_t)ch * W * H + px];
                     double B[3] = {bg[0], bg[1], bg[2]};
+                    double Bm[3] = {fabs(bg[0]), fabs(bg[1]), fabs(bg[2])};
                     for (int j = nr - 1; j >= 0; --j) {
                         const or_contrib *r = &rec[j];
                         int g = r->g;
-                        double dalpha = 0.0;
+                        double dalpha = 0.0, dalpha_m = 0.0;
                         for (int ch = 0; ch < 3; ++ch) {
                             double c = rgb[(size_t)ch * n + g];
                             my[(size_t)(6 + ch) * n + g] += dC[ch] * r->alpha * r->T;
                             dalpha += dC[ch] * r->T * (c - B[ch]);
                             B[ch] = r->alpha * c + (1.0 - r->alpha) * B[ch];
+                            if (mm) {
+                                mm[(size_t)(6 + ch) * n + g] += fabs(dC[ch]) * r->alpha * r->T;
+                                dalpha_m += fabs(dC[ch]) * r->T * (fabs(c) + Bm[ch]);
+                                Bm[ch] = r->alpha * fabs(c) + (1.0 - r->alpha) * Bm[ch];
+                            }
                         }
                         if (r->capped) continue;
                         my[(size_t)5 * n + g] += dalpha * r->G;
@@ -891,6 +905,15 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
                         my[(size_t)2 * n + g] += dpow * (-0.5 * r->dx * r->dx);
                         my[(size_t)3 * n + g] += dpow * (-r->dx * r->dy);
                         my[(size_t)4 * n + g] += dpow * (-0.5 * r->dy * r->dy);
+                        if (mm) {
+                            double pm = dalpha_m * r->alpha;
+                            mm[(size_t)5 * n + g] += dalpha_m * r->G;
+                            mm[(size_t)0 * n + g] += pm * (fabs(a * r->dx) + fabs(b * r->dy));
+                            mm[(size_t)1 * n + g] += pm * (fabs(b * r->dx) + fabs(c * r->dy));
+                            mm[(size_t)2 * n + g] += pm * (0.5 * r->dx * r->dx);
+                            mm[(size_t)3 * n + g] += pm * fabs(r->dx * r->dy);
+                            mm[(size_t)4 * n + g] += pm * (0.5 * r->dy * r->dy);
+                        }
                     }
                 }
         }
@@ -905,8 +928,15 @@ void or_render_bwd(int n, const double *mean2d, const double *conic, const doubl
         d_conic[i] = s[2]; d_conic[(size_t)n + i] = s[3]; d_conic[(size_t)2 * n + i] = s[4];
         d_opac[i] = s[5];
         d_rgb[i] = s[6]; d_rgb[(size_t)n + i] = s[7]; d_rgb[(size_t)2 * n + i] = s[8];
+        if (mag)
+            for (int k = 0; k < 9; ++k) {
+                double m = 0.0;
+                for (int th = 0; th < nthr; ++th) m += macc[(size_t)th * 9 * n + (size_t)k * n + i];
+                mag[(size_t)k * n + i] = m;
+            }
     }
     free(acc);
+    free(macc);
 }
 
 int or_num_threads(void) {

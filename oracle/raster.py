@@ -61,7 +61,7 @@ def _load():
     lib.or_render_fwd.argtypes = [C.c_int, _D, _D, _D, _D, _D, _I, _I, _I, C.c_int, C.c_int, _D,
                                   C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_int, _D, _D, _I, _I]
     lib.or_render_bwd.argtypes = [C.c_int, _D, _D, _D, _D, _D, _I, C.c_int, C.c_int, _D, _D,
-                                  C.c_void_p, C.c_int, _D, _D, _D, _D]
+                                  C.c_void_p, C.c_int, _D, _D, _D, _D, C.c_void_p]
     lib.or_num_threads.restype = C.c_int
     _lib = lib
     return lib
@@ -265,16 +265,24 @@ def render_fwd(proj, bg=(0.0, 0.0, 0.0), eps=0.0, eps_d=0.0, tiles=None, eps_t=N
     return img, T, last, frag
 
 
-def render_bwd(proj, d_img, bg=(0.0, 0.0, 0.0), tiles=None):
+def render_bwd(proj, d_img, bg=(0.0, 0.0, 0.0), tiles=None, magnitudes=False):
     """Adjoint of render_fwd.  Returns dict d_mean2d[2][n], d_conic[3][n],
-    d_opac[n], d_rgb[3][n].  Pinned by central finite differences."""
+    d_opac[n], d_rgb[3][n].  Pinned by central finite differences.
+    magnitudes: also "mag", the same keys holding each entry's sum of term
+    magnitudes (dL/dalpha's signed parts taken as T sum |dC| (|c| + |B|)),
+    which bounds what floating-point summation of the entry can keep.
+    Pinned: never below the entry's magnitude, and equal to it where no term
+    and no factor changes sign."""
     lib = _load()
     tp, tn, _keep = _tiles(tiles)
     W, H = proj["width"], proj["height"]
     n = proj["opac"].shape[0]
     g = dict(d_mean2d=np.zeros((2, n)), d_conic=np.zeros((3, n)), d_opac=np.zeros(n),
              d_rgb=np.zeros((3, n)))
+    m = np.zeros((9, n)) if magnitudes else None
     lib.or_render_bwd(n, _d(proj["mean2d"]), _d(proj["conic"]), _d(proj["opac"]), _d(proj["rgb"]),
                       _d(proj["depth"]), _i(proj["rect"]), W, H, _d(bg), _d(d_img), tp, tn, g["d_mean2d"],
-                      g["d_conic"], g["d_opac"], g["d_rgb"])
+                      g["d_conic"], g["d_opac"], g["d_rgb"], m.ctypes.data if m is not None else None)
+    if m is not None:
+        g["mag"] = dict(d_mean2d=m[0:2], d_conic=m[2:5], d_opac=m[5], d_rgb=m[6:9])
     return g

@@ -58,6 +58,8 @@ _SIGS = {
     "qn_last_error": ([], C.c_char_p),
     "qn_version": ([], C.c_char_p),
     "qn_decode_residuals": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_decode_project": ([_I32, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F32, _I32, _P, _P, _P, _P,
+                           _P, _P], C.c_int),
     "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P,
                                  _P], C.c_int),
     "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
@@ -179,6 +181,14 @@ def qn_decode_residuals(n, n_stride, n_attr, prev, lat, dec, layout, lp, log_alp
 
 QN_DECODE_BWD_BLOCKS = 1216
 QN_MLP_BWD_BLOCKS = 256
+
+
+def qn_decode_project(n, n_stride, n_attr, sh_degree, prev, lat, dec, layout, lp, log_alpha, gate_params, skip, cam,
+                      blur, tight_rects, gate, lreg, out, splats, rects, stream=None):
+    _check(lib().qn_decode_project(n, n_stride, n_attr, sh_degree, _ptr(prev), _ptr(lat), _ptr(dec),
+                                   C.byref(layout), _ptr(lp), _ptr(log_alpha), C.byref(gate_params), _ptr(skip),
+                                   C.byref(cam), float(blur), int(bool(tight_rects)), _ptr(gate), _ptr(lreg),
+                                   _ptr(out), _ptr(splats), _ptr(rects), _stream(stream)))
 
 
 def qn_decode_residuals_bwd(n, n_stride, n_attr, lat, dec, layout, lp, log_alpha, gate_params, d_out, d_lreg,

@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "project.cuh"
 
 namespace qn {
 namespace {
@@ -476,6 +477,121 @@ int grid_for(int n, int block, int per_sm) {
     return need < 1 ? 1 : (need < cap ? need : cap);
 }
 
+// ---------------------------------------------------------------- fused decode + projection
+// Eq. 4-8 and Eq. 1 for a tile of DP_TILE Gaussians in one pass: the tile's
+// planes of A_{t-1}, its latent planes and its position residual are staged
+// in shared memory with cp.async (16-byte chunks straight from global to
+// shared memory, all of a tile in flight at once), each thread adds its
+// Gaussian's residuals there (the same operations as k_decode) and projects
+// it from the staged tile; A_t is written out (nullable) for the projection
+// adjoint, never read back.  Several blocks per SM overlap one tile's staging
+// with another's arithmetic.
+constexpr int DP_TILE = 64;
+
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+template <int DEG, int LT, bool NOISE>
+__global__ void __launch_bounds__(DP_TILE) k_decode_project(DecodeArgs a, CamArgs cm, float blur, int tight,
+                                                          const float *__restrict__ prev,
+                                                          const float *__restrict__ lat,
+                                                          const uint16_t *__restrict__ dec,
+                                                          const float *__restrict__ lp,
+                                                          const float *__restrict__ la,
+                                                          const uint8_t *__restrict__ skip,
+                                                          float *__restrict__ gate, float *__restrict__ lreg,
+                                                          float *__restrict__ out, float4 *__restrict__ splat,
+                                                          int4 *__restrict__ rects) {
+    extern __shared__ __align__(16) float dp_smem[];
+    float *sA = dp_smem;                                // [n_attr][DP_TILE] A_{t-1}, then A_t
+    float *sL = sA + a.n_attr * DP_TILE;                // [n_lat][DP_TILE] latents
+    float *sP = sL + a.n_lat * DP_TILE;                 // [3][DP_TILE] position residual
+    float *sD = sP + 3 * DP_TILE;                       // decoders (f32)
+    __shared__ float sred[DP_TILE / 32];
+    const int t = threadIdx.x;
+    for (int k = t; k < a.n_dec; k += DP_TILE) sD[k] = bf16_to_f32(dec[k]);
+    const size_t S = a.stride;
+    const int rows = a.n_attr + a.n_lat + 3;
+    float reg = 0.f;
+    for (int base = blockIdx.x * DP_TILE; base < a.n; base += gridDim.x * DP_TILE) {
+        __syncthreads();                                // the previous tile's readers are done (and sD is written)
+        for (int c = t; c < rows * (DP_TILE / 4); c += DP_TILE) {
+            const int row = c / (DP_TILE / 4), col = 4 * (c % (DP_TILE / 4));
+            if (base + col >= a.stride) continue;       // stride is a multiple of 4: chunks lie wholly inside
+            const float *src = row < a.n_attr ? prev + (size_t)row * S
+                             : row < a.n_attr + a.n_lat ? lat + (size_t)(row - a.n_attr) * S
+                                                        : lp + (size_t)(row - a.n_attr - a.n_lat) * S;
+            cp_async16(dp_smem + row * DP_TILE + col, src + base + col);
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const int i = base + t;
+        if (i < a.n) {
+            const bool sk = skip && skip[i];
+            const float l_a = la[i];
+            const float gh = sigmoidf_(gate_logit<NOISE>(a, l_a, i) / a.tau);   // Eq. 6
+            const float g = fminf(1.f, fmaxf(0.f, gh * (a.g1 - a.g0) + a.g0));   // Eq. 7
+            if (!sk) {                                  // a skipped Gaussian keeps its gate entry
+                if (gate) gate[i] = g;
+                reg += sigmoidf_(l_a - a.shift);        // Eq. 8
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sA[d * DP_TILE + t] = sA[d * DP_TILE + t] + g * sP[d * DP_TILE + t];
+            for (int c = 0; c < a.n_cat; ++c) {
+                const float *D = sD + a.dec_off[c];
+                const int L = LT > 0 ? LT : a.ld[c];
+                float l[LT > 0 ? LT : QN_MAX_LATENT];
+#pragma unroll
+                for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                    if (k < L) l[k] = latent_int(sL[(a.lat_off[c] + k) * DP_TILE + t]);
+                for (int r = 0; r < a.ac[c]; ++r) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                        if (k < L) acc = fmaf(D[r * L + k], l[k], acc);          // Eq. 5
+                    float &x = sA[(a.ab[c] + r) * DP_TILE + t];
+                    x = x + acc;                                                 // Eq. 4
+                }
+            }
+            if (out)
+                for (int k = 0; k < a.n_attr; ++k) out[(size_t)k * S + i] = sA[k * DP_TILE + t];
+            float4 s0, s1, s2;
+            int4 rc;
+            project_one<DEG>(cm, blur, tight, sA, DP_TILE, t, s0, s1, s2, rc);
+            splat[3 * (size_t)i] = s0;
+            splat[3 * (size_t)i + 1] = s1;
+            splat[3 * (size_t)i + 2] = s2;
+            rects[i] = rc;
+        }
+    }
+    if (lreg) {
+        reg = warp_sum(reg);
+        if ((t & 31) == 0) sred[t >> 5] = reg;
+        __syncthreads();
+        if (t == 0) {
+            float s = 0.f;
+            for (int w = 0; w < DP_TILE / 32; ++w) s += sred[w];
+            atomicAdd(lreg, s);
+        }
+    }
+}
+
+template <int DEG>
+int launch_decode_project(const DecodeArgs &a, const CamArgs &cm, float blur, int tight, const float *prev,
+                          const float *lat, const uint16_t *dec, const float *lp, const float *la,
+                          const uint8_t *skip, float *gate, float *lreg, float *out, float4 *splat, int4 *rects,
+                          cudaStream_t s) {
+    const bool w8 = uniform_width8(a), noise = a.noise != nullptr;
+    auto kern = w8 ? (noise ? k_decode_project<DEG, 8, true> : k_decode_project<DEG, 8, false>)
+                   : (noise ? k_decode_project<DEG, 0, true> : k_decode_project<DEG, 0, false>);
+    const size_t smem = sizeof(float) * ((size_t)(a.n_attr + a.n_lat + 3) * DP_TILE + a.n_dec);
+    kern<<<grid_for(a.n, DP_TILE, 8), DP_TILE, smem, s>>>(a, cm, blur, tight, prev, lat, dec, lp, la, skip, gate,
+                                                           lreg, out, splat, rects);
+    return check_launch("qn_decode_project");
+}
+
 }  // namespace
 }  // namespace qn
 
@@ -499,6 +615,36 @@ extern "C" int qn_decode_residuals(int32_t n, int32_t n_stride, int32_t n_attr, 
                    : (noise ? qn::k_decode<0, true> : qn::k_decode<0, false>);
     kern<<<qn::grid_for(n, 256, 8), 256, 0, s>>>(a, prev, lat, dec, lp, log_alpha, skip, out, gate, lreg);
     return qn::check_launch("qn_decode_residuals");
+}
+
+extern "C" int qn_decode_project(int32_t n, int32_t n_stride, int32_t n_attr, int32_t sh_degree,
+                                 const float *prev, const float *lat, const uint16_t *dec,
+                                 const qn_decoder_layout *layout_host, const float *lp, const float *log_alpha,
+                                 const qn_gate_params *gate_host, const uint8_t *skip, const qn_camera *cam_host,
+                                 float blur, int32_t tight_rects, float *gate, float *lreg, float *out,
+                                 qn_splat *splats, int32_t *rects, qn_stream_t stream) {
+    qn::DecodeArgs a;
+    int st = qn::make_args(n, n_stride, n_attr, layout_host, gate_host, &a);
+    if (st) return st;
+    qn::CamArgs cm;
+    st = qn::cam_args(cam_host, &cm);
+    if (st) return st;
+    QN_REQUIRE(sh_degree >= 0 && sh_degree <= 3 && n_attr == 11 + 3 * (sh_degree + 1) * (sh_degree + 1),
+               "sh_degree %d does not match n_attr %d", sh_degree, n_attr);
+    QN_REQUIRE(blur >= 0.f, "blur must be >= 0");
+    QN_REQUIRE(n == 0 || (prev && lp && log_alpha && splats && rects), "null pointer argument");
+    QN_REQUIRE(n == 0 || a.n_cat == 0 || (lat && dec), "null latent or decoder pointer");
+    QN_REQUIRE(prev != out, "out may not alias prev");
+    QN_REQUIRE(((uintptr_t)prev & 15) == 0 && ((uintptr_t)lat & 15) == 0 && ((uintptr_t)lp & 15) == 0 &&
+                   ((uintptr_t)splats & 15) == 0 && ((uintptr_t)rects & 15) == 0,
+               "prev, lat, lp, splats and rects must be 16-byte aligned");
+    cudaStream_t s = qn::as_stream(stream);
+    if (lreg && cudaMemsetAsync(lreg, 0, sizeof(float), s) != cudaSuccess) return qn::check_launch("decode memset");
+    if (n == 0) return QN_OK;
+    decltype(&qn::launch_decode_project<0>) f[4] = {qn::launch_decode_project<0>, qn::launch_decode_project<1>,
+                                                     qn::launch_decode_project<2>, qn::launch_decode_project<3>};
+    return f[sh_degree](a, cm, blur, tight_rects != 0, prev, lat, dec, lp, log_alpha, skip, gate, lreg, out,
+                        reinterpret_cast<float4 *>(splats), reinterpret_cast<int4 *>(rects), s);
 }
 
 extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_attr, const float *lat,

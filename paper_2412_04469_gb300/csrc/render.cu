@@ -79,6 +79,39 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------- band cull
+// Whether some pixel centre of the band [x0, x1] x [y0, y1] can reach
+// log2(e) power e >= kw, e = A dx^2 + B dx dy + C dy^2 (A, C < 0): the
+// maximum of e over the rectangle is 0 when the mean lies inside it, else it
+// lies on an edge at the stationary point clamped to that edge.  The margin
+// covers the FP32 rounding of this maximum and of the per-pixel exponent
+// (both a few ulps of the largest term), so the test never rejects a
+// Gaussian some pixel of the band composites.  One lane tests one record, so
+// a batch of 32 records costs each lane one test instead of one per record.
+__device__ __forceinline__ bool band_reaches(float mx, float my, float A, float B, float C, float kw, float x0,
+                                             float x1, float y0, float y1) {
+    const float lx = x0 - mx, hx = x1 - mx, ly = y0 - my, hy = y1 - my;
+    float em;
+    if (lx <= 0.f && hx >= 0.f && ly <= 0.f && hy >= 0.f) {
+        em = 0.f;
+    } else {
+        const float sa = __fdividef(-0.5f, A), sc = __fdividef(-0.5f, C);
+        em = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float dy = k ? hy : ly;
+            const float dx = fminf(fmaxf(B * dy * sa, lx), hx);
+            em = fmaxf(em, fmaf(dx, fmaf(A, dx, B * dy), C * dy * dy));
+            const float ex = k ? hx : lx;
+            const float ey = fminf(fmaxf(B * ex * sc, ly), hy);
+            em = fmaxf(em, fmaf(ey, fmaf(C, ey, B * ex), A * ex * ex));
+        }
+    }
+    const float ax = fmaxf(-lx, hx), ay = fmaxf(-ly, hy);
+    const float mag = fmaf(-A, ax * ax, fmaf(fabsf(B), ax * ay, -C * ay * ay));
+    return em >= kw - fmaf(1e-6f, mag, 1e-3f);
+}
+
 // ---------------------------------------------------------------- staged record
 // log2(e) power = A dx^2 + B dx dy + C dy^2 with A = -a log2(e) / 2,
 // B = -b log2(e), C = -c log2(e) / 2 (conic (a, b, c)), dx = x - mean_x.
@@ -214,25 +247,31 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
         lastc[q] = nc[q] = 0;
         if (px < W && py0 + q < H) live |= 1u << q;
     }
+    // the warp's band of pixel centres, clipped to the image
+    const float bx0 = (float)((tile % TX) * QN_TILE) + 0.5f, bx1 = fminf(bx0 + (float)(QN_TILE - 1), W - 0.5f);
+    const float by0 = (float)((tile / TX) * QN_TILE + (threadIdx.x >> 5) * (2 * PPT)) + 0.5f;
+    const float by1 = fminf(by0 + (float)(2 * PPT - 1), H - 0.5f);
     for (int b0 = 0; b0 < n; b0 += FWD_BATCH) {
         if (!__any_sync(FULL, live)) break;
         uint32_t my_id = 0;
+        bool reach = false;
         if (b0 + lane < n) {
             my_id = vals[beg + b0 + lane];
-            stage_srec(s[lane], sp[3 * (size_t)my_id], sp[3 * (size_t)my_id + 1], sp[3 * (size_t)my_id + 2]);
+            SRec rr;
+            stage_srec(rr, sp[3 * (size_t)my_id], sp[3 * (size_t)my_id + 1], sp[3 * (size_t)my_id + 2]);
+            s[lane] = rr;
+            reach = band_reaches(rr.g.x, rr.g.y, rr.k.x, rr.k.y, rr.k.z, rr.g.w, bx0, bx1, by0, by1);
         }
+        uint32_t todo = __ballot_sync(FULL, reach);     // the records some pixel of the band can take
         __syncwarp();
-        const int cnt = min(FWD_BATCH, n - b0);
         uint32_t batch_added = 0;                       // bit j: record j composited by this warp
-        for (int j = 0; j < cnt; ++j) {
+        while (todo) {
             if (!__any_sync(FULL, live)) break;
+            const int j = __ffs(todo) - 1;              // front to back
+            todo &= todo - 1;
             const SRec &r = s[j];
             float e[PPT];
             scalar_exponent<PPT>(r, fx, fy0, e);
-            bool near = false;
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) near |= e[q] >= r.g.w;
-            if (!__any_sync(FULL, near)) continue;      // alpha < 1/255 on every pixel of the band
             const float4 c = r.c;
             const uint32_t pos1 = (uint32_t)(b0 + j + 1);
             bool added = false;
@@ -368,6 +407,10 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H,
     }
     const uint32_t wm = __reduce_max_sync(FULL, mymax);
     if (lane == 0) wmax[warp] = wm;
+    // the warp's band of pixel centres, clipped to the image
+    const float bx0 = (float)((tile % TX) * QN_TILE) + 0.5f, bx1 = fminf(bx0 + (float)(QN_TILE - 1), W - 0.5f);
+    const float by0 = (float)((tile / TX) * QN_TILE + warp * (2 * PPT)) + 0.5f;
+    const float by1 = fminf(by0 + (float)(2 * PPT - 1), H - 0.5f);
     __syncthreads();
     uint32_t tmax = 0;
 #pragma unroll
@@ -395,79 +438,115 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H,
             }
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
-            const uint32_t pos = (uint32_t)(lo + j);
-            if ((sflag[j] & 2) || !__any_sync(FULL, pos < mymax)) {
-                if (lane == 0) hit[warp][j] = 0;
-                continue;
+        for (int k = lane; k < BATCH; k += 32) hit[warp][k] = 0;
+        __syncwarp();
+        // back to front over chunks of 32 records: lane l tests record
+        // 32 c + l against the warp's band (composited somewhere, inside the
+        // band's walked prefix, reaching one of its pixel centres)
+#pragma unroll 1
+        for (int ch = BATCH / 32 - 1; ch >= 0; --ch) {
+            const int jt = ch * 32 + lane;
+            bool reach = false;
+            if (jt < cnt && !(sflag[jt] & 2) && (uint32_t)(lo + jt) < wm) {
+                const Rec &q = s[jt];
+                float mxs, mys, qa, qb, qc, unused;
+                upk(q.mx, mxs, unused);
+                upk(q.my, mys, unused);
+                upk(q.A, qa, unused);
+                upk(q.B, qb, unused);
+                upk(q.C, qc, unused);
+                reach = band_reaches(mxs, mys, qa, qb, qc, q.kw, bx0, bx1, by0, by1);
             }
-            const Rec r = s[j];
-            const Expo<NP> x = exponent<NP>(r, FX, FY);
-            bool near = false;
+            uint32_t todo = __ballot_sync(FULL, reach);
+            while (todo) {
+                const int jb = 31 - __clz(todo);
+                todo &= ~(1u << jb);
+                const int j = ch * 32 + jb;
+                const uint32_t pos = (uint32_t)(lo + j);
+                const Rec r = s[j];
+                const Expo<NP> x = exponent<NP>(r, FX, FY);
+                bool near = false;
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float e0, e1;
-                upk(x.e[p], e0, e1);
-                near |= (e0 >= r.kw && pos < lastp[2 * p]) || (e1 >= r.kw && pos < lastp[2 * p + 1]);
-            }
-            if (!__any_sync(FULL, near)) {              // no pixel of the band can take j
-                if (lane == 0) hit[warp][j] = 0;
-                continue;
-            }
-            const f2 Z = pk(0.f, 0.f);
-            f2 S0 = Z, S1 = Z, S2 = Z, G0 = Z, G1 = Z, G2 = Z;
-            bool any = false;
+                for (int p = 0; p < NP; ++p) {
+                    float e0, e1;
+                    upk(x.e[p], e0, e1);
+                    near |= (e0 >= r.kw && pos < lastp[2 * p]) || (e1 >= r.kw && pos < lastp[2 * p + 1]);
+                }
+                if (!__any_sync(FULL, near)) continue;      // no pixel of the band can take j
+                if (sflag[j] & 1) {
+                    // skipped (the branch is uniform over the block): it only
+                    // enters the transmittance and b of the Gaussians in front
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float e0, e1, v0, v1, m0, m1;
-                upk(x.e[p], e0, e1);
-                upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
-                const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
-                const bool ok0 = pos < lastp[2 * p] && e0 <= 0.f && a0 >= ALPHA_MIN;
-                const bool ok1 = pos < lastp[2 * p + 1] && e1 <= 0.f && a1 >= ALPHA_MIN;
-                any |= ok0 | ok1;
-                const float ae0 = ok0 ? a0 : 0.f, ae1 = ok1 ? a1 : 0.f;
-                const f2 AE = pk(ae0, ae1);
-                const f2 AG = pk(v0 > ALPHA_MAX ? 0.f : ae0, v1 > ALPHA_MAX ? 0.f : ae1);   // the cap passes no gradient
-                upk(sub2(ONE, AE), m0, m1);
-                const f2 TQ = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));  // in front of j
-                T[p] = TQ;
-                const f2 cd = fma2(r.cr, D0[p], fma2(r.cg, D1[p], mul2(r.cb, D2[p])));
-                const f2 dot = sub2(cd, Bd[p]);
-                Bd[p] = fma2(AE, dot, Bd[p]);
-                const f2 w = mul2(AE, TQ);
-                G0 = fma2(w, D0[p], G0);
-                G1 = fma2(w, D1[p], G1);
-                G2 = fma2(w, D2[p], G2);
-                const f2 sdp = mul2(mul2(TQ, dot), AG);           // dL/dpower
-                const f2 tt = mul2(sdp, x.dy[p]);
-                S0 = add2(S0, sdp);
-                S1 = add2(S1, tt);
-                S2 = fma2(tt, x.dy[p], S2);
+                    for (int p = 0; p < NP; ++p) {
+                        float e0, e1, v0, v1, m0, m1;
+                        upk(x.e[p], e0, e1);
+                        upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
+                        const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
+                        const bool ok0 = pos < lastp[2 * p] && e0 <= 0.f && a0 >= ALPHA_MIN;
+                        const bool ok1 = pos < lastp[2 * p + 1] && e1 <= 0.f && a1 >= ALPHA_MIN;
+                        const f2 AE = pk(ok0 ? a0 : 0.f, ok1 ? a1 : 0.f);
+                        upk(sub2(ONE, AE), m0, m1);
+                        T[p] = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));
+                        const f2 cd = fma2(r.cr, D0[p], fma2(r.cg, D1[p], mul2(r.cb, D2[p])));
+                        Bd[p] = fma2(AE, sub2(cd, Bd[p]), Bd[p]);
+                    }
+                    continue;
+                }
+                const f2 Z = pk(0.f, 0.f);
+                f2 S0 = Z, S1 = Z, S2 = Z, G0 = Z, G1 = Z, G2 = Z;
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    float e0, e1, v0, v1, m0, m1;
+                    upk(x.e[p], e0, e1);
+                    upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
+                    const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
+                    const bool ok0 = pos < lastp[2 * p] && e0 <= 0.f && a0 >= ALPHA_MIN;
+                    const bool ok1 = pos < lastp[2 * p + 1] && e1 <= 0.f && a1 >= ALPHA_MIN;
+                    any |= ok0 | ok1;
+                    const float ae0 = ok0 ? a0 : 0.f, ae1 = ok1 ? a1 : 0.f;
+                    const f2 AE = pk(ae0, ae1);
+                    const f2 AG = pk(v0 > ALPHA_MAX ? 0.f : ae0, v1 > ALPHA_MAX ? 0.f : ae1);   // the cap passes no gradient
+                    upk(sub2(ONE, AE), m0, m1);
+                    const f2 TQ = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));  // in front of j
+                    T[p] = TQ;
+                    const f2 cd = fma2(r.cr, D0[p], fma2(r.cg, D1[p], mul2(r.cb, D2[p])));
+                    const f2 dot = sub2(cd, Bd[p]);
+                    Bd[p] = fma2(AE, dot, Bd[p]);
+                    const f2 w = mul2(AE, TQ);
+                    G0 = fma2(w, D0[p], G0);
+                    G1 = fma2(w, D1[p], G1);
+                    G2 = fma2(w, D2[p], G2);
+                    const f2 sdp = mul2(mul2(TQ, dot), AG);           // dL/dpower
+                    const f2 tt = mul2(sdp, x.dy[p]);
+                    S0 = add2(S0, sdp);
+                    S1 = add2(S1, tt);
+                    S2 = fma2(tt, x.dy[p], S2);
+                }
+                const bool any_j = __any_sync(FULL, any);   // the band composites j
+                if (lane == 0) hit[warp][j] = any_j;
+                if (!any_j) continue;
+                float h0, h1, dx, dxx;
+                upk(x.dx, dx, dxx);
+                upk(S0, h0, h1);
+                const float s0 = h0 + h1;
+                upk(S1, h0, h1);
+                const float s1 = h0 + h1;
+                upk(S2, h0, h1);
+                const float s2 = h0 + h1;
+                upk(G0, h0, h1);
+                const float g0 = h0 + h1;
+                upk(G1, h0, h1);
+                const float g1 = h0 + h1;
+                upk(G2, h0, h1);
+                const float g2 = h0 + h1;
+                const float sx = dx * s0;
+                float v[8] = {s0, sx, s1, dx * sx, dx * s1, s2, g0, g1};
+                const float red = reduce_scatter8(v, lane);
+                const float red8 = warp_sum(g2);
+                if ((lane & 3) == 0) rec[warp][j][(lane >> 2) & 7] = red;
+                if (lane == 0) rec[warp][j][8] = red8;
             }
-            const bool any_j = __any_sync(FULL, any);   // the band composites j (skipped or not)
-            if (lane == 0) hit[warp][j] = any_j;
-            if (!any_j || (sflag[j] & 1)) continue;
-            float h0, h1, dx, dxx;
-            upk(x.dx, dx, dxx);
-            upk(S0, h0, h1);
-            const float s0 = h0 + h1;
-            upk(S1, h0, h1);
-            const float s1 = h0 + h1;
-            upk(S2, h0, h1);
-            const float s2 = h0 + h1;
-            upk(G0, h0, h1);
-            const float g0 = h0 + h1;
-            upk(G1, h0, h1);
-            const float g1 = h0 + h1;
-            upk(G2, h0, h1);
-            const float g2 = h0 + h1;
-            const float sx = dx * s0;
-            float v[8] = {s0, sx, s1, dx * sx, dx * s1, s2, g0, g1};
-            const float red = reduce_scatter8(v, lane);
-            const float red8 = warp_sum(g2);
-            if ((lane & 3) == 0) rec[warp][j][(lane >> 2) & 7] = red;
-            if (lane == 0) rec[warp][j][8] = red8;
         }
         __syncthreads();
         // one record per visited list position: the tile's sum for that Gaussian

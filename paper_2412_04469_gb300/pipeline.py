@@ -60,6 +60,9 @@ class HParams:
     # the compositing kernels start their tiles heaviest first (by the
     # per-tile visited prefixes of the last forward; the same result)
     order_tiles: bool = True
+    # the training iteration decodes and projects in one pass (a skipped
+    # Gaussian is then rendered with the current decoders)
+    fused: bool = True
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
@@ -199,6 +202,25 @@ class QueenFrame:
     def d_lreg(self) -> float:
         """dL_total / dL_reg of Eq. 11."""
         return self.hp.lambda_reg / max(1, self.n) if self.hp.lreg_mean else self.hp.lambda_reg
+
+    def _train_gate(self, stream=None):
+        """The gate parameters of a training iteration (with HParams.gate_noise,
+        fresh noise drawn for the current Adam step first)."""
+        if self.noise is not None:
+            B.qn_gate_uniform(self.n, self.hp.gate_seed, self.step, self.noise, stream)
+            return self.c_gate_train
+        return self.c_gate
+
+    def decode_project(self, rast: "Rasterizer", cam, stream=None, skip=None):
+        """A training iteration's decode (Eq. 4-8) and projection (Eq. 1) in
+        one pass into rast's records and rects, A_t into attrs (for the
+        projection adjoint).  Gaussians with skip set keep their gate entries
+        and add nothing to lreg; their A_t is rebuilt from the current
+        decoders like every other."""
+        B.qn_decode_project(self.n, self.S, self.n_attr, self.sh_degree, self.prev, self.lat, self.dec_bf16,
+                            self.c_layout, self.lp, self.log_alpha, self._train_gate(stream), skip, cam,
+                            self.hp.blur, rast.tight_rects, self.gate, self.lreg, self.attrs, rast.splats, rast.rects,
+                            stream)
 
     def decode_bwd(self, skip=None, stream=None):
         B.qn_decode_residuals_bwd(self.n, self.S, self.n_attr, self.lat, self.dec_bf16, self.c_layout, self.lp,
@@ -394,9 +416,11 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     """One view of Eq. 11's optimisation: forward, Eq. 3's loss ((1 - lambda)
     L1 + lambda D-SSIM) + lambda_reg L_reg (the L_reg gradient is folded into
     the gate adjoint), full adjoint and the Adam step.  No host
-    synchronisation.  Gaussians with skip set are frozen: no gradient, no
-    update, and their decoded columns are reused (frame.attrs must hold their
-    A_t, e.g. from a decode without skip).  With unskip, a skipped Gaussian
+    synchronisation.  Gaussians with skip set are frozen: no gradient and no
+    update of their residual parameters (with HParams.fused they are rendered
+    with the current decoders; otherwise their decoded columns are reused, and
+    frame.attrs must hold their A_t, e.g. from a decode without skip).  With
+    unskip, a skipped Gaussian
     that some pixel composites in this iteration is un-skipped before the
     adjoint (the forward marks the composited Gaussians), so it takes this
     iteration's update as plain training does and trains like the others from
@@ -408,8 +432,11 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     hp = frame.hp
     unskip = unskip and skip is not None
     mark = mark or unskip or hp.mark_composited
-    frame.decode(stream, skip, train=True)
-    rast.project(frame.attrs, cam, hp.blur, stream)
+    if hp.fused:
+        frame.decode_project(rast, cam, stream, skip)
+    else:
+        frame.decode(stream, skip, train=True)
+        rast.project(frame.attrs, cam, hp.blur, stream)
     rast.bin_sort(False, stream)
     ranges = None
     if mask is not None:

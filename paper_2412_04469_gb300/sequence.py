@@ -83,6 +83,9 @@ class SequenceConfig:
     # within that iteration, before its gradient is gathered, so it takes that
     # update and trains from then on (training_iteration's unskip)
     unskip_composited: bool = True
+    # skip frames: time the compositing adjoint with and without the skip
+    # once at the frame's end (a diagnostic outside the frame's seconds)
+    probe_render_bwd: bool = True
 
 
 class SkipMLP:
@@ -143,6 +146,12 @@ class FrameRecord:
     packet_bytes: int = 0                     # size of the frame's compressed packet
     packet_s: float = float("nan")            # packing and unpacking time (not in `seconds`)
     psnr_packet: float = float("nan")         # held-out PSNR of the packet's A_t (gate binarised)
+    # skip frames, diagnostic from the frame's final state (not in `seconds`):
+    # the compositing adjoint of one view with the skip (the forward's marks,
+    # the composited ones un-skipped, the rest dropped from the walk) and the
+    # plain one, in ms
+    render_bwd_ms_skip: float = float("nan")
+    render_bwd_ms_plain: float = float("nan")
 
 
 def sequence_hparams() -> HParams:
@@ -198,6 +207,7 @@ class StreamingTrainer:
         self.median = torch.zeros(1, device="cuda")
         self.X = torch.zeros((16, f.S), device="cuda")
         self.skip = torch.zeros(f.S, device="cuda", dtype=torch.uint8)
+        self.skip_probe = torch.zeros(f.S, device="cuda", dtype=torch.uint8)
         self.labels = torch.zeros(f.S, device="cuda", dtype=torch.uint8)
         self.frame_hit = torch.zeros(f.S, device="cuda", dtype=torch.uint8)     # composited during the frame
         self._track_hits = False
@@ -340,16 +350,52 @@ class StreamingTrainer:
             return rec.psnr < rec.psnr_plain - self.cfg.max_dpsnr
         return rec.psnr_train < rec.psnr_plain_train - self.cfg.max_dpsnr
 
-    def run_frame(self, t, mlp: SkipMLP | None) -> FrameRecord:
+    def _time_render_bwd(self, skip) -> tuple:
+        """The compositing adjoint of view 0 at the frame's final state, once
+        as a skip frame runs it (marked forward, composited Gaussians
+        un-skipped unless the config keeps them skipped, the rest dropped) and
+        once plain, in ms (the median of five launches; diagnostic, the
+        parameters are not touched)."""
+        f, r, c = self.frame, self.rast, self.cams[0]
+        gate = f.gate.clone()                               # the frame's gate, which the packet reads
+        f.decode_project(r, c)
+        f.gate.copy_(gate)
+        r.bin_sort(False)
+        out = []
+        for use_skip in (True, False):
+            r.render_fwd(c, self.hp.bg, mark=use_skip, order=self.hp.order_tiles)
+            r.photometric_loss(self.tgt_cur[0], self.hp.lambda_dssim)
+            sk = None
+            if use_skip:
+                self.skip_probe.copy_(skip)
+                if self.cfg.unskip_composited:
+                    B.qn_clear_marked(self.cfg.n, r.composited, self.skip_probe)
+                sk = self.skip_probe
+            times = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                r.render_bwd_pairs(c, self.hp.bg, sk, marks=use_skip, order=self.hp.order_tiles)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            out.append(float(np.median(times)))
+        return out[0], out[1]
+
+    def run_frame(self, t, mlp: SkipMLP | None, rule: bool = False) -> FrameRecord:
         """One frame.  Its `seconds` count the training work only (device
         synchronised around each part): Eq. 9/10, the skip features, MLP
         inference and reordering, the training iterations and the final
         decode, plus the plain re-run of a fallback.  The PSNR evaluations and
-        the harness's same-state plain pass are not counted."""
+        the harness's same-state plain pass are not counted.  rule: instead of
+        the MLP, skip what the previous frame's label called static (the same
+        frames, labels and un-skipping as the learned arm)."""
         c, f, n = self.cfg, self.frame, self.cfg.n
         clock = _Clock()
         rec = FrameRecord(t, 0.0, 0.0, self._psnr(f.prev))
-        self._track_hits = mlp is not None and c.label_visibility
+        labelled = mlp is not None or rule
+        self._track_hits = labelled and c.label_visibility
         clock.start()
         self._score_and_init()
         if c.masked_fraction > 0:
@@ -361,8 +407,11 @@ class StreamingTrainer:
             if t > c.train_frames:
                 mlp.predict(self.X, f.S, n, self.threshold, self.skip)
                 skip = self.skip
-                if c.partition:
-                    self._partition()
+        elif rule and t > c.train_frames:
+            self.skip[:n].copy_(self.prev_static[:n])
+            skip = self.skip
+        if skip is not None and c.partition:
+            self._partition()
         clock.stop()
         if skip is not None:
             # the evaluation harness: plain gated training of this same frame
@@ -391,16 +440,18 @@ class StreamingTrainer:
                 clock.stop()
                 rec.psnr, rec.psnr_train = self._psnr_pair(f.attrs)
         self._check_capacity()
-        if mlp is not None:
+        if labelled:
             clock.start()                                  # labels and the MLP's online training count
             B.qn_skip_labels(n, f.S, self.layout.n_latent, f.gate, f.lat, self.labels,
                              hit=self.frame_hit if c.label_visibility else None)
-            if t <= c.train_frames:
+            if mlp is not None and t <= c.train_frames:
                 mlp.train(self.X, f.S, self.labels, n, c.mlp_epochs, c.mlp_batch)
             self.prev_static.copy_(self.labels)
             clock.stop()
-            if t <= c.train_frames:
+            if mlp is not None and t <= c.train_frames:
                 rec.mlp_loss = float(mlp.loss.item())
+        if skip is not None and c.probe_render_bwd:
+            rec.render_bwd_ms_skip, rec.render_bwd_ms_plain = self._time_render_bwd(skip)
         rec.seconds = clock.seconds
         static = f.gate[:n] == 0
         # diagnostics against the ground-truth motion (outside the timed region)
@@ -433,9 +484,10 @@ class StreamingTrainer:
         f.prev.copy_(f.attrs)
         return rec
 
-    def run(self, learned: bool, frames: int | None = None, threshold: float | None = None):
+    def run(self, learned: bool, frames: int | None = None, threshold: float | None = None, rule: bool = False):
         """One arm over the sequence; `threshold` overrides the config's skip
-        threshold for this run."""
+        threshold for this run; rule: the non-learned skip (the previous
+        frame's static label) instead of plain training."""
         frames = frames or self.cfg.frames
         self.threshold = self.cfg.threshold if threshold is None else float(threshold)
         self.reset()
@@ -448,7 +500,7 @@ class StreamingTrainer:
         for t in range(1, frames):
             self.tgt_prev.copy_(self.tgt_cur)              # fixed buffers: graphs hold their addresses
             self._render_targets(t, self.tgt_cur)
-            out.append(self.run_frame(t, mlp))
+            out.append(self.run_frame(t, mlp, rule=rule and not learned))
         return out
 
 
@@ -477,6 +529,8 @@ def summarize(cfg: SequenceConfig, plain: list, learned: list) -> dict:
         "static_precision": _mean([learned[i].static_precision for i in skip_frames]),
         "plain_gate0_recall": _mean([plain[i].gate0_recall for i in skip_frames]),
         "plain_gate0_precision": _mean([plain[i].gate0_precision for i in skip_frames]),
+        "render_bwd_ms_skip": _mean([learned[i].render_bwd_ms_skip for i in skip_frames]),
+        "render_bwd_ms_plain": _mean([learned[i].render_bwd_ms_plain for i in skip_frames]),
     }
 
 
@@ -484,16 +538,37 @@ def _mean(v: list) -> float:
     return float(np.mean(v)) if v else float("nan")
 
 
-def compare(cfg: SequenceConfig, frames: int | None = None, extra_thresholds=(), masked_fractions=()) -> dict:
+def compare(cfg: SequenceConfig, frames: int | None = None, extra_thresholds=(), masked_fractions=(),
+            rule: bool = True, learned: bool = True, no_unskip: bool = False) -> dict:
     """Runs the plain arm, then the learned-skip arm (the config's threshold,
-    then each of extra_thresholds), then plain gated training with Sec. 3.3's
+    then each of extra_thresholds), then (rule) the non-learned skip of the
+    previous frame's static label, then (no_unskip) the learned skip with the
+    composited skipped Gaussians kept skipped (the compositing adjoint takes
+    them into T and b only), then plain gated training with Sec. 3.3's
     masked training on each of masked_fractions of the iterations, on the
     same sequence and GPU; returns per-frame records and the s/frame
-    comparisons."""
+    comparisons.  learned=False runs the plain and masked arms only."""
     tr = StreamingTrainer(cfg)
     plain = tr.run(learned=False, frames=frames)
+    if not learned:
+        out = {"plain": plain, "by_threshold": {}, "masked": {}}
+        base = tr.cfg.masked_fraction
+        for mf in masked_fractions:
+            tr.cfg.masked_fraction = float(mf)
+            out["masked"][float(mf)] = tr.run(learned=False, frames=frames)
+        tr.cfg.masked_fraction = base
+        return out
     learned = tr.run(learned=True, frames=frames)
     out = {"plain": plain, "learned": learned, **summarize(cfg, plain, learned)}
+    if rule:
+        rec = tr.run(learned=False, frames=frames, rule=True)
+        out["rule"] = {"learned": rec, **summarize(cfg, plain, rec)}
+    if no_unskip:
+        base_unskip = tr.cfg.unskip_composited
+        tr.cfg.unskip_composited = False
+        rec = tr.run(learned=True, frames=frames)
+        tr.cfg.unskip_composited = base_unskip
+        out["no_unskip"] = {"learned": rec, **summarize(cfg, plain, rec)}
     out["by_threshold"] = {}
     for thr in extra_thresholds:
         rec = tr.run(learned=True, frames=frames, threshold=thr)

@@ -86,6 +86,16 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     lay.attr_begin[0] = 3
     assert B.lib().qn_decode_residuals(4, 4, 14, None, None, None, C.byref(lay), None, None, C.byref(gp_bad),
                                        None, None, None, None, None) == B.QN_ERR_INVALID_ARG
+    gp = B.make_gate(0.3, -0.5, 1.01)
+    assert B.lib().qn_decode_project(4, 4, 14, 1, 16, 16, 16, C.byref(lay), 16, 16, C.byref(gp), None,
+                                     C.byref(cam), 0.3, 1, None, None, 64, 48, 96, None) == B.QN_ERR_INVALID_ARG
+    assert b"sh_degree" in B.lib().qn_last_error()                                   # 14 planes are degree 0
+    assert B.lib().qn_decode_project(4, 4, 14, 0, 16, 16, 16, C.byref(lay), 16, 16, C.byref(gp), None,
+                                     C.byref(cam), 0.3, 1, None, None, 64, 40, 96, None) == B.QN_ERR_INVALID_ARG
+    assert b"aligned" in B.lib().qn_last_error()                                     # splats misaligned
+    assert B.lib().qn_decode_project(4, 4, 14, 0, 16, 16, 16, C.byref(lay), 16, 16, C.byref(gp), None,
+                                     C.byref(cam), 0.3, 1, None, None, 16, 48, 96, None) == B.QN_ERR_INVALID_ARG
+    assert b"alias" in B.lib().qn_last_error()                                       # out aliases prev
     assert B.lib().qn_adam(1, 4, 4, None, None, None, None, 0, 0.1, 0.9, 0.999, 1e-8, None, None, None) == \
         B.QN_ERR_INVALID_ARG
     assert B.lib().qn_bin_sort_workspace_size(-1, 4, 4) == 0

@@ -33,13 +33,10 @@ TAU, G0, G1 = 0.3, -0.5, 1.01
 GRAD_FLOOR = 0.01
 MAX_FRAGILE_FED = 0.001
 EPS_A_FED, EPS_T_FED = 5e-6, 2e-5     # margins of the fed leg (see test_gpu_parity.py)
-RTOL_GRAD_PROJ64 = 2e-4                # gradients behind separately computed projections (ditto)
-# the conic gradient is the footprint's second moments sum s dx^2, sum s dx dy,
-# sum s dy^2 of s = dL/dpower, which changes sign across it: its terms carry
-# the FP32 rounding of alpha (the exponent's ~1e-6) through the transmittance
-# of 60-90-deep stacks (~1e-5 each), and the sum cancels by ~20 at the 1%
-# floor; measured worst 2.0e-4 (300k) and 1.5e-4 (1M)
-RTOL_CONIC_DEEP = 2.5e-4
+# a gradient entry that cancels is kept by FP32 only to a multiple of u times
+# the sum of its terms' magnitudes (the oracle's magnitude sums); 512 ulps as
+# in test_gpu_parity.py
+KMAG = 512 * 2.0 ** -24
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,16 +51,29 @@ def up(a, dtype=torch.float32):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
 
 
-def close(got, ref, rtol=1e-4, floor_frac=1e-2, what=""):
+def close(got, ref, rtol=1e-4, floor_frac=1e-2, what="", mag=None):
     got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
     if ref.size == 0:
         return
     den = np.maximum(np.abs(ref), floor_frac * np.abs(ref).max())
     err = np.abs(got - ref) / den
-    at = np.unravel_index(err.argmax(), err.shape)
+    tol = rtol * den if mag is None else np.maximum(rtol * den, KMAG * np.asarray(mag, np.float64))
+    ratio = np.abs(got - ref) / tol
+    at = np.unravel_index(ratio.argmax(), ratio.shape)
     nrm = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
-    print(f"  {what}: worst {err.max():.3e} of the {floor_frac:g} floor (bar {rtol:.1e}), norm-wise {nrm:.2e}")
-    assert err.max() <= rtol, f"{what}: {err.max():.3e} at {at}: got {got[at]:.9g} ref {ref[at]:.9g} den {den[at]:.3g}"
+    extra = "" if mag is None else f", {int((rtol * den < tol).sum())} entries under the magnitude bound"
+    print(f"  {what}: worst {err.max():.3e} of the {floor_frac:g} floor (bar {rtol:.1e}), worst "
+          f"{ratio.max():.3f} of its bound, norm-wise {nrm:.2e}{extra}")
+    assert ratio.max() <= 1.0, (f"{what}: {ratio.max():.3f} of its bound at {at}: got {got[at]:.9g} "
+                                f"ref {ref[at]:.9g} den {den[at]:.3g}")
+
+
+def close_grads(gs, ref, tag=""):
+    m = ref["mag"]
+    close(gs[:, 0:2].T, ref["d_mean2d"], floor_frac=GRAD_FLOOR, what="d_mean2d" + tag, mag=m["d_mean2d"])
+    close(gs[:, 2], ref["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity" + tag, mag=m["d_opac"])
+    close(gs[:, 4:7].T, ref["d_conic"], floor_frac=GRAD_FLOOR, what="d_conic" + tag, mag=m["d_conic"])
+    close(gs[:, 8:11].T, ref["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb" + tag, mag=m["d_rgb"])
 
 
 def _bench():
@@ -135,13 +145,10 @@ def test_full_size_path_on_sampled_outputs(name):
     rast.d_img.copy_(up(d_img_f))
     rast.render_bwd(c, bg)
     torch.cuda.synchronize()
-    gf = oracle.render_bwd(pf, d_img_f, bg, tiles=tiles_f)
+    gf = oracle.render_bwd(pf, d_img_f, bg, tiles=tiles_f, magnitudes=True)
     assert (np.abs(gf["d_rgb"]).max(axis=0) > 0).sum() >= 500
     gs = rast.d_splats[:n].cpu().numpy()
-    close(gs[:, 0:2].T, gf["d_mean2d"], floor_frac=GRAD_FLOOR, what="d_mean2d (fed)")
-    close(gs[:, 2], gf["d_opac"], floor_frac=GRAD_FLOOR, what="d_opacity (fed)")
-    close(gs[:, 4:7].T, gf["d_conic"], rtol=RTOL_CONIC_DEEP, floor_frac=GRAD_FLOOR, what="d_conic (fed)")
-    close(gs[:, 8:11].T, gf["d_rgb"], floor_frac=GRAD_FLOOR, what="d_rgb (fed)")
+    close_grads(gs, gf, " (fed)")
     # leg 2: the oracle's own FP64 projection, on the 16 sampled tiles
     insample = insample_all
     img, T, last, frag = oracle.render_fwd(proj, bg, eps=EPS_A, eps_d=EPS_D, tiles=tiles)
@@ -177,20 +184,16 @@ def test_full_size_path_on_sampled_outputs(name):
     rast.d_img.copy_(up(d_img))
     rast.render_bwd(c, bg)
     torch.cuda.synchronize()
-    g2 = oracle.render_bwd(proj, d_img, bg, tiles=tiles)
+    g2 = oracle.render_bwd(proj, d_img, bg, tiles=tiles, magnitudes=True)
     touched = np.abs(g2["d_mean2d"]).max(axis=0) > 0
     assert touched.sum() >= 500 and (gate_ref[touched] > 0).sum() >= 10     # enough Gaussians and open gates
     gs = rast.d_splats[:n].cpu().numpy()
-    close(gs[:, 0:2].T, g2["d_mean2d"], rtol=RTOL_GRAD_PROJ64, floor_frac=GRAD_FLOOR, what="d_mean2d")
-    close(gs[:, 2], g2["d_opac"], rtol=RTOL_GRAD_PROJ64, floor_frac=GRAD_FLOOR, what="d_opacity")
-    close(gs[:, 4:7].T, g2["d_conic"], rtol=RTOL_GRAD_PROJ64, floor_frac=GRAD_FLOOR, what="d_conic")
-    close(gs[:, 8:11].T, g2["d_rgb"], rtol=RTOL_GRAD_PROJ64, floor_frac=GRAD_FLOOR, what="d_rgb")
+    close_grads(gs, g2)
     # the projection and decode adjoints, each fed the same inputs on both
     # sides: the projection adjoint the GPU's decoded A_t and the oracle's
     # upstream gradient rounded to FP32, the decode adjoint that projection
-    # adjoint (as the binning and the compositing are compared: a needle-like
-    # Gaussian makes the projection adjoint ill-conditioned, and the FP32
-    # rounding of A_t alone moves it by more than the bar)
+    # adjoint (as the binning and the compositing are compared: the adjoint
+    # of a needle-like Gaussian is sensitive to the FP32 rounding of A_t)
     rec = np.zeros((n, 12), np.float32)
     rec[:, 0:2] = g2["d_mean2d"].T
     rec[:, 2] = g2["d_opac"]
@@ -202,21 +205,28 @@ def test_full_size_path_on_sampled_outputs(name):
     r64 = rec.astype(np.float64)
     dA = oracle.project_bwd(got_A.astype(np.float64), cam, deg, r64[:, 0:2].T, r64[:, 4:7].T, r64[:, 2],
                             r64[:, 8:11].T, blur=hp.blur)
-    # dL/dSigma' sums terms of the size of the conic's entries that cancel by
-    # the projected covariance's condition number kappa (needle-like
-    # Gaussians), so FP32 keeps 1e-4 only up to kappa ~ 50; above it the bar
-    # scales with kappa, for the few Gaussians concerned
+    # needle-like Gaussians included: the kernel forms dL/dSigma' in the
+    # eigenbasis of the projected covariance, so the flat bar holds for them
     A_, B_, C_ = proj["conic"]
     tr, dt = A_ + C_, A_ * C_ - B_ * B_
     disc = np.sqrt(np.maximum(tr * tr / 4 - dt, 0.0))
     kappa = np.where(dt > 0, (tr / 2 + disc) / np.maximum(tr / 2 - disc, 1e-30), 1.0)
-    tol = 1e-4 * np.maximum(1.0, kappa / 50.0)
-    assert (kappa[touched] > 50).mean() < 0.02
-    got = frame.d_attrs[:, :n].cpu().numpy().astype(np.float64)
-    den = np.maximum(np.abs(dA), GRAD_FLOOR * np.abs(dA).max())
-    err = np.abs(got - dA) / den / tol[None, :]
-    at = np.unravel_index(err.argmax(), err.shape)
-    assert err.max() <= 1.0, f"d_attrs: {err.max():.3f} of the bar at {at} (kappa {kappa[at[1]]:.0f})"
+    print(f"  touched Gaussians: {int(touched.sum())}, largest condition number {kappa[touched].max():.0f}")
+    got = frame.d_attrs[:, :n].cpu().numpy()
+    for k in range(dA.shape[0]):        # each attribute plane against its own 1% floor
+        if 3 <= k <= 6:
+            continue
+        if np.abs(dA[k]).max() == 0.0:
+            assert not got[k].any(), k
+        else:
+            close(got[k], dA[k], floor_frac=GRAD_FLOOR, what=f"d_attrs plane {k}")
+    # the rotation gradient is a 4-vector tangent to the unit quaternion:
+    # compared per Gaussian as a vector (a component that is small in this
+    # frame carries the rounding of the large ones)
+    nq = np.linalg.norm(dA[3:7], axis=0)
+    eq = np.linalg.norm(got[3:7] - dA[3:7], axis=0) / np.maximum(nq, GRAD_FLOOR * nq.max())
+    print(f"  d_attrs rotation (per Gaussian, norm-wise): worst {eq.max():.3e} at {eq.argmax()}")
+    assert eq.max() <= 1e-4, (eq.max(), int(eq.argmax()))
     frame.d_attrs[:, :n] = up(dA)
     frame.decode_bwd()
     torch.cuda.synchronize()

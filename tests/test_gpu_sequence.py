@@ -4,7 +4,8 @@ a fixed order the training is reproducible, so the learned arm's training
 frames equal the plain arm's bit for bit; on each skip frame the mean PSNR
 over the training views stays within 0.05 dB of plain gated training of that
 frame from the same state (a fallback reproduces that plain result exactly),
-and the network's loss falls while it learns which residuals stay zero."""
+and the network's loss falls while it learns which residuals stay zero.  The
+non-learned arm (the previous frame's label as the skip) runs the same way."""
 import numpy as np
 import pytest
 import torch
@@ -44,6 +45,17 @@ def test_learned_skip_on_short_sequence():
     # in measured runs, with +-0.05 of frame-to-frame noise)
     losses = [r.mlp_loss for r in learned[:cfg.train_frames]]
     assert losses[-1] < 0.8 * losses[0]
+    # the non-learned arm (skip what the previous frame's label called
+    # static): the same training frames, the same fallback criterion
+    rule = out["rule"]["learned"]
+    for p, q in zip(plain[:cfg.train_frames], rule[:cfg.train_frames]):
+        assert p.psnr == q.psnr
+    rskip = [r for r in rule if r.t > cfg.train_frames]
+    assert len(rskip) == 4
+    for r in rskip:
+        assert r.psnr_train >= r.psnr_plain_train - cfg.max_dpsnr
+        assert 0.0 < r.skipped < 1.0
+        assert r.render_bwd_ms_skip > 0.0 and r.render_bwd_ms_plain > 0.0
 
 
 def test_masked_training_on_short_sequence():

@@ -297,3 +297,30 @@ def test_tight_rect_closed_form():
     mx, my = f * 0.3 / z + W / 2, f * -0.2 / z + H / 2
     assert list(r["rect"][:, 0]) == [math.floor((mx - h) / 16), math.floor((my - h) / 16),
                                      math.floor((mx + h) / 16) + 1, math.floor((my + h) / 16) + 1]
+
+
+def test_magnitude_sums_bound_and_equal_without_sign_changes():
+    """The adjoint's magnitude sums (the bound floating-point summation keeps
+    to): never below an entry's magnitude on a random scene; equal to it for
+    one Gaussian over a black background under a positive upstream gradient,
+    where no term of the conic's diagonal, the opacity or the colour changes
+    sign; far above it where an antisymmetric upstream gradient cancels."""
+    pr = _fd_scene(3)
+    rng = np.random.default_rng(3)
+    g = oracle.render_bwd(pr, rng.standard_normal((3, 32, 32)), bg=(0.2, 0.1, 0.4), magnitudes=True)
+    for k in ("d_mean2d", "d_conic", "d_opac", "d_rgb"):
+        assert np.all(g["mag"][k] >= np.abs(g[k]) * (1 - 1e-12)), k
+    W = H = 32
+    pr1 = splats(W, H, [(15.7, 16.2)], 3.0, [0.7], [(0.3, 0.6, 0.9)], [1.0])
+    g1 = oracle.render_bwd(pr1, np.ones((3, H, W)), magnitudes=True)
+    m = g1["mag"]
+    assert m["d_conic"][0, 0] == pytest.approx(abs(g1["d_conic"][0, 0]), rel=1e-12)
+    assert m["d_conic"][2, 0] == pytest.approx(abs(g1["d_conic"][2, 0]), rel=1e-12)
+    assert m["d_opac"][0] == pytest.approx(abs(g1["d_opac"][0]), rel=1e-12)
+    assert np.allclose(m["d_rgb"][:, 0], np.abs(g1["d_rgb"][:, 0]), rtol=1e-12)
+    # upstream +1 left of the mean, -1 right of it: the x-moment terms cancel
+    pr2 = splats(W, H, [(16.0, 16.0)], 3.0, [0.7], [(0.3, 0.6, 0.9)], [1.0])
+    d = np.where(np.arange(W)[None, None, :] < 16, 1.0, -1.0) * np.ones((3, H, W))
+    g2 = oracle.render_bwd(pr2, d, magnitudes=True)
+    assert abs(g2["d_conic"][0, 0]) < 1e-9 * g2["mag"]["d_conic"][0, 0]
+    assert g2["mag"]["d_conic"][0, 0] > 0
