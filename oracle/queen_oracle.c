@@ -20,8 +20,11 @@
  *   Sec. 3.2.2, Eq. 6-8  hard-concrete gate and its L0 penalty
  *
  * Readings where the paper is silent (it only cites the 3D-GS rasterizer):
- *   - alpha = min(0.99, o exp(power)); skipped when alpha < 1/255 or power > 0;
+ *   - alpha = min(0.99, o exp(power)); skipped when alpha < 1/255;
  *     compositing stops before the Gaussian that would push T below 1e-4.
+ *     (power <= 0 for a positive definite conic; the 3D-GS rasterizer's
+ *     "power > 0" skip only fires on rounding at a footprint's centre, where
+ *     it would drop the Gaussian's largest term, and is not taken.)
  *   - pixel (u, v) is sampled at (u + 0.5, v + 0.5); p' = (fx x/z + cx, fy y/z + cy).
  *   - Sigma' gets `blur` added to its diagonal (opacity is not rescaled).
  *   - radius = ceil(3 sqrt(lambda_max)), lambda_max = mid + sqrt(max(0.1, mid^2 - det));
@@ -706,7 +709,6 @@ static int or_pixel(const or_dk *list, int m, int n, double px, double py, const
         double dx = px - mean2d[g], dy = py - mean2d[(size_t)n + g];
         double a = conic[g], b = conic[(size_t)n + g], c = conic[(size_t)2 * n + g];
         double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
-        if (power > 0.0) continue;
         double G = exp(power);
         double v = opac[g] * G;
         if (fabs(v - OR_C.alpha_min) <= eps * OR_C.alpha_min) fr |= 1;

@@ -327,8 +327,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
     float d_lreg, const uint8_t *__restrict__ skip, float *__restrict__ d_lat,
     float *__restrict__ partials, float *__restrict__ d_lp, float *__restrict__ d_la) {
     __shared__ __align__(16) float sD[MAX_RES_PLANES * 8];
-    __shared__ float s_dr[MAX_RES_PLANES][BWD_TILE + 1];
-    __shared__ __align__(16) float s_lT[BWD_TILE][LT8_STRIDE];
+    __shared__ float s_dr[2][MAX_RES_PLANES][BWD_TILE + 1];         // two tiles: one barrier per tile
+    __shared__ __align__(16) float s_lT[2][BWD_TILE][LT8_STRIDE];
     __shared__ float s_part[2][MAX_RES_PLANES * 8];
     for (int k = threadIdx.x; k < a.n_dec; k += BWD_THREADS) sD[k] = bf16_to_f32(dec[k]);
     const size_t S = a.stride;
@@ -349,51 +349,52 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
     const int step = gridDim.x * BWD_TILE;
     TileRegs t;
     load_tile<NOISE>(a, blockIdx.x * BWD_TILE, lane, row0, lat, lp, la, d_out, skip, t);
-    for (int base = blockIdx.x * BWD_TILE; base < a.n; base += step) {
+    int buf = 0;
+    for (int base = blockIdx.x * BWD_TILE; base < a.n; base += step, buf ^= 1) {
         const int i = base + lane;
         const bool valid = t.valid, sk = t.sk;
-        // the barrier also keeps the previous tile's readers ahead of the stores below
-        if (__syncthreads_and(!valid || sk)) {            // a tile of skipped Gaussians only zeroes them
-            if (valid) {
-                for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) d_lat[(size_t)k * S + i] = 0.f;
-                if (row0 == 0) {
-                    d_lp[i] = d_lp[S + i] = d_lp[2 * S + i] = 0.f;
-                    d_la[i] = 0.f;
-                }
-            }
-            load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);
-            continue;
-        }
+        // stage this tile in buffer buf: its last readers (two tiles ago) are
+        // behind the previous tile's barrier
 #pragma unroll
         for (int m = 0; m < PF_DR; ++m) {
             const int r = row0 + m * ROWS_PER_PASS;
-            if (r < n_res) s_dr[r][lane] = t.dr[m];
+            if (r < n_res) s_dr[buf][r][lane] = t.dr[m];
         }
 #pragma unroll
         for (int m = 0; m < PF_L; ++m) {
             const int k = row0 + m * ROWS_PER_PASS;
-            if (k < a.n_lat) s_lT[lane][k] = latent_int(t.l[m]);
+            if (k < a.n_lat) s_lT[buf][lane][k] = latent_int(t.l[m]);
         }
         if (row0 == 0 && valid) {
-            const float gh = sigmoidf_(t.lz / a.tau);
-            const float gt = gh * (a.g1 - a.g0) + a.g0;
-            const float g = fminf(1.f, fmaxf(0.f, gt));
-            const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
-            float dot = 0.f;
+            float dlp[3] = {0.f, 0.f, 0.f}, dla = 0.f;
+            if (!sk) {
+                const float gh = sigmoidf_(t.lz / a.tau);
+                const float gt = gh * (a.g1 - a.g0) + a.g0;
+                const float g = fminf(1.f, fmaxf(0.f, gt));
+                const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
+                float dot = 0.f;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                d_lp[d * S + i] = sk ? 0.f : g * t.dp[d];
-                dot = fmaf(t.dp[d], t.lp[d], dot);
+                for (int d = 0; d < 3; ++d) {
+                    dlp[d] = g * t.dp[d];
+                    dot = fmaf(t.dp[d], t.lp[d], dot);
+                }
+                const float p = sigmoidf_(t.la - a.shift);
+                dla = dot * dg + d_lreg * p * (1.f - p);
             }
-            const float p = sigmoidf_(t.la - a.shift);
-            d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) d_lp[d * S + i] = dlp[d];
+            d_la[i] = dla;
         }
         load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
-        __syncthreads();
+        if (!__syncthreads_or(valid && !sk)) {             // a tile of skipped Gaussians only zeroes them
+            if (valid)
+                for (int k = row0; k < a.n_lat; k += ROWS_PER_PASS) d_lat[(size_t)k * S + i] = 0.f;
+            continue;
+        }
         // STE: d_lat of latents 4 lh .. 4 lh + 3 of category lc
         if (valid && lc < a.n_cat) {
             const float *D = sD + a.dec_off[lc] + 4 * lh;
-            const float *dr = &s_dr[a.ab[lc] - 3][lane];
+            const float *dr = &s_dr[buf][a.ab[lc] - 3][lane];
             float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
 #pragma unroll 4
             for (int r = 0; r < a.ac[lc]; ++r) {
@@ -414,8 +415,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
         if (dd_on) {
 #pragma unroll 4
             for (int j = 16 * jh; j < 16 * jh + 16; ++j) {
-                const float d = s_dr[R][j];
-                const float4 l4 = *reinterpret_cast<const float4 *>(&s_lT[j][d_l]);
+                const float d = s_dr[buf][R][j];
+                const float4 l4 = *reinterpret_cast<const float4 *>(&s_lT[buf][j][d_l]);
                 acc[0] = fmaf(d, l4.x, acc[0]);
                 acc[1] = fmaf(d, l4.y, acc[1]);
                 acc[2] = fmaf(d, l4.z, acc[2]);

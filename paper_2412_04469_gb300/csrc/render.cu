@@ -178,10 +178,12 @@ __device__ __forceinline__ void pixel_coords(int tile, int TX, int &px, int &py0
 // FWD_PPT pixels of one column as independent scalar chains (packing them
 // buys no FP32 throughput here, and the forward's alpha test and update are
 // mostly compares and selects).  The per-pixel update is branch-free
-// (selects and zero weights).  Per pixel:
-//   alpha = min(0.99, o 2^e); skipped unless e <= 0 and alpha >= 1/255;
-//   T' = T (1 - alpha); stop before the Gaussian if T' < 1e-4;
-//   C += c alpha T; T = T'.
+// (an effective alpha that is 0 unless the Gaussian is taken).  Per pixel:
+//   alpha = min(0.99, o 2^e); skipped if alpha < 1/255 (e <= 0 holds for a
+//   positive definite conic, so its sign is not tested: a positive FP32 e
+//   only arises from rounding at the footprint's centre);
+//   stop before the Gaussian if T (1 - alpha) < 1e-4;
+//   C += c alpha T; T -= alpha T.
 // comp (nullable): set to 1 for every Gaussian some pixel composites (one
 // store per composited record and warp, after each batch).  order
 // (nullable): block b composites tile order[b] (heaviest first: the blocks
@@ -215,7 +217,8 @@ __device__ __forceinline__ void scalar_exponent(const SRec &r, float fx, float f
     }
 }
 
-template <bool COUNT, int PPT>
+// COUNT: write the contributor counts; MARK: set the composited marks.
+template <bool COUNT, bool MARK, int PPT>
 __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H, int TX,
                                                                   const uint32_t *__restrict__ ranges,
                                                                   const uint32_t *__restrict__ vals,
@@ -279,23 +282,24 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
             for (int q = 0; q < PPT; ++q) {
                 const float v = __fmul_rn(r.g.z, ex2_approx(e[q]));
                 const float al = fminf(v, ALPHA_MAX);
-                const bool ok = ((live >> q) & 1u) && e[q] <= 0.f && al >= ALPHA_MIN;
-                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, al));
-                const bool stop = Tn < T_MIN;
-                const bool add = ok && !stop;
-                if (ok && stop) live &= ~(1u << q);
-                const float w = add ? al * T[q] : 0.f;
+                const bool ok = ((live >> q) & 1u) && al >= ALPHA_MIN;
+                const bool add = ok && __fmul_rn(T[q], __fsub_rn(1.f, al)) >= T_MIN;
+                if (ok && !add) live &= ~(1u << q);     // stops before this Gaussian
+                // the update through the effective alpha ae (0 unless added):
+                // T <- T - ae T, C <- C + c ae T, on the FMA pipe
+                const float ae = add ? al : 0.f;
+                const float w = __fmul_rn(ae, T[q]);
                 c0[q] = fmaf(c.x, w, c0[q]);
                 c1[q] = fmaf(c.y, w, c1[q]);
                 c2[q] = fmaf(c.z, w, c2[q]);
-                T[q] = add ? Tn : T[q];
+                T[q] = __fsub_rn(T[q], w);
                 lastc[q] = add ? pos1 : lastc[q];
                 if (COUNT) nc[q] += add ? 1u : 0u;
-                added |= add;
+                if (MARK) added |= add;
             }
-            if (comp && __any_sync(FULL, added)) batch_added |= 1u << j;
+            if (MARK && __any_sync(FULL, added)) batch_added |= 1u << j;
         }
-        if (comp && ((batch_added >> lane) & 1u)) comp[my_id] = 1;
+        if (MARK && ((batch_added >> lane) & 1u)) comp[my_id] = 1;
         __syncwarp();
     }
     const size_t plane = (size_t)W * H;
@@ -482,8 +486,8 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H,
                         upk(x.e[p], e0, e1);
                         upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
                         const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
-                        const bool ok0 = pos < lastp[2 * p] && e0 <= 0.f && a0 >= ALPHA_MIN;
-                        const bool ok1 = pos < lastp[2 * p + 1] && e1 <= 0.f && a1 >= ALPHA_MIN;
+                        const bool ok0 = pos < lastp[2 * p] && a0 >= ALPHA_MIN;
+                        const bool ok1 = pos < lastp[2 * p + 1] && a1 >= ALPHA_MIN;
                         const f2 AE = pk(ok0 ? a0 : 0.f, ok1 ? a1 : 0.f);
                         upk(sub2(ONE, AE), m0, m1);
                         T[p] = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));
@@ -501,8 +505,8 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H,
                     upk(x.e[p], e0, e1);
                     upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
                     const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
-                    const bool ok0 = pos < lastp[2 * p] && e0 <= 0.f && a0 >= ALPHA_MIN;
-                    const bool ok1 = pos < lastp[2 * p + 1] && e1 <= 0.f && a1 >= ALPHA_MIN;
+                    const bool ok0 = pos < lastp[2 * p] && a0 >= ALPHA_MIN;
+                    const bool ok1 = pos < lastp[2 * p + 1] && a1 >= ALPHA_MIN;
                     any |= ok0 | ok1;
                     const float ae0 = ok0 ? a0 : 0.f, ae1 = ok1 ? a1 : 0.f;
                     const f2 AE = pk(ae0, ae1);
@@ -652,7 +656,8 @@ extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, 
     QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
     const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
     constexpr int PPT = QN_FWD_PPT;
-    auto kern = n_contrib ? qn::k_render_fwd<true, PPT> : qn::k_render_fwd<false, PPT>;
+    auto kern = n_contrib ? (composited ? qn::k_render_fwd<true, true, PPT> : qn::k_render_fwd<true, false, PPT>)
+                          : (composited ? qn::k_render_fwd<false, true, PPT> : qn::k_render_fwd<false, false, PPT>);
     kern<<<TX * TY, qn::Band<PPT>::THREADS, 0, qn::as_stream(stream)>>>(
         cam_host->width, cam_host->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg_host[0],
         bg_host[1], bg_host[2], img, T_final, last, n_contrib, composited, tile_order, tile_cost);
