@@ -37,7 +37,6 @@ METRIC = "fwd+bwd rasterize it/s @300k Gaussians 1352x1014; s/frame learned vs p
 L2_FLUSH_BYTES = 256 << 20
 # the reference arm times whole oracle iterations when its K + W steps fit in this
 REF_WHOLE_BUDGET_S = 300.0
-# kernels each stage launches (memsets are not counted)
 # kernels each stage launches (memsets are not counted); the step decodes and
 # projects in one kernel
 KERNELS_PER_STAGE = {"decode_project": 1, "bin_sort": 17, "render_fwd": 2, "loss": 4, "render_bwd": 1,

@@ -225,6 +225,34 @@ int qn_decode_project(int32_t n, int32_t n_stride, int32_t n_attr, int32_t sh_de
                       float *gate, float *lreg, float *out, qn_splat *splats, int32_t *rects,
                       qn_stream_t stream);
 
+/*
+ * qn_project_bwd then qn_decode_residuals_bwd in one pass, without A_t or
+ * dL/dA_t in memory: each block stages a tile of 64 Gaussians' columns of
+ * prev (A_{t-1}), lat and lp in shared memory, rebuilds A_t there with the
+ * operations of qn_decode_project (Eq. 4-8), runs the projection adjoint
+ * (Eq. 1) on it into a staged dL/dA_t, then the gate and decoder adjoints.
+ * d_lat, d_lp and d_log_alpha equal those of the two calls bit for bit (fed
+ * the A_t that qn_decode_project or qn_decode_residuals gives); d_dec is the
+ * same sum in another order (per-block partials of the tiles, then summed in
+ * block order: reproducible).
+ *   Arguments as for qn_decode_project and qn_decode_residuals_bwd:
+ *   d_splats [n] gradient records (read), d_lreg dL/dL_reg,
+ *   d_lat [sum lat_dim][n_stride], d_dec [sum attr_count*lat_dim],
+ *   d_lp [3][n_stride], d_log_alpha [n] (written),
+ *   partials [QN_DECODE_BWD_BLOCKS * sum attr_count*lat_dim] f32 scratch.
+ *   skip (nullable): skipped Gaussians get zero d_lat, d_lp, d_log_alpha and
+ *   add nothing to d_dec.
+ * prev, lat, lp and d_splats must be 16-byte aligned.
+ * Errors: QN_ERR_INVALID_ARG as for the calls it replaces, and for
+ * misaligned pointers.
+ */
+int qn_decode_project_bwd(int32_t n, int32_t n_stride, int32_t n_attr, int32_t sh_degree, const float *prev,
+                          const float *lat, const uint16_t *dec, const qn_decoder_layout *layout_host,
+                          const float *lp, const float *log_alpha, const qn_gate_params *gate_host,
+                          const uint8_t *skip, const qn_camera *cam_host, float blur, const qn_splat *d_splats,
+                          float d_lreg, float *d_lat, float *d_dec, float *d_lp, float *d_log_alpha,
+                          float *partials, qn_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Tile binning -- the tile-based rasterizer the paper builds on (Sec. 4).    */
 /* ------------------------------------------------------------------------ */

@@ -62,6 +62,8 @@ _SIGS = {
                            _P, _P], C.c_int),
     "qn_decode_residuals_bwd": ([_I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _P, _P, _P, _P, _P,
                                  _P], C.c_int),
+    "qn_decode_project_bwd": ([_I32, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _F32, _P, _F32, _P, _P,
+                               _P, _P, _P, _P], C.c_int),
     "qn_project": ([_I32, _I32, _I32, _P, _P, _F32, _I32, _P, _P, _P], C.c_int),
     "qn_project_bwd": ([_I32, _I32, _I32, _P, _P, _F32, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_workspace_size": ([_I32, _I32, _I32], _SZ),
@@ -189,6 +191,15 @@ def qn_decode_project(n, n_stride, n_attr, sh_degree, prev, lat, dec, layout, lp
                                    C.byref(layout), _ptr(lp), _ptr(log_alpha), C.byref(gate_params), _ptr(skip),
                                    C.byref(cam), float(blur), int(bool(tight_rects)), _ptr(gate), _ptr(lreg),
                                    _ptr(out), _ptr(splats), _ptr(rects), _stream(stream)))
+
+
+def qn_decode_project_bwd(n, n_stride, n_attr, sh_degree, prev, lat, dec, layout, lp, log_alpha, gate_params, skip,
+                          cam, blur, d_splats, d_lreg, d_lat, d_dec, d_lp, d_log_alpha, partials, stream=None):
+    """partials: QN_DECODE_BWD_BLOCKS * d_dec.numel() floats of scratch."""
+    _check(lib().qn_decode_project_bwd(n, n_stride, n_attr, sh_degree, _ptr(prev), _ptr(lat), _ptr(dec),
+                                       C.byref(layout), _ptr(lp), _ptr(log_alpha), C.byref(gate_params), _ptr(skip),
+                                       C.byref(cam), float(blur), _ptr(d_splats), float(d_lreg), _ptr(d_lat),
+                                       _ptr(d_dec), _ptr(d_lp), _ptr(d_log_alpha), _ptr(partials), _stream(stream)))
 
 
 def qn_decode_residuals_bwd(n, n_stride, n_attr, lat, dec, layout, lp, log_alpha, gate_params, d_out, d_lreg,

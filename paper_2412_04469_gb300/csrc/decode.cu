@@ -45,6 +45,18 @@ __device__ __forceinline__ float gate_logit(const DecodeArgs &a, float l_a, int 
     return l_a + (logf(u) - log1pf(-u));
 }
 
+// The gate's pre-clamp value gh (g1 - g0) + g0 (Eq. 7), the position update
+// p + g lp (Eq. 4) and the gate adjoint's d log alpha, each with its
+// roundings spelled out, so that every kernel that forms them (decode, fused
+// decode-projection, decode adjoint, fused adjoint) gets the same bits.
+__device__ __forceinline__ float gate_pre(const DecodeArgs &a, float gh) {
+    return __fmaf_rn(gh, __fsub_rn(a.g1, a.g0), a.g0);
+}
+__device__ __forceinline__ float pos_update(float p, float g, float lp) { return __fmaf_rn(g, lp, p); }
+__device__ __forceinline__ float d_log_alpha_of(float dot, float dg, float d_lreg, float p) {
+    return __fmaf_rn(dot, dg, __fmul_rn(__fmul_rn(d_lreg, p), __fsub_rn(1.f, p)));
+}
+
 // LT > 0: every category has latent width LT (compile-time loops, D rows
 // read as float4 broadcasts); LT == 0: any layout within the limits.
 template <int LT, bool NOISE>
@@ -65,11 +77,11 @@ __global__ void __launch_bounds__(256) k_decode(DecodeArgs a, const float *__res
         if (skip && skip[i]) continue;                 // frozen: out and gate already hold its values
         const float l_a = la[i];
         const float gh = sigmoidf_(gate_logit<NOISE>(a, l_a, i) / a.tau);   // Eq. 6
-        const float g = fminf(1.f, fmaxf(0.f, gh * (a.g1 - a.g0) + a.g0));   // Eq. 7
+        const float g = fminf(1.f, fmaxf(0.f, gate_pre(a, gh)));   // Eq. 7
         if (gate) gate[i] = g;
         reg += sigmoidf_(l_a - a.shift);                                // Eq. 8
 #pragma unroll
-        for (int d = 0; d < 3; ++d) out[d * S + i] = prev[d * S + i] + g * lp[d * S + i];
+        for (int d = 0; d < 3; ++d) out[d * S + i] = pos_update(prev[d * S + i], g, lp[d * S + i]);
         for (int c = 0; c < a.n_cat; ++c) {
             const float *D = sD + a.dec_off[c];
             if (LT > 0) {
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
         }
         if (row0 == 0 && valid) {
             const float gh = sigmoidf_(t.lz / a.tau);
-            const float gt = gh * (a.g1 - a.g0) + a.g0;
+            const float gt = gate_pre(a, gh);
             const float g = fminf(1.f, fmaxf(0.f, gt));
             const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
             float dot = 0.f;
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_decode_bwd(
                 dot = fmaf(t.dp[d], t.lp[d], dot);
             }
             const float p = sigmoidf_(t.la - a.shift);
-            d_la[i] = sk ? 0.f : dot * dg + d_lreg * p * (1.f - p);
+            d_la[i] = sk ? 0.f : d_log_alpha_of(dot, dg, d_lreg, p);
         }
         load_tile<NOISE>(a, base + step, lane, row0, lat, lp, la, d_out, skip, t);   // in flight during the compute
         __syncthreads();
@@ -369,7 +381,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
             float dlp[3] = {0.f, 0.f, 0.f}, dla = 0.f;
             if (!sk) {
                 const float gh = sigmoidf_(t.lz / a.tau);
-                const float gt = gh * (a.g1 - a.g0) + a.g0;
+                const float gt = gate_pre(a, gh);
                 const float g = fminf(1.f, fmaxf(0.f, gt));
                 const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
                 float dot = 0.f;
@@ -379,7 +391,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_decode_bwd8(
                     dot = fmaf(t.dp[d], t.lp[d], dot);
                 }
                 const float p = sigmoidf_(t.la - a.shift);
-                dla = dot * dg + d_lreg * p * (1.f - p);
+                dla = d_log_alpha_of(dot, dg, d_lreg, p);
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d) d_lp[d * S + i] = dlp[d];
@@ -533,13 +545,13 @@ __global__ void __launch_bounds__(DP_TILE) k_decode_project(DecodeArgs a, CamArg
             const bool sk = skip && skip[i];
             const float l_a = la[i];
             const float gh = sigmoidf_(gate_logit<NOISE>(a, l_a, i) / a.tau);   // Eq. 6
-            const float g = fminf(1.f, fmaxf(0.f, gh * (a.g1 - a.g0) + a.g0));   // Eq. 7
+            const float g = fminf(1.f, fmaxf(0.f, gate_pre(a, gh)));   // Eq. 7
             if (!sk) {                                  // a skipped Gaussian keeps its gate entry
                 if (gate) gate[i] = g;
                 reg += sigmoidf_(l_a - a.shift);        // Eq. 8
             }
 #pragma unroll
-            for (int d = 0; d < 3; ++d) sA[d * DP_TILE + t] = sA[d * DP_TILE + t] + g * sP[d * DP_TILE + t];
+            for (int d = 0; d < 3; ++d) sA[d * DP_TILE + t] = pos_update(sA[d * DP_TILE + t], g, sP[d * DP_TILE + t]);
             for (int c = 0; c < a.n_cat; ++c) {
                 const float *D = sD + a.dec_off[c];
                 const int L = LT > 0 ? LT : a.ld[c];
@@ -591,6 +603,221 @@ int launch_decode_project(const DecodeArgs &a, const CamArgs &cm, float blur, in
     kern<<<grid_for(a.n, DP_TILE, 8), DP_TILE, smem, s>>>(a, cm, blur, tight, prev, lat, dec, lp, la, skip, gate,
                                                            lreg, out, splat, rects);
     return check_launch("qn_decode_project");
+}
+
+// ---------------------------------------------------------------- fused projection + decode adjoint
+// The adjoints of qn_project and qn_decode_residuals for a tile of FB_TILE
+// Gaussians without A_t or dL/dA_t in HBM: the tile's planes of A_{t-1}, its
+// latents and its position residual are staged in shared memory (cp.async),
+// each thread rebuilds its Gaussian's A_t there with the forward's operations
+// (so the projection adjoint sees the A_t the forward projected), runs the
+// projection adjoint into a second staged tile, then the gate adjoint and
+// d_lat = D^T dr (in the decode adjoint's order: the same values bit for
+// bit), and after one barrier each thread adds its share of dD = sum dr l^T
+// over the tile.  Each block's dD partial is summed over blocks in block
+// order afterwards (reproducible; a different summation order from the
+// two-kernel path's).
+constexpr int FB_TILE = 64;
+constexpr int FB_S = 68;                        // staged plane stride: rows stay 16-byte aligned
+constexpr int FB_DS = 65;                       // dL/dA_t plane stride: the dD rows fall in different banks
+constexpr int FB_OWN = (MAX_RES_PLANES * QN_MAX_LATENT + FB_TILE - 1) / FB_TILE;
+
+// floats of the staged dL/dA_t, rounded up so that what follows stays 16-byte aligned
+__host__ __device__ __forceinline__ int fb_grad_floats(int n_attr) { return (n_attr * FB_DS + 3) & ~3; }
+
+size_t fused_bwd_smem(const DecodeArgs &a) {
+    return sizeof(float) * ((size_t)(a.n_attr + a.n_lat + 3) * FB_S + (size_t)fb_grad_floats(a.n_attr) +
+                            (size_t)FB_TILE * ((a.n_lat + 7) & ~3) + a.n_dec);
+}
+
+template <int DEG, int LT, bool NOISE>
+__global__ void __launch_bounds__(FB_TILE) k_decode_project_bwd(
+    DecodeArgs a, CamArgs cm, float blur, const float *__restrict__ prev, const float *__restrict__ lat,
+    const uint16_t *__restrict__ dec, const float *__restrict__ lp, const float *__restrict__ la,
+    const uint8_t *__restrict__ skip, const float4 *__restrict__ dsp, float d_lreg, float *__restrict__ d_lat,
+    float *__restrict__ partials, float *__restrict__ d_lp, float *__restrict__ d_la) {
+    extern __shared__ __align__(16) float fb_smem[];
+    float *sA = fb_smem;                                // [n_attr][FB_S]: A_{t-1}, then A_t
+    float *sL = sA + a.n_attr * FB_S;                   // [n_lat][FB_S]: latents as staged
+    float *sP = sL + a.n_lat * FB_S;                    // [3][FB_S]: position residual
+    float *sG = sP + 3 * FB_S;                          // [n_attr][FB_DS]: dL/dA_t
+    float *sT = sG + fb_grad_floats(a.n_attr);          // [FB_TILE][lts]: rounded latents, transposed (16-byte rows)
+    float *sD = sT + FB_TILE * ((a.n_lat + 7) & ~3);    // decoders (f32)
+    const int t = threadIdx.x;
+    for (int k = t; k < a.n_dec; k += FB_TILE) sD[k] = bf16_to_f32(dec[k]);
+    const size_t S = a.stride;
+    const int rows = a.n_attr + a.n_lat + 3;
+    const int lts = (a.n_lat + 7) & ~3;                // transposed latent row stride
+    constexpr int n_attr_c = 11 + 3 * (DEG + 1) * (DEG + 1);
+    // dD entries of this thread: with LT == 8, decoder row t (all 8 latents of
+    // its category); otherwise entries t, t + FB_TILE, ...
+    float acc[LT > 0 ? LT : FB_OWN];
+#pragma unroll
+    for (int q = 0; q < (LT > 0 ? LT : FB_OWN); ++q) acc[q] = 0.f;
+    int own_row = -1, own_lat = 0;                      // LT == 8: residual row and first latent plane
+    if (LT > 0) {
+        for (int c = 0; c < a.n_cat; ++c)
+            if (t >= a.ab[c] - 3 && t < a.ab[c] - 3 + a.ac[c]) { own_row = t; own_lat = a.lat_off[c]; }
+    }
+    for (int base = blockIdx.x * FB_TILE; base < a.n; base += gridDim.x * FB_TILE) {
+        __syncthreads();                                // the previous tile's readers are done
+        for (int c = t; c < rows * (FB_TILE / 4); c += FB_TILE) {
+            const int row = c / (FB_TILE / 4), col = 4 * (c % (FB_TILE / 4));
+            if (base + col >= a.stride) continue;       // stride is a multiple of 4: chunks lie wholly inside
+            const float *src = row < a.n_attr ? prev + (size_t)row * S
+                             : row < a.n_attr + a.n_lat ? lat + (size_t)(row - a.n_attr) * S
+                                                        : lp + (size_t)(row - a.n_attr - a.n_lat) * S;
+            cp_async16(fb_smem + row * FB_S + col, src + base + col);
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const int i = base + t;
+        const int cnt = min(FB_TILE, a.n - base);
+        if (t < cnt) {
+            const bool sk = skip && skip[i];
+            const float l_a = la[i];
+            const float gh = sigmoidf_(gate_logit<NOISE>(a, l_a, i) / a.tau);   // Eq. 6
+            const float gt = gate_pre(a, gh);
+            const float g = fminf(1.f, fmaxf(0.f, gt));                          // Eq. 7
+            // A_t, as qn_decode_project forms it (Eq. 4-5)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sA[d * FB_S + t] = pos_update(sA[d * FB_S + t], g, sP[d * FB_S + t]);
+            for (int c = 0; c < a.n_cat; ++c) {
+                const float *D = sD + a.dec_off[c];
+                const int L = LT > 0 ? LT : a.ld[c];
+                float l[LT > 0 ? LT : QN_MAX_LATENT];
+#pragma unroll
+                for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                    if (k < L) {
+                        l[k] = latent_int(sL[(a.lat_off[c] + k) * FB_S + t]);
+                        sT[t * lts + a.lat_off[c] + k] = l[k];
+                    }
+                for (int r = 0; r < a.ac[c]; ++r) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                        if (k < L) s = fmaf(D[r * L + k], l[k], s);
+                    float &x = sA[(a.ab[c] + r) * FB_S + t];
+                    x = x + s;
+                }
+            }
+            // dL/dA_t of this Gaussian (a skipped one gets none)
+            if (sk) {
+                for (int k = 0; k < n_attr_c; ++k) sG[k * FB_DS + t] = 0.f;
+            } else {
+                project_bwd_one<DEG>(cm, blur, sA, FB_S, t, dsp + 3 * (size_t)base, sG, FB_DS, t);
+            }
+            // the gate's adjoint (Eq. 6-8)
+            float dlp[3] = {0.f, 0.f, 0.f}, dla = 0.f;
+            if (!sk) {
+                const float dg = (gt > 0.f && gt < 1.f) ? (a.g1 - a.g0) * gh * (1.f - gh) / a.tau : 0.f;
+                float dot = 0.f;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float dp = sG[d * FB_DS + t];
+                    dlp[d] = g * dp;
+                    dot = fmaf(dp, sP[d * FB_S + t], dot);
+                }
+                const float p = sigmoidf_(l_a - a.shift);
+                dla = d_log_alpha_of(dot, dg, d_lreg, p);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) d_lp[d * S + i] = dlp[d];
+            d_la[i] = dla;
+            // STE: d_lat = D^T dr, each latent summed over its rows in order
+            for (int c = 0; c < a.n_cat; ++c) {
+                const float *D = sD + a.dec_off[c];
+                const int L = LT > 0 ? LT : a.ld[c];
+                const float *dr = sG + (a.ab[c]) * FB_DS + t;
+                float o[LT > 0 ? LT : QN_MAX_LATENT];
+#pragma unroll
+                for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k) o[k] = 0.f;
+                for (int r = 0; r < a.ac[c]; ++r) {
+                    const float dv = dr[r * FB_DS];
+#pragma unroll
+                    for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                        if (k < L) o[k] = fmaf(D[r * L + k], dv, o[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                    if (k < L) d_lat[(size_t)(a.lat_off[c] + k) * S + i] = sk ? 0.f : o[k];
+            }
+        }
+        __syncthreads();
+        // dD += sum over the tile of dr l^T (skipped Gaussians have dr = 0)
+        if (LT > 0) {
+            if (own_row >= 0) {
+                const float *dr = sG + (3 + own_row) * FB_DS;
+                for (int j = 0; j < cnt; ++j) {
+                    const float dv = dr[j];
+                    const float4 l0 = *reinterpret_cast<const float4 *>(sT + j * lts + own_lat);
+                    const float4 l1 = *reinterpret_cast<const float4 *>(sT + j * lts + own_lat + 4);
+                    acc[0] = fmaf(dv, l0.x, acc[0]);
+                    acc[1] = fmaf(dv, l0.y, acc[1]);
+                    acc[2] = fmaf(dv, l0.z, acc[2]);
+                    acc[3] = fmaf(dv, l0.w, acc[3]);
+                    acc[4] = fmaf(dv, l1.x, acc[4]);
+                    acc[5] = fmaf(dv, l1.y, acc[5]);
+                    acc[6] = fmaf(dv, l1.z, acc[6]);
+                    acc[7] = fmaf(dv, l1.w, acc[7]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < FB_OWN; ++q) {
+                const int e = t + q * FB_TILE;
+                if (e >= a.n_dec) break;
+                int c = 0;
+                while (c + 1 < a.n_cat && e >= a.dec_off[c + 1]) ++c;
+                const int L = a.ld[c], r = (e - a.dec_off[c]) / L, k = (e - a.dec_off[c]) % L;
+                const float *dr = sG + (a.ab[c] + r) * FB_DS;
+                const float *lk = sT + a.lat_off[c] + k;
+                float s = acc[q];
+                for (int j = 0; j < cnt; ++j) s = fmaf(dr[j], lk[j * lts], s);
+                acc[q] = s;
+            }
+        }
+    }
+    // this block's partial dD; summed over blocks in block order afterwards
+    if (LT > 0) {
+        if (own_row >= 0) {
+            int c = 0;
+            while (c + 1 < a.n_cat && !(own_row >= a.ab[c] - 3 && own_row < a.ab[c] - 3 + a.ac[c])) ++c;
+            const int e0 = a.dec_off[c] + (own_row - (a.ab[c] - 3)) * LT;
+#pragma unroll
+            for (int k = 0; k < LT; ++k) partials[(size_t)blockIdx.x * a.n_dec + e0 + k] = acc[k];
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < FB_OWN; ++q) {
+            const int e = t + q * FB_TILE;
+            if (e < a.n_dec) partials[(size_t)blockIdx.x * a.n_dec + e] = acc[q];
+        }
+    }
+}
+
+template <int DEG>
+int launch_decode_project_bwd(const DecodeArgs &a, const CamArgs &cm, float blur, const float *prev,
+                              const float *lat, const uint16_t *dec, const float *lp, const float *la,
+                              const uint8_t *skip, const float4 *dsp, float d_lreg, float *d_lat, float *d_dec,
+                              float *partials, float *d_lp, float *d_la, cudaStream_t s) {
+    const bool w8 = uniform_width8(a), noise = a.noise != nullptr;
+    auto kern = w8 ? (noise ? k_decode_project_bwd<DEG, 8, true> : k_decode_project_bwd<DEG, 8, false>)
+                   : (noise ? k_decode_project_bwd<DEG, 0, true> : k_decode_project_bwd<DEG, 0, false>);
+    const size_t smem = fused_bwd_smem(a);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return check_launch("qn_decode_project_bwd attribute");
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FB_TILE, smem);
+    int grid = div_up(a.n, FB_TILE);
+    grid = std::min(grid, std::max(per_sm, 1) * sms);
+    grid = std::min(grid, (int)QN_DECODE_BWD_BLOCKS);
+    kern<<<grid, FB_TILE, smem, s>>>(a, cm, blur, prev, lat, dec, lp, la, skip, dsp, d_lreg, d_lat, partials, d_lp,
+                                     d_la);
+    if (a.n_dec > 0) k_sum_partials<<<sum_partials_grid(a.n_dec), 256, 0, s>>>(a.n_dec, grid, partials, d_dec);
+    return check_launch("qn_decode_project_bwd");
 }
 
 }  // namespace
@@ -646,6 +873,42 @@ extern "C" int qn_decode_project(int32_t n, int32_t n_stride, int32_t n_attr, in
                                                      qn::launch_decode_project<2>, qn::launch_decode_project<3>};
     return f[sh_degree](a, cm, blur, tight_rects != 0, prev, lat, dec, lp, log_alpha, skip, gate, lreg, out,
                         reinterpret_cast<float4 *>(splats), reinterpret_cast<int4 *>(rects), s);
+}
+
+extern "C" int qn_decode_project_bwd(int32_t n, int32_t n_stride, int32_t n_attr, int32_t sh_degree,
+                                     const float *prev, const float *lat, const uint16_t *dec,
+                                     const qn_decoder_layout *layout_host, const float *lp, const float *log_alpha,
+                                     const qn_gate_params *gate_host, const uint8_t *skip,
+                                     const qn_camera *cam_host, float blur, const qn_splat *d_splats, float d_lreg,
+                                     float *d_lat, float *d_dec, float *d_lp, float *d_log_alpha, float *partials,
+                                     qn_stream_t stream) {
+    qn::DecodeArgs a;
+    int st = qn::make_args(n, n_stride, n_attr, layout_host, gate_host, &a);
+    if (st) return st;
+    qn::CamArgs cm;
+    st = qn::cam_args(cam_host, &cm);
+    if (st) return st;
+    QN_REQUIRE(sh_degree >= 0 && sh_degree <= 3 && n_attr == 11 + 3 * (sh_degree + 1) * (sh_degree + 1),
+               "sh_degree %d does not match n_attr %d", sh_degree, n_attr);
+    QN_REQUIRE(blur >= 0.f, "blur must be >= 0");
+    QN_REQUIRE(n == 0 || (prev && lp && log_alpha && d_splats && d_lp && d_log_alpha), "null pointer argument");
+    QN_REQUIRE(a.n_cat == 0 || (d_dec && (n == 0 || (lat && dec && d_lat && partials))),
+               "null latent/decoder/partials pointer");
+    QN_REQUIRE(((uintptr_t)prev & 15) == 0 && ((uintptr_t)lat & 15) == 0 && ((uintptr_t)lp & 15) == 0 &&
+                   ((uintptr_t)d_splats & 15) == 0,
+               "prev, lat, lp and d_splats must be 16-byte aligned");
+    cudaStream_t s = qn::as_stream(stream);
+    if (n == 0) {
+        if (a.n_dec > 0 && cudaMemsetAsync(d_dec, 0, sizeof(float) * a.n_dec, s) != cudaSuccess)
+            return qn::check_launch("decode_project_bwd memset");
+        return QN_OK;
+    }
+    decltype(&qn::launch_decode_project_bwd<0>) f[4] = {
+        qn::launch_decode_project_bwd<0>, qn::launch_decode_project_bwd<1>, qn::launch_decode_project_bwd<2>,
+        qn::launch_decode_project_bwd<3>};
+    return f[sh_degree](a, cm, blur, prev, lat, dec, lp, log_alpha, skip,
+                        reinterpret_cast<const float4 *>(d_splats), d_lreg, d_lat, d_dec, partials, d_lp,
+                        d_log_alpha, s);
 }
 
 extern "C" int qn_decode_residuals_bwd(int32_t n, int32_t n_stride, int32_t n_attr, const float *lat,

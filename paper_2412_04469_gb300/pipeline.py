@@ -63,6 +63,12 @@ class HParams:
     # the training iteration decodes and projects in one pass (a skipped
     # Gaussian is then rendered with the current decoders)
     fused: bool = True
+    # with fused, the projection and decode adjoints can also run in one
+    # pass that rebuilds A_t in shared memory, so A_t is never written (d_dec
+    # is then summed in another order).  Off: at 300k Gaussians it measured
+    # 0.129 ms against 0.105 ms for the two kernels (its ~800 bytes of shared
+    # memory per Gaussian leave ~8 warps per SM for a long serial chain)
+    fused_bwd: bool = False
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
@@ -211,16 +217,25 @@ class QueenFrame:
             return self.c_gate_train
         return self.c_gate
 
-    def decode_project(self, rast: "Rasterizer", cam, stream=None, skip=None):
+    def decode_project(self, rast: "Rasterizer", cam, stream=None, skip=None, keep_attrs: bool = True):
         """A training iteration's decode (Eq. 4-8) and projection (Eq. 1) in
         one pass into rast's records and rects, A_t into attrs (for the
-        projection adjoint).  Gaussians with skip set keep their gate entries
-        and add nothing to lreg; their A_t is rebuilt from the current
-        decoders like every other."""
+        projection adjoint) unless keep_attrs is False.  Gaussians with skip
+        set keep their gate entries and add nothing to lreg; their A_t is
+        rebuilt from the current decoders like every other."""
         B.qn_decode_project(self.n, self.S, self.n_attr, self.sh_degree, self.prev, self.lat, self.dec_bf16,
                             self.c_layout, self.lp, self.log_alpha, self._train_gate(stream), skip, cam,
-                            self.hp.blur, rast.tight_rects, self.gate, self.lreg, self.attrs, rast.splats, rast.rects,
-                            stream)
+                            self.hp.blur, rast.tight_rects, self.gate, self.lreg,
+                            self.attrs if keep_attrs else None, rast.splats, rast.rects, stream)
+
+    def decode_project_bwd(self, rast: "Rasterizer", cam, skip=None, stream=None):
+        """The projection adjoint (from rast.d_splats) and the decode adjoint
+        in one pass, A_t rebuilt from prev and the residuals as
+        decode_project forms it (the iteration's gate noise included)."""
+        B.qn_decode_project_bwd(self.n, self.S, self.n_attr, self.sh_degree, self.prev, self.lat, self.dec_bf16,
+                                self.c_layout, self.lp, self.log_alpha, self.c_gate_train, skip, cam, self.hp.blur,
+                                rast.d_splats, self.d_lreg, self.d_lat, self.d_dec, self.d_lp, self.d_log_alpha,
+                                self.dec_partials, stream)
 
     def decode_bwd(self, skip=None, stream=None):
         B.qn_decode_residuals_bwd(self.n, self.S, self.n_attr, self.lat, self.dec_bf16, self.c_layout, self.lp,
@@ -432,8 +447,9 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     hp = frame.hp
     unskip = unskip and skip is not None
     mark = mark or unskip or hp.mark_composited
+    fused_bwd = hp.fused and hp.fused_bwd
     if hp.fused:
-        frame.decode_project(rast, cam, stream, skip)
+        frame.decode_project(rast, cam, stream, skip, keep_attrs=not fused_bwd)
     else:
         frame.decode(stream, skip, train=True)
         rast.project(frame.attrs, cam, hp.blur, stream)
@@ -447,8 +463,11 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     if unskip:
         B.qn_clear_marked(rast.n, rast.composited, skip, stream)
     rast.render_bwd(cam, hp.bg, skip, stream, ranges=ranges, marks=mark, order=hp.order_tiles)
-    rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
-    frame.decode_bwd(skip, stream)
+    if fused_bwd:
+        frame.decode_project_bwd(rast, cam, skip, stream)
+    else:
+        rast.project_bwd(frame.attrs, cam, hp.blur, frame.d_attrs, skip, stream)
+        frame.decode_bwd(skip, stream)
     frame.adam(skip, stream)
 
 

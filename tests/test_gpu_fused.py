@@ -1,9 +1,11 @@
-"""The fused decode-and-project kernel of the training iteration,
-qn_decode_project (Eq. 4-8 then Eq. 1 on a tile staged in shared memory),
-against the two kernels it replaces (qn_decode_residuals, qn_project) and the
-oracle.  It runs the same operations in the same order, so A_t, the records,
-the rects and the gate match the two-kernel path bit for bit, and so does a
-whole training iteration.  Sizes span ragged last tiles, n = 1, every SH
+"""The fused kernels of the training iteration against the kernels they
+replace and the oracle: qn_decode_project (Eq. 4-8 then Eq. 1 on a tile
+staged in shared memory) against qn_decode_residuals + qn_project, and
+qn_decode_project_bwd (A_t rebuilt in shared memory, then the projection and
+decode adjoints) against qn_project_bwd + qn_decode_residuals_bwd.  They run
+the same operations in the same order, so A_t, the records, the rects, the
+gate, d_lat, d_lp and d_log_alpha match bit for bit; the decoder gradient is
+the same sum in another order.  Sizes span ragged last tiles, n = 1, every SH
 degree, the paper's N3DV decoder layout (latent widths 6/8/3/8/4), skip
 masks and the stochastic gate."""
 import numpy as np
@@ -104,16 +106,54 @@ def test_decode_project_equals_decode_then_project(n, deg, seed, lay, noise):
         close(sp[vis, 8:11].T, pr["rgb"][:, vis], what="rgb")
 
 
+@pytest.mark.parametrize("n,deg,seed,lay,noise", CASES)
+def test_decode_project_bwd_equals_project_bwd_then_decode_bwd(n, deg, seed, lay, noise):
+    B, f, r, c, cam, prev, res = _setup(n, deg, seed, _layout(lay, deg), noise)
+    rng = np.random.default_rng(seed)
+    f.decode_project(r, c)                       # A_t into attrs, this step's gate noise drawn
+    d = rng.standard_normal((n, 12)).astype(np.float32)
+    d[:, [3, 7, 11]] = 0.0
+    d[:, 4:7] *= 0.01
+    r.d_splats[:n] = up(d)
+    for skip in (up((np.arange(f.S) % 3 == 2).astype(np.uint8), torch.uint8), None):   # unmasked last
+        r.project_bwd(f.attrs, c, f.hp.blur, f.d_attrs, skip)
+        f.decode_bwd(skip)
+        torch.cuda.synchronize()
+        ref = [f.d_lat[:, :n].clone(), f.d_lp[:, :n].clone(), f.d_log_alpha[:n].clone(), f.d_dec.clone()]
+        for t in (f.d_lat, f.d_lp, f.d_log_alpha, f.d_dec):
+            t.fill_(7.0)
+        f.decode_project_bwd(r, c, skip)
+        torch.cuda.synchronize()
+        got = [f.d_lat[:, :n], f.d_lp[:, :n], f.d_log_alpha[:n], f.d_dec]
+        for name, a, b in zip(("d_lat", "d_lp", "d_log_alpha"), got[:3], ref[:3]):
+            assert torch.equal(a, b), name
+        close(got[3].cpu().numpy(), ref[3].cpu().numpy(), floor_frac=0.01, what="d_dec")   # another summation order
+    # against the oracle (the unmasked call above, no noise): the projection
+    # adjoint at the GPU's A_t, then the decode adjoint
+    if not noise:
+        d64 = d.astype(np.float64)
+        dA = oracle.project_bwd(f.attrs[:, :n].cpu().numpy().astype(np.float64), cam, deg, d64[:, 0:2].T,
+                                d64[:, 4:7].T, d64[:, 2], d64[:, 8:11].T, blur=f.hp.blur)
+        want = oracle.decode_bwd(res.lat, res.dec, res.lp, res.log_alpha, _layout(lay, deg), TAU, G0, G1, dA,
+                                 f.d_lreg)
+        close(f.d_lat[:, :n].cpu().numpy(), want[0], floor_frac=0.01, what="d_lat (oracle)")
+        close(f.d_dec.cpu().numpy(), want[1], floor_frac=0.01, what="d_dec (oracle)")
+        close(f.d_lp[:, :n].cpu().numpy(), want[2], floor_frac=0.01, what="d_lp (oracle)")
+        close(f.d_log_alpha[:n].cpu().numpy(), want[3], floor_frac=0.01, what="d_log_alpha (oracle)")
+
+
 def test_fused_training_iteration_matches_two_kernel_iteration():
     """A whole training iteration with the fused forward equals the same
     iteration with the separate kernels bit for bit: records, every gradient
-    and Adam's update."""
+    and Adam's update.  With the fused adjoint too, every per-Gaussian array
+    still matches bit for bit; the decoder gradient (another summation order)
+    and the decoders after Adam's step agree to rounding."""
     from paper_2412_04469_gb300.pipeline import training_iteration
     n, deg = 3000, 3
     outs = []
-    for fused in (False, True):
+    for fused, fused_bwd in ((False, False), (True, False), (True, True)):
         B, f, r, c, cam, prev, res = _setup(n, deg, 5, DecoderLayout.default(sh_degree=deg, latent=8))
-        f.hp.fused = fused
+        f.hp.fused, f.hp.fused_bwd = fused, fused_bwd
         f.decode()
         r.size_for_views(f.attrs, [c], f.hp.blur)
         tgt = up(S.make_image(160, 120, 5))
@@ -121,6 +161,12 @@ def test_fused_training_iteration_matches_two_kernel_iteration():
         torch.cuda.synchronize()
         outs.append((r.splats[:n].clone(), r.d_splats[:n].clone(), f.d_lat[:, :n].clone(), f.d_lp[:, :n].clone(),
                      f.d_log_alpha[:n].clone(), f.d_dec.clone(), f.lat[:, :n].clone(), f.dec.clone()))
-    (a, b) = outs
-    for k, name in enumerate(("splats", "d_splats", "d_lat", "d_lp", "d_log_alpha", "d_dec", "lat", "dec")):
+    a, b, fb = outs
+    names = ("splats", "d_splats", "d_lat", "d_lp", "d_log_alpha", "d_dec", "lat", "dec")
+    for k, name in enumerate(names):
         assert torch.equal(a[k], b[k]), name
+    for k, name in enumerate(names):
+        if name in ("d_dec", "dec"):
+            close(fb[k].cpu().numpy(), a[k].cpu().numpy(), floor_frac=0.01, what=name)
+        else:
+            assert torch.equal(fb[k], a[k]), name
