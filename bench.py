@@ -689,11 +689,12 @@ def cpu_baseline(name):
 
 def run_reference(args):
     """The oracle's line (the paper ships no code; the reference arm is the
-    FP64 CPU oracle on the machine's host cores).  Whole iterations, nothing
-    extrapolated, when the K + W steps fit in REF_WHOLE_BUDGET_S (one untimed
-    whole iteration sizes it, and counts as the first warm-up step);
-    otherwise each step is a bounded sample scaled to the whole iteration,
-    and the line says so under "estimate"."""
+    FP64 CPU oracle on the machine's host cores): whole iterations, nothing
+    extrapolated.  One untimed whole iteration sizes the run and counts as
+    the first warm-up step.  When the requested K + W steps would not fit in
+    --ref-budget seconds, it times fewer whole iterations (3 warm-up steps, as
+    many timed steps as fit, at least 3) and the line says so: `steps` is the
+    count timed, `steps_requested` the count asked for."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -704,50 +705,28 @@ def run_reference(args):
     n, deg, W, H, V, L = WORKLOADS[name]
     ntiles = ((W + 15) // 16) * ((H + 15) // 16)
     t_one = oracle_whole_step(name, 0)
-    base = {"impl": "reference", "metric": METRIC, "unit": "it/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(name), "n_gaussians": n, "width": W, "height": H, "views": V,
-                       "sh_degree": deg}}
-    if (args.steps + args.warmup) * t_one <= REF_WHOLE_BUDGET_S:
-        for w in range(1, args.warmup):
-            oracle_whole_step(name, w)
-        secs = [oracle_whole_step(name, args.warmup + s) for s in range(args.steps)]
-        value = args.steps / sum(secs)
-        sample = (f"whole iterations, nothing extrapolated: per step decode, projection and their adjoints on all "
-                  f"{n} Gaussians, compositing and its adjoint on all {ntiles} tiles, L1 and D-SSIM (Eq. 3) on the "
-                  f"whole image; {sum(secs):.1f} s over the {args.steps} timed steps")
-        out = dict(base, value=round(value, 6), ms_per_step=round(1e3 * sum(secs) / args.steps, 2))
+    budget = args.ref_budget
+    if (args.steps + args.warmup) * t_one <= budget:
+        steps, warmup = args.steps, args.warmup
     else:
-        # each step a bounded sample: about budget seconds of timed oracle
-        # work, split between the per-Gaussian stages and the compositing
-        budget = max(0.3, 100.0 / max(1, args.steps + args.warmup))
-        threads = oracle.num_threads()
-        # calibration (untimed): view 0 composited on every tile, then on two
-        # samples of the step's size; the ratio corrects the samples' per-tile
-        # time, which overstates it (threads wait behind the few deep tiles)
-        full0 = oracle_step(name, ntiles)
-        m = int(min(n, max(30_000, n * 0.4 * budget / max(full0["per_gauss"], 1e-6))))
-        k = int(min(ntiles, max(4 * threads, 0.4 * budget / max(3.0 * full0["per_tile"], 1e-5))))
-        samples = [oracle_step(name, k, m=m, tile_seed=1000 + q)["per_tile"] for q in range(2)]
-        calib = min(1.0, full0["per_tile"] / max(float(np.mean(samples)), 1e-9)) if k < ntiles else 1.0
-        for w in range(args.warmup):
-            oracle_step(name, k, view=w, m=m, calib=calib)
-        fulls, sampled = [], 0.0
-        for s in range(args.steps):
-            r = oracle_step(name, k, view=args.warmup + s, m=m, calib=calib)
-            fulls.append(r["full"])
-            sampled += r["sampled"]
-        value = args.steps / sum(fulls)
-        sample = "per step " + ORACLE_SAMPLE.format(
-            m=r["m"], n=n, k=k, nt=ntiles, dssim=r["dssim"], gauss_note=" (scaled by n/m)" if r["m"] < n else "",
-            tiles_note=(f" (per-call set-up timed apart; the per-tile time scaled to every tile with a "
-                        f"calibration of {calib:.2f} against a composite of all tiles of view 0)"
-                        if k < ntiles else "")) + f"; sampled time {sampled:.1f} s over the {args.steps} steps"
-        out = dict(base, value=round(value, 6), ms_per_step=round(1e3 * sum(fulls) / args.steps, 2),
-                   estimate=("value and ms_per_step scale bounded samples to whole iterations: "
-                             f"{args.steps + args.warmup} whole iterations (~{t_one:.1f} s each) would not fit "
-                             f"in {REF_WHOLE_BUDGET_S:.0f} s"))
+        warmup = 3
+        steps = min(args.steps, max(3, int((budget - warmup * t_one) // max(t_one, 1e-9))))
+    for w in range(1, warmup):
+        oracle_whole_step(name, w)
+    secs = [oracle_whole_step(name, warmup + s) for s in range(steps)]
+    value = steps / sum(secs)
+    sample = (f"whole iterations, nothing extrapolated: per step decode, projection and their adjoints on all "
+              f"{n} Gaussians, compositing and its adjoint on all {ntiles} tiles, L1 and D-SSIM (Eq. 3) on the "
+              f"whole image; {sum(secs):.1f} s over the {steps} timed steps")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "it/s", "n_gpus": world,
+           "steps": steps, "warmup": warmup, "ms_per_step": round(1e3 * sum(secs) / steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(name), "n_gaussians": n, "width": W, "height": H, "views": V,
+                      "sh_degree": deg}}
+    if (steps, warmup) != (args.steps, args.warmup):
+        out["steps_requested"], out["warmup_requested"] = args.steps, args.warmup
+        out["note"] = (f"{args.steps + args.warmup} whole iterations (~{t_one:.1f} s each) would not fit in "
+                       f"{budget:g} s, so {steps} timed after {warmup} warm-up steps")
     out["cpu_baseline"] = {"value": out["value"], "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
                            "sample": sample}
     out["e2e"] = {"value": out["value"], "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
@@ -760,6 +739,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-budget", type=float, default=REF_WHOLE_BUDGET_S,
+                    help="reference arm: seconds of whole oracle iterations to fit the K + W steps in")
     ap.add_argument("--workload", default="full", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-seq", action="store_true", help="skip the learned-skip sequence comparison")

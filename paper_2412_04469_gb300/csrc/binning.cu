@@ -523,12 +523,11 @@ __device__ __forceinline__ GatherChunk gather_chunk(int TX, int TY, uint32_t g, 
     return k;
 }
 
-// Adds the record of the Gaussian in tile (tx, ty) to acc[0..8] if its slot
-// lies in the tile's visited prefix; returns whether it did.
-__device__ __forceinline__ bool gather_tile(int TX, int tx, int ty, const GatherChunk &k,
-                                            const uint32_t *__restrict__ tile_off,
-                                            const uint32_t *__restrict__ visited,
-                                            const float4 *__restrict__ pair_grads, float acc[9]) {
+// The pair slot of the Gaussian in tile (tx, ty), or -1 when it lies past the
+// tile's visited prefix (no record there).
+__device__ __forceinline__ long long gather_slot(int TX, int tx, int ty, const GatherChunk &k,
+                                                 const uint32_t *__restrict__ tile_off,
+                                                 const uint32_t *__restrict__ visited) {
     const int t = ty * TX + tx;
     const uint32_t base = k.grow[t], vis = visited[t], off = tile_off[t];
     const uint4 x0 = k.mx[2 * tx], x1 = k.mx[2 * tx + 1], y0 = k.my[2 * ty], y1 = k.my[2 * ty + 1];
@@ -538,17 +537,21 @@ __device__ __forceinline__ bool gather_tile(int TX, int tx, int ty, const Gather
     uint32_t rank = 0;
 #pragma unroll
     for (int w = 0; w < CHUNK_WARPS; ++w) rank += __popc(m[w] & (w < k.wj ? ~0u : w == k.wj ? k.below : 0u));
-    if (base + rank >= vis) return false;               // past the tile's visited prefix
-    const float4 *p = pair_grads + 3 * (size_t)(off + base + rank);
+    return base + rank < vis ? (long long)off + base + rank : -1ll;
+}
+
+__device__ __forceinline__ void add_record(const float4 *__restrict__ pair_grads, long long slot, float acc[9]) {
+    const float4 *p = pair_grads + 3 * (size_t)slot;
     const float4 b0 = p[0], b1 = p[1], b2 = p[2];
     acc[0] += b0.x; acc[1] += b0.y; acc[2] += b0.z;
     acc[3] += b1.x; acc[4] += b1.y; acc[5] += b1.z;
     acc[6] += b2.x; acc[7] += b2.y; acc[8] += b2.z;
-    return true;
 }
 
 // Thread i of `threads` walks tiles i, i + threads, ... of rect r in row-major
-// order, stepping its (column, row) without a division per tile.
+// order, stepping its (column, row) without a division per tile, two tiles at
+// a time: both tiles' slot loads are in flight together, then both records,
+// added in walk order (the sums do not depend on the unrolling).
 __device__ __forceinline__ bool gather_walk(int TX, int4 r, int i, int threads, const GatherChunk &k,
                                             const uint32_t *__restrict__ tile_off,
                                             const uint32_t *__restrict__ visited,
@@ -557,14 +560,29 @@ __device__ __forceinline__ bool gather_walk(int TX, int4 r, int i, int threads, 
     bool found = false;
     int cx = rw > 0 ? i % rw : 0, cy = rw > 0 ? i / rw : 0;
     const int dq = rw > 0 ? threads / rw : 0, dr = rw > 0 ? threads % rw : 0;
-    for (int q = i; q < area; q += threads) {
-        found |= gather_tile(TX, r.x + cx, r.y + cy, k, tile_off, visited, pair_grads, acc);
+    for (int q = i; q < area; q += 2 * threads) {
+        const int ax = cx, ay = cy;
         cx += dr;
         cy += dq;
         if (cx >= rw) {
             cx -= rw;
             ++cy;
         }
+        const bool second = q + threads < area;
+        const int bx = cx, by = cy;
+        if (second) {
+            cx += dr;
+            cy += dq;
+            if (cx >= rw) {
+                cx -= rw;
+                ++cy;
+            }
+        }
+        const long long sa = gather_slot(TX, r.x + ax, r.y + ay, k, tile_off, visited);
+        const long long sb = second ? gather_slot(TX, r.x + bx, r.y + by, k, tile_off, visited) : -1ll;
+        if (sa >= 0) add_record(pair_grads, sa, acc);
+        if (sb >= 0) add_record(pair_grads, sb, acc);
+        found |= (sa >= 0) | (sb >= 0);
     }
     return found;
 }
@@ -668,7 +686,7 @@ __device__ __forceinline__ void gather_warp(int TX, int TY, uint32_t g, uint32_t
 // warp sums the wanted ones one after another.  The stride spreads the
 // front-most Gaussians, which own nearly all visited pairs, over every warp.
 // The grid is one wave of resident blocks.
-__global__ void __launch_bounds__(GATHER_THREADS, 4) k_bin_gather(int TX, int TY,
+__global__ void __launch_bounds__(GATHER_THREADS, 3) k_bin_gather(int TX, int TY,
                                                                const uint32_t *__restrict__ sorted,
                                                                const int4 *__restrict__ rects, const Header *hdr,
                                                                const uint32_t *__restrict__ big_list,

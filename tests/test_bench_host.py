@@ -56,3 +56,20 @@ def test_sequence_summary_of_hand_records():
     assert s["fallbacks"] == 1 and s["mean_skipped"] == pytest.approx(0.25)
     assert s["static_recall"] == pytest.approx(0.6) and s["static_precision"] == pytest.approx(0.99)
     assert s["plain_gate0_recall"] == pytest.approx(0.91) and s["plain_gate0_precision"] == pytest.approx(0.8)
+
+
+def test_reference_arm_times_fewer_whole_iterations_when_the_budget_is_short():
+    """With a budget that cannot hold the K + W requested whole iterations,
+    the reference arm times fewer of them (3 warm-up steps, at least 3 timed)
+    and says so; the timed steps fit inside the run's own wall time."""
+    import time
+    t0 = time.perf_counter()
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "small", "--steps", "500", "--warmup", "20", "--ref-budget", "0.01"],
+                         capture_output=True, text=True, timeout=600, check=True)
+    wall = time.perf_counter() - t0
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["steps"] == 3 and line["warmup"] == 3
+    assert line["steps_requested"] == 500 and line["warmup_requested"] == 20 and "note" in line
+    assert line["steps"] * line["ms_per_step"] * 1e-3 <= wall
+    assert line["value"] == pytest.approx(1e3 / line["ms_per_step"], rel=1e-3)
