@@ -240,21 +240,25 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
     const uint32_t beg = ranges[2 * tile], end = ranges[2 * tile + 1];
     const int n = (int)(end - beg);
     const float fx = px + 0.5f, fy0 = py0 + 0.5f;
+    // T < 0 marks a pixel that has stopped (its T negated) or lies outside
+    // the image: T (1 - alpha) is then negative and fails the 1e-4 test, so
+    // the per-pixel update needs no separate liveness test
     float T[PPT], c0[PPT], c1[PPT], c2[PPT];
     uint32_t lastc[PPT], nc[PPT];
-    uint32_t live = 0;                                  // bit q: pixel q still compositing
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        T[q] = 1.f;
+        T[q] = px < W && py0 + q < H ? 1.f : -1.f;
         c0[q] = c1[q] = c2[q] = 0.f;
         lastc[q] = nc[q] = 0;
-        if (px < W && py0 + q < H) live |= 1u << q;
     }
     // the warp's band of pixel centres, clipped to the image
     const float bx0 = (float)((tile % TX) * QN_TILE) + 0.5f, bx1 = fminf(bx0 + (float)(QN_TILE - 1), W - 0.5f);
     const float by0 = (float)((tile / TX) * QN_TILE + (threadIdx.x >> 5) * (2 * PPT)) + 0.5f;
     const float by1 = fminf(by0 + (float)(2 * PPT - 1), H - 0.5f);
     for (int b0 = 0; b0 < n; b0 += FWD_BATCH) {
+        bool live = false;                              // the warp stops between batches
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) live |= T[q] > 0.f;
         if (!__any_sync(FULL, live)) break;
         uint32_t my_id = 0;
         bool reach = false;
@@ -269,7 +273,6 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
         __syncwarp();
         uint32_t batch_added = 0;                       // bit j: record j composited by this warp
         while (todo) {
-            if (!__any_sync(FULL, live)) break;
             const int j = __ffs(todo) - 1;              // front to back
             todo &= todo - 1;
             const SRec &r = s[j];
@@ -282,17 +285,17 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
             for (int q = 0; q < PPT; ++q) {
                 const float v = __fmul_rn(r.g.z, ex2_approx(e[q]));
                 const float al = fminf(v, ALPHA_MAX);
-                const bool ok = ((live >> q) & 1u) && al >= ALPHA_MIN;
+                const bool ok = al >= ALPHA_MIN;
                 const bool add = ok && __fmul_rn(T[q], __fsub_rn(1.f, al)) >= T_MIN;
-                if (ok && !add) live &= ~(1u << q);     // stops before this Gaussian
                 // the update through the effective alpha ae (0 unless added):
-                // T <- T - ae T, C <- C + c ae T, on the FMA pipe
+                // T <- T - ae T, C <- C + c ae T, on the FMA pipe; a pixel
+                // that stops before this Gaussian keeps -|T|
                 const float ae = add ? al : 0.f;
                 const float w = __fmul_rn(ae, T[q]);
                 c0[q] = fmaf(c.x, w, c0[q]);
                 c1[q] = fmaf(c.y, w, c1[q]);
                 c2[q] = fmaf(c.z, w, c2[q]);
-                T[q] = __fsub_rn(T[q], w);
+                T[q] = ok && !add ? -fabsf(T[q]) : __fsub_rn(T[q], w);
                 lastc[q] = add ? pos1 : lastc[q];
                 if (COUNT) nc[q] += add ? 1u : 0u;
                 if (MARK) added |= add;
@@ -308,10 +311,11 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
         const int py = py0 + q;
         if (px >= W || py >= H) continue;
         const size_t o = (size_t)py * W + px;
-        img[o] = fmaf(T[q], bg0, c0[q]);
-        img[plane + o] = fmaf(T[q], bg1, c1[q]);
-        img[2 * plane + o] = fmaf(T[q], bg2, c2[q]);
-        Tf[o] = T[q];
+        const float t = fabsf(T[q]);
+        img[o] = fmaf(t, bg0, c0[q]);
+        img[plane + o] = fmaf(t, bg1, c1[q]);
+        img[2 * plane + o] = fmaf(t, bg2, c2[q]);
+        Tf[o] = t;
         last[o] = lastc[q];
         if (COUNT) ncon[o] = nc[q];
     }
