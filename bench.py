@@ -48,7 +48,7 @@ STAGES = list(KERNELS_PER_STAGE)
 NCU_TRAFFIC = {
     "render_bwd": {"bytes": 38.049792e6 + 12.687872e6,
                    "sources": ("paper_2412_04469_gb300/csrc/render.cu", "paper_2412_04469_gb300/csrc/common.cuh"),
-                   "sha256": "1e3e8ff4a1a170f2672b6d78addbb7907c3aecc7de0073865fe2e65e61535be5"},
+                   "sha256": "a9a033792455bce95b75282ca5ffd8cc124c110b5f0d6850a555400babfe2611"},
 }
 
 

@@ -1,10 +1,12 @@
 // Front-to-back alpha compositing per 16 x 16 tile (Sec. 3.1, Eq. 2) and its
 // adjoint.  A tile is split into horizontal bands of 2 PPT rows, one warp per
-// band; a lane owns PPT pixels of one column and works on them in pairs with
-// Blackwell's packed FP32 instructions (add/sub/mul/fma .f32x2: two lanes of
-// arithmetic per issued instruction).  Gaussian records are staged in shared
-// memory with every per-Gaussian scalar duplicated into a pair, so a 128-bit
-// broadcast load yields ready operand pairs.
+// band; a lane owns PPT pixels of one column.  A warp walks only the staged
+// records that can reach its band (one analytic test per record, lane j
+// testing record j).  The forward keeps each pixel as a scalar chain; the
+// adjoint works on its pixels in pairs with Blackwell's packed FP32
+// instructions (add/sub/mul/fma .f32x2: two lanes of arithmetic per issued
+// instruction), its staged records holding every per-Gaussian scalar
+// duplicated into a pair, so a 128-bit broadcast load yields operand pairs.
 #include "common.cuh"
 
 namespace qn {
