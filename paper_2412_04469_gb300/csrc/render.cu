@@ -474,15 +474,9 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H,
                 const int j = ch * 32 + jb;
                 const uint32_t pos = (uint32_t)(lo + j);
                 const Rec r = s[j];
+                // no per-pixel cull beyond the band test: it would reject about 5% of
+                // the records that pass it, for more instructions than those cost
                 const Expo<NP> x = exponent<NP>(r, FX, FY);
-                bool near = false;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    float e0, e1;
-                    upk(x.e[p], e0, e1);
-                    near |= (e0 >= r.kw && pos < lastp[2 * p]) || (e1 >= r.kw && pos < lastp[2 * p + 1]);
-                }
-                if (!__any_sync(FULL, near)) continue;      // no pixel of the band can take j
                 if (sflag[j] & 1) {
                     // skipped (the branch is uniform over the block): it only
                     // enters the transmittance and b of the Gaussians in front
