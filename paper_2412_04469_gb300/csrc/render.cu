@@ -21,6 +21,14 @@ constexpr float LOG2E = 1.4426950408889634f;
 // alpha >= 1/255 test anywhere and skips the Gaussian: the cull never changes
 // a result.
 constexpr float CULL_MARGIN = 1e-3f;
+// Below this opacity no pixel's alpha reaches ALPHA_MAX: alpha = o 2^e with
+// e <= 0 up to the rounding of the exponent (a positive e stays far below
+// 1e-5), so alpha <= o (1 + 1e-5) < 0.99.
+constexpr float CAP_FREE_OPACITY = 0.98997f;
+template <bool B>
+struct CapTag {
+    static constexpr bool value = B;
+};
 
 // pixels per lane (even): 16 x 16 / (32 PPT) warps per tile
 #ifndef QN_FWD_PPT
@@ -499,34 +507,46 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_bwd(int W, int H,
                 const f2 Z = pk(0.f, 0.f);
                 f2 S0 = Z, S1 = Z, S2 = Z, G0 = Z, G1 = Z, G2 = Z;
                 bool any = false;
+                // CAP: the record can reach the 0.99 cap.  alpha = o 2^e <= o (1 + 1e-5)
+                // (e <= 0 up to rounding), so below CAP_FREE_OPACITY min(alpha, 0.99)
+                // is alpha and the cap's zero gradient never applies: the branch
+                // without them gives the same bits with fewer instructions
+                auto walk = [&](auto cap_tag) {
+                    constexpr bool CAP = decltype(cap_tag)::value;
 #pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    float e0, e1, v0, v1, m0, m1;
-                    upk(x.e[p], e0, e1);
-                    upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
-                    const float a0 = fminf(v0, ALPHA_MAX), a1 = fminf(v1, ALPHA_MAX);
-                    const bool ok0 = pos < lastp[2 * p] && a0 >= ALPHA_MIN;
-                    const bool ok1 = pos < lastp[2 * p + 1] && a1 >= ALPHA_MIN;
-                    any |= ok0 | ok1;
-                    const float ae0 = ok0 ? a0 : 0.f, ae1 = ok1 ? a1 : 0.f;
-                    const f2 AE = pk(ae0, ae1);
-                    const f2 AG = pk(v0 > ALPHA_MAX ? 0.f : ae0, v1 > ALPHA_MAX ? 0.f : ae1);   // the cap passes no gradient
-                    upk(sub2(ONE, AE), m0, m1);
-                    const f2 TQ = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));  // in front of j
-                    T[p] = TQ;
-                    const f2 cd = fma2(r.cr, D0[p], fma2(r.cg, D1[p], mul2(r.cb, D2[p])));
-                    const f2 dot = sub2(cd, Bd[p]);
-                    Bd[p] = fma2(AE, dot, Bd[p]);
-                    const f2 w = mul2(AE, TQ);
-                    G0 = fma2(w, D0[p], G0);
-                    G1 = fma2(w, D1[p], G1);
-                    G2 = fma2(w, D2[p], G2);
-                    const f2 sdp = mul2(mul2(TQ, dot), AG);           // dL/dpower
-                    const f2 tt = mul2(sdp, x.dy[p]);
-                    S0 = add2(S0, sdp);
-                    S1 = add2(S1, tt);
-                    S2 = fma2(tt, x.dy[p], S2);
-                }
+                    for (int p = 0; p < NP; ++p) {
+                        float e0, e1, v0, v1, m0, m1;
+                        upk(x.e[p], e0, e1);
+                        upk(mul2(r.o, pk(ex2_approx(e0), ex2_approx(e1))), v0, v1);
+                        const float a0 = CAP ? fminf(v0, ALPHA_MAX) : v0, a1 = CAP ? fminf(v1, ALPHA_MAX) : v1;
+                        const bool ok0 = pos < lastp[2 * p] && a0 >= ALPHA_MIN;
+                        const bool ok1 = pos < lastp[2 * p + 1] && a1 >= ALPHA_MIN;
+                        any |= ok0 | ok1;
+                        const float ae0 = ok0 ? a0 : 0.f, ae1 = ok1 ? a1 : 0.f;
+                        const f2 AE = pk(ae0, ae1);
+                        const f2 AG = CAP ? pk(v0 > ALPHA_MAX ? 0.f : ae0, v1 > ALPHA_MAX ? 0.f : ae1)   // the cap passes no gradient
+                                          : AE;
+                        upk(sub2(ONE, AE), m0, m1);
+                        const f2 TQ = mul2(T[p], pk(ok0 ? rcp_approx(m0) : 1.f, ok1 ? rcp_approx(m1) : 1.f));  // in front of j
+                        T[p] = TQ;
+                        const f2 cd = fma2(r.cr, D0[p], fma2(r.cg, D1[p], mul2(r.cb, D2[p])));
+                        const f2 dot = sub2(cd, Bd[p]);
+                        Bd[p] = fma2(AE, dot, Bd[p]);
+                        const f2 w = mul2(AE, TQ);
+                        G0 = fma2(w, D0[p], G0);
+                        G1 = fma2(w, D1[p], G1);
+                        G2 = fma2(w, D2[p], G2);
+                        const f2 sdp = mul2(mul2(TQ, dot), AG);           // dL/dpower
+                        const f2 tt = mul2(sdp, x.dy[p]);
+                        S0 = add2(S0, sdp);
+                        S1 = add2(S1, tt);
+                        S2 = fma2(tt, x.dy[p], S2);
+                    }
+                };
+                float o_j, o_unused;
+                upk(r.o, o_j, o_unused);
+                if (o_j > CAP_FREE_OPACITY) walk(CapTag<true>{});   // uniform over the warp: one record
+                else walk(CapTag<false>{});
                 const bool any_j = __any_sync(FULL, any);   // the band composites j
                 if (lane == 0) hit[warp][j] = any_j;
                 if (!any_j) continue;

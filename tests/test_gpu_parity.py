@@ -432,11 +432,15 @@ def test_render_bwd_call_alone_gives_per_gaussian_gradients():
     oracle fed the same FP32 projection; the forward's composited marks,
     which let the walk drop the Gaussians no pixel composites, and the call
     split into its two passes give the same records bit for bit; a skip mask
-    zeroes exactly the skipped Gaussians and leaves the others' gradients."""
+    zeroes exactly the skipped Gaussians and leaves the others' gradients.
+    The scene holds faint Gaussians and opaque ones whose alpha is capped, so
+    both of the adjoint's branches (records that can reach the cap and those
+    that cannot) are compared."""
     from paper_2412_04469_gb300 import binding as Bd
     n, W, H, deg, blur, seed = 1500, 150, 110, 2, 0.3, 9
     A, cam = _scene(n, W, H, deg, seed)
     A[10, ::10] = np.log(0.004 / 0.996)    # faint: in the tile lists, below 1/255 at most pixels
+    A[10, 5::40] = 6.0                      # opaque (o = 0.9975): alpha capped at 0.99 near their centres
     bg = (0.05, 0.1, 0.2)
     r, c, _ = gpu_raster(A, cam, deg, blur, bg)
     comp = torch.zeros(n, device="cuda", dtype=torch.uint8)
