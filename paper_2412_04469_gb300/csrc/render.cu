@@ -291,25 +291,32 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
             const float4 c = r.c;
             const uint32_t pos1 = (uint32_t)(b0 + j + 1);
             bool added = false;
+            // CAP: the record can reach the 0.99 cap (below CAP_FREE_OPACITY,
+            // min(alpha, 0.99) is alpha; the branch is uniform over the warp)
+            auto pixels = [&](auto cap_tag) {
+                constexpr bool CAP = decltype(cap_tag)::value;
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                const float v = __fmul_rn(r.g.z, ex2_approx(e[q]));
-                const float al = fminf(v, ALPHA_MAX);
-                const bool ok = al >= ALPHA_MIN;
-                const bool add = ok && __fmul_rn(T[q], __fsub_rn(1.f, al)) >= T_MIN;
-                // the update through the effective alpha ae (0 unless added):
-                // T <- T - ae T, C <- C + c ae T, on the FMA pipe; a pixel
-                // that stops before this Gaussian keeps -|T|
-                const float ae = add ? al : 0.f;
-                const float w = __fmul_rn(ae, T[q]);
-                c0[q] = fmaf(c.x, w, c0[q]);
-                c1[q] = fmaf(c.y, w, c1[q]);
-                c2[q] = fmaf(c.z, w, c2[q]);
-                T[q] = ok && !add ? -fabsf(T[q]) : __fsub_rn(T[q], w);
-                lastc[q] = add ? pos1 : lastc[q];
-                if (COUNT) nc[q] += add ? 1u : 0u;
-                if (MARK) added |= add;
-            }
+                for (int q = 0; q < PPT; ++q) {
+                    const float v = __fmul_rn(r.g.z, ex2_approx(e[q]));
+                    const float al = CAP ? fminf(v, ALPHA_MAX) : v;
+                    const bool ok = al >= ALPHA_MIN;
+                    const bool add = ok && __fmul_rn(T[q], __fsub_rn(1.f, al)) >= T_MIN;
+                    // the update through the effective alpha ae (0 unless added):
+                    // T <- T - ae T, C <- C + c ae T, on the FMA pipe; a pixel
+                    // that stops before this Gaussian keeps -|T|
+                    const float ae = add ? al : 0.f;
+                    const float w = __fmul_rn(ae, T[q]);
+                    c0[q] = fmaf(c.x, w, c0[q]);
+                    c1[q] = fmaf(c.y, w, c1[q]);
+                    c2[q] = fmaf(c.z, w, c2[q]);
+                    T[q] = ok && !add ? -fabsf(T[q]) : __fsub_rn(T[q], w);
+                    lastc[q] = add ? pos1 : lastc[q];
+                    if (COUNT) nc[q] += add ? 1u : 0u;
+                    if (MARK) added |= add;
+                }
+            };
+            if (r.g.z > CAP_FREE_OPACITY) pixels(CapTag<true>{});
+            else pixels(CapTag<false>{});
             if (MARK && __any_sync(FULL, added)) batch_added |= 1u << j;
         }
         if (MARK && ((batch_added >> lane) & 1u)) comp[my_id] = 1;
