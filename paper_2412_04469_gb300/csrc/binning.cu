@@ -77,19 +77,38 @@ Layout layout_of(int n, int TX, int TY) {
 }
 
 // ---------------------------------------------------------------- step 0
-__global__ void k_bin_prep(int n, const float *__restrict__ depth, int dstride,
-                           const int4 *__restrict__ rects, uint32_t *__restrict__ keys,
-                           uint32_t *__restrict__ vals, Header *hdr) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool vis = false;
-    if (i < n) {
-        const int4 r = rects[i];
-        vis = r.z > r.x && r.w > r.y;
-        keys[i] = vis ? __float_as_uint(depth[(size_t)i * dstride]) : KEY_CULLED;
-        vals[i] = (uint32_t)i;
+// Keys (depth bits, culled last) and values of one sort block of SORT_TILE
+// Gaussians, and that block's histogram of the first pass's digit (what
+// k_radix_hist gives for it, without reading the keys again).
+__global__ void __launch_bounds__(SORT_THREADS) k_bin_prep(int n, const float *__restrict__ depth, int dstride,
+                                                           const int4 *__restrict__ rects,
+                                                           uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                           uint32_t *__restrict__ hist, uint32_t *__restrict__ dtot,
+                                                           Header *hdr) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * SORT_TILE;
+    uint32_t nvis = 0;
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int i = base + r * SORT_THREADS + threadIdx.x;
+        if (i < n) {
+            const int4 rc = rects[i];
+            const bool vis = rc.z > rc.x && rc.w > rc.y;
+            const uint32_t key = vis ? __float_as_uint(depth[(size_t)i * dstride]) : KEY_CULLED;
+            keys[i] = key;
+            vals[i] = (uint32_t)i;
+            nvis += vis ? 1u : 0u;
+            atomicAdd(&h[key & (RADIX - 1)], 1u);
+        }
     }
-    const unsigned b = __ballot_sync(FULL, vis);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&hdr->n_vis, (uint32_t)__popc(b));
+    nvis = __reduce_add_sync(FULL, nvis);
+    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&hdr->n_vis, nvis);
+    __syncthreads();
+    const uint32_t c = h[threadIdx.x];
+    hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = c;
+    if (c) atomicAdd(&dtot[threadIdx.x], c);              // integer: the total is order-independent
 }
 
 // ---------------------------------------------------------------- step 1: radix sort of depth keys
@@ -780,13 +799,14 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     uint32_t *dtot = reinterpret_cast<uint32_t *>(ws + L.dtot);
     if (cudaMemsetAsync(hdr, 0, L.keys0 - L.hdr, s) != cudaSuccess)      // header and digit totals
         return check_launch("qn_bin_sort memset");
-    k_bin_prep<<<div_up(n, 256), 256, 0, s>>>(n, depth, depth_stride, r4, k0, v0, hdr);
     const int nb = div_up(n, SORT_TILE);
+    k_bin_prep<<<nb, SORT_THREADS, 0, s>>>(n, depth, depth_stride, r4, k0, v0, hist, dtot, hdr);
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         uint32_t *ki = (pass & 1) ? k1 : k0, *vi = (pass & 1) ? v1 : v0;
         uint32_t *ko = (pass & 1) ? k0 : k1, *vo = (pass & 1) ? v0 : v1;
-        k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist, dtot + pass * RADIX);
+        if (pass > 0)                                   // the first pass's histogram came with the keys
+            k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist, dtot + pass * RADIX);
         k_radix_scan<<<RADIX / 32, 1024, 0, s>>>(hist, nb, dtot + pass * RADIX);
         k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo);
     }
