@@ -274,16 +274,22 @@ def run_gpu(args):
     # the loss back.  The copies run on their own stream into two target
     # buffers, so step k + 1's copy overlaps step k's compute; each step waits
     # for its copy, and a buffer is refilled only after the step that read it.
-    loss_host = torch.zeros(1).pin_memory()
+    # The loss goes, inside the step's graph, to one of two device slots, and
+    # is read back from there on the copy stream while the next step runs; a
+    # slot is rewritten only after its read-back, and the timed region ends
+    # after the last one.
+    loss_host = torch.zeros(2).pin_memory()
+    loss_slots = [torch.zeros(1, device="cuda") for _ in range(2)]
     tgt_bufs = [torch.empty_like(targets[0]) for _ in range(2)]
     copy_stream = torch.cuda.Stream()
     for b in range(2):
         for v in range(V):
             tgt_bufs[b].copy_(targets_host[v], non_blocking=True)
-            graphs.run(("e2e", v, b), cams[v], tgt_bufs[b])
+            graphs.run(("e2e", v, b), cams[v], tgt_bufs[b], loss_out=loss_slots[b])
     barrier()
     ready = [torch.cuda.Event() for _ in range(2)]
     done = [torch.cuda.Event() for _ in range(2)]
+    read = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def upload(k):
@@ -302,9 +308,15 @@ def run_gpu(args):
                 copy_stream.wait_event(done[1 - b])   # step k - 1 has read that buffer
             upload(k + 1)
         stream.wait_event(ready[b])
-        graphs.run(("e2e", v, b), cams[v], tgt_bufs[b])
+        if k >= 2:
+            stream.wait_event(read[b])                # step k - 2's loss has been read from slot b
+        graphs.run(("e2e", v, b), cams[v], tgt_bufs[b], loss_out=loss_slots[b])
         done[b].record(stream)
-        loss_host.copy_(rast.loss, non_blocking=True)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(done[b])
+            loss_host[b:b + 1].copy_(loss_slots[b], non_blocking=True)
+            read[b].record(copy_stream)
+    stream.wait_event(read[(args.steps - 1) % 2])     # the last read-back is inside the timed region
     e1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))

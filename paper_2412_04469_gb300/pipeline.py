@@ -487,20 +487,25 @@ class IterationGraph:
         self.pool = None
         self.warm = False
 
-    def _signature(self, target, skip, mask, unskip, mark):
+    def _signature(self, target, skip, mask, unskip, mark, loss_out):
         r = self.rast
         return (target.data_ptr(), None if skip is None else skip.data_ptr(), r.vals.data_ptr(),
                 r.pair_grads.data_ptr(), r.workspace.data_ptr(), None if mask is None else mask.pixel.data_ptr(),
-                bool(unskip), bool(mark))
+                bool(unskip), bool(mark), None if loss_out is None else loss_out.data_ptr())
 
-    def run(self, key, cam, target, skip=None, mask=None, unskip=False, mark=False):
-        sig = self._signature(target, skip, mask, unskip, mark)
+    def run(self, key, cam, target, skip=None, mask=None, unskip=False, mark=False, loss_out=None):
+        """loss_out (optional, a one-element device tensor): the iteration's
+        loss is copied there at its end, inside the graph, so a caller can
+        read it back while the next iteration overwrites rast.loss."""
+        sig = self._signature(target, skip, mask, unskip, mark, loss_out)
         ent = self.graphs.get(key)
         if ent is None or ent[1] != sig:
             if not self.warm:
                 # one eager iteration first: lazily allocated scratch must
                 # exist before capture; it is a real training step
                 training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip, mark=mark)
+                if loss_out is not None:
+                    loss_out.copy_(self.rast.loss)
                 self.warm = True
                 return
             if self.pool is None:
@@ -509,7 +514,9 @@ class IterationGraph:
             torch.cuda.synchronize()
             with torch.cuda.graph(g, pool=self.pool):
                 training_iteration(self.frame, self.rast, cam, target, skip, mask=mask, unskip=unskip, mark=mark)
-            ent = (g, sig, cam, target, skip, mask)     # keep what the graph points at alive
+                if loss_out is not None:
+                    loss_out.copy_(self.rast.loss)
+            ent = (g, sig, cam, target, skip, mask, loss_out)   # keep what the graph points at alive
             self.graphs[key] = ent
         ent[0].replay()
 
