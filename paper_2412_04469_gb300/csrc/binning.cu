@@ -40,6 +40,7 @@ struct Header {
     uint32_t overflow;
     unsigned long long pairs;
     uint32_t n_big;                                     // entries of the large-rect list
+    uint32_t prefix_done;                               // blocks of k_chunk_prefix finished
 };
 
 struct Layout {
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, c
 // Exclusive scan, in place and in digit-major order, of the [RADIX][nb]
 // per-block digit histogram: one warp per digit (RADIX / 32 blocks of 32
 // warps).  Warp d starts from the count of all smaller digits (from the digit
-// totals) and walks its digit's blocks 32 at a time (coalesced).
+// totals) and walks its digit's blocks 256 at a time.
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int nb,
                                                      const uint32_t *__restrict__ dtot) {
     const int lane = threadIdx.x & 31;
@@ -146,16 +147,30 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist
         below += e < d ? dtot[e] : 0u;
     }
     uint32_t run = __reduce_add_sync(FULL, below);
-    for (int b0 = 0; b0 < nb; b0 += 32) {
-        const int b = b0 + lane;
-        const uint32_t v = b < nb ? hist[(size_t)d * nb + b] : 0u;
-        uint32_t incl = v;
+    // SCAN_PER consecutive blocks per lane, SCAN_PER * 32 blocks per round,
+    // all of a round's loads in flight together
+    constexpr int SCAN_PER = 8;
+    uint32_t *row = hist + (size_t)d * nb;
+    for (int b0 = 0; b0 < nb; b0 += 32 * SCAN_PER) {
+        const int bl = b0 + lane * SCAN_PER;
+        uint32_t v[SCAN_PER];
+#pragma unroll
+        for (int q = 0; q < SCAN_PER; ++q) v[q] = bl + q < nb ? row[bl + q] : 0u;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int q = 0; q < SCAN_PER; ++q) mine += v[q];
+        uint32_t incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += x;
         }
-        if (b < nb) hist[(size_t)d * nb + b] = run + incl - v;
+        uint32_t at = run + incl - mine;
+#pragma unroll
+        for (int q = 0; q < SCAN_PER; ++q) {
+            if (bl + q < nb) row[bl + q] = at;
+            at += v[q];
+        }
         run += __shfl_sync(FULL, incl, 31);
     }
 }
@@ -174,12 +189,20 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift
     const int warp = threadIdx.x >> 5;
     base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
     const int blk = blockIdx.x * SORT_TILE;
+    uint32_t keys[SORT_ITEMS], vals[SORT_ITEMS];      // all of the block's loads in flight at once
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int i = blk + r * SORT_THREADS + threadIdx.x;
+        keys[r] = i < n ? kin[i] : 0u;
+        vals[r] = i < n ? vin[i] : 0u;
+    }
+#pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         for (int w = 0; w < W; ++w) wcnt[w][threadIdx.x] = 0;
         __syncthreads();
         const int i = blk + r * SORT_THREADS + threadIdx.x;
         const bool ok = i < n;
-        const uint32_t key = ok ? kin[i] : 0u;
+        const uint32_t key = keys[r];
         const uint32_t d = (key >> shift) & (RADIX - 1);
         const unsigned act = __ballot_sync(FULL, ok);
         const unsigned peers = __match_any_sync(FULL, ok ? d : 0xffffffffu) & act;
@@ -201,7 +224,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift
         if (ok) {
             const uint32_t pos = wcnt[warp][d] + rank;
             kout[pos] = key;
-            vout[pos] = vin[i];
+            vout[pos] = vals[r];
         }
         __syncthreads();
     }
@@ -329,14 +352,77 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
     }
 }
 
+// Exclusive scan of tile totals -> tile offsets, ranges and P, by one block of
+// 1024 threads: thread i takes a run of consecutive tiles (loads in batches
+// of 8), then a shuffle scan of the 64-bit run sums within each warp and over
+// the warps.  total is read through L2: other blocks of the same launch wrote it.
+__device__ void tile_offsets(int n_tiles, const uint32_t *__restrict__ total, uint32_t *__restrict__ off,
+                             uint32_t *__restrict__ ranges, Header *hdr, unsigned long long capacity,
+                             long long *n_pairs) {
+    __shared__ unsigned long long wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = div_up_dev(n_tiles, 1024);
+    const int b = threadIdx.x * per, e = min(n_tiles, b + per);
+    unsigned long long s = 0;
+    for (int t0 = b; t0 < e; t0 += 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = t0 + k < e ? __ldcg(total + t0 + k) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += v[k];
+    }
+    unsigned long long incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long x = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = wsum[lane];
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long x = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += x;
+        }
+        wsum[lane] = wi - w;                            // exclusive over warps
+    }
+    __syncthreads();
+    unsigned long long run = wsum[warp] + incl - s;
+    __shared__ unsigned long long total_pairs;
+    if (threadIdx.x == 1023) total_pairs = wsum[31] + incl;
+    __syncthreads();
+    const unsigned long long PT = total_pairs;
+    const bool over = PT > capacity || PT > 0xffffffffull;
+    for (int t = b; t < e; ++t) {
+        const uint32_t v = __ldcg(total + t);
+        off[t] = (uint32_t)run;
+        ranges[2 * (size_t)t] = over ? 0u : (uint32_t)run;
+        ranges[2 * (size_t)t + 1] = over ? 0u : (uint32_t)(run + v);
+        run += v;
+    }
+    if (threadIdx.x == 0) {
+        hdr->pairs = PT;
+        hdr->overflow = over ? 1u : 0u;
+        if (n_pairs) *n_pairs = (long long)PT;
+    }
+}
+
 // In place: counts[c][t] <- sum_{c' < c} counts[c'][t]; tile_total[t] = sum_c.
 // Block = 32 tiles (lanes) x 32 chunk segments (warps).  Each warp walks its
 // segment PREFIX_BATCH chunks at a time with the loads issued together (the
-// walk is otherwise one dependent memory round trip per chunk).
+// walk is otherwise one dependent memory round trip per chunk).  The block
+// that finishes last (a ticket counter; nothing waits) then scans the tile
+// totals into the tile offsets, the ranges and P.
 constexpr int PREFIX_BATCH = 8;
 
 __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles, uint32_t *__restrict__ counts,
-                                                       uint32_t *__restrict__ tile_total) {
+                                                       uint32_t *__restrict__ tile_total,
+                                                       uint32_t *__restrict__ tile_off, uint32_t *__restrict__ ranges,
+                                                       Header *hdr, unsigned long long capacity,
+                                                       long long *n_pairs) {
     __shared__ uint32_t seg[32][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + lane;
@@ -386,41 +472,14 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
             run += v;
         }
     }
-}
-
-// Exclusive scan of tile totals -> tile offsets, ranges and P (one block).
-__global__ void __launch_bounds__(1024) k_tile_offsets(int n_tiles, const uint32_t *__restrict__ total,
-                                                       uint32_t *__restrict__ off, uint32_t *__restrict__ ranges,
-                                                       Header *hdr, unsigned long long capacity,
-                                                       long long *n_pairs) {
-    __shared__ unsigned long long part[1024];
-    const int per = div_up_dev(n_tiles, 1024);
-    const int b = threadIdx.x * per, e = min(n_tiles, b + per);
-    unsigned long long s = 0;
-    for (int t = b; t < e; ++t) s += total[t];
-    part[threadIdx.x] = s;
+    __shared__ bool last;
+    __threadfence();                                    // this block's tile totals before its ticket
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const unsigned long long x = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
-        __syncthreads();
-        part[threadIdx.x] += x;
-        __syncthreads();
-    }
-    const unsigned long long P = part[1023];
-    const bool over = P > capacity || P > 0xffffffffull;
-    unsigned long long run = part[threadIdx.x] - s;
-    for (int t = b; t < e; ++t) {
-        const uint32_t v = total[t];
-        off[t] = (uint32_t)run;
-        ranges[2 * (size_t)t] = over ? 0u : (uint32_t)run;
-        ranges[2 * (size_t)t + 1] = over ? 0u : (uint32_t)(run + v);
-        run += v;
-    }
-    if (threadIdx.x == 0) {
-        hdr->pairs = P;
-        hdr->overflow = over ? 1u : 0u;
-        if (n_pairs) *n_pairs = (long long)P;
-    }
+    if (threadIdx.x == 0) last = atomicAdd(&hdr->prefix_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    tile_offsets(n_tiles, tile_total, tile_off, ranges, hdr, capacity, n_pairs);
 }
 
 // Writes chunk c's members tile by tile: one thread per tile of the chunk's
@@ -815,9 +874,9 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     uint32_t *masks = reinterpret_cast<uint32_t *>(ws + L.masks);
     k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts, masks,
                                               reinterpret_cast<uint32_t *>(ws + L.big));
-    k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total);
-    k_tile_offsets<<<1, 1024, 0, s>>>(n_tiles, tile_total, tile_off, ranges, hdr,
-                                      (unsigned long long)capacity, reinterpret_cast<long long *>(n_pairs));
+    k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total, tile_off, ranges,
+                                                        hdr, (unsigned long long)capacity,
+                                                        reinterpret_cast<long long *>(n_pairs));
     const int vec = ((uintptr_t)vals & 15) == 0;       // 16-byte stores need a 16-byte aligned vals
     k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
                                                tile_off, masks, vals, reinterpret_cast<unsigned long long *>(keys),
