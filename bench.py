@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 REF_WHOLE_BUDGET_S = 300.0
 # kernels each stage launches (memsets are not counted); the step decodes and
 # projects in one kernel
-KERNELS_PER_STAGE = {"decode_project": 1, "bin_sort": 15, "render_fwd": 2, "loss": 4, "render_bwd": 1,
+KERNELS_PER_STAGE = {"decode_project": 1, "bin_sort": 14, "render_fwd": 2, "loss": 4, "render_bwd": 1,
                      "gather": 1, "project_bwd": 1, "decode_bwd": 2, "adam": 2}
 STAGES = list(KERNELS_PER_STAGE)
 # DRAM bytes per launch of a kernel on the full workload, from one ncu capture
@@ -212,7 +212,7 @@ def run_gpu(args):
         """One iteration issued stage by stage with an event between stages."""
         c = cams[v]
         mk, od = hp.mark_composited, hp.order_tiles
-        calls = (lambda: frame.decode_project(rast, c), lambda: rast.bin_sort(False),
+        calls = (lambda: frame.decode_project(rast, c), lambda: rast.bin_sort(False, lazy=hp.lazy_lists),
                  lambda: rast.render_fwd(c, hp.bg, mark=mk, order=od),
                  lambda: rast.photometric_loss(targets[v], hp.lambda_dssim),
                  lambda: rast.render_bwd_pairs(c, hp.bg, marks=mk, order=od), lambda: rast.gather(c),
@@ -344,13 +344,20 @@ def run_gpu(args):
     Pvis = float(np.mean(Pvis_list))
     n_vis = int((rast.rects[:, 2] > rast.rects[:, 0]).sum().item())
     px = W * H
+    chunks, tiles = (n_vis + 255) // 256, rast.TX * rast.TY
     # algorithmic bytes per launch: what each stage must read and write once
     # (a projected record or a pair's gradient record is 48 bytes)
     algo_bytes = {
         # read A_{t-1} 236 + latents 128 + lp 12 + log alpha 4, write the 2D record 48
         # (and A_t 236 for the projection adjoint)
-        "decode_project": (428.0 + 236.0) * n, "bin_sort": 20.0 * n + 36.0 * P,
-        "render_fwd": 20.0 * px + 4.0 * Pvis + 48.0 * n_vis,
+        "decode_project": (428.0 + 236.0) * n,
+        # depth sort: key and index in, out, and the rect read (20 per Gaussian); then with the lists
+        # written, the lower bound of a (key, value) sort over the P pairs (36 per pair), else the
+        # (chunk, tile) counts (written, read twice, written back) and the chunk masks (written)
+        "bin_sort": 20.0 * n + (16.0 * chunks * tiles + 32.0 * chunks * (rast.TX + rast.TY) if hp.lazy_lists
+                                else 36.0 * P),
+        # (with lists formed in the forward, it also writes the walked prefix: 4 per visited pair)
+        "render_fwd": 20.0 * px + (8.0 if hp.lazy_lists else 4.0) * Pvis + 48.0 * n_vis,
         # L1: img, target, d_img; D-SSIM: img, target, 3 maps out, 3 maps in, img, target, d_img += (3 channels)
         "loss": 36.0 * px + (144.0 * px if hp.lambda_dssim > 0 else 0.0),
         "render_bwd": 20.0 * px + 52.0 * Pvis + 48.0 * n_vis, "gather": 48.0 * Pvis + 48.0 * n_vis,
@@ -359,7 +366,7 @@ def run_gpu(args):
     }
     avg = {s: float(np.mean(stage_ms[s])) for s in STAGES}
     # the dominant kernel: the longest stage that is one kernel (the binning
-    # stage is 15 kernels, none of them as long as the compositing adjoint)
+    # stage is 14 kernels, none of them as long as the compositing adjoint)
     dom = max((s for s in STAGES if KERNELS_PER_STAGE[s] == 1), key=lambda s: avg[s])
     hbm_peak, peak_kind = peaks()
     achieved = algo_bytes[dom] / (avg[dom] * 1e-3) / 1e9

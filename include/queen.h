@@ -270,8 +270,11 @@ size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y);
  *   depth [n] f32 (read; > 0 for every Gaussian with a non-empty rect),
  *     it may be a strided view: element i at depth[i * depth_stride]
  *   rects [n] int4 (read)
- *   vals  [pair_capacity] u32 Gaussian index per sorted pair (written)
- *   keys  [pair_capacity] u64 sorted keys (written; nullable)
+ *   vals  [pair_capacity] u32 Gaussian index per sorted pair (written;
+ *     nullable: with vals NULL the lists are not written -- ranges, n_pairs
+ *     and the workspace are -- and qn_render_fwd_binned forms each tile's
+ *     list from the workspace as it composites, writing the part it walks)
+ *   keys  [pair_capacity] u64 sorted keys (written; nullable; needs vals)
  *   ranges [tiles_x * tiles_y][2] u32: (#pairs with tile < t, #pairs with tile <= t)
  *   n_pairs [1] i64 device: the pair count P (written)
  *   n_pairs_host (nullable): if given, the call synchronises `stream`, stores
@@ -295,7 +298,8 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
  * counterpart; this is a convenience of this library.
  *
  * Arguments, results and errors are those of qn_bin_sort, minus `workspace`
- * and `workspace_bytes`.  The scratch space is a fixed file-scope device
+ * and `workspace_bytes`; vals is required when pair_capacity > 0 (the
+ * workspace is private, so the lists must be written).  The scratch space is a fixed file-scope device
  * array of QN_BIN_SORT_STATIC_BYTES (40 MiB), which every GPU that loads this
  * library keeps until the process exits.  A problem whose
  * qn_bin_sort_workspace_size exceeds that is rejected with
@@ -324,7 +328,8 @@ int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_stride, con
 
 /*
  * Per pixel (u, v) at (u + 0.5, v + 0.5), front to back over its tile's list:
- *   alpha = min(0.99, o exp(power)); skipped when power > 0 or alpha < 1/255;
+ *   alpha = min(0.99, o exp(power)); skipped when alpha < 1/255 (no test of
+ *   power > 0: for a positive definite conic it only fires on rounding);
  *   stop before a Gaussian that would leave T < 1e-4;
  *   C += c alpha T; T *= 1 - alpha.   img = C + T bg.
  *   img [3][H][W] f32, T_final [H][W] f32, last [H][W] u32 = 1 + list position
@@ -343,6 +348,25 @@ int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
                   const qn_splat *splats, const float *bg_host, float *img, float *T_final,
                   uint32_t *last, uint32_t *n_contrib, uint8_t *composited, const uint32_t *tile_order,
                   uint32_t *tile_cost, qn_stream_t stream);
+
+/*
+ * qn_render_fwd for a binning that left the lists unwritten (qn_bin_sort with
+ * vals = NULL; n, workspace and workspace_bytes those of that call, the
+ * workspace unchanged since): each tile's list -- the same list, in the same
+ * order -- is formed from the workspace as the tile composites, and every
+ * list position a pixel of the tile walks (at least every position below the
+ * tile's largest `last`, which is all qn_render_bwd reads) is written to
+ * vals[ranges[2 t] + position]; the rest of vals is left as it is.  Every
+ * output equals qn_render_fwd's on the written lists, bit for bit.  ranges
+ * may be qn_bin_sort's or qn_mask_ranges' output (its empty tiles walk
+ * nothing).  vals [pair_capacity of the binning] u32 (written in part).
+ * Errors: those of qn_render_fwd, and QN_ERR_INVALID_ARG for a missing,
+ * misaligned or too small workspace.
+ */
+int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, const void *workspace, size_t workspace_bytes,
+                         const uint32_t *ranges, uint32_t *vals, const qn_splat *splats, const float *bg_host,
+                         float *img, float *T_final, uint32_t *last, uint32_t *n_contrib, uint8_t *composited,
+                         const uint32_t *tile_order, uint32_t *tile_cost, qn_stream_t stream);
 
 /*
  * tile_order = the tiles by descending tile_cost (costs above 1023 count as

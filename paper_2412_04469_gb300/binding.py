@@ -70,6 +70,7 @@ _SIGS = {
     "qn_bin_sort": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_bin_sort_noalloc": ([_I32, _P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_render_fwd_binned": ([_P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_tile_order": ([_I32, _P, _P, _P], C.c_int),
     "qn_render_bwd": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P, _P], C.c_int),
     "qn_render_bwd_pairs": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P], C.c_int),
@@ -257,6 +258,16 @@ def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=N
     _check(lib().qn_render_fwd(C.byref(cam), _ptr(ranges), _ptr(vals), _ptr(splats), _bg(bg), _ptr(img),
                                _ptr(T_final), _ptr(last), _ptr(n_contrib), _ptr(composited), _ptr(tile_order),
                                _ptr(tile_cost), _stream(stream)))
+
+
+def qn_render_fwd_binned(cam, n, workspace, ranges, vals, splats, bg, img, T_final, last, n_contrib=None,
+                         stream=None, composited=None, tile_order=None, tile_cost=None):
+    """qn_render_fwd for a qn_bin_sort call made with vals=None: the lists are
+    formed from the binning workspace; the walked positions are written to vals."""
+    _check(lib().qn_render_fwd_binned(C.byref(cam), n, _ptr(workspace), _nbytes(workspace), _ptr(ranges),
+                                      _ptr(vals), _ptr(splats), _bg(bg), _ptr(img), _ptr(T_final), _ptr(last),
+                                      _ptr(n_contrib), _ptr(composited), _ptr(tile_order), _ptr(tile_cost),
+                                      _stream(stream)))
 
 
 def qn_tile_order(n_tiles, tile_cost, tile_order, stream=None):

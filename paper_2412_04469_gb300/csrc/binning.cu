@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "bins.cuh"
 #include "common.cuh"
 
 namespace qn {
@@ -24,8 +25,8 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // keys per block per pass
 constexpr int RADIX = 256;
-constexpr int CHUNK = 256;                             // Gaussians per binning chunk
-constexpr int CHUNK_WARPS = CHUNK / 32;
+constexpr int CHUNK = BIN_CHUNK;                       // Gaussians per binning chunk
+constexpr int CHUNK_WARPS = BIN_CHUNK_WARPS;
 // Rects above this many tiles are listed by the binning and summed by a whole
 // block in the gather (0.2% of the visible Gaussians of a 300k-Gaussian
 // 1352x1014 view, 2% at 1M and 1920x1080, where the largest covers ~4300
@@ -810,6 +811,22 @@ __global__ void __launch_bounds__(GATHER_THREADS, 3) k_bin_gather(int TX, int TY
 }  // namespace
 }  // namespace qn
 
+namespace qn {
+int bin_view(int32_t n, int32_t tiles_x, int32_t tiles_y, const void *workspace, size_t workspace_bytes,
+             BinView &v) {
+    QN_REQUIRE(n >= 0 && tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
+               "bad n or tile grid");
+    QN_REQUIRE(workspace && ((uintptr_t)workspace & 255) == 0, "binning workspace is required, 256-byte aligned");
+    const Layout L = layout_of(n, tiles_x, tiles_y);
+    QN_REQUIRE(workspace_bytes >= L.total, "binning workspace too small (%zu < %zu)", workspace_bytes, L.total);
+    const char *ws = static_cast<const char *>(workspace);
+    v.masks = reinterpret_cast<const uint32_t *>(ws + L.masks);
+    v.sorted = reinterpret_cast<const uint32_t *>(ws + L.vals0);   // after the 4 passes, back in vals0
+    v.n_vis = reinterpret_cast<const uint32_t *>(ws + L.hdr + offsetof(Header, n_vis));
+    return QN_OK;
+}
+}  // namespace qn
+
 extern "C" size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y) {
     if (n < 0 || tiles_x <= 0 || tiles_y <= 0) return 0;
     return qn::layout_of(n, tiles_x, tiles_y).total;
@@ -827,7 +844,7 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     QN_REQUIRE(pair_capacity >= 0, "pair_capacity must be >= 0");
     QN_REQUIRE(ranges && n_pairs, "ranges and n_pairs are required");
     QN_REQUIRE(n == 0 || (depth && rects && workspace), "null pointer argument");
-    QN_REQUIRE(pair_capacity == 0 || vals, "vals is required when pair_capacity > 0");
+    QN_REQUIRE(vals || !keys, "keys need vals (with vals NULL the lists are not written)");
     QN_REQUIRE(((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
                "rects must be 16-byte and workspace 256-byte aligned");
     const int n_tiles = tiles_x * tiles_y;
@@ -877,10 +894,12 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total, tile_off, ranges,
                                                         hdr, (unsigned long long)capacity,
                                                         reinterpret_cast<long long *>(n_pairs));
-    const int vec = ((uintptr_t)vals & 15) == 0;       // 16-byte stores need a 16-byte aligned vals
-    k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
-                                               tile_off, masks, vals, reinterpret_cast<unsigned long long *>(keys),
-                                               vec);
+    if (vals) {                                        // else the compositing forward writes what it walks
+        const int vec = ((uintptr_t)vals & 15) == 0;   // 16-byte stores need a 16-byte aligned vals
+        k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
+                                                   tile_off, masks, vals,
+                                                   reinterpret_cast<unsigned long long *>(keys), vec);
+    }
     int st = check_launch("qn_bin_sort");
     if (st) return st;
     if (n_pairs_host) {
@@ -1003,6 +1022,7 @@ extern "C" int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_
                                    uint64_t *keys, uint32_t *ranges, int64_t *n_pairs, int64_t *n_pairs_host,
                                    qn_stream_t stream) {
     QN_REQUIRE(n >= 0 && tiles_x > 0 && tiles_y > 0, "bad n or tile grid");
+    QN_REQUIRE(pair_capacity == 0 || vals, "vals is required when pair_capacity > 0 (the workspace is private)");
     const size_t need = qn_bin_sort_workspace_size(n, tiles_x, tiles_y);
     if (need > (size_t)QN_BIN_SORT_STATIC_BYTES) {
         qn::set_error("qn_bin_sort_noalloc: %d Gaussians on a %dx%d tile grid need %zu bytes of workspace, "

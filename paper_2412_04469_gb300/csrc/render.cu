@@ -7,6 +7,7 @@
 // instructions (add/sub/mul/fma .f32x2: two lanes of arithmetic per issued
 // instruction), its staged records holding every per-Gaussian scalar
 // duplicated into a pair, so a 128-bit broadcast load yields operand pairs.
+#include "bins.cuh"
 #include "common.cuh"
 
 namespace qn {
@@ -36,6 +37,11 @@ struct CapTag {
 #endif
 #ifndef QN_BWD_PPT
 #define QN_BWD_PPT 4
+#endif
+
+// resident blocks per SM the forward that walks unwritten lists is compiled for
+#ifndef QN_FWD_LAZY_BLOCKS
+#define QN_FWD_LAZY_BLOCKS 0
 #endif
 
 template <int PPT>
@@ -181,6 +187,98 @@ __device__ __forceinline__ void pixel_coords(int tile, int TX, int &px, int &py0
     py0 = (tile / TX) * QN_TILE + warp * (2 * PPT) + (lane >> 4) * PPT;
 }
 
+// ---------------------------------------------------------------- unwritten lists
+// A warp's walk of its tile's list when the binning left the lists unwritten
+// (the layout is described with BinView): a window of 32 chunks, lane l
+// holding the member count of chunk cw + l in the tile (excl: the counts of
+// the window's chunks below it) and that chunk's eight words for the tile in
+// shared memory ([word][lane]).  Position p of the list is member p - wbase
+// of the window: its chunk is found by a binary search over excl, its word by
+// the counts of the words before it, the member by clearing the lower set
+// bits of that word.
+struct ListWalk {
+    int cw;                  // the window's first chunk
+    uint32_t wbase, wtot;    // members before the window, in it
+    uint32_t excl;           // lane l: members of chunks cw .. cw + l - 1 in the tile
+};
+
+__device__ __forceinline__ void walk_load(ListWalk &lw, uint32_t (*wm)[32], const uint32_t *__restrict__ masks,
+                                          int TX, int TY, int tx, int ty, int nchunks, int lane) {
+    static_assert(BIN_CHUNK_WARPS == 8, "a tile's words of one chunk are two uint4");
+    const int c = lw.cw + lane;
+    uint32_t w[BIN_CHUNK_WARPS] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (c < nchunks) {
+        // 16-byte aligned: the workspace's mask array is, a chunk's words take
+        // 32 (TX + TY) bytes and a column's / row's 32
+        const uint4 *mx = reinterpret_cast<const uint4 *>(masks + (size_t)c * BIN_CHUNK_WARPS * (TX + TY));
+        const uint4 x0 = mx[2 * tx], x1 = mx[2 * tx + 1], y0 = mx[2 * TX + 2 * ty], y1 = mx[2 * TX + 2 * ty + 1];
+        w[0] = x0.x & y0.x; w[1] = x0.y & y0.y; w[2] = x0.z & y0.z; w[3] = x0.w & y0.w;
+        w[4] = x1.x & y1.x; w[5] = x1.y & y1.y; w[6] = x1.z & y1.z; w[7] = x1.w & y1.w;
+    }
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < BIN_CHUNK_WARPS; ++i) {
+        wm[i][lane] = w[i];
+        cnt += __popc(w[i]);
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += x;
+    }
+    lw.excl = incl - cnt;
+    lw.wtot = __shfl_sync(FULL, incl, 31);
+    __syncwarp();
+}
+
+// The Gaussian at position p of the tile's list for the lanes with need set
+// (the warp's positions ascend from call to call); returns whether it was
+// found (always, for a list consistent with the masks).
+__device__ __forceinline__ bool walk_member(ListWalk &lw, uint32_t (*wm)[32], uint32_t p, bool need,
+                                            const uint32_t *__restrict__ masks, const uint32_t *__restrict__ sorted,
+                                            int TX, int TY, int tx, int ty, int nchunks, int lane, uint32_t &id) {
+    bool found = false;
+    for (;;) {
+        const bool here = need && p < lw.wbase + lw.wtot;
+        const uint32_t r = here ? p - lw.wbase : 0u;
+        int L = 0;                                      // the last chunk with excl <= r
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const uint32_t e = __shfl_sync(FULL, lw.excl, L + st);
+            if (e <= r) L += st;
+        }
+        uint32_t k = r - __shfl_sync(FULL, lw.excl, L);
+        if (here) {
+            int wsel = 0;
+            uint32_t word = 0;
+            bool got = false;
+#pragma unroll
+            for (int i = 0; i < BIN_CHUNK_WARPS; ++i) {
+                const uint32_t x = wm[i][L];
+                const uint32_t c = __popc(x);
+                if (!got && k < c) {
+                    got = true;
+                    wsel = i;
+                    word = x;
+                } else if (!got) {
+                    k -= c;
+                }
+            }
+            for (uint32_t i = 0; i < k; ++i) word &= word - 1;
+            id = sorted[(size_t)(lw.cw + L) * BIN_CHUNK + wsel * 32 + (__ffs(word) - 1)];
+            found = true;
+            need = false;
+        }
+        if (!__any_sync(FULL, need) || lw.cw + 32 >= nchunks) break;
+        lw.wbase += lw.wtot;                            // the next 32 chunks
+        lw.cw += 32;
+        __syncwarp();                                   // every lane is done with the old words
+        walk_load(lw, wm, masks, TX, TY, tx, ty, nchunks, lane);
+    }
+    return found;
+}
+
 // ---------------------------------------------------------------- forward
 // Every warp composites its band independently: it stages its own copy of
 // each batch of records (48 bytes: mean, opacity, scaled conic and cull bound,
@@ -228,10 +326,15 @@ __device__ __forceinline__ void scalar_exponent(const SRec &r, float fx, float f
 }
 
 // COUNT: write the contributor counts; MARK: set the composited marks.
-template <bool COUNT, bool MARK, int PPT>
-__global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H, int TX,
+// LAZY: the lists were not written; each warp walks its tile's list from the
+// binning's chunk masks (BinView) and writes the positions it walks to
+// vals_out (both warps of a tile write the same values), so that the list's
+// walked prefix is there for the adjoint.
+template <bool COUNT, bool MARK, int PPT, bool LAZY>
+__global__ void __launch_bounds__(Band<PPT>::THREADS, LAZY ? QN_FWD_LAZY_BLOCKS : 0) k_render_fwd(int W, int H, int TX, int TY,
                                                                   const uint32_t *__restrict__ ranges,
                                                                   const uint32_t *__restrict__ vals,
+                                                                  BinView bins, uint32_t *__restrict__ vals_out,
                                                                   const float4 *__restrict__ sp, float bg0, float bg1,
                                                                   float bg2, float *__restrict__ img,
                                                                   float *__restrict__ Tf, uint32_t *__restrict__ last,
@@ -242,6 +345,7 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
     constexpr int WARPS = Band<PPT>::WARPS;
     __shared__ SRec sbuf[WARPS][FWD_BATCH];
     __shared__ uint32_t wmax[WARPS];
+    __shared__ uint32_t wmask[LAZY ? WARPS : 1][LAZY ? BIN_CHUNK_WARPS : 1][32];
     SRec *s = sbuf[threadIdx.x >> 5];
     const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int lane = threadIdx.x & 31;
@@ -265,6 +369,8 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
     const float bx0 = (float)((tile % TX) * QN_TILE) + 0.5f, bx1 = fminf(bx0 + (float)(QN_TILE - 1), W - 0.5f);
     const float by0 = (float)((tile / TX) * QN_TILE + (threadIdx.x >> 5) * (2 * PPT)) + 0.5f;
     const float by1 = fminf(by0 + (float)(2 * PPT - 1), H - 0.5f);
+    ListWalk lw{-32, 0u, 0u, 0u};
+    const int nchunks = LAZY ? (int)((__ldg(bins.n_vis) + BIN_CHUNK - 1) / BIN_CHUNK) : 0;
     for (int b0 = 0; b0 < n; b0 += FWD_BATCH) {
         bool live = false;                              // the warp stops between batches
 #pragma unroll
@@ -272,8 +378,15 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
         if (!__any_sync(FULL, live)) break;
         uint32_t my_id = 0;
         bool reach = false;
-        if (b0 + lane < n) {
+        bool have = b0 + lane < n;
+        if constexpr (LAZY) {
+            have = walk_member(lw, wmask[threadIdx.x >> 5], (uint32_t)(b0 + lane), have, bins.masks,
+                               bins.sorted, TX, TY, tile % TX, tile / TX, nchunks, lane, my_id);
+            if (have) vals_out[beg + b0 + lane] = my_id;
+        } else if (have) {
             my_id = vals[beg + b0 + lane];
+        }
+        if (have) {
             SRec rr;
             stage_srec(rr, sp[3 * (size_t)my_id], sp[3 * (size_t)my_id + 1], sp[3 * (size_t)my_id + 2]);
             s[lane] = rr;
@@ -674,6 +787,26 @@ int launch_render_bwd(const qn_camera *cam, const uint32_t *ranges, const uint32
 
 }  // namespace qn
 
+namespace qn {
+namespace {
+template <bool LAZY>
+int launch_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals, const BinView &bins,
+                      uint32_t *vals_out, const qn_splat *splats, const float *bg_host, float *img, float *T_final,
+                      uint32_t *last, uint32_t *n_contrib, uint8_t *composited, const uint32_t *tile_order,
+                      uint32_t *tile_cost, qn_stream_t stream) {
+    const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
+    constexpr int PPT = QN_FWD_PPT;
+    auto kern = n_contrib ? (composited ? k_render_fwd<true, true, PPT, LAZY> : k_render_fwd<true, false, PPT, LAZY>)
+                          : (composited ? k_render_fwd<false, true, PPT, LAZY> : k_render_fwd<false, false, PPT, LAZY>);
+    kern<<<TX * TY, Band<PPT>::THREADS, 0, as_stream(stream)>>>(
+        cam_host->width, cam_host->height, TX, TY, ranges, vals, bins, vals_out,
+        reinterpret_cast<const float4 *>(splats), bg_host[0], bg_host[1], bg_host[2], img, T_final, last, n_contrib,
+        composited, tile_order, tile_cost);
+    return check_launch(LAZY ? "qn_render_fwd_binned" : "qn_render_fwd");
+}
+}  // namespace
+}  // namespace qn
+
 extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint32_t *vals,
                              const qn_splat *splats, const float *bg_host, float *img, float *T_final,
                              uint32_t *last, uint32_t *n_contrib, uint8_t *composited, const uint32_t *tile_order,
@@ -681,14 +814,25 @@ extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, 
     int st = qn::check_render_args(cam_host, ranges, vals, splats);
     if (st) return st;
     QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
+    return qn::launch_render_fwd<false>(cam_host, ranges, vals, qn::BinView{nullptr, nullptr, nullptr}, nullptr,
+                                        splats, bg_host, img, T_final, last, n_contrib, composited, tile_order,
+                                        tile_cost, stream);
+}
+
+extern "C" int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, const void *workspace,
+                                    size_t workspace_bytes, const uint32_t *ranges, uint32_t *vals,
+                                    const qn_splat *splats, const float *bg_host, float *img, float *T_final,
+                                    uint32_t *last, uint32_t *n_contrib, uint8_t *composited,
+                                    const uint32_t *tile_order, uint32_t *tile_cost, qn_stream_t stream) {
+    int st = qn::check_render_args(cam_host, ranges, vals, splats);
+    if (st) return st;
+    QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
     const int TX = (cam_host->width + QN_TILE - 1) / QN_TILE, TY = (cam_host->height + QN_TILE - 1) / QN_TILE;
-    constexpr int PPT = QN_FWD_PPT;
-    auto kern = n_contrib ? (composited ? qn::k_render_fwd<true, true, PPT> : qn::k_render_fwd<true, false, PPT>)
-                          : (composited ? qn::k_render_fwd<false, true, PPT> : qn::k_render_fwd<false, false, PPT>);
-    kern<<<TX * TY, qn::Band<PPT>::THREADS, 0, qn::as_stream(stream)>>>(
-        cam_host->width, cam_host->height, TX, ranges, vals, reinterpret_cast<const float4 *>(splats), bg_host[0],
-        bg_host[1], bg_host[2], img, T_final, last, n_contrib, composited, tile_order, tile_cost);
-    return qn::check_launch("qn_render_fwd");
+    qn::BinView bins;
+    st = qn::bin_view(n, TX, TY, workspace, workspace_bytes, bins);
+    if (st) return st;
+    return qn::launch_render_fwd<true>(cam_host, ranges, nullptr, bins, vals, splats, bg_host, img, T_final, last,
+                                       n_contrib, composited, tile_order, tile_cost, stream);
 }
 
 extern "C" int qn_tile_order(int32_t n_tiles, const uint32_t *tile_cost, uint32_t *tile_order, qn_stream_t stream) {

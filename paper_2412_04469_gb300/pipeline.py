@@ -69,6 +69,11 @@ class HParams:
     # 0.129 ms against 0.105 ms for the two kernels (its ~800 bytes of shared
     # memory per Gaussian leave ~8 warps per SM for a long serial chain)
     fused_bwd: bool = False
+    # the binning leaves the per-tile lists unwritten and the compositing
+    # forward forms each tile's list from the binning's chunk masks as it
+    # goes, writing only the prefix it walks (~5% of the pairs); the same
+    # result
+    lazy_lists: bool = True
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
@@ -278,6 +283,7 @@ class Rasterizer:
         self.tile_cost = torch.zeros(self.TX * self.TY, device=dev, dtype=torch.int32)
         self.tile_order = torch.arange(self.TX * self.TY, device=dev, dtype=torch.int32)
         self.keep_keys = keep_keys
+        self.lazy = False                                          # the last bin_sort left the lists unwritten
         self.set_capacity(pair_capacity)
         self.img = torch.zeros((3, height, width), device=dev)
         self.T_final = torch.zeros((height, width), device=dev)
@@ -297,11 +303,15 @@ class Rasterizer:
         B.qn_project(self.n, self.S, self.sh_degree, attrs, cam, blur, self.splats, self.rects, self.tight_rects,
                      stream)
 
-    def bin_sort(self, sync=False, stream=None, rects=None):
+    def bin_sort(self, sync=False, stream=None, rects=None, lazy=False):
+        """With lazy, the per-tile lists are not written: the next render_fwd
+        forms them from the binning workspace and writes the part it walks
+        (all the adjoint reads); the keys are then not written either."""
         depth_ptr = self.splats.data_ptr() + 3 * 4
+        self.lazy = bool(lazy)
         return B.qn_bin_sort(self.n, depth_ptr, 12, self.rects if rects is None else rects, self.TX, self.TY,
-                             self.workspace, self.capacity, self.vals, self.keys, self.ranges, self.n_pairs, sync,
-                             stream)
+                             self.workspace, self.capacity, None if lazy else self.vals,
+                             None if lazy else self.keys, self.ranges, self.n_pairs, sync, stream)
 
     def render_fwd(self, cam, bg, n_contrib=None, stream=None, ranges=None, mark=False, order=False):
         """Compositing; with mark, `composited` holds afterwards the Gaussians
@@ -310,9 +320,18 @@ class Rasterizer:
         this forward's costs."""
         if mark:
             self.composited.zero_()
-        B.qn_render_fwd(cam, self.ranges if ranges is None else ranges, self.vals, self.splats, bg, self.img,
-                        self.T_final, self.last, n_contrib, stream, composited=self.composited if mark else None,
-                        tile_order=self.tile_order if order else None, tile_cost=self.tile_cost if order else None)
+        rg = self.ranges if ranges is None else ranges
+        if self.lazy:
+            B.qn_render_fwd_binned(cam, self.n, self.workspace, rg, self.vals, self.splats, bg, self.img,
+                                   self.T_final, self.last, n_contrib, stream,
+                                   composited=self.composited if mark else None,
+                                   tile_order=self.tile_order if order else None,
+                                   tile_cost=self.tile_cost if order else None)
+        else:
+            B.qn_render_fwd(cam, rg, self.vals, self.splats, bg, self.img, self.T_final, self.last, n_contrib,
+                            stream, composited=self.composited if mark else None,
+                            tile_order=self.tile_order if order else None,
+                            tile_cost=self.tile_cost if order else None)
         if order:
             B.qn_tile_order(self.TX * self.TY, self.tile_cost, self.tile_order, stream)
 
@@ -453,7 +472,7 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     else:
         frame.decode(stream, skip, train=True)
         rast.project(frame.attrs, cam, hp.blur, stream)
-    rast.bin_sort(False, stream)
+    rast.bin_sort(False, stream, lazy=hp.lazy_lists)
     ranges = None
     if mask is not None:
         rast.mask_ranges(mask, stream)

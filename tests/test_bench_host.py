@@ -18,7 +18,7 @@ def test_bench_imports_and_counts():
     assert bench.STAGES == list(bench.KERNELS_PER_STAGE)
     # fused decode+projection, 17 binning, forward + tile order, 4 loss, adjoint, gather, projection
     # adjoint, 2 decode adjoint, 2 Adam
-    assert sum(bench.KERNELS_PER_STAGE.values()) == 29
+    assert sum(bench.KERNELS_PER_STAGE.values()) == 28
     assert bench.workload_name("full") == "queen_residual_step_n300000_sh3_1352x1014_v20"
 
 

@@ -147,13 +147,16 @@ def test_fused_training_iteration_matches_two_kernel_iteration():
     iteration with the separate kernels bit for bit: records, every gradient
     and Adam's update.  With the fused adjoint too, every per-Gaussian array
     still matches bit for bit; the decoder gradient (another summation order)
-    and the decoders after Adam's step agree to rounding."""
+    and the decoders after Adam's step agree to rounding.  Lists formed in
+    the compositing forward (the default) or written by the binning give the
+    same iteration bit for bit."""
     from paper_2412_04469_gb300.pipeline import training_iteration
     n, deg = 3000, 3
     outs = []
-    for fused, fused_bwd in ((False, False), (True, False), (True, True)):
+    for fused, fused_bwd, lazy in ((False, False, True), (True, False, True), (True, True, True),
+                                   (True, False, False)):
         B, f, r, c, cam, prev, res = _setup(n, deg, 5, DecoderLayout.default(sh_degree=deg, latent=8))
-        f.hp.fused, f.hp.fused_bwd = fused, fused_bwd
+        f.hp.fused, f.hp.fused_bwd, f.hp.lazy_lists = fused, fused_bwd, lazy
         f.decode()
         r.size_for_views(f.attrs, [c], f.hp.blur)
         tgt = up(S.make_image(160, 120, 5))
@@ -161,10 +164,11 @@ def test_fused_training_iteration_matches_two_kernel_iteration():
         torch.cuda.synchronize()
         outs.append((r.splats[:n].clone(), r.d_splats[:n].clone(), f.d_lat[:, :n].clone(), f.d_lp[:, :n].clone(),
                      f.d_log_alpha[:n].clone(), f.d_dec.clone(), f.lat[:, :n].clone(), f.dec.clone()))
-    a, b, fb = outs
+    a, b, fb, written = outs
     names = ("splats", "d_splats", "d_lat", "d_lp", "d_log_alpha", "d_dec", "lat", "dec")
     for k, name in enumerate(names):
         assert torch.equal(a[k], b[k]), name
+        assert torch.equal(written[k], b[k]), name
     for k, name in enumerate(names):
         if name in ("d_dec", "dec"):
             close(fb[k].cpu().numpy(), a[k].cpu().numpy(), floor_frac=0.01, what=name)
