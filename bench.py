@@ -212,7 +212,7 @@ def run_gpu(args):
         """One iteration issued stage by stage with an event between stages."""
         c = cams[v]
         mk, od = hp.mark_composited, hp.order_tiles
-        calls = (lambda: frame.decode_project(rast, c), lambda: rast.bin_sort(False, lazy=hp.lazy_lists),
+        calls = (lambda: frame.decode_project(rast, c), lambda: rast.bin_sort(False, lazy=hp.lazy_lists, list_max=hp.list_max),
                  lambda: rast.render_fwd(c, hp.bg, mark=mk, order=od),
                  lambda: rast.photometric_loss(targets[v], hp.lambda_dssim),
                  lambda: rast.render_bwd_pairs(c, hp.bg, marks=mk, order=od), lambda: rast.gather(c),

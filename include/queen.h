@@ -270,11 +270,8 @@ size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t tiles_y);
  *   depth [n] f32 (read; > 0 for every Gaussian with a non-empty rect),
  *     it may be a strided view: element i at depth[i * depth_stride]
  *   rects [n] int4 (read)
- *   vals  [pair_capacity] u32 Gaussian index per sorted pair (written;
- *     nullable: with vals NULL the lists are not written -- ranges, n_pairs
- *     and the workspace are -- and qn_render_fwd_binned forms each tile's
- *     list from the workspace as it composites, writing the part it walks)
- *   keys  [pair_capacity] u64 sorted keys (written; nullable; needs vals)
+ *   vals  [pair_capacity] u32 Gaussian index per sorted pair (written)
+ *   keys  [pair_capacity] u64 sorted keys (written; nullable)
  *   ranges [tiles_x * tiles_y][2] u32: (#pairs with tile < t, #pairs with tile <= t)
  *   n_pairs [1] i64 device: the pair count P (written)
  *   n_pairs_host (nullable): if given, the call synchronises `stream`, stores
@@ -287,6 +284,20 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
                 int64_t pair_capacity, uint32_t *vals, uint64_t *keys, uint32_t *ranges,
                 int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream);
 
+/*
+ * qn_bin_sort that writes only the lists of the tiles holding at most
+ * list_max pairs (none for 0, all for 0xffffffff) and no keys; ranges,
+ * n_pairs, n_pairs_host and the workspace as qn_bin_sort leaves them.  The
+ * other lists are formed by qn_render_fwd_binned as it composites, which
+ * writes the part of each it walks.  The point: most pairs belong to long
+ * lists, of which compositing visits a short prefix, while a short list is
+ * often walked to its end.  Arguments, results and errors as qn_bin_sort.
+ */
+int qn_bin_sort_partial(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                        int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,
+                        int64_t pair_capacity, uint32_t list_max, uint32_t *vals, uint32_t *ranges,
+                        int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream);
+
 /* Size of the device array that qn_bin_sort_noalloc uses as its workspace. */
 #define QN_BIN_SORT_STATIC_BYTES (40u << 20)
 
@@ -298,8 +309,7 @@ int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32
  * counterpart; this is a convenience of this library.
  *
  * Arguments, results and errors are those of qn_bin_sort, minus `workspace`
- * and `workspace_bytes`; vals is required when pair_capacity > 0 (the
- * workspace is private, so the lists must be written).  The scratch space is a fixed file-scope device
+ * and `workspace_bytes`.  The scratch space is a fixed file-scope device
  * array of QN_BIN_SORT_STATIC_BYTES (40 MiB), which every GPU that loads this
  * library keeps until the process exits.  A problem whose
  * qn_bin_sort_workspace_size exceeds that is rejected with
@@ -350,16 +360,16 @@ int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
                   uint32_t *tile_cost, qn_stream_t stream);
 
 /*
- * qn_render_fwd for a binning that left the lists unwritten (qn_bin_sort with
- * vals = NULL; n, workspace and workspace_bytes those of that call, the
- * workspace unchanged since): each tile's list -- the same list, in the same
- * order -- is formed from the workspace as the tile composites, and every
+ * qn_render_fwd after qn_bin_sort_partial (n, workspace, workspace_bytes and
+ * vals those of that call, the workspace unchanged since): a tile whose list
+ * was written reads it from vals; a longer one is formed from the workspace
+ * -- the same list, in the same order -- as the tile composites, and every
  * list position a pixel of the tile walks (at least every position below the
  * tile's largest `last`, which is all qn_render_bwd reads) is written to
  * vals[ranges[2 t] + position]; the rest of vals is left as it is.  Every
- * output equals qn_render_fwd's on the written lists, bit for bit.  ranges
- * may be qn_bin_sort's or qn_mask_ranges' output (its empty tiles walk
- * nothing).  vals [pair_capacity of the binning] u32 (written in part).
+ * output equals qn_render_fwd's on fully written lists, bit for bit.  ranges
+ * may be the binning's or qn_mask_ranges' output (its empty tiles walk
+ * nothing).  vals [pair_capacity of the binning] u32 (read, written in part).
  * Errors: those of qn_render_fwd, and QN_ERR_INVALID_ARG for a missing,
  * misaligned or too small workspace.
  */

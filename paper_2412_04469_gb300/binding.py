@@ -52,7 +52,7 @@ class qn_adam_group(C.Structure):
 
 _lib = None
 _P = C.c_void_p
-_I32, _I64, _F32, _SZ = C.c_int32, C.c_int64, C.c_float, C.c_size_t
+_I32, _I64, _F32, _SZ, _U32 = C.c_int32, C.c_int64, C.c_float, C.c_size_t, C.c_uint32
 
 _SIGS = {
     "qn_last_error": ([], C.c_char_p),
@@ -71,6 +71,7 @@ _SIGS = {
     "qn_bin_sort_noalloc": ([_I32, _P, _I32, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_fwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "qn_render_fwd_binned": ([_P, _I32, _P, _SZ, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "qn_bin_sort_partial": ([_I32, _P, _I32, _P, _I32, _I32, _P, _SZ, _I64, _U32, _P, _P, _P, _P, _P], C.c_int),
     "qn_tile_order": ([_I32, _P, _P, _P], C.c_int),
     "qn_render_bwd": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P, _P], C.c_int),
     "qn_render_bwd_pairs": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P], C.c_int),
@@ -237,6 +238,18 @@ def qn_bin_sort(n, depth, depth_stride, rects, tiles_x, tiles_y, workspace, pair
     return int(host.value) if sync else None
 
 
+def qn_bin_sort_partial(n, depth, depth_stride, rects, tiles_x, tiles_y, workspace, pair_capacity, list_max, vals,
+                        ranges, n_pairs, sync=True, stream=None):
+    """qn_bin_sort writing only the lists of at most list_max pairs; returns P
+    (int) when sync is True (the call synchronises), else None."""
+    host = C.c_int64(0)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().qn_bin_sort_partial(n, _ptr(depth), depth_stride, _ptr(rects), tiles_x, tiles_y, _ptr(workspace),
+                                     ws_bytes, int(pair_capacity), int(list_max), _ptr(vals), _ptr(ranges),
+                                     _ptr(n_pairs), C.addressof(host) if sync else None, _stream(stream)))
+    return int(host.value) if sync else None
+
+
 def qn_bin_sort_noalloc(n, depth, depth_stride, rects, tiles_x, tiles_y, pair_capacity, vals, keys, ranges,
                         n_pairs, sync=True, stream=None):
     """qn_bin_sort on the library's fixed device workspace, for callers that
@@ -262,8 +275,8 @@ def qn_render_fwd(cam, ranges, vals, splats, bg, img, T_final, last, n_contrib=N
 
 def qn_render_fwd_binned(cam, n, workspace, ranges, vals, splats, bg, img, T_final, last, n_contrib=None,
                          stream=None, composited=None, tile_order=None, tile_cost=None):
-    """qn_render_fwd for a qn_bin_sort call made with vals=None: the lists are
-    formed from the binning workspace; the walked positions are written to vals."""
+    """qn_render_fwd after qn_bin_sort_partial: the lists it left unwritten are
+    formed from the binning workspace; their walked positions are written to vals."""
     _check(lib().qn_render_fwd_binned(C.byref(cam), n, _ptr(workspace), _nbytes(workspace), _ptr(ranges),
                                       _ptr(vals), _ptr(splats), _bg(bg), _ptr(img), _ptr(T_final), _ptr(last),
                                       _ptr(n_contrib), _ptr(composited), _ptr(tile_order), _ptr(tile_cost),

@@ -42,11 +42,17 @@ struct Header {
     unsigned long long pairs;
     uint32_t n_big;                                     // entries of the large-rect list
     uint32_t prefix_done;                               // blocks of k_chunk_prefix finished
+    uint32_t list_max;                                  // lists of at most this many pairs are written
 };
 
 struct Layout {
-    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, visited, hit, total;
+    size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, visited, hit, occ,
+        total;
 };
+
+// 32-chunk words of the per-tile chunk occupancy (bit c % 32 of word c / 32:
+// chunk c has a member in the tile)
+int occ_words(int n) { return div_up(div_up(n > 0 ? n : 1, CHUNK), 32); }
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -74,6 +80,7 @@ Layout layout_of(int n, int TX, int TY) {
     // written by the compositing adjoint's first pass, read by its gather
     L.visited = o; o = align_up(o + 4 * (size_t)n_tiles);       // visited prefix of each tile's list
     L.hit = o; o = align_up(o + (size_t)(n > 0 ? n : 1));        // Gaussians with a contributing record
+    L.occ = o; o = align_up(o + 4 * (size_t)occ_words(n) * n_tiles);   // [word][tile]
     L.total = o;
     return L;
 }
@@ -359,7 +366,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
 // the warps.  total is read through L2: other blocks of the same launch wrote it.
 __device__ void tile_offsets(int n_tiles, const uint32_t *__restrict__ total, uint32_t *__restrict__ off,
                              uint32_t *__restrict__ ranges, Header *hdr, unsigned long long capacity,
-                             long long *n_pairs) {
+                             long long *n_pairs, uint32_t list_max) {
     __shared__ unsigned long long wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = div_up_dev(n_tiles, 1024);
@@ -407,6 +414,7 @@ __device__ void tile_offsets(int n_tiles, const uint32_t *__restrict__ total, ui
     if (threadIdx.x == 0) {
         hdr->pairs = PT;
         hdr->overflow = over ? 1u : 0u;
+        hdr->list_max = list_max;
         if (n_pairs) *n_pairs = (long long)PT;
     }
 }
@@ -414,21 +422,28 @@ __device__ void tile_offsets(int n_tiles, const uint32_t *__restrict__ total, ui
 // In place: counts[c][t] <- sum_{c' < c} counts[c'][t]; tile_total[t] = sum_c.
 // Block = 32 tiles (lanes) x 32 chunk segments (warps).  Each warp walks its
 // segment PREFIX_BATCH chunks at a time with the loads issued together (the
-// walk is otherwise one dependent memory round trip per chunk).  The block
-// that finishes last (a ticket counter; nothing waits) then scans the tile
-// totals into the tile offsets, the ranges and P.
+// walk is otherwise one dependent memory round trip per chunk).  With occ,
+// the occupancy bits (count > 0) of the block's tiles are gathered in shared
+// memory ([word][tile], occ_w words) and written to occ[word][tile].  The
+// block that finishes last (a ticket counter; nothing waits) then scans the
+// tile totals into the tile offsets, the ranges and P.
 constexpr int PREFIX_BATCH = 8;
 
 __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles, uint32_t *__restrict__ counts,
                                                        uint32_t *__restrict__ tile_total,
                                                        uint32_t *__restrict__ tile_off, uint32_t *__restrict__ ranges,
                                                        Header *hdr, unsigned long long capacity,
-                                                       long long *n_pairs) {
+                                                       long long *n_pairs, uint32_t list_max,
+                                                       uint32_t *__restrict__ occ, int occ_w) {
     __shared__ uint32_t seg[32][33];
+    extern __shared__ uint32_t socc[];                  // [occ_w][32] when occ is given
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + lane;
     const int per = div_up_dev(n_chunks, 32);
     const int c0 = warp * per, c1 = min(n_chunks, c0 + per);
+    if (occ)
+        for (int i = threadIdx.x; i < occ_w * 32; i += blockDim.x) socc[i] = 0;
+    __syncthreads();
     uint32_t s = 0;
     if (t < n_tiles) {
         int c = c0;
@@ -437,12 +452,21 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
 #pragma unroll
             for (int k = 0; k < PREFIX_BATCH; ++k) v[k] = counts[(size_t)(c + k) * n_tiles + t];
 #pragma unroll
-            for (int k = 0; k < PREFIX_BATCH; ++k) s += v[k];
+            for (int k = 0; k < PREFIX_BATCH; ++k) {
+                s += v[k];
+                if (occ && v[k]) atomicOr(&socc[((c + k) >> 5) * 32 + lane], 1u << ((c + k) & 31));
+            }
         }
-        for (; c < c1; ++c) s += counts[(size_t)c * n_tiles + t];
+        for (; c < c1; ++c) {
+            const uint32_t v = counts[(size_t)c * n_tiles + t];
+            s += v;
+            if (occ && v) atomicOr(&socc[(c >> 5) * 32 + lane], 1u << (c & 31));
+        }
     }
     seg[warp][lane] = s;
     __syncthreads();
+    if (occ && t < n_tiles)
+        for (int w = warp; w < occ_w; w += 32) occ[(size_t)w * n_tiles + t] = socc[w * 32 + lane];
     if (warp == 0) {
         uint32_t run = 0;
         for (int w = 0; w < 32; ++w) {
@@ -480,13 +504,27 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
     __syncthreads();
     if (!last) return;
     __threadfence();
-    tile_offsets(n_tiles, tile_total, tile_off, ranges, hdr, capacity, n_pairs);
+    tile_offsets(n_tiles, tile_total, tile_off, ranges, hdr, capacity, n_pairs, list_max);
+}
+
+// The chunk prefix's shared occupancy bits above the 48 KB default: set once
+// per process (before any graph capture that the first call precedes).
+constexpr size_t PREFIX_MAX_OCC_SMEM = 192 * 1024;
+cudaError_t prefix_attributes() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(k_chunk_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)PREFIX_MAX_OCC_SMEM);
+    });
+    return err;
 }
 
 // Writes chunk c's members tile by tile: one thread per tile of the chunk's
 // bounding box writes the tile's members in depth order (the set bits of the
 // per-warp words, warp by warp) to consecutive slots from the chunk's first
-// slot in that tile.
+// slot in that tile.  Tiles holding more than list_max pairs are left out
+// (the compositing forward forms their lists).
 __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const uint32_t *__restrict__ sorted,
                                                          const int4 *__restrict__ rects,
                                                          const float *__restrict__ depth, int dstride,
@@ -494,7 +532,9 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
                                                          const uint32_t *__restrict__ tile_off,
                                                          const uint32_t *__restrict__ masks,
                                                          uint32_t *__restrict__ vals,
-                                                         unsigned long long *__restrict__ keys, int vec) {
+                                                         unsigned long long *__restrict__ keys, int vec,
+                                                         const uint32_t *__restrict__ tile_total,
+                                                         uint32_t list_max) {
     __shared__ ChunkSmem s;
     __shared__ uint32_t dbits[CHUNK];                   // depth bits of the members (for keys)
     const int c = blockIdx.x;
@@ -518,6 +558,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
         }
         if (!any) continue;
         const int t = ty * TX + tx;
+        if (list_max != 0xffffffffu && tile_total[t] > list_max) continue;
         uint32_t pos = tile_off[t] + grow[t];
         if (keys || !vec) {
 #pragma unroll
@@ -823,6 +864,9 @@ int bin_view(int32_t n, int32_t tiles_x, int32_t tiles_y, const void *workspace,
     v.masks = reinterpret_cast<const uint32_t *>(ws + L.masks);
     v.sorted = reinterpret_cast<const uint32_t *>(ws + L.vals0);   // after the 4 passes, back in vals0
     v.n_vis = reinterpret_cast<const uint32_t *>(ws + L.hdr + offsetof(Header, n_vis));
+    v.list_max = reinterpret_cast<const uint32_t *>(ws + L.hdr + offsetof(Header, list_max));
+    v.occ = reinterpret_cast<const uint32_t *>(ws + L.occ);
+    v.occ_w = occ_words(n);
     return QN_OK;
 }
 }  // namespace qn
@@ -832,11 +876,14 @@ extern "C" size_t qn_bin_sort_workspace_size(int32_t n, int32_t tiles_x, int32_t
     return qn::layout_of(n, tiles_x, tiles_y).total;
 }
 
-extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
-                           int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,
-                           int64_t pair_capacity, uint32_t *vals, uint64_t *keys, uint32_t *ranges,
-                           int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream) {
-    using namespace qn;
+namespace qn {
+namespace {
+// Both binning entry points: the lists of the tiles holding at most list_max
+// pairs are written (all of them for list_max = 0xffffffff).
+int bin_sort_impl(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects, int32_t tiles_x,
+                  int32_t tiles_y, void *workspace, size_t workspace_bytes, int64_t pair_capacity,
+                  uint32_t list_max, uint32_t *vals, uint64_t *keys, uint32_t *ranges, int64_t *n_pairs,
+                  int64_t *n_pairs_host, qn_stream_t stream) {
     QN_REQUIRE(n >= 0, "n must be >= 0");
     QN_REQUIRE(tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
                "tile grid %dx%d out of range", tiles_x, tiles_y);
@@ -844,12 +891,15 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     QN_REQUIRE(pair_capacity >= 0, "pair_capacity must be >= 0");
     QN_REQUIRE(ranges && n_pairs, "ranges and n_pairs are required");
     QN_REQUIRE(n == 0 || (depth && rects && workspace), "null pointer argument");
-    QN_REQUIRE(vals || !keys, "keys need vals (with vals NULL the lists are not written)");
+    QN_REQUIRE(pair_capacity == 0 || vals, "vals is required when pair_capacity > 0");
     QN_REQUIRE(((uintptr_t)rects & 15) == 0 && ((uintptr_t)workspace & 255) == 0,
                "rects must be 16-byte and workspace 256-byte aligned");
     const int n_tiles = tiles_x * tiles_y;
     const Layout L = layout_of(n, tiles_x, tiles_y);
     QN_REQUIRE(n == 0 || workspace_bytes >= L.total, "workspace too small (%zu < %zu)", workspace_bytes, L.total);
+    QN_REQUIRE(list_max == 0xffffffffu || 32 * 4 * (size_t)occ_words(n) <= PREFIX_MAX_OCC_SMEM,
+               "%d Gaussians are too many for lists formed in the compositing forward (at most %d)", n,
+               (int)(PREFIX_MAX_OCC_SMEM / 128 * 32 * CHUNK));
     const int64_t capacity = std::min<int64_t>(pair_capacity, 0xffffffffll);   // pair positions are 32-bit
     cudaStream_t s = as_stream(stream);
     if (n == 0) {
@@ -891,14 +941,21 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
     uint32_t *masks = reinterpret_cast<uint32_t *>(ws + L.masks);
     k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts, masks,
                                               reinterpret_cast<uint32_t *>(ws + L.big));
-    k_chunk_prefix<<<div_up(n_tiles, 32), 1024, 0, s>>>(n_chunks, n_tiles, counts, tile_total, tile_off, ranges,
-                                                        hdr, (unsigned long long)capacity,
-                                                        reinterpret_cast<long long *>(n_pairs));
-    if (vals) {                                        // else the compositing forward writes what it walks
+    // the occupancy bits only for lists the compositing forward forms
+    uint32_t *occ = list_max != 0xffffffffu ? reinterpret_cast<uint32_t *>(ws + L.occ) : nullptr;
+    const int occ_w = occ_words(n);
+    const size_t occ_smem = occ ? sizeof(uint32_t) * 32 * (size_t)occ_w : 0;
+    if (occ_smem > 48 * 1024 && prefix_attributes() != cudaSuccess) return check_launch("k_chunk_prefix attributes");
+    k_chunk_prefix<<<div_up(n_tiles, 32), 1024, occ_smem, s>>>(n_chunks, n_tiles, counts, tile_total, tile_off,
+                                                               ranges, hdr, (unsigned long long)capacity,
+                                                               reinterpret_cast<long long *>(n_pairs), list_max, occ,
+                                                               occ_w);
+    if (list_max > 0 && vals) {                         // the other lists: the compositing forward
         const int vec = ((uintptr_t)vals & 15) == 0;   // 16-byte stores need a 16-byte aligned vals
         k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,
                                                    tile_off, masks, vals,
-                                                   reinterpret_cast<unsigned long long *>(keys), vec);
+                                                   reinterpret_cast<unsigned long long *>(keys), vec, tile_total,
+                                                   list_max);
     }
     int st = check_launch("qn_bin_sort");
     if (st) return st;
@@ -912,6 +969,24 @@ extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, 
         }
     }
     return QN_OK;
+}
+}  // namespace
+}  // namespace qn
+
+extern "C" int qn_bin_sort(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                           int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,
+                           int64_t pair_capacity, uint32_t *vals, uint64_t *keys, uint32_t *ranges,
+                           int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream) {
+    return qn::bin_sort_impl(n, depth, depth_stride, rects, tiles_x, tiles_y, workspace, workspace_bytes,
+                             pair_capacity, 0xffffffffu, vals, keys, ranges, n_pairs, n_pairs_host, stream);
+}
+
+extern "C" int qn_bin_sort_partial(int32_t n, const float *depth, int32_t depth_stride, const int32_t *rects,
+                                   int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes,
+                                   int64_t pair_capacity, uint32_t list_max, uint32_t *vals, uint32_t *ranges,
+                                   int64_t *n_pairs, int64_t *n_pairs_host, qn_stream_t stream) {
+    return qn::bin_sort_impl(n, depth, depth_stride, rects, tiles_x, tiles_y, workspace, workspace_bytes,
+                             pair_capacity, list_max, vals, nullptr, ranges, n_pairs, n_pairs_host, stream);
 }
 
 namespace {
@@ -1022,7 +1097,6 @@ extern "C" int qn_bin_sort_noalloc(int32_t n, const float *depth, int32_t depth_
                                    uint64_t *keys, uint32_t *ranges, int64_t *n_pairs, int64_t *n_pairs_host,
                                    qn_stream_t stream) {
     QN_REQUIRE(n >= 0 && tiles_x > 0 && tiles_y > 0, "bad n or tile grid");
-    QN_REQUIRE(pair_capacity == 0 || vals, "vals is required when pair_capacity > 0 (the workspace is private)");
     const size_t need = qn_bin_sort_workspace_size(n, tiles_x, tiles_y);
     if (need > (size_t)QN_BIN_SORT_STATIC_BYTES) {
         qn::set_error("qn_bin_sort_noalloc: %d Gaussians on a %dx%d tile grid need %zu bytes of workspace, "

@@ -1,5 +1,5 @@
-// What the compositing forward reads of the binning workspace when the tile
-// lists were left unwritten (qn_bin_sort with vals = NULL): the depth-sorted
+// What the compositing forward reads of the binning workspace when only the
+// short tile lists were written (qn_bin_sort_partial): the depth-sorted
 // visible Gaussians cut into chunks of BIN_CHUNK, and per chunk a column word
 // and a row word per tile column / row and per 32 members (bit j of word w:
 // member 32 w + j's rect covers that column / row).  Tile t = (tx, ty) holds
@@ -20,6 +20,9 @@ struct BinView {
     const uint32_t *masks;   // per chunk: column words [tiles_x][BIN_CHUNK_WARPS], then row words [tiles_y][...]
     const uint32_t *sorted;  // depth-sorted Gaussian indices (visible ones first)
     const uint32_t *n_vis;   // device: the number of visible Gaussians
+    const uint32_t *list_max;  // device: the lists of at most this many pairs were written
+    const uint32_t *occ;     // [occ_w][tiles]: bit c % 32 of word c / 32 -- chunk c has a member in the tile
+    int occ_w;               // ceil(chunks / 32)
 };
 
 // The view of a workspace of qn_bin_sort for n Gaussians on a tiles_x x

@@ -188,95 +188,113 @@ __device__ __forceinline__ void pixel_coords(int tile, int TX, int &px, int &py0
 }
 
 // ---------------------------------------------------------------- unwritten lists
-// A warp's walk of its tile's list when the binning left the lists unwritten
-// (the layout is described with BinView): a window of 32 chunks, lane l
-// holding the member count of chunk cw + l in the tile (excl: the counts of
-// the window's chunks below it) and that chunk's eight words for the tile in
-// shared memory ([word][lane]).  Position p of the list is member p - wbase
-// of the window: its chunk is found by a binary search over excl, its word by
-// the counts of the words before it, the member by clearing the lower set
-// bits of that word.
+// A warp's walk of its tile's list when the binning did not write it (the
+// layout is described with BinView).  The warp lists the tile's members up to
+// 32 chunks at a time into a ring of depth-sorted indices in shared memory,
+// in list order, and a batch reads its 32 positions from the ring.  The
+// chunks come from the tile's occupancy bits (the chunks holding a member of
+// the tile, 32 bits a lane, 1024 chunks a warp-wide block), so a sparse tile
+// skips its empty chunks: lane l takes the l-th occupied chunk from the
+// cursor on, loads that chunk's eight words for the tile, and a scan of their
+// member counts places each chunk's members.  Chunks are taken while the ring
+// has room (a chunk holds at most 256 members of a tile, and fewer than 32
+// listed members are unread when more are listed, so the first always fits).
+constexpr int WALK_RING = 512;                          // per warp, a power of two >= 256 + 32
+
 struct ListWalk {
-    int cw;                  // the window's first chunk
-    uint32_t wbase, wtot;    // members before the window, in it
-    uint32_t excl;           // lane l: members of chunks cw .. cw + l - 1 in the tile
+    int cur;                 // the next chunk to consider
+    int ob;                  // the occupancy block held (words 32 ob .. 32 ob + 31)
+    uint32_t ow;             // lane l: occupancy word 32 ob + l
+    uint32_t listed;         // members listed so far (list positions 0 .. listed - 1)
 };
 
-__device__ __forceinline__ void walk_load(ListWalk &lw, uint32_t (*wm)[32], const uint32_t *__restrict__ masks,
-                                          int TX, int TY, int tx, int ty, int nchunks, int lane) {
+// Position of the r-th (from 0) set bit of m (r < popc(m)).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc(m & ((1u << s) - 1u));
+        if (r >= c) {
+            r -= c;
+            m >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+__device__ __forceinline__ void walk_window(ListWalk &lw, uint32_t *ring, uint32_t consumed, const BinView &bins,
+                                            int TX, int TY, int tx, int ty, int nchunks, int lane) {
     static_assert(BIN_CHUNK_WARPS == 8, "a tile's words of one chunk are two uint4");
-    const int c = lw.cw + lane;
+    static_assert((WALK_RING & (WALK_RING - 1)) == 0 && WALK_RING >= BIN_CHUNK + 32, "ring size");
+    const size_t n_tiles = (size_t)TX * TY, t = (size_t)ty * TX + tx;
+    // the occupied chunks from the cursor on, within the block held; an
+    // exhausted block gives way to the next
+    uint32_t m, mexcl, mtot;
+    for (;;) {
+        const int wl = 32 * lw.ob + lane, wc = lw.cur >> 5;
+        m = wl < wc ? 0u : (wl == wc ? lw.ow & (~0u << (lw.cur & 31)) : lw.ow);
+        const uint32_t mc = __popc(m);
+        uint32_t incl = mc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += x;
+        }
+        mexcl = incl - mc;
+        mtot = __shfl_sync(FULL, incl, 31);
+        if (mtot > 0) break;
+        lw.ob += 1;
+        lw.cur = 1024 * lw.ob;
+        if (lw.cur >= nchunks) return;                  // no chunk left
+        const int w = 32 * lw.ob + lane;
+        lw.ow = w < bins.occ_w ? bins.occ[(size_t)w * n_tiles + t] : 0u;
+    }
+    // lane l: the l-th occupied chunk (the word by a binary search over the
+    // words' counts, then the bit)
+    int L = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) {
+        const uint32_t e = __shfl_sync(FULL, mexcl, L + st);
+        if (e <= (uint32_t)lane) L += st;
+    }
+    const uint32_t r = (uint32_t)lane - __shfl_sync(FULL, mexcl, L);
+    const uint32_t word = __shfl_sync(FULL, m, L);
+    const bool valid = (uint32_t)lane < mtot;
+    const int c = valid ? 32 * (32 * lw.ob + L) + nth_set_bit(word, (int)r) : 0;
     uint32_t w[BIN_CHUNK_WARPS] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    if (c < nchunks) {
+    if (valid) {
         // 16-byte aligned: the workspace's mask array is, a chunk's words take
         // 32 (TX + TY) bytes and a column's / row's 32
-        const uint4 *mx = reinterpret_cast<const uint4 *>(masks + (size_t)c * BIN_CHUNK_WARPS * (TX + TY));
+        const uint4 *mx = reinterpret_cast<const uint4 *>(bins.masks + (size_t)c * BIN_CHUNK_WARPS * (TX + TY));
         const uint4 x0 = mx[2 * tx], x1 = mx[2 * tx + 1], y0 = mx[2 * TX + 2 * ty], y1 = mx[2 * TX + 2 * ty + 1];
         w[0] = x0.x & y0.x; w[1] = x0.y & y0.y; w[2] = x0.z & y0.z; w[3] = x0.w & y0.w;
         w[4] = x1.x & y1.x; w[5] = x1.y & y1.y; w[6] = x1.z & y1.z; w[7] = x1.w & y1.w;
     }
     uint32_t cnt = 0;
 #pragma unroll
-    for (int i = 0; i < BIN_CHUNK_WARPS; ++i) {
-        wm[i][lane] = w[i];
-        cnt += __popc(w[i]);
-    }
+    for (int i = 0; i < BIN_CHUNK_WARPS; ++i) cnt += __popc(w[i]);
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t x = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += x;
     }
-    lw.excl = incl - cnt;
-    lw.wtot = __shfl_sync(FULL, incl, 31);
-    __syncwarp();
-}
-
-// The Gaussian at position p of the tile's list for the lanes with need set
-// (the warp's positions ascend from call to call); returns whether it was
-// found (always, for a list consistent with the masks).
-__device__ __forceinline__ bool walk_member(ListWalk &lw, uint32_t (*wm)[32], uint32_t p, bool need,
-                                            const uint32_t *__restrict__ masks, const uint32_t *__restrict__ sorted,
-                                            int TX, int TY, int tx, int ty, int nchunks, int lane, uint32_t &id) {
-    bool found = false;
-    for (;;) {
-        const bool here = need && p < lw.wbase + lw.wtot;
-        const uint32_t r = here ? p - lw.wbase : 0u;
-        int L = 0;                                      // the last chunk with excl <= r
+    const uint32_t room = (uint32_t)WALK_RING - (lw.listed - consumed);
+    const bool take = valid && incl <= room;            // the chunks that fit: a prefix of the lanes
+    const int ntake = __popc(__ballot_sync(FULL, take));
+    if (take) {
+        uint32_t pos = lw.listed + incl - cnt;
+        const uint32_t g0 = (uint32_t)c * BIN_CHUNK;
 #pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-            const uint32_t e = __shfl_sync(FULL, lw.excl, L + st);
-            if (e <= r) L += st;
+        for (int i = 0; i < BIN_CHUNK_WARPS; ++i) {
+            for (uint32_t b = w[i]; b; b &= b - 1) ring[pos++ & (WALK_RING - 1)] = g0 + 32 * i + (__ffs(b) - 1);
         }
-        uint32_t k = r - __shfl_sync(FULL, lw.excl, L);
-        if (here) {
-            int wsel = 0;
-            uint32_t word = 0;
-            bool got = false;
-#pragma unroll
-            for (int i = 0; i < BIN_CHUNK_WARPS; ++i) {
-                const uint32_t x = wm[i][L];
-                const uint32_t c = __popc(x);
-                if (!got && k < c) {
-                    got = true;
-                    wsel = i;
-                    word = x;
-                } else if (!got) {
-                    k -= c;
-                }
-            }
-            for (uint32_t i = 0; i < k; ++i) word &= word - 1;
-            id = sorted[(size_t)(lw.cw + L) * BIN_CHUNK + wsel * 32 + (__ffs(word) - 1)];
-            found = true;
-            need = false;
-        }
-        if (!__any_sync(FULL, need) || lw.cw + 32 >= nchunks) break;
-        lw.wbase += lw.wtot;                            // the next 32 chunks
-        lw.cw += 32;
-        __syncwarp();                                   // every lane is done with the old words
-        walk_load(lw, wm, masks, TX, TY, tx, ty, nchunks, lane);
     }
-    return found;
+    lw.listed += __shfl_sync(FULL, incl, ntake - 1);
+    const int nfill = (int)min(mtot, 32u);
+    lw.cur = ntake < nfill ? __shfl_sync(FULL, c, ntake) : __shfl_sync(FULL, c, ntake - 1) + 1;
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------- forward
@@ -326,10 +344,10 @@ __device__ __forceinline__ void scalar_exponent(const SRec &r, float fx, float f
 }
 
 // COUNT: write the contributor counts; MARK: set the composited marks.
-// LAZY: the lists were not written; each warp walks its tile's list from the
-// binning's chunk masks (BinView) and writes the positions it walks to
-// vals_out (both warps of a tile write the same values), so that the list's
-// walked prefix is there for the adjoint.
+// LAZY: only the lists of at most list_max pairs were written (to vals); for
+// a longer list each warp walks it from the binning's chunk masks (BinView)
+// and writes the positions it walks to vals_out (both warps of a tile write
+// the same values), so that the list's walked prefix is there for the adjoint.
 template <bool COUNT, bool MARK, int PPT, bool LAZY>
 __global__ void __launch_bounds__(Band<PPT>::THREADS, LAZY ? QN_FWD_LAZY_BLOCKS : 0) k_render_fwd(int W, int H, int TX, int TY,
                                                                   const uint32_t *__restrict__ ranges,
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS, LAZY ? QN_FWD_LAZY_BLOCKS 
     constexpr int WARPS = Band<PPT>::WARPS;
     __shared__ SRec sbuf[WARPS][FWD_BATCH];
     __shared__ uint32_t wmax[WARPS];
-    __shared__ uint32_t wmask[LAZY ? WARPS : 1][LAZY ? BIN_CHUNK_WARPS : 1][32];
+    __shared__ uint32_t ring[LAZY ? WARPS : 1][LAZY ? WALK_RING : 1];
     SRec *s = sbuf[threadIdx.x >> 5];
     const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
     const int lane = threadIdx.x & 31;
@@ -369,8 +387,11 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS, LAZY ? QN_FWD_LAZY_BLOCKS 
     const float bx0 = (float)((tile % TX) * QN_TILE) + 0.5f, bx1 = fminf(bx0 + (float)(QN_TILE - 1), W - 0.5f);
     const float by0 = (float)((tile / TX) * QN_TILE + (threadIdx.x >> 5) * (2 * PPT)) + 0.5f;
     const float by1 = fminf(by0 + (float)(2 * PPT - 1), H - 0.5f);
-    ListWalk lw{-32, 0u, 0u, 0u};
-    const int nchunks = LAZY ? (int)((__ldg(bins.n_vis) + BIN_CHUNK - 1) / BIN_CHUNK) : 0;
+    // LAZY: a list longer than list_max was not written and is walked here
+    const bool walk = LAZY && (uint32_t)n > __ldg(bins.list_max);
+    const int nchunks = walk ? (int)((__ldg(bins.n_vis) + BIN_CHUNK - 1) / BIN_CHUNK) : 0;
+    ListWalk lw{0, 0, 0u, 0u};
+    if (walk && lane < bins.occ_w) lw.ow = bins.occ[(size_t)lane * TX * TY + tile];
     for (int b0 = 0; b0 < n; b0 += FWD_BATCH) {
         bool live = false;                              // the warp stops between batches
 #pragma unroll
@@ -379,10 +400,16 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS, LAZY ? QN_FWD_LAZY_BLOCKS 
         uint32_t my_id = 0;
         bool reach = false;
         bool have = b0 + lane < n;
-        if constexpr (LAZY) {
-            have = walk_member(lw, wmask[threadIdx.x >> 5], (uint32_t)(b0 + lane), have, bins.masks,
-                               bins.sorted, TX, TY, tile % TX, tile / TX, nchunks, lane, my_id);
-            if (have) vals_out[beg + b0 + lane] = my_id;
+        if (LAZY && walk) {
+            uint32_t *rg = ring[threadIdx.x >> 5];
+            const uint32_t need = (uint32_t)min(n, b0 + FWD_BATCH);
+            while (lw.listed < need && lw.cur < nchunks)
+                walk_window(lw, rg, (uint32_t)b0, bins, TX, TY, tile % TX, tile / TX, nchunks, lane);
+            have = have && (uint32_t)(b0 + lane) < lw.listed;   // (always, for a list consistent with the masks)
+            if (have) {
+                my_id = bins.sorted[rg[(b0 + lane) & (WALK_RING - 1)]];
+                vals_out[beg + b0 + lane] = my_id;
+            }
         } else if (have) {
             my_id = vals[beg + b0 + lane];
         }
@@ -814,7 +841,8 @@ extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, 
     int st = qn::check_render_args(cam_host, ranges, vals, splats);
     if (st) return st;
     QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
-    return qn::launch_render_fwd<false>(cam_host, ranges, vals, qn::BinView{nullptr, nullptr, nullptr}, nullptr,
+    return qn::launch_render_fwd<false>(cam_host, ranges, vals,
+                                        qn::BinView{nullptr, nullptr, nullptr, nullptr, nullptr, 0}, nullptr,
                                         splats, bg_host, img, T_final, last, n_contrib, composited, tile_order,
                                         tile_cost, stream);
 }
@@ -831,7 +859,7 @@ extern "C" int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, const 
     qn::BinView bins;
     st = qn::bin_view(n, TX, TY, workspace, workspace_bytes, bins);
     if (st) return st;
-    return qn::launch_render_fwd<true>(cam_host, ranges, nullptr, bins, vals, splats, bg_host, img, T_final, last,
+    return qn::launch_render_fwd<true>(cam_host, ranges, vals, bins, vals, splats, bg_host, img, T_final, last,
                                        n_contrib, composited, tile_order, tile_cost, stream);
 }
 

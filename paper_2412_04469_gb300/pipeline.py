@@ -69,11 +69,14 @@ class HParams:
     # 0.129 ms against 0.105 ms for the two kernels (its ~800 bytes of shared
     # memory per Gaussian leave ~8 warps per SM for a long serial chain)
     fused_bwd: bool = False
-    # the binning leaves the per-tile lists unwritten and the compositing
-    # forward forms each tile's list from the binning's chunk masks as it
-    # goes, writing only the prefix it walks (~5% of the pairs); the same
-    # result
+    # the binning writes only the tile lists of at most list_max pairs; the
+    # compositing forward forms each longer list from the binning's chunk
+    # masks as it goes, writing only the prefix it walks (~1 M of the 21.8 M
+    # pairs of a 300k-Gaussian view); the same result.  Writing the short
+    # lists in the binning measured slower (list_max 1024 / 2048 / 4096:
+    # 0.949 / 0.957 / 0.966 ms a step against 0.929 for none)
     lazy_lists: bool = True
+    list_max: int = 0
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-15
@@ -303,15 +306,19 @@ class Rasterizer:
         B.qn_project(self.n, self.S, self.sh_degree, attrs, cam, blur, self.splats, self.rects, self.tight_rects,
                      stream)
 
-    def bin_sort(self, sync=False, stream=None, rects=None, lazy=False):
-        """With lazy, the per-tile lists are not written: the next render_fwd
-        forms them from the binning workspace and writes the part it walks
-        (all the adjoint reads); the keys are then not written either."""
+    def bin_sort(self, sync=False, stream=None, rects=None, lazy=False, list_max=0):
+        """With lazy, only the tile lists of at most list_max pairs are
+        written: the next render_fwd forms the others from the binning
+        workspace and writes the part of each it walks (all the adjoint
+        reads); the keys are then not written either."""
         depth_ptr = self.splats.data_ptr() + 3 * 4
+        rc = self.rects if rects is None else rects
         self.lazy = bool(lazy)
-        return B.qn_bin_sort(self.n, depth_ptr, 12, self.rects if rects is None else rects, self.TX, self.TY,
-                             self.workspace, self.capacity, None if lazy else self.vals,
-                             None if lazy else self.keys, self.ranges, self.n_pairs, sync, stream)
+        if lazy:
+            return B.qn_bin_sort_partial(self.n, depth_ptr, 12, rc, self.TX, self.TY, self.workspace, self.capacity,
+                                         list_max, self.vals, self.ranges, self.n_pairs, sync, stream)
+        return B.qn_bin_sort(self.n, depth_ptr, 12, rc, self.TX, self.TY, self.workspace, self.capacity,
+                             self.vals, self.keys, self.ranges, self.n_pairs, sync, stream)
 
     def render_fwd(self, cam, bg, n_contrib=None, stream=None, ranges=None, mark=False, order=False):
         """Compositing; with mark, `composited` holds afterwards the Gaussians
@@ -472,7 +479,7 @@ def training_iteration(frame: QueenFrame, rast: Rasterizer, cam, target, skip=No
     else:
         frame.decode(stream, skip, train=True)
         rast.project(frame.attrs, cam, hp.blur, stream)
-    rast.bin_sort(False, stream, lazy=hp.lazy_lists)
+    rast.bin_sort(False, stream, lazy=hp.lazy_lists, list_max=hp.list_max)
     ranges = None
     if mask is not None:
         rast.mask_ranges(mask, stream)

@@ -82,12 +82,12 @@ def test_invalid_arguments_fail_before_any_launch(lib):
     assert B.lib().qn_bin_sort(4, 16, 1, 32, 4, 4, 256, 16, 1 << 40, 64, None, 128, 256, None, None) == \
         B.QN_ERR_INVALID_ARG                                                          # workspace too small
     assert b"workspace too small" in B.lib().qn_last_error()
-    assert B.lib().qn_bin_sort(4, 16, 1, 32, 4, 4, 256, 1 << 20, 64, None, 512, 128, 256, None, None) == \
-        B.QN_ERR_INVALID_ARG                                                          # keys without vals
-    assert b"keys need vals" in B.lib().qn_last_error()
-    assert B.lib().qn_bin_sort_noalloc(4, 16, 1, 32, 4, 4, 64, None, None, 128, 256, None, None) == \
-        B.QN_ERR_INVALID_ARG                                                          # private workspace
+    assert B.lib().qn_bin_sort_partial(4, 16, 1, 32, 4, 4, 256, 1 << 20, 64, 2048, None, 128, 256, None, None) == \
+        B.QN_ERR_INVALID_ARG                                                          # vals is the output
     assert b"vals is required" in B.lib().qn_last_error()
+    assert B.lib().qn_bin_sort_partial(4, 16, 1, 32, 4, 4, 256, 16, 64, 0, 64, 128, 256, None, None) == \
+        B.QN_ERR_INVALID_ARG                                                          # workspace too small
+    assert b"workspace too small" in B.lib().qn_last_error()
     for ws, nb, what in ((None, 0, b"workspace is required"), (264, 1 << 20, b"256-byte aligned"),
                          (256, 16, b"too small")):
         assert B.lib().qn_render_fwd_binned(C.byref(cam), 4, ws, nb, 16, 16, 32, bg, 64, 128, 256, None, None,

@@ -1,11 +1,12 @@
-"""Tile lists formed inside the compositing forward (qn_bin_sort with
-vals = NULL, then qn_render_fwd_binned) against the written lists
-(qn_bin_sort, qn_render_fwd): every output of the forward bit for bit, every
-position the forward writes equal to the written list's, every position below
-a tile's largest `last` written, and the adjoint bit for bit -- on scenes of
-one chunk to ~80 chunks (several 32-chunk windows per tile), with contributor
-counts, composited marks and tile orders, on masked ranges and on an
-overflowing pair buffer."""
+"""Tile lists formed inside the compositing forward (qn_bin_sort_partial,
+which writes only the lists of at most list_max pairs, then
+qn_render_fwd_binned) against fully written lists (qn_bin_sort,
+qn_render_fwd): every output of the forward bit for bit, every written
+position equal to the full list's, the short lists written whole, every
+position below a tile's largest `last` written, and the adjoint bit for bit --
+on scenes of one chunk to ~80 chunks (several 32-chunk windows per tile), for
+list_max from none to all, with contributor counts, composited marks and tile
+orders, on masked ranges and on an overflowing pair buffer."""
 import numpy as np
 import pytest
 import torch
@@ -53,11 +54,14 @@ def _raster(n, W, H, deg, seed, capacity=None):
 FWD_OUT = ("img", "T_final", "last", "composited", "tile_cost")
 
 
-def _forward(r, c, bg, lazy, count, mark, order, ranges=None):
-    r.vals.fill_(-1)                                             # what the forward leaves unwritten stays -1
+ALL = 0xffffffff
+
+
+def _forward(r, c, bg, lazy, count, mark, order, ranges=None, list_max=0):
+    r.vals.fill_(-1)                                             # what nothing writes stays -1
     r.tile_order.copy_(torch.arange(r.TX * r.TY, device="cuda", dtype=torch.int32).flip(0))
     r.tile_cost.zero_()
-    r.bin_sort(sync=True, lazy=lazy)
+    r.bin_sort(sync=True, lazy=lazy, list_max=list_max)
     ncon = torch.zeros((r.H, r.W), device="cuda", dtype=torch.int32) if count else None
     r.render_fwd(c, bg, n_contrib=ncon, ranges=ranges, mark=mark, order=order)
     torch.cuda.synchronize()
@@ -81,13 +85,15 @@ SCENES = [  # n, W, H, sh degree, seed
 
 
 @pytest.mark.parametrize("n,W,H,deg,seed", SCENES)
-@pytest.mark.parametrize("count,mark,order", [(False, False, False), (True, True, True), (False, True, False)])
-def test_lazy_forward_equals_written_lists(n, W, H, deg, seed, count, mark, order):
+@pytest.mark.parametrize("count,mark,order,list_max", [(False, False, False, 0), (True, True, True, 0),
+                                                       (False, True, False, 300), (True, False, True, 2048),
+                                                       (False, False, True, ALL)])
+def test_lazy_forward_equals_written_lists(n, W, H, deg, seed, count, mark, order, list_max):
     r, c, P = _raster(n, W, H, deg, seed)
     bg = (0.3, 0.2, 0.1)
     full = _forward(r, c, bg, False, count, mark, order)
     vm = _tile_max_last(r)
-    lazy = _forward(r, c, bg, True, count, mark, order)
+    lazy = _forward(r, c, bg, True, count, mark, order, list_max=list_max)
     for k in FWD_OUT:
         assert torch.equal(lazy[k], full[k]), k
     if count:
@@ -96,11 +102,13 @@ def test_lazy_forward_equals_written_lists(n, W, H, deg, seed, count, mark, orde
     vf, vl = full["vals"].cpu().numpy()[:P], lazy["vals"].cpu().numpy()[:P]
     written = vl != -1
     assert np.array_equal(vl[written], vf[written])              # what is written is the list
-    beg = r.ranges.cpu().numpy()[:, 0].astype(np.int64)
+    rg = r.ranges.cpu().numpy().astype(np.int64)
     need = np.zeros(P, bool)
     for t in np.nonzero(vm)[0]:
-        need[beg[t]:beg[t] + vm[t]] = True
-    assert written[need].all()                                   # all the adjoint reads
+        need[rg[t, 0]:rg[t, 0] + vm[t]] = True                  # all the adjoint reads
+    for t in np.nonzero(rg[:, 1] - rg[:, 0] <= list_max)[0]:
+        need[rg[t, 0]:rg[t, 1]] = True                          # the short lists, whole
+    assert written[need].all()
 
 
 @pytest.mark.parametrize("n,W,H,deg,seed", SCENES[1:])
@@ -109,14 +117,14 @@ def test_lazy_adjoint_equals_written_lists(n, W, H, deg, seed):
     bg = (0.3, 0.2, 0.1)
     d_img = up(S.make_image(W, H, seed) - 0.5)
     out = []
-    for lazy in (False, True):
-        _forward(r, c, bg, lazy, False, True, True)
+    for lazy, lm in ((False, 0), (True, 0), (True, 300)):
+        _forward(r, c, bg, lazy, False, True, True, list_max=lm)
         r.d_img.copy_(d_img)
         r.d_splats.zero_()
         r.render_bwd(c, bg, marks=True, order=True)
         torch.cuda.synchronize()
         out.append(r.d_splats.clone())
-    assert torch.equal(out[0], out[1])
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
 
 
 def test_lazy_forward_on_masked_ranges():
@@ -127,7 +135,7 @@ def test_lazy_forward_on_masked_ranges():
     outs = []
     for lazy in (False, True):
         r.vals.fill_(-1)
-        r.bin_sort(sync=True, lazy=lazy)
+        r.bin_sort(sync=True, lazy=lazy, list_max=0)
         B().qn_mask_ranges(r.TX * r.TY, r.ranges, tiles, r.ranges_masked)
         r.render_fwd(c, (0.0, 0.0, 0.0), ranges=r.ranges_masked)
         torch.cuda.synchronize()
@@ -145,7 +153,7 @@ def test_lazy_forward_with_an_overflowing_pair_buffer():
     r, c, P = _raster(3000, 160, 120, 0, 4, capacity=100)
     assert P > 100
     r.vals.fill_(-1)
-    r.bin_sort(sync=False, lazy=True)
+    r.bin_sort(sync=False, lazy=True, list_max=2048)
     r.render_fwd(c, (0.25, 0.5, 0.75))
     torch.cuda.synchronize()
     assert (r.vals == -1).all()                                   # nothing walked, nothing written
