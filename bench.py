@@ -42,21 +42,22 @@ REF_WHOLE_BUDGET_S = 300.0
 KERNELS_PER_STAGE = {"decode_project": 1, "bin_sort": 14, "render_fwd": 2, "loss": 4, "render_bwd": 1,
                      "gather": 1, "project_bwd": 1, "decode_bwd": 2, "adam": 2}
 STAGES = list(KERNELS_PER_STAGE)
-# DRAM bytes per launch of a kernel on the full workload, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum); valid while the sources it
-# was built from are unchanged (their SHA-256 is checked), else reported null
+# DRAM bytes per launch of a kernel on one workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); valid for that workload while
+# the sources it was built from are unchanged (their SHA-256 is checked), else
+# reported null
 NCU_TRAFFIC = {
-    "render_bwd": {"bytes": 38.052352e6 + 12.559360e6,
+    "render_bwd": {"workload": "full", "bytes": 38.052352e6 + 12.559360e6,
                    "sources": ("paper_2412_04469_gb300/csrc/render.cu", "paper_2412_04469_gb300/csrc/common.cuh",
                                "paper_2412_04469_gb300/csrc/bins.cuh"),
                    "sha256": "466a4c8b1932027072a964e460c70082295ee3203231071e318a9f67ab647cac"},
 }
 
 
-def ncu_traffic(stage):
+def ncu_traffic(stage, workload):
     import hashlib
     rec = NCU_TRAFFIC.get(stage)
-    if rec is None:
+    if rec is None or rec["workload"] != workload:
         return None
     h = hashlib.sha256()
     for f in rec["sources"]:
@@ -373,7 +374,7 @@ def run_gpu(args):
     achieved = algo_bytes[dom] / (avg[dom] * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-            "traffic": ncu_traffic(dom), "algorithmic_bytes": algo_bytes[dom]}
+            "traffic": ncu_traffic(dom, args.workload), "algorithmic_bytes": algo_bytes[dom]}
     # FP32 arithmetic of the compositing adjoint as the method defines it:
     # 12 flop per alpha evaluation (every pixel up to its last contributor),
     # 41 more per contributing evaluation, and a 45-flop reduction of the
@@ -398,7 +399,7 @@ def run_gpu(args):
         roof_alu = dict(roof)
         roof = {"bound": "alu", "kernel": dom, "achieved": alu["achieved"], "peak": alu["peak"],
                 "unit": "TFLOP/s", "frac": alu["frac"], "peak_source": f"{n_sm} SM x 128 FP32 lanes x 2 x median SM clock",
-                "traffic": ncu_traffic(dom), "algorithmic_bytes": algo_bytes[dom],
+                "traffic": ncu_traffic(dom, args.workload), "algorithmic_bytes": algo_bytes[dom],
                 "hbm": {k: roof_alu[k] for k in ("achieved", "peak", "unit", "frac")}, "sfu": sfu}
     else:
         roof["alu_render_bwd"] = alu

@@ -73,3 +73,11 @@ def test_reference_arm_times_fewer_whole_iterations_when_the_budget_is_short():
     assert line["steps_requested"] == 500 and line["warmup_requested"] == 20 and "note" in line
     assert line["steps"] * line["ms_per_step"] * 1e-3 <= wall
     assert line["value"] == pytest.approx(1e3 / line["ms_per_step"], rel=1e-3)
+
+
+def test_measured_traffic_is_reported_only_for_its_workload_and_sources():
+    import bench
+    rec = bench.NCU_TRAFFIC["render_bwd"]
+    assert bench.ncu_traffic("render_bwd", rec["workload"]) == rec["bytes"]
+    assert bench.ncu_traffic("render_bwd", "large") is None
+    assert bench.ncu_traffic("gather", rec["workload"]) is None
