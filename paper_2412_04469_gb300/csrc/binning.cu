@@ -43,7 +43,14 @@ struct Header {
     uint32_t n_big;                                     // entries of the large-rect list
     uint32_t prefix_done;                               // blocks of k_chunk_prefix finished
     uint32_t list_max;                                  // lists of at most this many pairs are written
+    uint32_t key_or, key_nor;                           // OR of the sort keys, OR of their complements
 };
+
+// Whether every sort key has the same 8-bit digit at `shift` (a stable pass on
+// it is then the identity): no bit of the digit is 1 in one key and 0 in another.
+__device__ __forceinline__ bool digit_constant(const Header *hdr, int shift) {
+    return (((hdr->key_or & hdr->key_nor) >> shift) & (RADIX - 1)) == 0;
+}
 
 struct Layout {
     size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, visited, hit, occ,
@@ -98,7 +105,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_bin_prep(int n, const float *_
     h[threadIdx.x] = 0;
     __syncthreads();
     const int base = blockIdx.x * SORT_TILE;
-    uint32_t nvis = 0;
+    uint32_t nvis = 0, kor = 0, knor = 0;
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         const int i = base + r * SORT_THREADS + threadIdx.x;
@@ -109,11 +116,19 @@ __global__ void __launch_bounds__(SORT_THREADS) k_bin_prep(int n, const float *_
             keys[i] = key;
             vals[i] = (uint32_t)i;
             nvis += vis ? 1u : 0u;
+            kor |= key;
+            knor |= ~key;
             atomicAdd(&h[key & (RADIX - 1)], 1u);
         }
     }
     nvis = __reduce_add_sync(FULL, nvis);
-    if ((threadIdx.x & 31) == 0 && nvis) atomicAdd(&hdr->n_vis, nvis);
+    kor = __reduce_or_sync(FULL, kor);
+    knor = __reduce_or_sync(FULL, knor);
+    if ((threadIdx.x & 31) == 0) {
+        if (nvis) atomicAdd(&hdr->n_vis, nvis);
+        atomicOr(&hdr->key_or, kor);
+        atomicOr(&hdr->key_nor, knor);
+    }
     __syncthreads();
     const uint32_t c = h[threadIdx.x];
     hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = c;
@@ -123,7 +138,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_bin_prep(int n, const float *_
 // ---------------------------------------------------------------- step 1: radix sort of depth keys
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, const uint32_t *__restrict__ keys,
                                                              uint32_t *__restrict__ hist,
-                                                             uint32_t *__restrict__ dtot) {
+                                                             uint32_t *__restrict__ dtot, const Header *hdr) {
+    if (digit_constant(hdr, shift)) return;             // the pass is a copy
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -144,7 +160,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, c
 // warps).  Warp d starts from the count of all smaller digits (from the digit
 // totals) and walks its digit's blocks 256 at a time.
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int nb,
-                                                     const uint32_t *__restrict__ dtot) {
+                                                     const uint32_t *__restrict__ dtot, const Header *hdr,
+                                                     int shift) {
+    if (digit_constant(hdr, shift)) return;             // the pass is a copy
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * 32 + (threadIdx.x >> 5);
     constexpr int PER = RADIX / 32;
@@ -184,18 +202,18 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist
 }
 
 // Stable scatter: within a block items are ranked in their original order
-// (round by round, warp by warp, lane by lane).
+// (round by round, warp by warp, lane by lane).  A pass whose digit is the
+// same in every key is the identity: the block copies its items.
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift,
                                                                 const uint32_t *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
                                                                 const uint32_t *__restrict__ offs,
                                                                 uint32_t *__restrict__ kout,
-                                                                uint32_t *__restrict__ vout) {
+                                                                uint32_t *__restrict__ vout, const Header *hdr) {
     constexpr int W = SORT_THREADS / 32;
     __shared__ uint32_t base[RADIX];          // running count of each digit in this block
     __shared__ uint32_t wcnt[W][RADIX];
     const int warp = threadIdx.x >> 5;
-    base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
     const int blk = blockIdx.x * SORT_TILE;
     uint32_t keys[SORT_ITEMS], vals[SORT_ITEMS];      // all of the block's loads in flight at once
 #pragma unroll
@@ -204,6 +222,18 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift
         keys[r] = i < n ? kin[i] : 0u;
         vals[r] = i < n ? vin[i] : 0u;
     }
+    if (digit_constant(hdr, shift)) {
+#pragma unroll
+        for (int r = 0; r < SORT_ITEMS; ++r) {
+            const int i = blk + r * SORT_THREADS + threadIdx.x;
+            if (i < n) {
+                kout[i] = keys[r];
+                vout[i] = vals[r];
+            }
+        }
+        return;
+    }
+    base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {
         for (int w = 0; w < W; ++w) wcnt[w][threadIdx.x] = 0;
@@ -932,9 +962,9 @@ int bin_sort_impl(int32_t n, const float *depth, int32_t depth_stride, const int
         uint32_t *ki = (pass & 1) ? k1 : k0, *vi = (pass & 1) ? v1 : v0;
         uint32_t *ko = (pass & 1) ? k0 : k1, *vo = (pass & 1) ? v0 : v1;
         if (pass > 0)                                   // the first pass's histogram came with the keys
-            k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist, dtot + pass * RADIX);
-        k_radix_scan<<<RADIX / 32, 1024, 0, s>>>(hist, nb, dtot + pass * RADIX);
-        k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo);
+            k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist, dtot + pass * RADIX, hdr);
+        k_radix_scan<<<RADIX / 32, 1024, 0, s>>>(hist, nb, dtot + pass * RADIX, hdr, shift);
+        k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo, hdr);
     }
     // after 4 passes the sorted (depth, index) order is back in k0 / v0
     const int n_chunks = div_up(n, CHUNK);

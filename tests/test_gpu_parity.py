@@ -352,6 +352,22 @@ def test_pair_buffer_sizing_and_overflow_report():
     assert not rast.ranges.cpu().numpy().any()          # every range (0, 0): nothing to composite
 
 
+@pytest.mark.parametrize("low_zero", [False, True])
+@pytest.mark.parametrize("empty_frac", [0.0, 0.1])
+def test_bin_sort_with_constant_digits(low_zero, empty_frac):
+    """Depths in [2, 4) share their top byte, and with low_zero their low byte
+    too: a radix pass on a digit every key shares is a copy on the GPU.  With
+    culled Gaussians (empty rects, keys all ones) no digit is shared."""
+    n, tx, ty = 20000, 85, 64
+    depth, rect = S.make_bin_inputs(n, tx, ty, 21, max_extent=9, empty_frac=empty_frac)
+    depth = (2.0 + (depth - 0.2) / 9.8 * 1.999).astype(np.float32)
+    if low_zero:
+        depth = (depth.view(np.uint32) & np.uint32(0xFFFFFF00)).view(np.float32)
+    k_ref, v_ref, r_ref = oracle.bin_sort(depth, rect, tx, ty)
+    P, k, v, r, _ = _gpu_bin(depth, rect, tx, ty)
+    assert np.array_equal(k, k_ref) and np.array_equal(v, v_ref) and np.array_equal(r, r_ref)
+
+
 def test_bin_sort_all_culled_and_tie_heavy():
     depth, rect = S.make_bin_inputs(1000, 8, 8, 12, max_extent=8, tie_frac=0.9, empty_frac=0.0)
     depth[:] = depth[0]                                  # every key's depth bits equal
