@@ -287,6 +287,10 @@ class Rasterizer:
         self.tile_order = torch.arange(self.TX * self.TY, device=dev, dtype=torch.int32)
         self.keep_keys = keep_keys
         self.lazy = False                                          # the last bin_sort left the lists unwritten
+        # tile_order is refreshed on a side stream while the loss runs; the
+        # next reader of tile_order waits for it
+        self._order_stream = None
+        self._order_pending = False
         self.set_capacity(pair_capacity)
         self.img = torch.zeros((3, height, width), device=dev)
         self.T_final = torch.zeros((height, width), device=dev)
@@ -320,11 +324,26 @@ class Rasterizer:
         return B.qn_bin_sort(self.n, depth_ptr, 12, rc, self.TX, self.TY, self.workspace, self.capacity,
                              self.vals, self.keys, self.ranges, self.n_pairs, sync, stream)
 
+    @staticmethod
+    def _torch_stream(stream):
+        if stream is None:
+            return torch.cuda.current_stream()
+        return torch.cuda.ExternalStream(stream) if isinstance(stream, int) else stream
+
+    def _join_order(self, stream):
+        """The stream waits for the last tile_order refresh (on the side stream)."""
+        if self._order_pending:
+            self._torch_stream(stream).wait_event(self._order_done)
+            self._order_pending = False
+
     def render_fwd(self, cam, bg, n_contrib=None, stream=None, ranges=None, mark=False, order=False):
         """Compositing; with mark, `composited` holds afterwards the Gaussians
         some pixel composited; with order, the tiles start heaviest first (by
         the previous ordered forward's costs) and tile_order is refreshed from
-        this forward's costs."""
+        this forward's costs -- on a side stream, forked from `stream` here and
+        joined by the next call that reads tile_order (render_fwd,
+        render_bwd, render_bwd_pairs), so that it overlaps the loss."""
+        self._join_order(stream)
         if mark:
             self.composited.zero_()
         rg = self.ranges if ranges is None else ranges
@@ -340,7 +359,15 @@ class Rasterizer:
                             tile_order=self.tile_order if order else None,
                             tile_cost=self.tile_cost if order else None)
         if order:
-            B.qn_tile_order(self.TX * self.TY, self.tile_cost, self.tile_order, stream)
+            main = self._torch_stream(stream)
+            if self._order_stream is None:
+                self._order_stream = torch.cuda.Stream(device=self.splats.device)
+                self._order_fork, self._order_done = torch.cuda.Event(), torch.cuda.Event()
+            self._order_fork.record(main)
+            self._order_stream.wait_event(self._order_fork)
+            B.qn_tile_order(self.TX * self.TY, self.tile_cost, self.tile_order, self._order_stream)
+            self._order_done.record(self._order_stream)
+            self._order_pending = True
 
     def loss_grad(self, target, w=1.0, mse=False, stream=None):
         B.qn_image_loss(self.img.numel(), self.img, target, w, mse, self.loss, self.d_img, stream)
@@ -365,6 +392,7 @@ class Rasterizer:
         """Compositing adjoint into d_splats; with marks, the adjoint drops the
         Gaussians the last marked forward did not composite; with order, the
         tiles start in tile_order."""
+        self._join_order(stream)
         B.qn_render_bwd(cam, self.n, self.rects, self.ranges if ranges is None else ranges, self.vals, self.splats,
                         bg, self.T_final, self.last, self.d_img, skip, self.composited if marks else None,
                         self.workspace, self.pair_grads, self.d_splats, stream,
@@ -372,6 +400,7 @@ class Rasterizer:
 
     def render_bwd_pairs(self, cam, bg, skip=None, stream=None, ranges=None, marks=False, order=False):
         """First pass of render_bwd (per-pair records)."""
+        self._join_order(stream)
         B.qn_render_bwd_pairs(cam, self.n, self.ranges if ranges is None else ranges, self.vals, self.splats, bg,
                               self.T_final, self.last, self.d_img, skip, self.composited if marks else None,
                               self.workspace, self.pair_grads, stream, tile_order=self.tile_order if order else None)
