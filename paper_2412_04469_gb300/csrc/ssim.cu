@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "packed.cuh"
 
 namespace qn {
 namespace {
@@ -51,7 +52,9 @@ constexpr int SS_ROWS_PER_WARP = (SS_HR + SS_WARPS - 1) / SS_WARPS;             
 constexpr float SS_C1 = 0.01f * 0.01f, SS_C2 = 0.03f * 0.03f;
 constexpr float SS_SHIFT = 0.5f;
 
-// shared memory: np staged planes [HR][HW] then nq row sums [HR][TW]
+// shared memory: np staged planes [HR][HW] then nq row sums [HR][TW]; the
+// first two staged planes are interleaved into one plane of pairs, and so are
+// the row sums two by two, so that the passes run on packed f32x2 arithmetic
 constexpr size_t ss_smem(int np, int nq) {
     return sizeof(float) * ((size_t)np * SS_HR * SS_HW + (size_t)nq * SS_HR * SS_TW);
 }
@@ -62,12 +65,15 @@ struct Window {
     float cum[SS_K + 1];    // cum[j] = g[0] + ... + g[j-1] (the window is symmetric)
 };
 
-// s[p][r][c] = planes[p][y0 - R + r][x0 - R + c] - shift, zero outside the
-// image: warp w stages rows w, w + 8, ...; lane l columns l and 32 + l (< 42).
-// All loads of a thread are issued before its first store.
+// Plane p of the block plus its halo, shifted: planes[p][y0 - R + r][x0 - R + c]
+// - shift (zero outside the image) at row r, column c -- planes 0 and 1
+// interleaved as pairs in s2 [HR][HW], a third plane in s1 [HR][HW].  Warp w
+// stages rows w, w + 8, ...; lane l columns l and 32 + l (< 42).  All loads
+// of a thread are issued before its first store.
 template <int NP>
 __device__ __forceinline__ void stage_rows(const float *const (&planes)[NP], int W, int H, int x0, int y0,
-                                           float shift, float *s) {
+                                           float shift, f2 *s2, float *s1) {
+    static_assert(NP == 2 || NP == 3, "two planes paired, and a third");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int xa = x0 - SS_R + lane, xb = xa + 32;
     const bool ina = xa >= 0 && xa < W, inb = lane < 2 * SS_R && xb < W;
@@ -87,11 +93,13 @@ __device__ __forceinline__ void stage_rows(const float *const (&planes)[NP], int
     for (int k = 0; k < SS_ROWS_PER_WARP; ++k) {
         const int r = warp + k * SS_WARPS;
         if (r >= SS_HR) break;
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            float *row = s + ((size_t)p * SS_HR + r) * SS_HW;
-            row[lane] = a[p][k];
-            if (lane < 2 * SS_R) row[32 + lane] = b[p][k];
+        f2 *row2 = s2 + (size_t)r * SS_HW;
+        row2[lane] = pk(a[0][k], a[1][k]);
+        if (lane < 2 * SS_R) row2[32 + lane] = pk(b[0][k], b[1][k]);
+        if (NP == 3) {
+            float *row1 = s1 + (size_t)r * SS_HW;
+            row1[lane] = a[NP - 1][k];
+            if (lane < 2 * SS_R) row1[32 + lane] = b[NP - 1][k];
         }
     }
 }
@@ -115,25 +123,33 @@ __device__ __forceinline__ int mask_count(const int *n_masked, int W, int H) {
 
 // The vertical pass of warp w: staged row-sum rows 8w .. 8w + 17, each read
 // once and added into the accumulators of the output rows o (0..7) whose
-// window covers it (tap t - o).
-template <int NQ>
-__device__ __forceinline__ void column_pass(const Window &win, const float *hs, float (&acc)[SS_RPW][NQ]) {
+// window covers it (tap t - o): NP planes of pairs hp [NP][HR][TW] and one
+// plane h1 [HR][TW].
+template <int NP>
+__device__ __forceinline__ void column_pass(const Window &win, const f2 *hp, const float *h1,
+                                            f2 (&accp)[SS_RPW][NP], float (&acc1)[SS_RPW]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 0; o < SS_RPW; ++o)
+    for (int o = 0; o < SS_RPW; ++o) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[o][q] = 0.f;
+        for (int q = 0; q < NP; ++q) accp[o][q] = pk(0.f, 0.f);
+        acc1[o] = 0.f;
+    }
 #pragma unroll
     for (int t = 0; t < SS_RPW + 2 * SS_R; ++t) {
-        float h[NQ];
+        const size_t at = (size_t)(SS_RPW * warp + t) * SS_TW + lane;
+        f2 h[NP];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) h[q] = hs[((size_t)q * SS_HR + SS_RPW * warp + t) * SS_TW + lane];
+        for (int q = 0; q < NP; ++q) h[q] = hp[(size_t)q * SS_HR * SS_TW + at];
+        const float hs = h1[at];
 #pragma unroll
         for (int o = 0; o < SS_RPW; ++o) {
             const int i = t - o;
             if (i >= 0 && i < SS_K) {
+                const f2 g = pk(win.g[i], win.g[i]);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) acc[o][q] = fmaf(win.g[i], h[q], acc[o][q]);
+                for (int q = 0; q < NP; ++q) accp[o][q] = fma2(g, h[q], accp[o][q]);
+                acc1[o] = fmaf(win.g[i], hs, acc1[o]);
             }
         }
     }
@@ -172,42 +188,43 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_fwd(int W, int H, int C, co
                                                         const uint8_t *__restrict__ pmask,
                                                         const int *__restrict__ n_masked, float *__restrict__ maps,
                                                         float *__restrict__ partials) {
-    extern __shared__ float smem[];
-    float *sxy = smem;                                    // [2][HR][HW]
-    float *hs = smem + 2 * SS_HR * SS_HW;                 // [5][HR][TW]
+    extern __shared__ f2 smem2[];
+    f2 *suv = smem2;                                      // [HR][HW] (u, v)
+    f2 *hp = suv + SS_HR * SS_HW;                         // [2][HR][TW] (E u, E v), (E u^2, E v^2)
+    float *h1 = reinterpret_cast<float *>(hp + 2 * SS_HR * SS_TW);   // [HR][TW] E uv
     __shared__ float red[SS_WARPS];
     const int c = blockIdx.z;
     const size_t plane = (size_t)W * H;
     const int x0 = blockIdx.x * SS_TW, y0 = blockIdx.y * SS_TR;
     {
         const float *const planes[2] = {img + c * plane, tgt + c * plane};
-        stage_rows<2>(planes, W, H, x0, y0, SS_SHIFT, sxy);
+        stage_rows<2>(planes, W, H, x0, y0, SS_SHIFT, suv, nullptr);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int r = warp; r < SS_HR; r += SS_WARPS) {
-        const float *u = sxy + r * SS_HW + lane, *v = sxy + (SS_HR + r) * SS_HW + lane;
-        float a = 0.f, b = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+        const f2 *uv = suv + r * SS_HW + lane;
+        f2 ab = pk(0.f, 0.f), sq = pk(0.f, 0.f);
+        float xy = 0.f;
 #pragma unroll
         for (int j = 0; j < SS_K; ++j) {
-            const float uj = u[j], vj = v[j], g = win.g[j];
-            const float gu = g * uj, gv = g * vj;
-            a += gu;
-            b += gv;
-            xx = fmaf(gu, uj, xx);
-            yy = fmaf(gv, vj, yy);
+            const f2 q = uv[j], guv = mul2(pk(win.g[j], win.g[j]), q);   // (g u, g v)
+            ab = add2(ab, guv);
+            sq = fma2(guv, q, sq);
+            float gu, gv, uj, vj;
+            upk(guv, gu, gv);
+            upk(q, uj, vj);
             xy = fmaf(gu, vj, xy);
         }
-        float *h = hs + r * SS_TW + lane;
-        h[0 * SS_HR * SS_TW] = a;
-        h[1 * SS_HR * SS_TW] = b;
-        h[2 * SS_HR * SS_TW] = xx;
-        h[3 * SS_HR * SS_TW] = yy;
-        h[4 * SS_HR * SS_TW] = xy;
+        const size_t at = (size_t)r * SS_TW + lane;
+        hp[at] = ab;
+        hp[SS_HR * SS_TW + at] = sq;
+        h1[at] = xy;
     }
     __syncthreads();
-    float acc[SS_RPW][5];
-    column_pass<5>(win, hs, acc);
+    f2 accp[SS_RPW][2];
+    float acc1[SS_RPW];
+    column_pass<2>(win, hp, h1, accp, acc1);
     const int cnt = mask_count(n_masked, W, H);
     const float scale = cnt > 0 ? -w / ((float)C * (float)cnt) : 0.f;       // dL/dSSIM
     const int x = x0 + lane;
@@ -221,7 +238,11 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_fwd(int W, int H, int C, co
             const size_t p = (size_t)y * W + x;
             SsimOut out = {0.f, 0.f, 0.f, 0.f};
             if (!pmask || pmask[p]) {
-                out = ssim_pixel(acc[o], sx * mass_1d(win, y, H), scale);
+                float m[5];
+                upk(accp[o][0], m[0], m[1]);
+                upk(accp[o][1], m[2], m[3]);
+                m[4] = acc1[o];
+                out = ssim_pixel(m, sx * mass_1d(win, y, H), scale);
                 ssum += out.S;
             }
             maps[(0 * (size_t)C + c) * plane + p] = out.da;
@@ -267,29 +288,34 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_bwd(int W, int H, int C, co
                                                         int blocks, const float *__restrict__ partials,
                                                         const int *__restrict__ n_masked, float w,
                                                         float *__restrict__ loss) {
-    extern __shared__ float smem[];
-    float *sm = smem;                                     // [3][HR][HW]
-    float *hs = smem + 3 * SS_HR * SS_HW;                 // [3][HR][TW]
+    extern __shared__ f2 smem2[];
+    f2 *s01 = smem2;                                      // [HR][HW] maps 0 and 1
+    float *s2 = reinterpret_cast<float *>(s01 + SS_HR * SS_HW);      // [HR][HW] map 2
+    f2 *hp = reinterpret_cast<f2 *>(s2 + SS_HR * SS_HW);             // [HR][TW] row sums of maps 0, 1
+    float *h1 = reinterpret_cast<float *>(hp + SS_HR * SS_TW);       // [HR][TW] row sums of map 2
     const int c = blockIdx.z;
     const size_t plane = (size_t)W * H;
     const int x0 = blockIdx.x * SS_TW, y0 = blockIdx.y * SS_TR;
     {
         const float *const planes[3] = {maps + c * plane, maps + (C + (size_t)c) * plane,
                                         maps + (2 * (size_t)C + c) * plane};
-        stage_rows<3>(planes, W, H, x0, y0, 0.f, sm);
+        stage_rows<3>(planes, W, H, x0, y0, 0.f, s01, s2);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int r = warp; r < SS_HR; r += SS_WARPS) {
-        float s[3] = {0.f, 0.f, 0.f};
+        f2 a01 = pk(0.f, 0.f);
+        float a2 = 0.f;
+        const f2 *row01 = s01 + (size_t)r * SS_HW + lane;
+        const float *row2 = s2 + (size_t)r * SS_HW + lane;
 #pragma unroll
         for (int j = 0; j < SS_K; ++j) {
-            const float g = win.g[j];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) s[q] = fmaf(g, sm[((size_t)q * SS_HR + r) * SS_HW + lane + j], s[q]);
+            a01 = fma2(pk(win.g[j], win.g[j]), row01[j], a01);
+            a2 = fmaf(win.g[j], row2[j], a2);
         }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) hs[((size_t)q * SS_HR + r) * SS_TW + lane] = s[q];
+        const size_t at = (size_t)r * SS_TW + lane;
+        hp[at] = a01;
+        h1[at] = a2;
     }
     __syncthreads();
     // this thread's outputs: x, y and d_img loaded now, used after the column pass
@@ -303,14 +329,17 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_bwd(int W, int H, int C, co
         py[o] = in ? __ldg(tgt + p) : 0.f;
         pd[o] = in ? d_img[p] : 0.f;
     }
-    float f[SS_RPW][3];
-    column_pass<3>(win, hs, f);
+    f2 fp[SS_RPW][1];
+    float f2s[SS_RPW];
+    column_pass<1>(win, hp, h1, fp, f2s);
     if (x < W) {
 #pragma unroll
         for (int o = 0; o < SS_RPW; ++o) {
             if (yb + o >= H) break;
             const size_t p = c * plane + (size_t)(yb + o) * W + x;
-            d_img[p] = pd[o] + f[o][0] + 2.f * (px[o] - SS_SHIFT) * f[o][1] + (py[o] - SS_SHIFT) * f[o][2];
+            float fa, fb;
+            upk(fp[o][0], fa, fb);
+            d_img[p] = pd[o] + fa + 2.f * (px[o] - SS_SHIFT) * fb + (py[o] - SS_SHIFT) * f2s[o];
         }
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) finish_loss(blocks, W, H, C, partials, n_masked, w, loss);
