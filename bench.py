@@ -49,7 +49,7 @@ STAGES = list(KERNELS_PER_STAGE)
 NCU_TRAFFIC = {
     "render_bwd": {"workload": "full", "bytes": 38.052352e6 + 12.559360e6,
                    "sources": ("paper_2412_04469_gb300/csrc/render.cu", "paper_2412_04469_gb300/csrc/common.cuh",
-                               "paper_2412_04469_gb300/csrc/bins.cuh"),
+                               "paper_2412_04469_gb300/csrc/bins.cuh", "paper_2412_04469_gb300/csrc/packed.cuh"),
                    "sha256": "466a4c8b1932027072a964e460c70082295ee3203231071e318a9f67ab647cac"},
 }
 

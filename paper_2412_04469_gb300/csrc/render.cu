@@ -9,6 +9,7 @@
 // duplicated into a pair, so a 128-bit broadcast load yields operand pairs.
 #include "bins.cuh"
 #include "common.cuh"
+#include "packed.cuh"
 
 namespace qn {
 namespace {
@@ -51,38 +52,6 @@ struct Band {
     static constexpr int WARPS = QN_TILE / (2 * PPT);   // warps per tile
     static constexpr int THREADS = 32 * WARPS;
 };
-
-// ---------------------------------------------------------------- packed pairs
-// Two floats in one 64-bit register pair; the .rn forms round each half
-// exactly as the scalar __fadd_rn / __fmul_rn / __fmaf_rn do.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {   // a b + c
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
