@@ -75,9 +75,19 @@ def test_reference_arm_times_fewer_whole_iterations_when_the_budget_is_short():
     assert line["value"] == pytest.approx(1e3 / line["ms_per_step"], rel=1e-3)
 
 
-def test_measured_traffic_is_reported_only_for_its_workload_and_sources():
+def test_measured_traffic_is_reported_only_for_its_workload_and_sources(monkeypatch):
+    import hashlib
+    import os
     import bench
-    rec = bench.NCU_TRAFFIC["render_bwd"]
-    assert bench.ncu_traffic("render_bwd", rec["workload"]) == rec["bytes"]
-    assert bench.ncu_traffic("render_bwd", "large") is None
-    assert bench.ncu_traffic("gather", rec["workload"]) is None
+    srcs = bench.NCU_TRAFFIC["render_bwd"]["sources"]
+    h = hashlib.sha256()
+    for f in srcs:
+        with open(os.path.join(bench.ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    rec = {"workload": "full", "bytes": 123.0, "sources": srcs, "sha256": h.hexdigest()}
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "render_bwd", rec)
+    assert bench.ncu_traffic("render_bwd", "full") == 123.0
+    assert bench.ncu_traffic("render_bwd", "large") is None              # another workload
+    assert bench.ncu_traffic("gather", "full") is None                   # no capture
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "render_bwd", dict(rec, sha256="0" * 64))
+    assert bench.ncu_traffic("render_bwd", "full") is None               # the sources changed since
