@@ -40,11 +40,6 @@ struct CapTag {
 #define QN_BWD_PPT 4
 #endif
 
-// resident blocks per SM the forward that walks unwritten lists is compiled for
-#ifndef QN_FWD_LAZY_BLOCKS
-#define QN_FWD_LAZY_BLOCKS 0
-#endif
-
 template <int PPT>
 struct Band {
     static_assert(PPT % 2 == 0 && QN_TILE % (2 * PPT) == 0, "pixels per lane");
@@ -318,7 +313,7 @@ __device__ __forceinline__ void scalar_exponent(const SRec &r, float fx, float f
 // and writes the positions it walks to vals_out (both warps of a tile write
 // the same values), so that the list's walked prefix is there for the adjoint.
 template <bool COUNT, bool MARK, int PPT, bool LAZY>
-__global__ void __launch_bounds__(Band<PPT>::THREADS, LAZY ? QN_FWD_LAZY_BLOCKS : 0) k_render_fwd(int W, int H, int TX, int TY,
+__global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H, int TX, int TY,
                                                                   const uint32_t *__restrict__ ranges,
                                                                   const uint32_t *__restrict__ vals,
                                                                   BinView bins, uint32_t *__restrict__ vals_out,
