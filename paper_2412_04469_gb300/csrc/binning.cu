@@ -269,9 +269,11 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift
 }
 
 // ---------------------------------------------------------------- step 2: counting pass on the tile digit
+// A chunk's masks in shared memory, tile-major like their workspace slot: a
+// tile column's (row's) CHUNK_WARPS words are 32 contiguous bytes.
 struct ChunkSmem {
-    uint32_t mx[CHUNK_WARPS][QN_MAX_TILES_X];
-    uint32_t my[CHUNK_WARPS][QN_MAX_TILES_Y];
+    __align__(16) uint32_t mx[QN_MAX_TILES_X][CHUNK_WARPS];
+    __align__(16) uint32_t my[QN_MAX_TILES_Y][CHUNK_WARPS];
     int4 rect[CHUNK];
     uint32_t id[CHUNK];
     int ux0, uy0, ux1, uy1;
@@ -318,29 +320,38 @@ __device__ void build_masks(int TX, int TY, ChunkSmem &s) {
     const int4 r = s.rect[j];
     for (int tx = 0; tx < TX; ++tx) {
         const unsigned b = __ballot_sync(FULL, r.x <= tx && tx < r.z);
-        if ((j & 31) == 0) s.mx[warp][tx] = b;
+        if ((j & 31) == 0) s.mx[tx][warp] = b;
     }
     for (int ty = 0; ty < TY; ++ty) {
         const unsigned b = __ballot_sync(FULL, r.y <= ty && ty < r.w);
-        if ((j & 31) == 0) s.my[warp][ty] = b;
+        if ((j & 31) == 0) s.my[ty][warp] = b;
     }
     __syncthreads();
 }
 
-// Copies the chunk's masks between shared memory (warp-major, as the ballots
-// build them) and their tile-major workspace slot (word i = tile i / 8, warp
-// i % 8), coalesced on the global side.
+// Copies the chunk's masks between shared memory and their workspace slot
+// (both tile-major: word i = tile i / 8, warp i % 8).
 __device__ void store_masks(int TX, int TY, const ChunkSmem &s, uint32_t *__restrict__ gm) {
-    for (int i = threadIdx.x; i < CHUNK_WARPS * TX; i += blockDim.x) gm[i] = s.mx[i % CHUNK_WARPS][i / CHUNK_WARPS];
+    const uint32_t *sx = &s.mx[0][0], *sy = &s.my[0][0];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TX; i += blockDim.x) gm[i] = sx[i];
     uint32_t *gy = gm + CHUNK_WARPS * TX;
-    for (int i = threadIdx.x; i < CHUNK_WARPS * TY; i += blockDim.x) gy[i] = s.my[i % CHUNK_WARPS][i / CHUNK_WARPS];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TY; i += blockDim.x) gy[i] = sy[i];
 }
 
 __device__ void fetch_masks(int TX, int TY, const uint32_t *__restrict__ gm, ChunkSmem &s) {
-    for (int i = threadIdx.x; i < CHUNK_WARPS * TX; i += blockDim.x) s.mx[i % CHUNK_WARPS][i / CHUNK_WARPS] = gm[i];
+    uint32_t *sx = &s.mx[0][0], *sy = &s.my[0][0];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TX; i += blockDim.x) sx[i] = gm[i];
     const uint32_t *gy = gm + CHUNK_WARPS * TX;
-    for (int i = threadIdx.x; i < CHUNK_WARPS * TY; i += blockDim.x) s.my[i % CHUNK_WARPS][i / CHUNK_WARPS] = gy[i];
+    for (int i = threadIdx.x; i < CHUNK_WARPS * TY; i += blockDim.x) sy[i] = gy[i];
     __syncthreads();
+}
+
+// The chunk's members in a tile: column words x0, x1 against the row's words.
+__device__ __forceinline__ uint32_t tile_members(uint4 x0, uint4 x1, const ChunkSmem &s, int ty) {
+    const uint4 y0 = *reinterpret_cast<const uint4 *>(&s.my[ty][0]);
+    const uint4 y1 = *reinterpret_cast<const uint4 *>(&s.my[ty][4]);
+    return __popc(x0.x & y0.x) + __popc(x0.y & y0.y) + __popc(x0.z & y0.z) + __popc(x0.w & y0.w) +
+           __popc(x1.x & y1.x) + __popc(x1.y & y1.y) + __popc(x1.z & y1.z) + __popc(x1.w & y1.w);
 }
 
 __device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ sorted,
@@ -349,12 +360,6 @@ __device__ void load_chunk(int c, int TX, int TY, const uint32_t *__restrict__ s
     build_masks(TX, TY, s);
 }
 
-__device__ __forceinline__ uint32_t chunk_count(const ChunkSmem &s, int tx, int ty) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int w = 0; w < CHUNK_WARPS; ++w) c += __popc(s.mx[w][tx] & s.my[w][ty]);
-    return c;
-}
 
 __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const uint32_t *__restrict__ sorted,
                                                         const int4 *__restrict__ rects, Header *hdr,
@@ -384,9 +389,15 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
         at = __shfl_sync(FULL, at, 0);
         if (big) big_list[at + __popc(b & ((1u << lane) - 1u))] = (uint32_t)c * CHUNK + j;
     }
-    for (int t = threadIdx.x; t < n_tiles; t += CHUNK) {
-        const int tx = t % TX, ty = t / TX;
-        row[t] = (tx >= s.ux0 && tx < s.ux1 && ty >= s.uy0 && ty < s.uy1) ? chunk_count(s, tx, ty) : 0u;
+    // thread (column tx, row phase g): its column's words in registers, the
+    // rows g, g + k, ... (k = CHUNK / TX row phases; a row's stores coalesce)
+    const int k = CHUNK / TX, tx = threadIdx.x % TX, g = threadIdx.x / TX;
+    if (g < k) {
+        const uint4 x0 = *reinterpret_cast<const uint4 *>(&s.mx[tx][0]);
+        const uint4 x1 = *reinterpret_cast<const uint4 *>(&s.mx[tx][4]);
+        const bool colin = tx >= s.ux0 && tx < s.ux1;
+        for (int ty = g; ty < TY; ty += k)
+            row[ty * TX + tx] = colin && ty >= s.uy0 && ty < s.uy1 ? tile_members(x0, x1, s, ty) : 0u;
     }
 }
 
@@ -583,7 +594,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_scatter(int TX, int TY, const u
         bool any = false;
 #pragma unroll
         for (int w = 0; w < CHUNK_WARPS; ++w) {
-            m[w] = s.mx[w][tx] & s.my[w][ty];
+            m[w] = s.mx[tx][w] & s.my[ty][w];
             any |= m[w] != 0;
         }
         if (!any) continue;
