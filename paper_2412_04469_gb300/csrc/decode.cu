@@ -559,7 +559,25 @@ __global__ void __launch_bounds__(DP_TILE) k_decode_project(DecodeArgs a, CamArg
 #pragma unroll
                 for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
                     if (k < L) l[k] = latent_int(sL[(a.lat_off[c] + k) * DP_TILE + t]);
-                for (int r = 0; r < a.ac[c]; ++r) {
+                // Eq. 5 and Eq. 4, four residuals at a time: their fmaf chains
+                // (each the same as one residual's alone) interleave, and the
+                // four stores follow them
+                int r = 0;
+                for (; r + 4 <= a.ac[c]; r += 4) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
+                        if (k < L) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[q] = fmaf(D[(r + q) * L + k], l[k], acc[q]);
+                        }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float &x = sA[(a.ab[c] + r + q) * DP_TILE + t];
+                        x = x + acc[q];
+                    }
+                }
+                for (; r < a.ac[c]; ++r) {
                     float acc = 0.f;
 #pragma unroll
                     for (int k = 0; k < (LT > 0 ? LT : QN_MAX_LATENT); ++k)
