@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
         }
     }
     __shared__ bool last;
-    __threadfence();                                    // this block's tile totals before its ticket
+    if (warp == 0) __threadfence();                     // this block's tile totals (warp 0's) before its ticket
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&hdr->prefix_done, 1u) == gridDim.x - 1;
     __syncthreads();

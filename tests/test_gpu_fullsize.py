@@ -235,3 +235,44 @@ def test_full_size_path_on_sampled_outputs(name):
     close(frame.d_dec.cpu().numpy(), want[1], floor_frac=GRAD_FLOOR, what="d_dec")
     close(frame.d_lp[:, :n].cpu().numpy(), want[2], floor_frac=GRAD_FLOOR, what="d_lp")
     close(frame.d_log_alpha[:n].cpu().numpy(), want[3], floor_frac=GRAD_FLOOR, what="d_log_alpha")
+
+
+@pytest.mark.parametrize("name", ["full", "large"])
+def test_full_size_lists_formed_in_the_forward_equal_the_written_lists(name):
+    """At the benchmark's sizes, the training iteration's binning (no pair
+    lists written) and forward (each tile's list formed from the chunk masks)
+    give the written-list forward's image, transmittance and last contributors
+    bit for bit, write every list position the adjoint reads with the written
+    list's value, and so give the same adjoint bit for bit."""
+    bench = _bench()
+    frame, rast, ccams, targets, _, lay, prev, res, cams = bench.setup(name, quick=True)
+    hp = frame.hp
+    c, bg = ccams[0], hp.bg
+    frame.decode()
+    rast.project(frame.attrs, c, hp.blur)
+    out = []
+    for lazy in (False, True):
+        rast.vals.fill_(-1)
+        rast.bin_sort(sync=True, lazy=lazy, list_max=hp.list_max)
+        rast.render_fwd(c, bg, mark=True, order=False)
+        rast.photometric_loss(targets[0], hp.lambda_dssim)
+        rast.d_splats.zero_()
+        rast.render_bwd(c, bg, marks=True)
+        torch.cuda.synchronize()
+        out.append((rast.img.clone(), rast.T_final.clone(), rast.last.clone(), rast.composited.clone(),
+                    rast.vals.clone(), rast.d_splats.clone()))
+    (i0, t0, l0, m0, v0, g0), (i1, t1, l1, m1, v1, g1) = out
+    assert torch.equal(i0, i1) and torch.equal(t0, t1) and torch.equal(l0, l1) and torch.equal(m0, m1)
+    assert torch.equal(g0, g1)
+    TX, TY = rast.TX, rast.TY
+    pad = torch.zeros((TY * 16, TX * 16), dtype=torch.long, device="cuda")
+    pad[:rast.H, :rast.W] = l0.long()
+    vm = pad.view(TY, 16, TX, 16).amax(dim=(1, 3)).reshape(-1).cpu().numpy()
+    beg = rast.ranges[:, 0].cpu().numpy().astype(np.int64)
+    w0, w1 = v0.cpu().numpy(), v1.cpu().numpy()
+    need = np.zeros(w0.size, bool)
+    for t in np.nonzero(vm)[0]:
+        need[beg[t]:beg[t] + vm[t]] = True
+    written = w1 != -1
+    assert written[need].all() and np.array_equal(w1[written], w0[written])
+    print(f"  {name}: {int(written.sum())} of {int(rast.n_pairs.item())} list positions written by the forward")
