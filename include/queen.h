@@ -370,10 +370,13 @@ int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, const uint3
  * output equals qn_render_fwd's on fully written lists, bit for bit.  ranges
  * may be the binning's or qn_mask_ranges' output (its empty tiles walk
  * nothing).  vals [pair_capacity of the binning] u32 (read, written in part).
+ * The call also writes into the workspace, for qn_render_bwd's gather, the
+ * first list position of each chunk of Gaussians it walks in each tile (with
+ * list_max 0 the binning leaves those to it).
  * Errors: those of qn_render_fwd, and QN_ERR_INVALID_ARG for a missing,
  * misaligned or too small workspace.
  */
-int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, const void *workspace, size_t workspace_bytes,
+int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, void *workspace, size_t workspace_bytes,
                          const uint32_t *ranges, uint32_t *vals, const qn_splat *splats, const float *bg_host,
                          float *img, float *T_final, uint32_t *last, uint32_t *n_contrib, uint8_t *composited,
                          const uint32_t *tile_order, uint32_t *tile_cost, qn_stream_t stream);

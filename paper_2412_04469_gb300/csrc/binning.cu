@@ -54,7 +54,7 @@ __device__ __forceinline__ bool digit_constant(const Header *hdr, int shift) {
 
 struct Layout {
     size_t hdr, dtot, keys0, vals0, keys1, vals1, hist, counts, tile_total, tile_off, masks, big, visited, hit, occ,
-        total;
+        wext, total;
 };
 
 // 32-chunk words of the per-tile chunk occupancy (bit c % 32 of word c / 32:
@@ -88,6 +88,9 @@ Layout layout_of(int n, int TX, int TY) {
     L.visited = o; o = align_up(o + 4 * (size_t)n_tiles);       // visited prefix of each tile's list
     L.hit = o; o = align_up(o + (size_t)(n > 0 ? n : 1));        // Gaussians with a contributing record
     L.occ = o; o = align_up(o + 4 * (size_t)occ_words(n) * n_tiles);   // [word][tile]
+    // lists formed in the forward: per tile, the chunks below this one had
+    // their first list position (the counts' prefix) written by the forward
+    L.wext = o; o = align_up(o + 4 * (size_t)n_tiles);
     L.total = o;
     return L;
 }
@@ -460,10 +463,11 @@ __device__ void tile_offsets(int n_tiles, const uint32_t *__restrict__ total, ui
     }
 }
 
-// In place: counts[c][t] <- sum_{c' < c} counts[c'][t]; tile_total[t] = sum_c.
-// Block = 32 tiles (lanes) x 32 chunk segments (warps).  Each warp walks its
-// segment PREFIX_BATCH chunks at a time with the loads issued together (the
-// walk is otherwise one dependent memory round trip per chunk).  With occ,
+// In place: counts[c][t] <- sum_{c' < c} counts[c'][t] (unless list_max is
+// 0); tile_total[t] = sum_c.  Block = 32 tiles (lanes) x 32 chunk segments
+// (warps).  Each warp walks its segment PREFIX_BATCH chunks at a time with
+// the loads issued together (the walk is otherwise one dependent memory
+// round trip per chunk).  With occ,
 // the occupancy bits (count > 0) of the block's tiles are gathered in shared
 // memory ([word][tile], occ_w words) and written to occ[word][tile].  The
 // block that finishes last (a ticket counter; nothing waits) then scans the
@@ -518,7 +522,10 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
         if (t < n_tiles) tile_total[t] = run;
     }
     __syncthreads();
-    if (t < n_tiles) {
+    // the per-chunk list positions: the chunk scatter of written lists reads
+    // them; with no list written (list_max 0) the forward writes those of
+    // the chunks it walks instead
+    if (t < n_tiles && list_max != 0u) {
         uint32_t run = seg[warp][lane];
         int c = c0;
         for (; c + PREFIX_BATCH <= c1; c += PREFIX_BATCH) {
@@ -665,12 +672,15 @@ constexpr int GATHER_WARPS = GATHER_THREADS / 32;
 struct GatherChunk {
     const uint4 *mx, *my;                               // a tile column's / row's CHUNK_WARPS words
     const uint32_t *grow;                               // the chunk's first slot in each tile
+    const uint32_t *wext;                               // nullable: the forward's walked chunk extent per tile
+    uint32_t c;                                         // the chunk
     int wj;                                             // g's warp in the chunk
     unsigned below;                                     // g's lower lanes in that warp
 };
 
 __device__ __forceinline__ GatherChunk gather_chunk(int TX, int TY, uint32_t g, const uint32_t *__restrict__ gbase,
-                                                    const uint32_t *__restrict__ masks) {
+                                                    const uint32_t *__restrict__ masks,
+                                                    const uint32_t *__restrict__ wext) {
     // 16-byte aligned: the workspace slot is, a chunk's masks take 32 (TX + TY)
     // bytes and a tile's words 32
     static_assert(CHUNK_WARPS == 8, "a tile's mask words are two uint4");
@@ -679,18 +689,23 @@ __device__ __forceinline__ GatherChunk gather_chunk(int TX, int TY, uint32_t g, 
     k.mx = reinterpret_cast<const uint4 *>(masks + (size_t)c * CHUNK_WARPS * (TX + TY));
     k.my = k.mx + 2 * TX;
     k.grow = gbase + (size_t)c * TX * TY;
+    k.wext = wext;
+    k.c = (uint32_t)c;
     k.wj = j >> 5;
     k.below = (1u << (j & 31)) - 1u;
     return k;
 }
 
 // The pair slot of the Gaussian in tile (tx, ty), or -1 when it lies past the
-// tile's visited prefix (no record there).
+// tile's visited prefix (no record there).  With wext (lists formed in the
+// forward) a chunk at or past the tile's walked extent has no written list
+// position and lies past the visited prefix.
 __device__ __forceinline__ long long gather_slot(int TX, int tx, int ty, const GatherChunk &k,
                                                  const uint32_t *__restrict__ tile_off,
                                                  const uint32_t *__restrict__ visited) {
     const int t = ty * TX + tx;
     const uint32_t base = k.grow[t], vis = visited[t], off = tile_off[t];
+    const uint32_t ext = k.wext ? k.wext[t] : 0xffffffffu;
     const uint4 x0 = k.mx[2 * tx], x1 = k.mx[2 * tx + 1], y0 = k.my[2 * ty], y1 = k.my[2 * ty + 1];
     const uint32_t m[CHUNK_WARPS] = {x0.x & y0.x, x0.y & y0.y, x0.z & y0.z, x0.w & y0.w,
                                      x1.x & y1.x, x1.y & y1.y, x1.z & y1.z, x1.w & y1.w};
@@ -698,7 +713,7 @@ __device__ __forceinline__ long long gather_slot(int TX, int tx, int ty, const G
     uint32_t rank = 0;
 #pragma unroll
     for (int w = 0; w < CHUNK_WARPS; ++w) rank += __popc(m[w] & (w < k.wj ? ~0u : w == k.wj ? k.below : 0u));
-    return base + rank < vis ? (long long)off + base + rank : -1ll;
+    return k.c < ext && base + rank < vis ? (long long)off + base + rank : -1ll;
 }
 
 __device__ __forceinline__ void add_record(const float4 *__restrict__ pair_grads, long long slot, float acc[9]) {
@@ -768,7 +783,8 @@ __device__ void gather_big(int TX, int TY, uint32_t n_big, const uint32_t *__res
                            const uint32_t *__restrict__ gbase, const uint32_t *__restrict__ tile_off,
                            const uint32_t *__restrict__ visited, const float4 *__restrict__ pair_grads,
                            const uint8_t *__restrict__ skip, const uint8_t *__restrict__ ghit,
-                           const uint32_t *__restrict__ masks, float4 *__restrict__ out, GatherSmem &sm) {
+                           const uint32_t *__restrict__ masks, const uint32_t *__restrict__ wext,
+                           float4 *__restrict__ out, GatherSmem &sm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const size_t G = gridDim.x;
     for (size_t e0 = blockIdx.x; e0 < n_big; e0 += G * GATHER_THREADS) {
@@ -799,7 +815,7 @@ __device__ void gather_big(int TX, int TY, uint32_t n_big, const uint32_t *__res
         }
         __syncthreads();
         for (int i = 0; i < total; ++i) {
-            const GatherChunk k = gather_chunk(TX, TY, sm.g[i], gbase, masks);
+            const GatherChunk k = gather_chunk(TX, TY, sm.g[i], gbase, masks, wext);
             float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             gather_walk(TX, sm.rect[i], tid, GATHER_THREADS, k, tile_off, visited, pair_grads, acc);
             const float red = reduce_scatter8(acc, lane);  // lane 4q holds the sum of value q
@@ -825,8 +841,9 @@ __device__ __forceinline__ void gather_warp(int TX, int TY, uint32_t g, uint32_t
                                             const uint32_t *__restrict__ tile_off,
                                             const uint32_t *__restrict__ visited,
                                             const float4 *__restrict__ pair_grads,
-                                            const uint32_t *__restrict__ masks, float4 *__restrict__ out) {
-    const GatherChunk k = gather_chunk(TX, TY, g, gbase, masks);
+                                            const uint32_t *__restrict__ masks,
+                                            const uint32_t *__restrict__ wext, float4 *__restrict__ out) {
+    const GatherChunk k = gather_chunk(TX, TY, g, gbase, masks, wext);
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const bool found = gather_walk(TX, r, lane, 32, k, tile_off, visited, pair_grads, acc);
     if (!__any_sync(FULL, found)) return;               // no visited pair: stays 0
@@ -858,12 +875,15 @@ __global__ void __launch_bounds__(GATHER_THREADS, 3) k_bin_gather(int TX, int TY
                                                                const uint8_t *__restrict__ skip,
                                                                const uint8_t *__restrict__ ghit,
                                                                const uint32_t *__restrict__ masks,
+                                                               const uint32_t *__restrict__ wext_ws,
                                                                float4 *__restrict__ out) {
     __shared__ GatherSmem sm;
     if (hdr->overflow) return;
     const uint32_t n_vis = hdr->n_vis;
+    // with no list written the list positions are those the forward wrote
+    const uint32_t *wext = hdr->list_max == 0u ? wext_ws : nullptr;
     gather_big(TX, TY, hdr->n_big, big_list, sorted, rects, gbase, tile_off, visited, pair_grads, skip, ghit,
-               masks, out, sm);
+               masks, wext, out, sm);
     const uint32_t W = (uint32_t)((gridDim.x * (size_t)blockDim.x) >> 5);
     const uint32_t w = (uint32_t)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -885,7 +905,7 @@ __global__ void __launch_bounds__(GATHER_THREADS, 3) k_bin_gather(int TX, int TY
             const int4 r = make_int4(__shfl_sync(FULL, rr.x, l), __shfl_sync(FULL, rr.y, l),
                                      __shfl_sync(FULL, rr.z, l), __shfl_sync(FULL, rr.w, l));
             gather_warp(TX, TY, (uint32_t)(w + (size_t)(k0 + l) * W), gid, r, lane, gbase, tile_off, visited,
-                        pair_grads, masks, out);
+                        pair_grads, masks, wext, out);
         }
     }
 }
@@ -894,20 +914,21 @@ __global__ void __launch_bounds__(GATHER_THREADS, 3) k_bin_gather(int TX, int TY
 }  // namespace qn
 
 namespace qn {
-int bin_view(int32_t n, int32_t tiles_x, int32_t tiles_y, const void *workspace, size_t workspace_bytes,
-             BinView &v) {
+int bin_view(int32_t n, int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes, BinView &v) {
     QN_REQUIRE(n >= 0 && tiles_x > 0 && tiles_y > 0 && tiles_x <= QN_MAX_TILES_X && tiles_y <= QN_MAX_TILES_Y,
                "bad n or tile grid");
     QN_REQUIRE(workspace && ((uintptr_t)workspace & 255) == 0, "binning workspace is required, 256-byte aligned");
     const Layout L = layout_of(n, tiles_x, tiles_y);
     QN_REQUIRE(workspace_bytes >= L.total, "binning workspace too small (%zu < %zu)", workspace_bytes, L.total);
-    const char *ws = static_cast<const char *>(workspace);
+    char *ws = static_cast<char *>(workspace);
     v.masks = reinterpret_cast<const uint32_t *>(ws + L.masks);
     v.sorted = reinterpret_cast<const uint32_t *>(ws + L.vals0);   // after the 4 passes, back in vals0
     v.n_vis = reinterpret_cast<const uint32_t *>(ws + L.hdr + offsetof(Header, n_vis));
     v.list_max = reinterpret_cast<const uint32_t *>(ws + L.hdr + offsetof(Header, list_max));
     v.occ = reinterpret_cast<const uint32_t *>(ws + L.occ);
     v.occ_w = occ_words(n);
+    v.gbase = reinterpret_cast<uint32_t *>(ws + L.counts);
+    v.wext = reinterpret_cast<uint32_t *>(ws + L.wext);
     return QN_OK;
 }
 }  // namespace qn
@@ -1103,7 +1124,7 @@ extern "C" int qn_render_bwd_gather(const qn_camera *cam_host, int32_t n, const 
         reinterpret_cast<const uint32_t *>(ws + L.counts), reinterpret_cast<const uint32_t *>(ws + L.tile_off),
         reinterpret_cast<const uint32_t *>(ws + L.visited), reinterpret_cast<const float4 *>(pair_scratch), skip,
         reinterpret_cast<const uint8_t *>(ws + L.hit), reinterpret_cast<const uint32_t *>(ws + L.masks),
-        reinterpret_cast<float4 *>(d_splats));
+        reinterpret_cast<const uint32_t *>(ws + L.wext), reinterpret_cast<float4 *>(d_splats));
     return check_launch("qn_render_bwd gather");
 }
 

@@ -23,12 +23,17 @@ struct BinView {
     const uint32_t *list_max;  // device: the lists of at most this many pairs were written
     const uint32_t *occ;     // [occ_w][tiles]: bit c % 32 of word c / 32 -- chunk c has a member in the tile
     int occ_w;               // ceil(chunks / 32)
+    // written by the walk when no list was written (list_max 0), for the
+    // adjoint's gather: gbase[c][t] the first list position of chunk c's
+    // members in tile t (for the chunks walked), wext[t] the chunk the walk of
+    // tile t stopped at (every occupied chunk below it walked)
+    uint32_t *gbase;         // [chunks][tiles]
+    uint32_t *wext;          // [tiles]
 };
 
 // The view of a workspace of qn_bin_sort for n Gaussians on a tiles_x x
 // tiles_y grid; QN_OK, or QN_ERR_INVALID_ARG (message set) when the workspace
 // is missing, misaligned or too small.
-int bin_view(int32_t n, int32_t tiles_x, int32_t tiles_y, const void *workspace, size_t workspace_bytes,
-             BinView &v);
+int bin_view(int32_t n, int32_t tiles_x, int32_t tiles_y, void *workspace, size_t workspace_bytes, BinView &v);
 
 }  // namespace qn

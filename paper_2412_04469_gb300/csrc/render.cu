@@ -249,6 +249,7 @@ __device__ __forceinline__ void walk_window(ListWalk &lw, uint32_t *ring, uint32
     const int ntake = __popc(__ballot_sync(FULL, take));
     if (take) {
         uint32_t pos = lw.listed + incl - cnt;
+        bins.gbase[(size_t)c * n_tiles + t] = pos;      // the chunk's first list position in the tile
         const uint32_t g0 = (uint32_t)c * BIN_CHUNK;
 #pragma unroll
         for (int i = 0; i < BIN_CHUNK_WARPS; ++i) {
@@ -439,6 +440,18 @@ __global__ void __launch_bounds__(Band<PPT>::THREADS) k_render_fwd(int W, int H,
         Tf[o] = t;
         last[o] = lastc[q];
         if (COUNT) ncon[o] = nc[q];
+    }
+    if constexpr (LAZY) {
+        // the walked chunk extent of the tile (the warps' furthest cursor)
+        __shared__ uint32_t wcur[WARPS];
+        if (lane == 0) wcur[threadIdx.x >> 5] = walk ? (uint32_t)lw.cur : 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t e = 0;
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) e = max(e, wcur[w]);
+            bins.wext[tile] = e;
+        }
     }
     if (cost) {
         uint32_t m = 0;
@@ -806,12 +819,13 @@ extern "C" int qn_render_fwd(const qn_camera *cam_host, const uint32_t *ranges, 
     if (st) return st;
     QN_REQUIRE(img && T_final && last && bg_host, "null pointer argument");
     return qn::launch_render_fwd<false>(cam_host, ranges, vals,
-                                        qn::BinView{nullptr, nullptr, nullptr, nullptr, nullptr, 0}, nullptr,
+                                        qn::BinView{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr},
+                                        nullptr,
                                         splats, bg_host, img, T_final, last, n_contrib, composited, tile_order,
                                         tile_cost, stream);
 }
 
-extern "C" int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, const void *workspace,
+extern "C" int qn_render_fwd_binned(const qn_camera *cam_host, int32_t n, void *workspace,
                                     size_t workspace_bytes, const uint32_t *ranges, uint32_t *vals,
                                     const qn_splat *splats, const float *bg_host, float *img, float *T_final,
                                     uint32_t *last, uint32_t *n_contrib, uint8_t *composited,
