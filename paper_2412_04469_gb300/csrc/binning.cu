@@ -12,6 +12,10 @@
 // Every pair of one Gaussian shares its depth bits, so sorting the depth
 // digits on the Gaussians first and then the tile digit stably on the pairs is
 // exactly the LSD order of the 64-bit key; the output equals the stable sort.
+// qn_bin_sort_partial stops before writing the lists longer than list_max
+// (with list_max 0, every list): the compositing forward forms them from the
+// chunk masks, walking only the chunks that hold a member of its tile (a
+// per-tile occupancy bitmap over the chunks, built with the tile totals).
 #include <algorithm>
 #include <mutex>
 
