@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_bin_prep(int n, const float *_
                                                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                                            uint32_t *__restrict__ hist, uint32_t *__restrict__ dtot,
                                                            Header *hdr) {
+    pdl_enter();
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_bin_prep(int n, const float *_
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, const uint32_t *__restrict__ keys,
                                                              uint32_t *__restrict__ hist,
                                                              uint32_t *__restrict__ dtot, const Header *hdr) {
+    pdl_enter();
     if (digit_constant(hdr, shift)) return;             // the pass is a copy
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(int n, int shift, c
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *__restrict__ hist, int nb,
                                                      const uint32_t *__restrict__ dtot, const Header *hdr,
                                                      int shift) {
+    pdl_enter();
     if (digit_constant(hdr, shift)) return;             // the pass is a copy
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * 32 + (threadIdx.x >> 5);
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int n, int shift
                                                                 const uint32_t *__restrict__ offs,
                                                                 uint32_t *__restrict__ kout,
                                                                 uint32_t *__restrict__ vout, const Header *hdr) {
+    pdl_enter();
     constexpr int W = SORT_THREADS / 32;
     __shared__ uint32_t base[RADIX];          // running count of each digit in this block
     __shared__ uint32_t wcnt[W][RADIX];
@@ -373,6 +377,7 @@ __global__ void __launch_bounds__(CHUNK) k_chunk_counts(int TX, int TY, const ui
                                                         uint32_t *__restrict__ counts,
                                                         uint32_t *__restrict__ masks,
                                                         uint32_t *__restrict__ big_list) {
+    pdl_enter();
     __shared__ ChunkSmem s;
     const int c = blockIdx.x;
     const uint32_t n_vis = hdr->n_vis;
@@ -484,6 +489,7 @@ __global__ void __launch_bounds__(1024) k_chunk_prefix(int n_chunks, int n_tiles
                                                        Header *hdr, unsigned long long capacity,
                                                        long long *n_pairs, uint32_t list_max,
                                                        uint32_t *__restrict__ occ, int occ_w) {
+    pdl_enter();
     __shared__ uint32_t seg[32][33];
     extern __shared__ uint32_t socc[];                  // [occ_w][32] when occ is given
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -992,30 +998,32 @@ int bin_sort_impl(int32_t n, const float *depth, int32_t depth_stride, const int
     if (cudaMemsetAsync(hdr, 0, L.keys0 - L.hdr, s) != cudaSuccess)      // header and digit totals
         return check_launch("qn_bin_sort memset");
     const int nb = div_up(n, SORT_TILE);
-    k_bin_prep<<<nb, SORT_THREADS, 0, s>>>(n, depth, depth_stride, r4, k0, v0, hist, dtot, hdr);
+    pdl_launch(k_bin_prep, nb, SORT_THREADS, 0, s, n, depth, depth_stride, r4, k0, v0, hist, dtot, hdr);
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         uint32_t *ki = (pass & 1) ? k1 : k0, *vi = (pass & 1) ? v1 : v0;
         uint32_t *ko = (pass & 1) ? k0 : k1, *vo = (pass & 1) ? v0 : v1;
         if (pass > 0)                                   // the first pass's histogram came with the keys
-            k_radix_hist<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, hist, dtot + pass * RADIX, hdr);
-        k_radix_scan<<<RADIX / 32, 1024, 0, s>>>(hist, nb, dtot + pass * RADIX, hdr, shift);
-        k_radix_scatter<<<nb, SORT_THREADS, 0, s>>>(n, shift, ki, vi, hist, ko, vo, hdr);
+            pdl_launch(k_radix_hist, nb, SORT_THREADS, 0, s, n, shift, (const uint32_t *)ki, hist,
+                       dtot + pass * RADIX, (const Header *)hdr);
+        pdl_launch(k_radix_scan, RADIX / 32, 1024, 0, s, hist, nb, (const uint32_t *)(dtot + pass * RADIX),
+                   (const Header *)hdr, shift);
+        pdl_launch(k_radix_scatter, nb, SORT_THREADS, 0, s, n, shift, (const uint32_t *)ki, (const uint32_t *)vi,
+                   (const uint32_t *)hist, ko, vo, (const Header *)hdr);
     }
     // after 4 passes the sorted (depth, index) order is back in k0 / v0
     const int n_chunks = div_up(n, CHUNK);
     uint32_t *masks = reinterpret_cast<uint32_t *>(ws + L.masks);
-    k_chunk_counts<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, hdr, counts, masks,
-                                              reinterpret_cast<uint32_t *>(ws + L.big));
+    pdl_launch(k_chunk_counts, n_chunks, CHUNK, 0, s, tiles_x, tiles_y, (const uint32_t *)v0, r4, hdr, counts, masks,
+               reinterpret_cast<uint32_t *>(ws + L.big));
     // the occupancy bits only for lists the compositing forward forms
     uint32_t *occ = list_max != 0xffffffffu ? reinterpret_cast<uint32_t *>(ws + L.occ) : nullptr;
     const int occ_w = occ_words(n);
     const size_t occ_smem = occ ? sizeof(uint32_t) * 32 * (size_t)occ_w : 0;
     if (occ_smem > 48 * 1024 && prefix_attributes() != cudaSuccess) return check_launch("k_chunk_prefix attributes");
-    k_chunk_prefix<<<div_up(n_tiles, 32), 1024, occ_smem, s>>>(n_chunks, n_tiles, counts, tile_total, tile_off,
-                                                               ranges, hdr, (unsigned long long)capacity,
-                                                               reinterpret_cast<long long *>(n_pairs), list_max, occ,
-                                                               occ_w);
+    pdl_launch(k_chunk_prefix, div_up(n_tiles, 32), 1024, occ_smem, s, n_chunks, n_tiles, counts, tile_total,
+               tile_off, ranges, hdr, (unsigned long long)capacity, reinterpret_cast<long long *>(n_pairs),
+               list_max, occ, occ_w);
     if (list_max > 0 && vals) {                         // the other lists: the compositing forward
         const int vec = ((uintptr_t)vals & 15) == 0;   // 16-byte stores need a 16-byte aligned vals
         k_chunk_scatter<<<n_chunks, CHUNK, 0, s>>>(tiles_x, tiles_y, v0, r4, depth, depth_stride, hdr, counts,

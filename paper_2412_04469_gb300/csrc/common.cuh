@@ -68,6 +68,33 @@ inline int sum_partials_grid(int count) { return (int)(((int64_t)count * 32 + 25
 
 __device__ __forceinline__ int div_up_dev(int a, int b) { return (a + b - 1) / b; }
 
+// Programmatic dependent launch: a kernel launched by pdl_launch may be
+// scheduled while the kernel before it in the stream is still running.  Its
+// first statement is pdl_enter(): it waits until that kernel has completed
+// and its writes are visible (so nothing of the kernel overlaps its
+// predecessor but its launch), then lets the next kernel be scheduled early
+// in turn.  Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Compositing (render.cu), used by the workspace-aware entry points of the
 // compositing adjoint (binning.cu): argument checks shared by both passes, and
 // the first pass of the adjoint (per-pair records, visited prefixes, marks).
